@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the AMOEBA polarization solve on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path on the 23,556-atom water box (the
+DHFR-sized workload, float64, PCG to 1e-5 Debye): cell + neighbour lists,
+per-pair tensors, permanent field (real + PME + self), the PCG solve (each
+iteration one T*mu = real + PME + self) and the polarization energy.
+
+value = unique pairs x T*mu applications in the step / step time  (pairs/s)
+ms_per_step = solve time from positions to energy.
+
+Multi-GPU: independent replicas (one per rank, same workload, no data-path
+collective), weak scaling; a barrier and a max over ranks bracket the timing.
+
+--impl reference times the CPU oracle (float64 numpy) on the host cores: each
+step applies T once to the same workload (real + PME + self), a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "T·μ pairs/s & solve ms, FP64 vs mixed @1e-5 D RMS; serving p50/p99"
+UNIT = "pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default="water-23556")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ oracle side
+
+def oracle_sample(workload, steps: int, warmup: int):
+    """Time T*mu applications of the CPU oracle on the workload (one per step)."""
+    import numpy as np
+    from oracle import Setup
+    from oracle.solver import Operator
+    w = workload
+    sysm = w.system()
+    st = Setup(box=w.L, cutoff=w.cutoff, beta=w.beta, grid=w.grid, order=w.order)
+    t0 = time.perf_counter()
+    op = Operator(sysm, st)
+    t_build = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    mu = rng.normal(size=(sysm.n, 3)) * 0.1
+    for _ in range(warmup):
+        op.apply_T(mu)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        op.apply_T(mu)
+        times.append(time.perf_counter() - t0)
+    return op.n_pairs, times, t_build
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1906_01211_gb300.synth import WORKLOADS
+    w = WORKLOADS[args.workload]
+    pairs, times, t_build = oracle_sample(w, args.steps, args.warmup)
+    total = sum(times)
+    value = pairs * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "n_atoms": 3 * w.n_waters, "box": w.L,
+                                        "pme_grid": w.grid, "cutoff": w.cutoff, "beta": w.beta},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} T*mu applications (real+PME+self) on {w.name}, "
+                                   f"operator geometry built once ({t_build:.1f} s, untimed)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU side
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1906_01211_gb300 import amoebapol as ap
+    from paper_1906_01211_gb300.synth import WORKLOADS
+
+    w = WORKLOADS[args.workload]
+    sysm = w.system()
+    n = sysm.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def solver(precision):
+        return ap.Polarization(ap.Config(box=w.L, cutoff=w.cutoff, ewald_beta=w.beta, pme_grid=w.grid,
+                                         tol_debye=w.tol_debye, precision=precision), stream)
+
+    host = [np.ascontiguousarray(a) for a in
+            (sysm.xyz, sysm.q, sysm.dip, sysm.quad, sysm.alpha, sysm.thole, sysm.mol.astype(np.int32))]
+    pinned = [torch.from_numpy(a).pin_memory() for a in host]
+    dev_in = [t.to(dev) for t in pinned]
+    h2d_bytes = sum(t.numel() * t.element_size() for t in pinned)
+    E0 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    mu_host = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    p = solver("fp64")
+    n_pairs = None
+
+    def step(inputs):
+        p.set_system(*inputs)
+        p.permanent_field(out=E0)
+        mu, it, rms = p.solve(E0)
+        U = p.energy(mu, E0)
+        return mu, it, rms, U
+
+    for _ in range(args.warmup):
+        mu, it, rms, U = step(dev_in)
+    n_pairs = p.pair_count()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    p.profile(True)
+    launches0 = p.launch_count()
+    step_ms, applications = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mu, it, rms, U = step(dev_in)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        applications.append(1 + it)
+    torch.cuda.synchronize()
+    launches = p.launch_count() - launches0
+    phases = p.profile_read()
+    p.profile(False)
+    clk = clocks.stop() if clocks else None
+    t_total = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    apps = sum(applications)
+    value = world * n_pairs * apps / (t_total / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_in = [t.to(dev, non_blocking=True) for t in pinned]
+        mu, it, rms, U = step(d_in)
+        mu_host.copy_(mu, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        tt = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e_value = world * n_pairs * apps / (e2e_total / 1e3)
+    d2h_bytes = mu_host.numel() * 8 + 8
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+
+    # ---- roofline of the dominant kernel (real-space T*v, float64 pipe)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12  # SMs x 2 DFMA/clk x 2 flop x clock, TFLOP/s
+    t_ms, t_cnt = phases["t_real"]
+    t_launch_ms = t_ms / max(t_cnt, 1)
+    flops_launch = 2 * n_pairs * 18 + 6 * n  # 9 FMA per directed pair entry + self term
+    achieved = flops_launch / (t_launch_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_t_real64 (real-space T*v, float64)", "bound": "alu",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (1.25 TFLOP/s nominal)"}
+    phase_ms = {k: round(v[0] / args.steps, 4) for k, v in phases.items()}
+
+    # ---- mixed precision on the same workload, against the float64 result
+    mixed = None
+    if not args.no_mixed:
+        mu64 = mu.clone()
+        pm = solver("mixed")
+        ms_m = []
+        for k in range(args.warmup + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pm.set_system(*dev_in)
+            E0m = pm.permanent_field()
+            mum, itm, rmsm = pm.solve(E0m)
+            Um = pm.energy(mum, E0m)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                ms_m.append(e0.elapsed_time(e1))
+        d = (mum - mu64).double()
+        mixed = {"solve_ms": statistics.mean(ms_m), "iters": itm, "fp64_checks": pm.last_solve_stats()[1],
+                 "rms_vs_fp64_gpu_debye": float(4.8032047 * torch.sqrt((d * d).sum() / n)),
+                 "energy_rel_vs_fp64_gpu": abs(Um / U - 1.0)}
+        pm.close()
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        pairs_o, times, t_build = oracle_sample(w, 2, 0)
+        cpu = {"value": pairs_o * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} T*mu applications (real+PME+self) of the float64 numpy oracle "
+                         f"on {w.name}; geometry terms built once ({t_build:.1f} s, untimed)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_atoms": n, "box": w.L, "cutoff": w.cutoff, "beta": w.beta,
+                   "pme_grid": w.grid, "tol_debye": w.tol_debye, "unique_pairs": n_pairs,
+                   "tmu_applications_per_step": apps / args.steps,
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "solve_ms": t_total / args.steps,
+        "tmu_pairs_per_s_operator": n_pairs / ((phases["t_real"][0] + phases["t_recip"][0])
+                                               / max(phases["t_real"][1], 1) / 1e3),
+        "phase_ms_per_step": phase_ms,
+        "mixed": mixed,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                "d2h_bytes_per_step": d2h_bytes, "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+if __name__ == "__main__":
+    main()

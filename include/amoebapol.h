@@ -1,0 +1,150 @@
+/*
+ * amoebapol.h - C ABI of the GB300 (sm_103a) AMOEBA induced-dipole solver.
+ *
+ * The computation is the polarization step that dominates the AMOEBA runs of
+ * the Tinker-HP performance study (arXiv:1906.01211), Section "Hotspots":
+ *   - the right-hand side of the polarization equation, the permanent
+ *     multipole field E0 (routine efld0_direct2);
+ *   - the matrix-vector product T*mu applied at each iteration of the
+ *     polarization solver (routine tmatxb_pme2), about nine calls per step
+ *     (Section "Sequential performance");
+ *   - the dipole polarization energy (routine epolar1).
+ * The solver is preconditioned conjugate gradients on
+ *     (diag(1/alpha) - T) mu = E0,
+ * T = real-space Ewald (erfc-screened, Thole-damped) dipole field over cell
+ * neighbour lists + smooth-PME reciprocal part + Ewald self term.
+ *
+ * Conventions for every call below.
+ *   Pointers: all array arguments are DEVICE pointers owned by the caller,
+ *     row-major, float64, indexed by the caller's atom order:
+ *       positions, dipoles, fields, induced dipoles: [N][3];
+ *       quadrupoles: [N][6] as xx, yy, zz, xy, xz, yz (traceless, Buckingham:
+ *       potential r.Theta.r / r^5);  charges, alpha, thole: [N];  mol: int32 [N].
+ *     Scalars returned through pointers (iters, rms, U, counts) are HOST pointers.
+ *   Units: Angstrom, e, e*Angstrom, e*Angstrom^2, Angstrom^3; fields e/Angstrom^2;
+ *     energy kcal/mol (Coulomb constant 332.0637133); residual RMS in Debye
+ *     (4.8032047 D per e*Angstrom).
+ *   Stream: work is enqueued on the stream given to amp_create; device
+ *     outputs are valid once that stream has reached the call's end. Calls that
+ *     return host scalars synchronise the stream.
+ *   Errors: every int-returning call returns AMP_OK (0) or a negative code;
+ *     amp_last_error() gives a message. After AMP_ERR_CUDA the context should
+ *     be destroyed.
+ *   Memory: the context owns its device buffers (cell lists, neighbour lists,
+ *     pair tensors, PME grids, cuFFT plans, solver vectors); they are sized by
+ *     amp_set_system and reused by every later call. No call allocates inside
+ *     the solver loop.
+ */
+#ifndef AMOEBAPOL_H
+#define AMOEBAPOL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMP_OK 0
+#define AMP_ERR_ARG (-1)           /* invalid argument or configuration */
+#define AMP_ERR_CUDA (-2)          /* CUDA or cuFFT failure */
+#define AMP_ERR_OOM (-3)           /* device allocation failed */
+#define AMP_ERR_NOT_CONVERGED (-4) /* PCG reached max_iter above tolerance */
+#define AMP_ERR_GEOMETRY (-5)      /* cutoff >= box/2, list overflow, bad cell */
+#define AMP_ERR_STATE (-6)         /* call order: no system set */
+
+#define AMP_FP64 0   /* all pair math, grids and FFTs in float64 */
+#define AMP_MIXED 1  /* float32 pair geometry/damping and PME, float64
+                        accumulation, scalars, self terms and a final float64
+                        residual check ("decreasing precision", paper
+                        Section "Conclusion") */
+
+typedef struct amp_ctx amp_ctx;
+
+typedef struct {
+  double box;        /* cubic box edge (Angstrom); must be > 2 * cutoff */
+  double cutoff;     /* real-space cutoff (Angstrom) */
+  double ewald_beta; /* Ewald splitting parameter (1/Angstrom), > 0 */
+  int pme_grid;      /* PME points per axis, >= 8 */
+  int pme_order;     /* B-spline order; must be 5 */
+  double tol_debye;  /* PCG stop: RMS of alpha*residual in Debye < tol */
+  int max_iter;      /* PCG iteration cap (>= 1) */
+  int precision;     /* AMP_FP64 or AMP_MIXED */
+} amp_config;
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*;
+ * NULL = legacy default stream). Validates cfg. Returns AMP_ERR_ARG on a bad
+ * configuration (then *out is NULL). */
+int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream);
+
+/* Free every device buffer and plan of the context. NULL is ignored. */
+void amp_destroy(amp_ctx* ctx);
+
+/* Message of the last error on this context (static storage inside ctx). */
+const char* amp_last_error(const amp_ctx* ctx);
+
+/* Load a system of n_atoms sites and build the geometry-dependent state:
+ * cell list (atoms re-ordered by cell), neighbour lists within the cutoff
+ * (paper, Section "Hotspots": cell-based list builder mlistcell), per-pair
+ * damped interaction tensors and permanent-field terms, and PME B-spline
+ * weights. Inputs as described above; alpha must be > 0. Re-allocates only
+ * when the system grows. Synchronises the stream once (list sizes). */
+int amp_set_system(amp_ctx* ctx, int n_atoms, const double* xyz, const double* q,
+                   const double* dip, const double* quad, const double* alpha,
+                   const double* thole, const int* mol);
+
+/* Permanent-multipole field at every site, E0 [N][3] (real space with the
+ * intramolecular exclusion + PME + self). The right-hand side of the
+ * polarization equation (routine efld0_direct2). */
+int amp_permanent_field(amp_ctx* ctx, double* E0);
+
+/* Tmu = T * mu for any mu [N][3] (real + reciprocal + self), the operator
+ * applied at each solver iteration (routine tmatxb_pme2). */
+int amp_apply_T(amp_ctx* ctx, const double* mu, double* Tmu);
+
+/* Solve (1/alpha - T) mu = E0 by diagonal-preconditioned CG.
+ * use_guess = 0: start from mu = alpha*E0 (mu is output only);
+ * use_guess = 1: start from the mu passed in.
+ * On return mu holds the solution; *iters the number of iterations and
+ * *rms_debye the final preconditioned-residual RMS (Debye). In AMP_MIXED the
+ * final check is a float64 residual; if it is above tol, iterations continue.
+ * Returns AMP_ERR_NOT_CONVERGED (mu still written) if max_iter is reached. */
+int amp_solve_induced(amp_ctx* ctx, const double* E0, double* mu, int use_guess,
+                      int* iters, double* rms_debye);
+
+/* Polarization energy U = -1/2 C sum_i mu_i . E0_i (kcal/mol) into *U (host). */
+int amp_polarization_energy(amp_ctx* ctx, const double* mu, const double* E0, double* U);
+
+/* Number of unique atom pairs within the cutoff of the current system. */
+int amp_pair_count(const amp_ctx* ctx, long long* n_pairs);
+
+/* Phase timers (CUDA events recorded on the context's stream around each
+ * phase's launches; no effect on results). Phases: */
+#define AMP_PHASE_LIST 0        /* cell sort + neighbour lists (kernel a) */
+#define AMP_PHASE_PAIR 1        /* per-pair tensors and permanent-field terms */
+#define AMP_PHASE_E0_REAL 2     /* real-space permanent field row sums */
+#define AMP_PHASE_E0_RECIP 3    /* PME of the permanent multipoles */
+#define AMP_PHASE_T_REAL 4      /* real-space T*v, one launch per application */
+#define AMP_PHASE_T_RECIP 5     /* PME of dipoles: spread, FFTs, gather */
+#define AMP_PHASE_PCG 6         /* fused PCG vector updates and reductions */
+#define AMP_PHASE_FP64_CHECK 7  /* mixed path: float64 residual check */
+#define AMP_PHASE_ENERGY 8      /* energy reduction */
+#define AMP_NPHASE 9
+
+/* enable != 0: start recording (clears totals); 0: stop. */
+int amp_profile(amp_ctx* ctx, int enable);
+
+/* Synchronise the stream and return, per phase, the summed milliseconds and
+ * the number of timed intervals since amp_profile(ctx, 1). Arrays of
+ * AMP_NPHASE entries (host). */
+int amp_profile_read(amp_ctx* ctx, double* ms, long long* count);
+
+/* Number of kernels of this library launched on the context so far (library
+ * kernels only; cuFFT's own kernels are not included). */
+int amp_launch_count(const amp_ctx* ctx, long long* n);
+
+/* Iterations and float64 residual checks of the last solve (host pointers,
+ * either may be NULL). */
+int amp_last_solve_stats(const amp_ctx* ctx, int* iters, int* fp64_checks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMOEBAPOL_H */

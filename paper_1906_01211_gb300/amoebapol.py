@@ -1,0 +1,283 @@
+"""Python binding of libamoebapol (the C ABI in include/amoebapol.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. The low-level functions carry the C names; ``Polarization`` wraps
+them for torch CUDA tensors (PyTorch supplies device memory and the stream).
+
+Importing this module loads ``libamoebapol.so`` and raises if it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamoebapol.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "amoebapol.h")
+
+AMP_OK = 0
+AMP_ERR_ARG = -1
+AMP_ERR_CUDA = -2
+AMP_ERR_OOM = -3
+AMP_ERR_NOT_CONVERGED = -4
+AMP_ERR_GEOMETRY = -5
+AMP_ERR_STATE = -6
+AMP_FP64 = 0
+AMP_MIXED = 1
+PHASES = ("list", "pair", "e0_real", "e0_recip", "t_real", "t_recip", "pcg", "fp64_check", "energy")
+
+
+class amp_config(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double),
+        ("cutoff", ctypes.c_double),
+        ("ewald_beta", ctypes.c_double),
+        ("pme_grid", ctypes.c_int),
+        ("pme_order", ctypes.c_int),
+        ("tol_debye", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class AmpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libamoebapol error {code}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} not found: build it with `python -m paper_1906_01211_gb300.build` "
+            "(the CUDA library is required; there is no CPU path)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    sig = {
+        "amp_create": (I, [ctypes.POINTER(P), ctypes.POINTER(amp_config), P]),
+        "amp_destroy": (None, [P]),
+        "amp_last_error": (ctypes.c_char_p, [P]),
+        "amp_set_system": (I, [P, I, P, P, P, P, P, P, P]),
+        "amp_permanent_field": (I, [P, P]),
+        "amp_apply_T": (I, [P, P, P]),
+        "amp_solve_induced": (I, [P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "amp_polarization_energy": (I, [P, P, P, ctypes.POINTER(D)]),
+        "amp_pair_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+        "amp_profile": (I, [P, I]),
+        "amp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
+        "amp_last_solve_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "amp_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/amoebapol.h."""
+    text = open(HEADER_PATH).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+\**(amp_\w+)\s*\(", text, re.M)))
+
+
+def _check(ctx, code: int):
+    if code != AMP_OK:
+        msg = _lib.amp_last_error(ctx)
+        raise AmpError(code, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------------- C names
+
+def amp_create(cfg: amp_config, stream: int | None = None):
+    h = ctypes.c_void_p()
+    code = _lib.amp_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(stream or 0))
+    if code != AMP_OK:
+        raise AmpError(code, "amp_create: invalid configuration or device error")
+    return h
+
+
+def amp_destroy(ctx):
+    _lib.amp_destroy(ctx)
+
+
+def amp_last_error(ctx) -> str:
+    m = _lib.amp_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def amp_set_system(ctx, n, xyz, q, dip, quad, alpha, thole, mol):
+    _check(ctx, _lib.amp_set_system(ctx, int(n), xyz, q, dip, quad, alpha, thole, mol))
+
+
+def amp_permanent_field(ctx, E0):
+    _check(ctx, _lib.amp_permanent_field(ctx, E0))
+
+
+def amp_apply_T(ctx, mu, Tmu):
+    _check(ctx, _lib.amp_apply_T(ctx, mu, Tmu))
+
+
+def amp_solve_induced(ctx, E0, mu, use_guess: bool):
+    it = ctypes.c_int(0)
+    rms = ctypes.c_double(0.0)
+    code = _lib.amp_solve_induced(ctx, E0, mu, int(bool(use_guess)), ctypes.byref(it), ctypes.byref(rms))
+    return code, it.value, rms.value
+
+
+def amp_polarization_energy(ctx, mu, E0) -> float:
+    u = ctypes.c_double(0.0)
+    _check(ctx, _lib.amp_polarization_energy(ctx, mu, E0, ctypes.byref(u)))
+    return u.value
+
+
+def amp_pair_count(ctx) -> int:
+    n = ctypes.c_longlong(0)
+    _check(ctx, _lib.amp_pair_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def amp_profile(ctx, enable: bool):
+    _check(ctx, _lib.amp_profile(ctx, int(bool(enable))))
+
+
+def amp_profile_read(ctx) -> dict:
+    """{phase: (milliseconds, intervals)} since profiling was enabled."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(ctx, _lib.amp_profile_read(ctx, ms, cnt))
+    return {name: (ms[k], cnt[k]) for k, name in enumerate(PHASES)}
+
+
+def amp_launch_count(ctx) -> int:
+    n = ctypes.c_longlong(0)
+    _check(ctx, _lib.amp_launch_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def amp_last_solve_stats(ctx):
+    it = ctypes.c_int(0)
+    chk = ctypes.c_int(0)
+    _check(ctx, _lib.amp_last_solve_stats(ctx, ctypes.byref(it), ctypes.byref(chk)))
+    return it.value, chk.value
+
+
+# ----------------------------------------------------------------- torch wrapper
+
+@dataclass
+class Config:
+    box: float
+    cutoff: float = 7.0
+    ewald_beta: float = 0.5446
+    pme_grid: int = 24
+    pme_order: int = 5
+    tol_debye: float = 1e-8
+    max_iter: int = 100
+    precision: str = "fp64"
+
+    def to_c(self) -> amp_config:
+        prec = {"fp64": AMP_FP64, "mixed": AMP_MIXED}[self.precision]
+        return amp_config(self.box, self.cutoff, self.ewald_beta, self.pme_grid, self.pme_order,
+                          self.tol_debye, self.max_iter, prec)
+
+
+class Polarization:
+    """One solver context on the current CUDA device and stream.
+
+    Tensors are torch CUDA float64 (mol: int32), contiguous, in the caller's
+    atom order: xyz/dip/E0/mu (N, 3), quad (N, 6), q/alpha/thole/mol (N,).
+    """
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = amp_create(cfg.to_c(), self.stream.cuda_stream)
+        self.n = 0
+        self._keep = ()
+
+    def close(self):
+        if self.ctx is not None:
+            amp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, t, dtype):
+        torch = self.torch
+        t = torch.as_tensor(t)
+        if t.device.type != "cuda" or t.dtype != dtype or not t.is_contiguous():
+            t = t.to(device="cuda", dtype=dtype).contiguous()
+        return t
+
+    def set_system(self, xyz, q, dip, quad, alpha, thole, mol):
+        torch = self.torch
+        f64 = torch.float64
+        arrs = (self._dev(xyz, f64), self._dev(q, f64), self._dev(dip, f64), self._dev(quad, f64),
+                self._dev(alpha, f64), self._dev(thole, f64), self._dev(mol, torch.int32))
+        self.n = int(arrs[0].shape[0])
+        amp_set_system(self.ctx, self.n, *[a.data_ptr() for a in arrs])
+        self._keep = arrs  # inputs stay alive while the stream may read them
+
+    def set_synthetic(self, system):
+        """Upload a ``synth.System`` (numpy arrays)."""
+        self.set_system(system.xyz, system.q, system.dip, system.quad, system.alpha, system.thole, system.mol)
+
+    def permanent_field(self, out=None):
+        torch = self.torch
+        out = out if out is not None else torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        amp_permanent_field(self.ctx, out.data_ptr())
+        return out
+
+    def apply_T(self, mu, out=None):
+        torch = self.torch
+        mu = self._dev(mu, torch.float64)
+        out = out if out is not None else torch.empty_like(mu)
+        amp_apply_T(self.ctx, mu.data_ptr(), out.data_ptr())
+        return out
+
+    def solve(self, E0, mu=None, check=True):
+        """Returns (mu, iterations, final RMS in Debye)."""
+        torch = self.torch
+        E0 = self._dev(E0, torch.float64)
+        guess = mu is not None
+        mu = self._dev(mu, torch.float64).clone() if guess else torch.empty_like(E0)
+        code, it, rms = amp_solve_induced(self.ctx, E0.data_ptr(), mu.data_ptr(), guess)
+        if check:
+            _check(self.ctx, code)
+        return mu, it, rms
+
+    def energy(self, mu, E0) -> float:
+        torch = self.torch
+        mu = self._dev(mu, torch.float64)
+        E0 = self._dev(E0, torch.float64)
+        return amp_polarization_energy(self.ctx, mu.data_ptr(), E0.data_ptr())
+
+    def pair_count(self) -> int:
+        return amp_pair_count(self.ctx)
+
+    def profile(self, enable: bool):
+        amp_profile(self.ctx, enable)
+
+    def profile_read(self) -> dict:
+        return amp_profile_read(self.ctx)
+
+    def launch_count(self) -> int:
+        return amp_launch_count(self.ctx)
+
+    def last_solve_stats(self):
+        return amp_last_solve_stats(self.ctx)

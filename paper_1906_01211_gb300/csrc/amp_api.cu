@@ -1,0 +1,282 @@
+// C ABI of libamoebapol (declared in include/amoebapol.h): context lifetime,
+// system upload, and the calls that follow the paper's statement of the
+// polarization problem (Section "Hotspots"): right-hand side (efld0_direct2),
+// operator (tmatxb_pme2), solve, energy (epolar1).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "amp_internal.cuh"
+
+namespace amp {
+
+int dev_alloc_bytes(amp_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, AMP_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return AMP_OK;
+}
+
+void dev_free(amp_ctx* c, void* p) {
+  if (!p) return;
+  for (auto& a : c->allocs)
+    if (a == p) a = nullptr;
+  cudaFree(p);
+}
+
+constexpr int kEvPool = 8192;
+
+void prof_begin(amp_ctx* c, int phase) {
+  if (!c->prof) return;
+  if (c->ev_used + 2 > (int)c->ev_pool.size()) prof_resolve(c);
+  cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+  c->ev_phase[c->ev_used / 2] = phase;
+}
+
+void prof_end(amp_ctx* c, int phase) {
+  if (!c->prof) return;
+  (void)phase;
+  cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream);
+  c->ev_used += 2;
+}
+
+int prof_resolve(amp_ctx* c) {
+  if (c->ev_used == 0) return AMP_OK;
+  int r = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
+  if (r) return r;
+  for (int k = 0; k < c->ev_used; k += 2) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_pool[k], c->ev_pool[k + 1]);
+    const int ph = c->ev_phase[k / 2];
+    c->prof_ms[ph] += ms;
+    c->prof_cnt[ph] += 1;
+  }
+  c->ev_used = 0;
+  return AMP_OK;
+}
+
+int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* t);
+void launch_to32(amp_ctx* c, const double4_32a* v, float4* o);
+
+static int alloc_atoms(amp_ctx* c, int n) {
+  if (n <= c->n_cap) return AMP_OK;
+  void** bufs[] = {(void**)&c->cell_of, (void**)&c->perm, (void**)&c->inv_perm, (void**)&c->slot_tmp,
+                   (void**)&c->atomA, (void**)&c->atomB, (void**)&c->atomC, (void**)&c->atomD,
+                   (void**)&c->alph, (void**)&c->pos32, (void**)&c->full_cnt, (void**)&c->half_cnt,
+                   (void**)&c->full_start, (void**)&c->half_start, (void**)&c->theta, (void**)&c->theta32,
+                   (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
+                   (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32};
+  for (void** b : bufs) {
+    dev_free(c, *b);
+    *b = nullptr;
+  }
+  const int cap = n;
+  int r;
+  if ((r = dev_alloc(c, &c->cell_of, cap)) || (r = dev_alloc(c, &c->perm, cap)) ||
+      (r = dev_alloc(c, &c->inv_perm, cap)) || (r = dev_alloc(c, &c->slot_tmp, cap)) ||
+      (r = dev_alloc(c, &c->atomA, cap)) || (r = dev_alloc(c, &c->atomB, cap)) ||
+      (r = dev_alloc(c, &c->atomC, cap)) || (r = dev_alloc(c, &c->atomD, cap)) ||
+      (r = dev_alloc(c, &c->alph, cap)) || (r = dev_alloc(c, &c->pos32, cap)) ||
+      (r = dev_alloc(c, &c->full_cnt, cap)) || (r = dev_alloc(c, &c->half_cnt, cap)) ||
+      (r = dev_alloc(c, &c->full_start, cap + 1)) || (r = dev_alloc(c, &c->half_start, cap + 1)) ||
+      (r = pme_alloc_atoms(c, cap)) || (r = dev_alloc(c, &c->E0s, cap)) || (r = dev_alloc(c, &c->mu, cap)) ||
+      (r = dev_alloc(c, &c->res, cap)) || (r = dev_alloc(c, &c->zv, cap)) || (r = dev_alloc(c, &c->pv, cap)) ||
+      (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
+      (r = dev_alloc(c, &c->p32, cap)))
+    return r;
+  c->n_cap = cap;
+  return AMP_OK;
+}
+
+}  // namespace amp
+
+using namespace amp;
+
+extern "C" {
+
+int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
+  if (!out) return AMP_ERR_ARG;
+  *out = nullptr;
+  if (!cfg) return AMP_ERR_ARG;
+  if (!(cfg->box > 0.0) || !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) || !(cfg->ewald_beta > 0.0) ||
+      cfg->pme_grid < 8 || cfg->pme_grid > 512 || cfg->pme_order != kOrder || !(cfg->tol_debye > 0.0) ||
+      cfg->max_iter < 1 || (cfg->precision != AMP_FP64 && cfg->precision != AMP_MIXED))
+    return AMP_ERR_ARG;
+  amp_ctx* c = new (std::nothrow) amp_ctx();
+  if (!c) return AMP_ERR_OOM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cuda_stream;
+  int r;
+  if ((r = dev_alloc(c, &c->flags, 4)) || (r = dev_alloc(c, &c->iflags, 4)) || (r = dev_alloc(c, &c->scal, 8)) ||
+      (r = dev_alloc(c, &c->partials, 4 * kReduceBlocks))) {
+    amp_destroy(c);
+    return r;
+  }
+  if (cudaMallocHost((void**)&c->hbuf, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hibuf, 8 * sizeof(int)) != cudaSuccess) {
+    amp_destroy(c);
+    return AMP_ERR_OOM;
+  }
+  if ((r = pme_setup(c))) {
+    amp_destroy(c);
+    return r;
+  }
+  *out = c;
+  return AMP_OK;
+}
+
+void amp_destroy(amp_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->plan_d2z) cufftDestroy(c->plan_d2z);
+  if (c->plan_z2d) cufftDestroy(c->plan_z2d);
+  if (c->plan_r2c) cufftDestroy(c->plan_r2c);
+  if (c->plan_c2r) cufftDestroy(c->plan_c2r);
+  for (void* p : c->allocs)
+    if (p) cudaFree(p);
+  if (c->hbuf) cudaFreeHost(c->hbuf);
+  if (c->hibuf) cudaFreeHost(c->hibuf);
+  delete c;
+}
+
+const char* amp_last_error(const amp_ctx* c) { return c ? c->err : "null context"; }
+
+int amp_set_system(amp_ctx* c, int n, const double* xyz, const double* q, const double* dip, const double* quad,
+                   const double* alpha, const double* thole, const int* mol) {
+  if (!c) return AMP_ERR_ARG;
+  c->have_system = false;
+  if (n < 2 || !xyz || !q || !dip || !quad || !alpha || !thole || !mol)
+    return fail(c, AMP_ERR_ARG, "amp_set_system: n >= 2 and all arrays are required");
+  int r;
+  if ((r = alloc_atoms(c, n))) return r;
+  c->n = n;
+  {
+    PhaseScope ps(c, AMP_PHASE_LIST);
+    if ((r = build_cells_and_lists(c, xyz, q, dip, quad, alpha, thole, mol))) return r;
+  }
+  {
+    PhaseScope ps(c, AMP_PHASE_PAIR);
+    launch_pair_build(c);
+  }
+  {
+    PhaseScope ps(c, AMP_PHASE_E0_RECIP);
+    launch_pme_theta(c);
+  }
+  if ((r = cuda_check(c, cudaGetLastError(), "set_system launch"))) return r;
+  c->have_system = true;
+  return AMP_OK;
+}
+
+int amp_permanent_field(amp_ctx* c, double* E0) {
+  if (!c) return AMP_ERR_ARG;
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!E0) return fail(c, AMP_ERR_ARG, "E0 is null");
+  {
+    PhaseScope ps(c, AMP_PHASE_E0_REAL);
+    launch_e0_real(c, c->E0s);
+  }
+  int r;
+  {
+    PhaseScope ps(c, AMP_PHASE_E0_RECIP);
+    r = pme_permanent_field(c, c->E0s);
+  }
+  if (r) return r;
+  launch_from_sorted(c, c->E0s, E0);
+  return cuda_check(c, cudaGetLastError(), "permanent_field launch");
+}
+
+int amp_apply_T(amp_ctx* c, const double* mu, double* Tmu) {
+  if (!c) return AMP_ERR_ARG;
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!mu || !Tmu) return fail(c, AMP_ERR_ARG, "null vector");
+  launch_to_sorted(c, mu, c->tmp);
+  if (c->cfg.precision == AMP_MIXED) launch_to32(c, c->tmp, c->p32);
+  int r = apply_T_sorted(c, c->tmp, c->p32, c->tv);
+  if (r) return r;
+  launch_from_sorted(c, c->tv, Tmu);
+  return cuda_check(c, cudaGetLastError(), "apply_T launch");
+}
+
+int amp_solve_induced(amp_ctx* c, const double* E0, double* mu, int use_guess, int* iters, double* rms) {
+  if (!c) return AMP_ERR_ARG;
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!E0 || !mu) return fail(c, AMP_ERR_ARG, "null vector");
+  launch_to_sorted(c, E0, c->E0s);
+  if (use_guess) launch_to_sorted(c, mu, c->mu);
+  int r = solve(c, use_guess != 0);
+  if (r != AMP_OK && r != AMP_ERR_NOT_CONVERGED) return r;
+  launch_from_sorted(c, c->mu, mu);
+  if (iters) *iters = c->stats.iters;
+  if (rms) *rms = c->stats.rms;
+  int e = cuda_check(c, cudaGetLastError(), "solve launch");
+  return e ? e : r;
+}
+
+int amp_polarization_energy(amp_ctx* c, const double* mu, const double* E0, double* U) {
+  if (!c) return AMP_ERR_ARG;
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!mu || !E0 || !U) return fail(c, AMP_ERR_ARG, "null pointer");
+  return energy(c, mu, E0, U);
+}
+
+int amp_profile(amp_ctx* c, int enable) {
+  if (!c) return AMP_ERR_ARG;
+  if (enable) {
+    if (c->ev_pool.empty()) {
+      c->ev_pool.resize(kEvPool);
+      c->ev_phase.resize(kEvPool / 2);
+      for (auto& e : c->ev_pool)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(c, AMP_ERR_CUDA, "cudaEventCreate failed");
+    }
+    c->ev_used = 0;
+    for (int k = 0; k < AMP_NPHASE; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_cnt[k] = 0;
+    }
+    c->prof = true;
+  } else {
+    int r = prof_resolve(c);
+    c->prof = false;
+    return r;
+  }
+  return AMP_OK;
+}
+
+int amp_profile_read(amp_ctx* c, double* ms, long long* count) {
+  if (!c || !ms || !count) return AMP_ERR_ARG;
+  int r = prof_resolve(c);
+  if (r) return r;
+  for (int k = 0; k < AMP_NPHASE; ++k) {
+    ms[k] = c->prof_ms[k];
+    count[k] = c->prof_cnt[k];
+  }
+  return AMP_OK;
+}
+
+int amp_last_solve_stats(const amp_ctx* c, int* iters, int* fp64_checks) {
+  if (!c) return AMP_ERR_ARG;
+  if (iters) *iters = c->stats.iters;
+  if (fp64_checks) *fp64_checks = c->stats.fp64_checks;
+  return AMP_OK;
+}
+
+int amp_launch_count(const amp_ctx* c, long long* n) {
+  if (!c || !n) return AMP_ERR_ARG;
+  *n = c->n_launch;
+  return AMP_OK;
+}
+
+int amp_pair_count(const amp_ctx* c, long long* n_pairs) {
+  if (!c || !n_pairs) return AMP_ERR_ARG;
+  *n_pairs = c->have_system ? c->n_half : 0;
+  return AMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Internal declarations shared by the translation units of libamoebapol.
+//
+// Data layout on the device (all arrays are in "cell order": atoms re-ordered
+// so that the atoms of one cell are contiguous; perm[s] is the caller's index
+// of sorted atom s):
+//   atomA[s] = (x, y, z, q)                 float64, unwrapped positions
+//   atomB[s] = (dx, dy, dz, 1/sqrt(alpha))  permanent dipole
+//   atomC[s] = (Qxx, Qyy, Qzz, Qxy)
+//   atomD[s] = (Qxz, Qyz, thole, mol)       mol stored as a double
+//   pos32[s] = positions wrapped into [0, L), float32 (list pre-filter, mixed)
+//   vectors (E0, mu, residual, ...) are double4_32a (x, y, z, 0) per atom.
+// Neighbour lists:
+//   full list  CSR rows full_start[s]..full_start[s+1]: entry k holds the
+//              neighbour index full_j[k] and full_ref[k] = 2*pid + side, where
+//              pid is the unique-pair id and side = 0 if the row owns the pair;
+//   half list  (half_i[pid], half_j[pid]) for every unique pair, owned by the
+//              row for which (i < j) != ((i + j) odd) — each pair exactly once,
+//              about half of each row's neighbours.
+// Pair data indexed by pid (computed once per geometry):
+//   T64/T32[pid*6 + {xx,yy,zz,xy,xz,yz}]  damped dipole-field tensor
+//   Ep64/Ep32[pid*6 + side*3 + a]         permanent field at the side's atom
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "amoebapol.h"
+
+namespace amp {
+
+constexpr int kOrder = 5;
+constexpr double kDebye = 4.8032047;
+constexpr double kCoulomb = 332.0637133;
+constexpr double kSqrtPi = 1.7724538509055160273;
+constexpr int kRowGroup = 16;       // lanes that share one neighbour row
+constexpr int kReduceBlocks = 296;  // 2 x 152 SMs: blocks of the PCG kernels
+constexpr int kReduceThreads = 256;
+
+struct Stats {
+  int iters = 0;
+  double rms = 0.0;
+  int fp64_checks = 0;
+};
+
+}  // namespace amp
+
+struct amp_ctx {
+  amp_config cfg{};
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+  int n = 0, n_cap = 0;
+
+  // cells
+  int nc = 0, ncell = 0, ncell_cap = 0;
+  int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
+  int *perm = nullptr, *inv_perm = nullptr, *slot_tmp = nullptr;
+  double4_32a *atomA = nullptr, *atomB = nullptr, *atomC = nullptr, *atomD = nullptr;
+  double2* alph = nullptr;  // (alpha, 1/alpha) per sorted atom
+  float4* pos32 = nullptr;
+
+  // neighbour lists
+  int *full_cnt = nullptr, *half_cnt = nullptr, *full_start = nullptr, *half_start = nullptr;
+  int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr;
+  long long n_full = 0, n_half = 0, cap_full = 0, cap_half = 0;
+  int* flags = nullptr;  // [0] list overflow / search failure
+
+  // pair data
+  double* T64 = nullptr;
+  double* Ep64 = nullptr;
+  float* T32 = nullptr;
+  float* Ep32 = nullptr;
+
+  // PME
+  int K = 0;
+  double* theta = nullptr;  // [n][3 axes][4 derivatives][5 points]
+  float* theta32 = nullptr;
+  int4* gbase = nullptr;    // [n] base grid index per axis
+  double* grid64 = nullptr;
+  double2* cgrid64 = nullptr;
+  double* G64 = nullptr;
+  float* grid32 = nullptr;
+  float2* cgrid32 = nullptr;
+  float* G32 = nullptr;
+  cufftHandle plan_d2z = 0, plan_z2d = 0, plan_r2c = 0, plan_c2r = 0;
+  bool plans = false;
+
+  // vectors in cell order
+  double4_32a *E0s = nullptr, *mu = nullptr, *res = nullptr, *zv = nullptr, *pv = nullptr;
+  double4_32a *qv = nullptr, *tv = nullptr, *tmp = nullptr;
+  float4* p32 = nullptr;
+  double* partials = nullptr;  // block partial sums (two sets)
+  int n_parts_cap = 0;
+  double* scal = nullptr;      // device scalars of the solver: rz[2], rms, pq
+  int* iflags = nullptr;       // device solver state: stop, iters, conv, status
+  double* hbuf = nullptr;      // pinned host readback
+  int* hibuf = nullptr;
+
+  // phase timers
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_phase;  // phase of each begin/end pair in flight
+  int ev_used = 0;
+  double prof_ms[AMP_NPHASE] = {0};
+  long long prof_cnt[AMP_NPHASE] = {0};
+
+  long long n_launch = 0;      // kernels this library has launched (own kernels only)
+  std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
+  amp::Stats stats;
+  bool have_system = false;
+};
+
+namespace amp {
+
+int fail(amp_ctx* c, int code, const char* fmt, ...);
+int dev_alloc_bytes(amp_ctx* c, void** p, size_t bytes);
+void dev_free(amp_ctx* c, void* p);
+template <typename T>
+inline int dev_alloc(amp_ctx* c, T** p, long long count) {
+  void* q = nullptr;
+  int r = dev_alloc_bytes(c, &q, sizeof(T) * (size_t)(count > 0 ? count : 1));
+  *p = (T*)q;
+  return r;
+}
+int cuda_check(amp_ctx* c, cudaError_t e, const char* what);
+
+// Phase timers: record an event pair around a phase on the context stream.
+void prof_begin(amp_ctx* c, int phase);
+void prof_end(amp_ctx* c, int phase);
+int prof_resolve(amp_ctx* c);
+struct PhaseScope {
+  amp_ctx* c;
+  int ph;
+  PhaseScope(amp_ctx* c_, int ph_) : c(c_), ph(ph_) { prof_begin(c, ph); }
+  ~PhaseScope() { prof_end(c, ph); }
+};
+
+// neighbour lists (amp_nblist.cu)
+int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const double* dip,
+                          const double* quad, const double* alpha, const double* thole,
+                          const int* mol);
+
+// pair terms and real-space sums (amp_pair.cu)
+void launch_pair_build(amp_ctx* c);
+void launch_e0_real(amp_ctx* c, double4_32a* out);  // out = real-space E0 + self
+void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out);  // out = T_real v + self v
+void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out);
+void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out);
+
+// PME (amp_pme.cu)
+int pme_setup(amp_ctx* c);
+int pme_alloc_atoms(amp_ctx* c, int n_cap);
+void launch_pme_theta(amp_ctx* c);
+int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
+int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out_add);  // float64 grid
+int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out_add);  // float32 grid
+
+// solver (amp_pcg.cu)
+void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst);
+void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst);
+int solve(amp_ctx* c, bool use_guess);
+int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
+
+}  // namespace amp
+
+// launch geometry helpers
+static inline int amp_blocks(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  return b < 1 ? 1 : (int)b;
+}

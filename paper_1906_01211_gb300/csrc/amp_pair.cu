@@ -1,0 +1,320 @@
+// Real-space pair terms (kernels b' and b).
+//
+// The right-hand side of the polarization equation (paper, Section "Hotspots":
+// efld0_direct2) and the real-space part of the matrix-vector product applied
+// at every solver iteration (tmatxb_pme2) are sums over neighbour pairs. The
+// paper's CPU code recomputes every pair quantity on the fly at each call
+// (Section "General Structure"). Here every quantity that depends only on the
+// geometry is computed once per geometry, for each unique pair:
+//   - the damped dipole-field tensor T_ij = -B1u I + B2u r r^T (6 numbers),
+//     B1u = B1 - (1 - l3) / r^3, B2u = B2 - 3 (1 - l5) / r^5;
+//   - the permanent field of j at i and of i at j, with the intramolecular
+//     exclusion (s = 0: B_n - bare_n) and Thole damping (s = 1).
+// B_0 = erfc(beta r)/r, B_n = [(2n-1) B_{n-1} + (2 beta^2)^n e^{-beta^2 r^2}/(beta sqrt(pi))]/r^2;
+// Thole x = a r^3 / sqrt(alpha_i alpha_j), a = min(a_i, a_j):
+// 1 - l3 = e^-x, 1 - l5 = (1 + x) e^-x, 1 - l7 = (1 + x + 0.6 x^2) e^-x.
+// On GB300 float64 arithmetic is scarce while HBM is plentiful, so storing
+// 6 + 6 numbers per pair and streaming them at every iteration replaces the
+// erfc/exp work of the paper's per-call recomputation.
+//
+// Each iteration then reduces over the full neighbour rows: a group of
+// kRowGroup lanes per atom sums T_ij v_j, no atomics, fixed order.
+#include "amp_internal.cuh"
+
+namespace amp {
+namespace {
+
+struct PairGeom {
+  double L, beta, twob2, gpre, selfc;
+};
+
+template <typename R>
+struct Kern {
+  R b1e, b2e, b3e;  // permanent-field coefficients (exclusion applied)
+  R b1u, b2u;       // dipole-field coefficients
+};
+
+// Field at displacement r (field point minus source) of a multipole:
+// E = q B1 r - B1 d + B2 (d.r) r - 2/3 B2 Theta r + 1/3 B3 (r.Theta.r) r
+template <typename R>
+__device__ __forceinline__ void multipole_field(R rx, R ry, R rz, R q, R dx, R dy, R dz, R qxx, R qyy, R qzz,
+                                                R qxy, R qxz, R qyz, R b1, R b2, R b3, R& ex, R& ey, R& ez) {
+  const R tx = qxx * rx + qxy * ry + qxz * rz;
+  const R ty = qxy * rx + qyy * ry + qyz * rz;
+  const R tz = qxz * rx + qyz * ry + qzz * rz;
+  const R rtr = rx * tx + ry * ty + rz * tz;
+  const R dr = dx * rx + dy * ry + dz * rz;
+  const R rad = q * b1 + b2 * dr + b3 * rtr * (R)(1.0 / 3.0);
+  const R c2 = b2 * (R)(2.0 / 3.0);
+  ex = rad * rx - b1 * dx - c2 * tx;
+  ey = rad * ry - b1 * dy - c2 * ty;
+  ez = rad * rz - b1 * dz - c2 * tz;
+}
+
+// Kernel coefficients of one pair in precision R (float64 or float32).
+template <typename R>
+__device__ __forceinline__ Kern<R> pair_kernels(R r2, R ai_isa, R aj_isa, R thi, R thj, bool same_mol,
+                                                const PairGeom& g) {
+  Kern<R> k;
+  const R r = sqrt(r2);
+  const R ir = (R)1 / r;
+  const R ir2 = ir * ir;
+  const R beta = (R)g.beta;
+  const R br = beta * r;
+  const R ex2 = exp(-br * br);
+  const R b0 = erfc(br) * ir;
+  R fac = ex2 * (R)g.gpre;  // e^{-b^2 r^2} / (beta sqrt(pi)) * (2 beta^2)
+  const R tb2 = (R)g.twob2;
+  const R b1 = (b0 + fac) * ir2;
+  fac *= tb2;
+  const R b2 = ((R)3 * b1 + fac) * ir2;
+  fac *= tb2;
+  const R b3 = ((R)5 * b2 + fac) * ir2;
+  const R bare1 = ir * ir2;
+  const R bare2 = (R)3 * bare1 * ir2;
+  const R bare3 = (R)5 * bare2 * ir2;
+  const R x = min(thi, thj) * r2 * r * ai_isa * aj_isa;
+  const R e = exp(-x);
+  const R d3 = e, d5 = ((R)1 + x) * e, d7 = ((R)1 + x + (R)0.6 * x * x) * e;
+  k.b1u = b1 - d3 * bare1;
+  k.b2u = b2 - d5 * bare2;
+  if (same_mol) {
+    k.b1e = b1 - bare1;
+    k.b2e = b2 - bare2;
+    k.b3e = b3 - bare3;
+  } else {
+    k.b1e = b1 - d3 * bare1;
+    k.b2e = b2 - d5 * bare2;
+    k.b3e = b3 - d7 * bare3;
+  }
+  return k;
+}
+
+__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pair_build(long long nh, const int* __restrict__ half_i,
+                                                    const int* __restrict__ half_j, const double4_32a* __restrict__ A,
+                                                    const double4_32a* __restrict__ B, const double4_32a* __restrict__ C,
+                                                    const double4_32a* __restrict__ D, PairGeom g, R* __restrict__ T,
+                                                    R* __restrict__ Ep) {
+  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pid >= nh) return;
+  const int i = half_i[pid], j = half_j[pid];
+  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], ci = C[i], cj = C[j], di = D[i], dj = D[j];
+  // geometry in float64 (exact minimum image), then the precision of the path
+  const double rx64 = min_image(ai.x - aj.x, g.L), ry64 = min_image(ai.y - aj.y, g.L),
+               rz64 = min_image(ai.z - aj.z, g.L);
+  const R rx = (R)rx64, ry = (R)ry64, rz = (R)rz64;
+  const R r2 = rx * rx + ry * ry + rz * rz;
+  const Kern<R> k = pair_kernels<R>(r2, (R)bi.w, (R)bj.w, (R)di.z, (R)dj.z, di.w == dj.w, g);
+  R* t = T + 6 * pid;
+  t[0] = k.b2u * rx * rx - k.b1u;
+  t[1] = k.b2u * ry * ry - k.b1u;
+  t[2] = k.b2u * rz * rz - k.b1u;
+  t[3] = k.b2u * rx * ry;
+  t[4] = k.b2u * rx * rz;
+  t[5] = k.b2u * ry * rz;
+  R ex, ey, ez;
+  multipole_field<R>(rx, ry, rz, (R)aj.w, (R)bj.x, (R)bj.y, (R)bj.z, (R)cj.x, (R)cj.y, (R)cj.z, (R)cj.w,
+                     (R)dj.x, (R)dj.y, k.b1e, k.b2e, k.b3e, ex, ey, ez);
+  R* e = Ep + 6 * pid;
+  e[0] = ex;
+  e[1] = ey;
+  e[2] = ez;
+  multipole_field<R>(-rx, -ry, -rz, (R)ai.w, (R)bi.x, (R)bi.y, (R)bi.z, (R)ci.x, (R)ci.y, (R)ci.z, (R)ci.w,
+                     (R)di.x, (R)di.y, k.b1e, k.b2e, k.b3e, ex, ey, ez);
+  e[3] = ex;
+  e[4] = ey;
+  e[5] = ez;
+}
+
+// float64 products T_ij v_j and T_ij v_i of every pair, tensor recomputed on
+// the fly in float64 (the mixed path's float64 residual check).
+__global__ void __launch_bounds__(256) k_pair_tv_direct(long long nh, const int* __restrict__ half_i,
+                                                        const int* __restrict__ half_j,
+                                                        const double4_32a* __restrict__ A,
+                                                        const double4_32a* __restrict__ B,
+                                                        const double4_32a* __restrict__ D, PairGeom g,
+                                                        const double4_32a* __restrict__ v, double* __restrict__ out) {
+  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pid >= nh) return;
+  const int i = half_i[pid], j = half_j[pid];
+  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], di = D[i], dj = D[j];
+  const double rx = min_image(ai.x - aj.x, g.L), ry = min_image(ai.y - aj.y, g.L), rz = min_image(ai.z - aj.z, g.L);
+  const double r2 = rx * rx + ry * ry + rz * rz;
+  const Kern<double> k = pair_kernels<double>(r2, bi.w, bj.w, di.z, dj.z, true, g);
+  const double4_32a vi = v[i], vj = v[j];
+  double s = k.b2u * (rx * vj.x + ry * vj.y + rz * vj.z);
+  double* o = out + 6 * pid;
+  o[0] = s * rx - k.b1u * vj.x;
+  o[1] = s * ry - k.b1u * vj.y;
+  o[2] = s * rz - k.b1u * vj.z;
+  s = k.b2u * (rx * vi.x + ry * vi.y + rz * vi.z);
+  o[3] = s * rx - k.b1u * vi.x;
+  o[4] = s * ry - k.b1u * vi.y;
+  o[5] = s * rz - k.b1u * vi.z;
+}
+
+// Sum over the kRowGroup lanes of one row. The mask names exactly the lanes
+// of this group, so groups past the last row may exit early.
+__device__ __forceinline__ double group_sum(double v) {
+  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
+#pragma unroll
+  for (int o = kRowGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kRowGroup);
+  return v;
+}
+
+// out_i = sum over row entries of the stored per-pair vectors (side-selected)
+// + selfc * self_i.xyz. Used for E0 (stored permanent fields) and for the
+// float64 direct products.
+template <typename R>
+__global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __restrict__ full_start,
+                                                         const int* __restrict__ full_ref,
+                                                         const R* __restrict__ pv, double selfc,
+                                                         const double4_32a* __restrict__ selfv,
+                                                         double4_32a* __restrict__ out) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gid / kRowGroup, l = gid % kRowGroup;
+  if (i >= n) return;  // whole groups exit together (n rows, kRowGroup | 32)
+  double sx = 0, sy = 0, sz = 0;
+  const int e = full_start[i + 1];
+  for (int k = full_start[i] + l; k < e; k += kRowGroup) {
+    const int ref = full_ref[k];
+    const R* p = pv + 6 * (long long)(ref >> 1) + 3 * (ref & 1);
+    sx += (double)p[0];
+    sy += (double)p[1];
+    sz += (double)p[2];
+  }
+  sx = group_sum(sx);
+  sy = group_sum(sy);
+  sz = group_sum(sz);
+  if (l == 0) {
+    const double4_32a s = selfv[i];
+    out[i] = make_double4_32a(sx + selfc * s.x, sy + selfc * s.y, sz + selfc * s.z, 0.0);
+  }
+}
+
+// out_i = sum_j T_ij v_j + selfc v_i, float64 tensors.
+__global__ void __launch_bounds__(256) k_t_real64(int n, const int* __restrict__ full_start,
+                                                  const int* __restrict__ full_j, const int* __restrict__ full_ref,
+                                                  const double* __restrict__ T, double selfc,
+                                                  const double4_32a* __restrict__ v, double4_32a* __restrict__ out) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gid / kRowGroup, l = gid % kRowGroup;
+  if (i >= n) return;
+  double sx = 0, sy = 0, sz = 0;
+  const int e = full_start[i + 1];
+  for (int k = full_start[i] + l; k < e; k += kRowGroup) {
+    const int j = full_j[k];
+    const double2* t = reinterpret_cast<const double2*>(T + 6 * (long long)(full_ref[k] >> 1));
+    const double2 t0 = t[0], t1 = t[1], t2 = t[2];  // (xx,yy) (zz,xy) (xz,yz)
+    const double4_32a vj = v[j];
+    sx += t0.x * vj.x + t1.y * vj.y + t2.x * vj.z;
+    sy += t1.y * vj.x + t0.y * vj.y + t2.y * vj.z;
+    sz += t2.x * vj.x + t2.y * vj.y + t1.x * vj.z;
+  }
+  sx = group_sum(sx);
+  sy = group_sum(sy);
+  sz = group_sum(sz);
+  if (l == 0) {
+    const double4_32a vi = v[i];
+    out[i] = make_double4_32a(sx + selfc * vi.x, sy + selfc * vi.y, sz + selfc * vi.z, 0.0);
+  }
+}
+
+// Mixed precision: float32 tensors and float32 copy of v, products summed in
+// float32 per lane over its share of the row, then the row total in float64.
+__global__ void __launch_bounds__(256) k_t_real32(int n, const int* __restrict__ full_start,
+                                                  const int* __restrict__ full_j, const int* __restrict__ full_ref,
+                                                  const float* __restrict__ T, double selfc,
+                                                  const float4* __restrict__ v32, const double4_32a* __restrict__ v64,
+                                                  double4_32a* __restrict__ out) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gid / kRowGroup, l = gid % kRowGroup;
+  if (i >= n) return;
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  const int e = full_start[i + 1];
+  for (int k = full_start[i] + l; k < e; k += kRowGroup) {
+    const int j = full_j[k];
+    const float2* t = reinterpret_cast<const float2*>(T + 6 * (long long)(full_ref[k] >> 1));
+    const float2 t0 = t[0], t1 = t[1], t2 = t[2];
+    const float4 vj = v32[j];
+    sx += t0.x * vj.x + t1.y * vj.y + t2.x * vj.z;
+    sy += t1.y * vj.x + t0.y * vj.y + t2.y * vj.z;
+    sz += t2.x * vj.x + t2.y * vj.y + t1.x * vj.z;
+  }
+  double dx = group_sum((double)sx);
+  double dy = group_sum((double)sy);
+  double dz = group_sum((double)sz);
+  if (l == 0) {
+    const double4_32a vi = v64[i];
+    out[i] = make_double4_32a(dx + selfc * vi.x, dy + selfc * vi.y, dz + selfc * vi.z, 0.0);
+  }
+}
+
+PairGeom geom(const amp_ctx* c) {
+  PairGeom g;
+  const double b = c->cfg.ewald_beta;
+  g.L = c->cfg.box;
+  g.beta = b;
+  g.twob2 = 2.0 * b * b;
+  g.gpre = 2.0 * b * b / (b * kSqrtPi);
+  g.selfc = 4.0 * b * b * b / (3.0 * kSqrtPi);
+  return g;
+}
+
+}  // namespace
+
+void launch_pair_build(amp_ctx* c) {
+  if (c->n_half == 0) return;
+  const PairGeom g = geom(c);
+  const int blocks = amp_blocks(c->n_half, 256);
+  c->n_launch += 1;
+  if (c->cfg.precision == AMP_FP64)
+    k_pair_build<double><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
+                                                        c->atomC, c->atomD, g, c->T64, c->Ep64);
+  else
+    k_pair_build<float><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
+                                                       c->atomC, c->atomD, g, c->T32, c->Ep32);
+}
+
+// Self term of the permanent field: +4 beta^3/(3 sqrt(pi)) d_i, d_i from atomB.
+void launch_e0_real(amp_ctx* c, double4_32a* out) {
+  const PairGeom g = geom(c);
+  const int blocks = amp_blocks((long long)c->n * kRowGroup, 256);
+  c->n_launch += 1;
+  if (c->cfg.precision == AMP_FP64)
+    k_row_sum_pairvec<double><<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref, c->Ep64, g.selfc,
+                                                             c->atomB, out);
+  else
+    k_row_sum_pairvec<float><<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref, c->Ep32, g.selfc,
+                                                            c->atomB, out);
+}
+
+void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out) {
+  const PairGeom g = geom(c);
+  c->n_launch += 1;
+  k_t_real64<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
+      c->n, c->full_start, c->full_j, c->full_ref, c->T64, g.selfc, v, out);
+}
+
+void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out) {
+  const PairGeom g = geom(c);
+  c->n_launch += 1;
+  k_t_real32<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
+      c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64, out);
+}
+
+void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out) {
+  const PairGeom g = geom(c);
+  c->n_launch += c->n_half > 0 ? 2 : 1;
+  if (c->n_half > 0)
+    k_pair_tv_direct<<<amp_blocks(c->n_half, 256), 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j,
+                                                                        c->atomA, c->atomB, c->atomD, g, v,
+                                                                        c->Ep64);
+  k_row_sum_pairvec<double><<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
+      c->n, c->full_start, c->full_ref, c->Ep64, g.selfc, v, out);
+}
+
+}  // namespace amp

@@ -1,0 +1,402 @@
+// Preconditioned conjugate gradients on (1/alpha - T) mu = E0 (kernel d).
+//
+// The paper's solver applies T*mu about nine times per step (Section
+// "Sequential performance") and names only "the convergence method"
+// (Section "Hotspots"). The method here is CG with the diagonal preconditioner
+// M = diag(alpha) (Saad, Algorithm 9.1):
+//   r = E0 - A mu; z = alpha r; p = z;
+//   loop: q = A p; gamma = r.z / p.q; mu += gamma p; r -= gamma q; z = alpha r;
+//         stop if DEBYE sqrt(sum |z_i|^2 / N) < tol;
+//         beta = (r.z)_new / (r.z)_old; p = z + beta p.
+// All scalars stay on the device in float64; the vector updates are fused
+// into three grid-stride kernels whose block partial sums are reduced again
+// by every block in a fixed order (deterministic, no host round trip). Every
+// kernel of an iteration returns at once when the device "stop" flag is set,
+// so the host can enqueue several iterations between flag reads.
+#include "amp_internal.cuh"
+
+namespace amp {
+namespace {
+
+constexpr int NT = kReduceThreads;
+constexpr int NB = kReduceBlocks;
+
+// iflags: [0] stop, [1] iterations done, [2] converged this iteration,
+//         [3] status (0 running, 1 converged, 2 max_iter, 3 breakdown)
+// scal:   [0], [1] r.z double buffer indexed by iteration parity,
+//         [2] last RMS (Debye), [3] energy
+enum { F_STOP = 0, F_ITERS = 1, F_CONV = 2, F_STATUS = 3 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of two values; result valid in every thread.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+  __shared__ double ra, rb;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double x = l < NT / 32 ? sa[l] : 0.0, y = l < NT / 32 ? sb[l] : 0.0;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (l == 0) {
+      ra = x;
+      rb = y;
+    }
+  }
+  __syncthreads();
+  a = ra;
+  b = rb;
+  __syncthreads();
+}
+
+// Every block re-reduces the NB partials in the same order.
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, double& a, double& b) {
+  a = 0.0;
+  b = 0.0;
+  for (int k = threadIdx.x; k < NB; k += NT) {
+    a += part[k];
+    b += part[NB + k];
+  }
+  block_sum2(a, b);
+}
+
+__device__ __forceinline__ void write_partials(double* __restrict__ part, double a, double b) {
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = a;
+    part[NB + blockIdx.x] = b;
+  }
+}
+
+__device__ __forceinline__ double dot3(const double4_32a& a, const double4_32a& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+__global__ void k_mu_from_e0(int n, const double4_32a* __restrict__ e0, const double2* __restrict__ al,
+                             double4_32a* __restrict__ mu) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double a = al[s].x;
+    const double4_32a e = e0[s];
+    mu[s] = make_double4_32a(a * e.x, a * e.y, a * e.z, 0.0);
+  }
+}
+
+// r = E0 - mu/alpha + t (t = T mu); z = alpha r; p = z; partials (r.z, z.z)
+__global__ void __launch_bounds__(NT) k_pcg_init(int n, const double4_32a* __restrict__ e0,
+                                                 const double4_32a* __restrict__ mu, const double4_32a* __restrict__ t,
+                                                 const double2* __restrict__ al, double4_32a* __restrict__ r,
+                                                 double4_32a* __restrict__ z, double4_32a* __restrict__ p,
+                                                 float4* __restrict__ p32, double* __restrict__ part) {
+  double rz = 0.0, zz = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double2 a = al[s];
+    const double4_32a e = e0[s], m = mu[s], tt = t[s];
+    const double4_32a rr = make_double4_32a(e.x - m.x * a.y + tt.x, e.y - m.y * a.y + tt.y, e.z - m.z * a.y + tt.z, 0.0);
+    const double4_32a zz4 = make_double4_32a(a.x * rr.x, a.x * rr.y, a.x * rr.z, 0.0);
+    r[s] = rr;
+    z[s] = zz4;
+    p[s] = zz4;
+    if (p32) p32[s] = make_float4((float)zz4.x, (float)zz4.y, (float)zz4.z, 0.f);
+    rz += dot3(rr, zz4);
+    zz += dot3(zz4, zz4);
+  }
+  write_partials(part, rz, zz);
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_init_finish(int n, const double* __restrict__ part, double tol,
+                                                        double* __restrict__ scal, int* __restrict__ fl) {
+  double rz, zz;
+  reduce_partials(part, rz, zz);
+  if (threadIdx.x == 0) {
+    const double rms = kDebye * sqrt(zz / (double)n);
+    scal[fl[F_ITERS] & 1] = rz;
+    scal[2] = rms;
+    fl[F_CONV] = 0;
+    if (rms < tol) {
+      fl[F_STOP] = 1;
+      fl[F_STATUS] = 1;
+    } else {
+      fl[F_STOP] = 0;
+      fl[F_STATUS] = 0;
+    }
+  }
+}
+
+// q = p/alpha - t; partials (p.q, 0)
+__global__ void __launch_bounds__(NT) k_pcg_q(int n, const double4_32a* __restrict__ p, const double4_32a* __restrict__ t,
+                                              const double2* __restrict__ al, double4_32a* __restrict__ q,
+                                              double* __restrict__ part, const int* __restrict__ fl) {
+  if (fl[F_STOP]) return;
+  double pq = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double ia = al[s].y;
+    const double4_32a pp = p[s], tt = t[s];
+    const double4_32a qq = make_double4_32a(pp.x * ia - tt.x, pp.y * ia - tt.y, pp.z * ia - tt.z, 0.0);
+    q[s] = qq;
+    pq += dot3(pp, qq);
+  }
+  write_partials(part, pq, 0.0);
+}
+
+// gamma = r.z / p.q; mu += gamma p; r -= gamma q; z = alpha r; partials (r.z, z.z)
+__global__ void __launch_bounds__(NT) k_pcg_update(int n, double4_32a* __restrict__ mu, double4_32a* __restrict__ r,
+                                                   double4_32a* __restrict__ z, const double4_32a* __restrict__ p,
+                                                   const double4_32a* __restrict__ q, const double2* __restrict__ al,
+                                                   const double* __restrict__ part_in, double* __restrict__ part,
+                                                   const double* __restrict__ scal, int* __restrict__ fl) {
+  if (fl[F_STOP]) return;
+  double pq, unused;
+  reduce_partials(part_in, pq, unused);
+  if (!(pq > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[F_CONV] = -1;  // breakdown: operator not SPD
+    return;
+  }
+  const double gamma = scal[fl[F_ITERS] & 1] / pq;
+  double rz = 0.0, zz = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double a = al[s].x;
+    const double4_32a pp = p[s], qq = q[s];
+    double4_32a m = mu[s], rr = r[s];
+    m.x += gamma * pp.x;
+    m.y += gamma * pp.y;
+    m.z += gamma * pp.z;
+    rr.x -= gamma * qq.x;
+    rr.y -= gamma * qq.y;
+    rr.z -= gamma * qq.z;
+    const double4_32a zz4 = make_double4_32a(a * rr.x, a * rr.y, a * rr.z, 0.0);
+    mu[s] = m;
+    r[s] = rr;
+    z[s] = zz4;
+    rz += dot3(rr, zz4);
+    zz += dot3(zz4, zz4);
+  }
+  write_partials(part, rz, zz);
+}
+
+// convergence test on z; beta = rz_new/rz_old; p = z + beta p
+__global__ void __launch_bounds__(NT) k_pcg_dir(int n, const double4_32a* __restrict__ z, double4_32a* __restrict__ p,
+                                                float4* __restrict__ p32, const double* __restrict__ part,
+                                                double* __restrict__ scal, int* __restrict__ fl, double tol) {
+  if (fl[F_STOP] || fl[F_CONV] < 0) return;
+  double rz, zz;
+  reduce_partials(part, rz, zz);
+  const double rms = kDebye * sqrt(zz / (double)n);
+  const int it = fl[F_ITERS];
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[2] = rms;
+  if (rms < tol) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[F_CONV] = 1;
+    return;
+  }
+  const double beta = rz / scal[it & 1];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double4_32a zz4 = z[s];
+    double4_32a pp = p[s];
+    pp.x = zz4.x + beta * pp.x;
+    pp.y = zz4.y + beta * pp.y;
+    pp.z = zz4.z + beta * pp.z;
+    p[s] = pp;
+    if (p32) p32[s] = make_float4((float)pp.x, (float)pp.y, (float)pp.z, 0.f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[(it + 1) & 1] = rz;
+}
+
+__global__ void k_pcg_advance(int* __restrict__ fl, int max_iter) {
+  if (fl[F_STOP]) return;
+  fl[F_ITERS] += 1;
+  if (fl[F_CONV] == 1) {
+    fl[F_STOP] = 1;
+    fl[F_STATUS] = 1;
+  } else if (fl[F_CONV] < 0) {
+    fl[F_STOP] = 1;
+    fl[F_STATUS] = 3;
+  } else if (fl[F_ITERS] >= max_iter) {
+    fl[F_STOP] = 1;
+    fl[F_STATUS] = 2;
+  }
+}
+
+__global__ void k_to_sorted(int n, const int* __restrict__ perm, const double* __restrict__ src,
+                            double4_32a* __restrict__ dst) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  dst[s] = make_double4_32a(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0);
+}
+
+__global__ void k_from_sorted(int n, const int* __restrict__ perm, const double4_32a* __restrict__ src,
+                              double* __restrict__ dst) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  const double4_32a v = src[s];
+  dst[3 * i] = v.x;
+  dst[3 * i + 1] = v.y;
+  dst[3 * i + 2] = v.z;
+}
+
+__global__ void k_to32(int n, const double4_32a* __restrict__ v, float4* __restrict__ o) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double4_32a a = v[s];
+    o[s] = make_float4((float)a.x, (float)a.y, (float)a.z, 0.f);
+  }
+}
+
+// U = -1/2 C sum mu . E0 over the caller's [N][3] arrays
+__global__ void __launch_bounds__(NT) k_energy_partial(long long m, const double* __restrict__ mu,
+                                                       const double* __restrict__ e0, double* __restrict__ part) {
+  double s = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x)
+    s += mu[k] * e0[k];
+  write_partials(part, s, 0.0);
+}
+
+__global__ void __launch_bounds__(NT) k_energy_finish(const double* __restrict__ part, double* __restrict__ out) {
+  double s, unused;
+  reduce_partials(part, s, unused);
+  if (threadIdx.x == 0) *out = -0.5 * kCoulomb * s;
+}
+
+}  // namespace
+
+void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst) {
+  c->n_launch += 1;
+  k_to_sorted<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->perm, src, dst);
+}
+
+void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst) {
+  c->n_launch += 1;
+  k_from_sorted<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->perm, src, dst);
+}
+
+void launch_to32(amp_ctx* c, const double4_32a* v, float4* o) {
+  c->n_launch += 1;
+  k_to32<<<NB, NT, 0, c->stream>>>(c->n, v, o);
+}
+
+// t = T v in the solver's working precision (v32 must mirror v in mixed mode).
+int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* t) {
+  const bool fp64 = c->cfg.precision == AMP_FP64;
+  {
+    PhaseScope ps(c, AMP_PHASE_T_REAL);
+    if (fp64)
+      launch_t_real(c, v, t);
+    else
+      launch_t_real32(c, v32, v, t);
+  }
+  PhaseScope ps(c, AMP_PHASE_T_RECIP);
+  return fp64 ? pme_dipole_field(c, v, t) : pme_dipole_field32(c, v32, t);
+}
+
+// t = T v with every term in float64 (mixed path: pair tensors recomputed).
+int apply_T_sorted_fp64(amp_ctx* c, const double4_32a* v, double4_32a* t) {
+  if (c->cfg.precision == AMP_FP64) return apply_T_sorted(c, v, nullptr, t);
+  PhaseScope ps(c, AMP_PHASE_FP64_CHECK);
+  launch_t_real_fp64_direct(c, v, t);
+  return pme_dipole_field(c, v, t);
+}
+
+static int read_flags(amp_ctx* c) {
+  cudaMemcpyAsync(c->hibuf, c->iflags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "solver flag read");
+}
+
+static int enqueue_iteration(amp_ctx* c) {
+  const int n = c->n;
+  cudaStream_t st = c->stream;
+  const bool mixed = c->cfg.precision == AMP_MIXED;
+  double* pa = c->partials;
+  double* pb = c->partials + 2 * NB;
+  int r = apply_T_sorted(c, c->pv, mixed ? c->p32 : nullptr, c->tv);
+  if (r) return r;
+  PhaseScope ps(c, AMP_PHASE_PCG);
+  c->n_launch += 4;
+  k_pcg_q<<<NB, NT, 0, st>>>(n, c->pv, c->tv, c->alph, c->qv, pa, c->iflags);
+  k_pcg_update<<<NB, NT, 0, st>>>(n, c->mu, c->res, c->zv, c->pv, c->qv, c->alph, pa, pb, c->scal, c->iflags);
+  k_pcg_dir<<<NB, NT, 0, st>>>(n, c->zv, c->pv, mixed ? c->p32 : nullptr, pb, c->scal, c->iflags,
+                               c->cfg.tol_debye);
+  k_pcg_advance<<<1, 1, 0, st>>>(c->iflags, c->cfg.max_iter);
+  return AMP_OK;
+}
+
+// Residual of the current mu with the float64 or working operator, then
+// restart the recurrence from it.
+static int restart(amp_ctx* c, bool fp64_operator) {
+  const bool mixed = c->cfg.precision == AMP_MIXED;
+  int r;
+  if (fp64_operator) {
+    r = apply_T_sorted_fp64(c, c->mu, c->tv);
+  } else {
+    if (mixed) launch_to32(c, c->mu, c->p32);
+    r = apply_T_sorted(c, c->mu, mixed ? c->p32 : nullptr, c->tv);
+  }
+  if (r) return r;
+  PhaseScope ps(c, AMP_PHASE_PCG);
+  c->n_launch += 2;
+  k_pcg_init<<<NB, NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->alph, c->res, c->zv, c->pv,
+                                       mixed ? c->p32 : nullptr, c->partials);
+  k_pcg_init_finish<<<1, NT, 0, c->stream>>>(c->n, c->partials, c->cfg.tol_debye, c->scal, c->iflags);
+  return AMP_OK;
+}
+
+int solve(amp_ctx* c, bool use_guess) {
+  const bool mixed = c->cfg.precision == AMP_MIXED;
+  cudaStream_t st = c->stream;
+  int r;
+  if (!use_guess) c->n_launch += 1;
+  if (!use_guess) k_mu_from_e0<<<NB, NT, 0, st>>>(c->n, c->E0s, c->alph, c->mu);
+  if ((r = cuda_check(c, cudaMemsetAsync(c->iflags, 0, sizeof(int) * 4, st), "memset"))) return r;
+  if ((r = restart(c, !mixed))) return r;
+  const int chunk = 4;
+  c->stats.fp64_checks = 0;
+  for (int round = 0; round < 8; ++round) {
+    while (true) {
+      for (int k = 0; k < chunk; ++k)
+        if ((r = enqueue_iteration(c))) return r;
+      if ((r = read_flags(c))) return r;
+      if (c->hibuf[0]) break;
+    }
+    if (!mixed || c->hibuf[3] != 1) break;
+    // mixed: check the converged dipoles with the float64 operator
+    if ((r = restart(c, true))) return r;
+    c->stats.fp64_checks++;
+    if ((r = read_flags(c))) return r;
+    if (c->hibuf[3] == 1 || c->hibuf[1] >= c->cfg.max_iter) break;
+  }
+  if ((r = cuda_check(c, cudaGetLastError(), "solver launch"))) return r;
+  c->stats.iters = c->hibuf[1];
+  c->stats.rms = c->hbuf[2];
+  const int status = c->hibuf[3];
+  if (status == 3) return fail(c, AMP_ERR_NOT_CONVERGED, "PCG breakdown: p.Ap <= 0");
+  if (status != 1)
+    return fail(c, AMP_ERR_NOT_CONVERGED, "PCG not converged after %d iterations (RMS %.3e D)", c->stats.iters,
+                c->stats.rms);
+  return AMP_OK;
+}
+
+int energy(amp_ctx* c, const double* mu, const double* E0, double* U) {
+  {
+    PhaseScope ps(c, AMP_PHASE_ENERGY);
+    c->n_launch += 2;
+    k_energy_partial<<<NB, NT, 0, c->stream>>>(3LL * c->n, mu, E0, c->partials);
+    k_energy_finish<<<1, NT, 0, c->stream>>>(c->partials, c->scal + 3);
+  }
+  cudaMemcpyAsync(c->hbuf + 3, c->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  int r = cuda_check(c, cudaStreamSynchronize(c->stream), "energy");
+  if (r) return r;
+  *U = c->hbuf[3];
+  return AMP_OK;
+}
+
+}  // namespace amp

@@ -1,0 +1,375 @@
+// Smooth particle-mesh Ewald (kernels c and c').
+//
+// Reciprocal-space part of the permanent field and of T*mu (the paper's
+// "reciprocal polarization", Section "Sequential performance"; not vectorized
+// in the CPU code, Section "Conclusion"). Smooth PME (Essmann et al. 1995)
+// with multipolar spreading (Sagui, Pedersen & Darden 2004), order 5:
+//   u = K x / L (mod K) per axis, k0 = floor(u), f = u - k0; grid point
+//   k0 - t (mod K), t = 0..4, has weight M5(f + t) (cardinal B-spline);
+//   Q(g) = sum_i (q_i + d_i . grad + 1/3 Theta_i : grad grad) W_i(g), grad = (K/L) d/du;
+//   phi = unnormalised C2R( G . R2C(Q) ),
+//   G(m) = exp(-pi^2 m~^2/beta^2) / (pi V m~^2) |b1 b2 b3|^2, G(0) = 0;
+//   E_i = -sum_g grad W_i(g) phi(g).
+// The 3D FFTs are cuFFT (library call). Spreading uses float64 (or float32 in
+// the mixed path) atomics into the grid; gathering is one thread per atom.
+// |b(m)|^2 = 1/|sum_{k=0}^{3} M5(k+1) e^{2 pi i m k/K}|^2; where that sum
+// vanishes (m = K/2, even K) the mean of the neighbours m-1, m+1 is used.
+#include <cmath>
+#include <vector>
+
+#include "amp_internal.cuh"
+
+namespace amp {
+namespace {
+
+constexpr int kTh = 3 * 4 * kOrder;  // per atom: 3 axes x derivatives 0..3 x 5 points
+
+// Weights M5(f + t) and their first three derivatives (t = 0..4) by the
+// B-spline recursion M_n(u) = [u M_{n-1}(u) + (n - u) M_{n-1}(u - 1)]/(n - 1).
+__device__ __forceinline__ void bspline5(double f, double s, double w[4][kOrder]) {
+  double m2[2] = {f, 1.0 - f};
+  double m3[3], m4[4], m5[5];
+  for (int t = 0; t < 3; ++t) {
+    const double a = t < 2 ? m2[t] : 0.0, b = t >= 1 ? m2[t - 1] : 0.0;
+    m3[t] = ((f + t) * a + (3.0 - f - t) * b) * 0.5;
+  }
+  for (int t = 0; t < 4; ++t) {
+    const double a = t < 3 ? m3[t] : 0.0, b = t >= 1 ? m3[t - 1] : 0.0;
+    m4[t] = ((f + t) * a + (4.0 - f - t) * b) * (1.0 / 3.0);
+  }
+  for (int t = 0; t < 5; ++t) {
+    const double a = t < 4 ? m4[t] : 0.0, b = t >= 1 ? m4[t - 1] : 0.0;
+    m5[t] = ((f + t) * a + (5.0 - f - t) * b) * 0.25;
+  }
+  for (int t = 0; t < 5; ++t) {
+    const double a4 = t < 4 ? m4[t] : 0.0, b4 = t >= 1 ? m4[t - 1] : 0.0;
+    const double a3 = t < 3 ? m3[t] : 0.0, b3 = (t >= 1 && t - 1 < 3) ? m3[t - 1] : 0.0,
+                 c3 = (t >= 2 && t - 2 < 3) ? m3[t - 2] : 0.0;
+    const double a2 = t < 2 ? m2[t] : 0.0, b2 = (t >= 1 && t - 1 < 2) ? m2[t - 1] : 0.0,
+                 c2 = (t >= 2 && t - 2 < 2) ? m2[t - 2] : 0.0, d2 = (t >= 3 && t - 3 < 2) ? m2[t - 3] : 0.0;
+    w[0][t] = m5[t];
+    w[1][t] = (a4 - b4) * s;
+    w[2][t] = (a3 - 2.0 * b3 + c3) * s * s;
+    w[3][t] = (a2 - 3.0 * b2 + 3.0 * c2 - d2) * s * s * s;
+  }
+}
+
+__global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int K, double* __restrict__ theta,
+                        float* __restrict__ theta32, int4* __restrict__ gbase) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double4_32a a = A[s];
+  const double xs[3] = {a.x, a.y, a.z};
+  const double sc = (double)K / L;
+  int base[3];
+  double* th = theta + (long long)kTh * s;
+  for (int ax = 0; ax < 3; ++ax) {
+    double u = xs[ax] * sc;
+    u = u - (double)K * floor(u / (double)K);
+    if (u >= (double)K) u -= (double)K;
+    if (u < 0.0) u += (double)K;
+    const double k0 = floor(u);
+    base[ax] = (int)k0;
+    double w[4][kOrder];
+    bspline5(u - k0, sc, w);
+    for (int d = 0; d < 4; ++d)
+      for (int t = 0; t < kOrder; ++t) {
+        th[(ax * 4 + d) * kOrder + t] = w[d][t];
+        if (theta32) theta32[(long long)kTh * s + (ax * 4 + d) * kOrder + t] = (float)w[d][t];
+      }
+  }
+  gbase[s] = make_int4(base[0], base[1], base[2], 0);
+}
+
+template <typename R>
+struct Wts {
+  R x[3][kOrder], y[3][kOrder], z[3][kOrder];
+};
+
+template <typename R>
+__device__ __forceinline__ void load_wts(const R* __restrict__ th, int nd, Wts<R>& w) {
+  for (int d = 0; d < nd; ++d)
+    for (int t = 0; t < kOrder; ++t) {
+      w.x[d][t] = th[(0 * 4 + d) * kOrder + t];
+      w.y[d][t] = th[(1 * 4 + d) * kOrder + t];
+      w.z[d][t] = th[(2 * 4 + d) * kOrder + t];
+    }
+}
+
+__device__ __forceinline__ int wrapk(int g, int K) { return g < 0 ? g + K : g; }
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_spread_multipoles(int n, const R* __restrict__ theta,
+                                                           const int4* __restrict__ gbase,
+                                                           const double4_32a* __restrict__ A,
+                                                           const double4_32a* __restrict__ B,
+                                                           const double4_32a* __restrict__ C,
+                                                           const double4_32a* __restrict__ D, int K,
+                                                           R* __restrict__ grid) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  Wts<R> w;
+  load_wts<R>(theta + (long long)kTh * s, 3, w);
+  const int4 b = gbase[s];
+  const double4_32a a = A[s], bb = B[s], c = C[s], d = D[s];
+  const R q = (R)a.w, dx = (R)bb.x, dy = (R)bb.y, dz = (R)bb.z;
+  const R qxx = (R)c.x, qyy = (R)c.y, qzz = (R)c.z, qxy = (R)c.w, qxz = (R)d.x, qyz = (R)d.y;
+  const R third = (R)(1.0 / 3.0), two3 = (R)(2.0 / 3.0);
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const int gx = wrapk(b.x - tx, K);
+    for (int ty = 0; ty < kOrder; ++ty) {
+      const int gy = wrapk(b.y - ty, K);
+      const R x0y0 = w.x[0][tx] * w.y[0][ty], x1y0 = w.x[1][tx] * w.y[0][ty], x0y1 = w.x[0][tx] * w.y[1][ty];
+      const R a0 = q * x0y0 + dx * x1y0 + dy * x0y1 +
+                   third * (qxx * w.x[2][tx] * w.y[0][ty] + qyy * w.x[0][tx] * w.y[2][ty] +
+                            (R)2 * qxy * w.x[1][tx] * w.y[1][ty]);
+      const R a1 = dz * x0y0 + two3 * (qxz * x1y0 + qyz * x0y1);
+      const R a2 = third * qzz * x0y0;
+      R* row = grid + ((long long)gx * K + gy) * K;
+      for (int tz = 0; tz < kOrder; ++tz) {
+        const int gz = wrapk(b.z - tz, K);
+        atomicAdd(row + gz, a0 * w.z[0][tz] + a1 * w.z[1][tz] + a2 * w.z[2][tz]);
+      }
+    }
+  }
+}
+
+template <typename R, typename V>
+__global__ void __launch_bounds__(128) k_spread_dipoles(int n, const R* __restrict__ theta,
+                                                        const int4* __restrict__ gbase, const V* __restrict__ v,
+                                                        int K, R* __restrict__ grid) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  Wts<R> w;
+  load_wts<R>(theta + (long long)kTh * s, 2, w);
+  const int4 b = gbase[s];
+  const V m = v[s];
+  const R mx = (R)m.x, my = (R)m.y, mz = (R)m.z;
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const int gx = wrapk(b.x - tx, K);
+    for (int ty = 0; ty < kOrder; ++ty) {
+      const int gy = wrapk(b.y - ty, K);
+      const R a0 = mx * w.x[1][tx] * w.y[0][ty] + my * w.x[0][tx] * w.y[1][ty];
+      const R a1 = mz * w.x[0][tx] * w.y[0][ty];
+      R* row = grid + ((long long)gx * K + gy) * K;
+      for (int tz = 0; tz < kOrder; ++tz) {
+        const int gz = wrapk(b.z - tz, K);
+        atomicAdd(row + gz, a0 * w.z[0][tz] + a1 * w.z[1][tz]);
+      }
+    }
+  }
+}
+
+template <typename C, typename R>
+__global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict__ G) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const R g = G[k];
+  C v = cg[k];
+  v.x *= g;
+  v.y *= g;
+  cg[k] = v;
+}
+
+// out_i += -sum_g grad W_i(g) phi(g)
+template <typename R>
+__global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict__ theta,
+                                                      const int4* __restrict__ gbase, const R* __restrict__ phi,
+                                                      int K, double4_32a* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  Wts<R> w;
+  load_wts<R>(theta + (long long)kTh * s, 2, w);
+  const int4 b = gbase[s];
+  R ex = 0, ey = 0, ez = 0;
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const int gx = wrapk(b.x - tx, K);
+    for (int ty = 0; ty < kOrder; ++ty) {
+      const int gy = wrapk(b.y - ty, K);
+      const R* row = phi + ((long long)gx * K + gy) * K;
+      R s0 = 0, s1 = 0;
+      for (int tz = 0; tz < kOrder; ++tz) {
+        const R p = row[wrapk(b.z - tz, K)];
+        s0 += w.z[0][tz] * p;
+        s1 += w.z[1][tz] * p;
+      }
+      ex += w.x[1][tx] * w.y[0][ty] * s0;
+      ey += w.x[0][tx] * w.y[1][ty] * s0;
+      ez += w.x[0][tx] * w.y[0][ty] * s1;
+    }
+  }
+  double4_32a o = out[s];
+  o.x -= (double)ex;
+  o.y -= (double)ey;
+  o.z -= (double)ez;
+  out[s] = o;
+}
+
+// Host: B-spline moduli and influence function, float64.
+double m5_at(double u) {  // M5 at integer-shifted u by the recursion (host side)
+  double m[6] = {0};
+  // M2 on [0, 2]
+  auto M = [](int n, double x, auto&& self) -> double {
+    if (n == 2) return x <= 0.0 || x >= 2.0 ? 0.0 : 1.0 - std::fabs(x - 1.0);
+    return (x * self(n - 1, x, self) + (n - x) * self(n - 1, x - 1.0, self)) / (n - 1);
+  };
+  (void)m;
+  return M(5, u, M);
+}
+
+std::vector<double> moduli(int K) {
+  std::vector<double> b2(K, 0.0);
+  std::vector<char> ok(K, 0);
+  for (int m = 0; m < K; ++m) {
+    double re = 0, im = 0;
+    for (int k = 0; k < kOrder - 1; ++k) {
+      const double mk = m5_at(k + 1.0);
+      const double ang = 2.0 * M_PI * (double)m * (double)k / (double)K;
+      re += mk * std::cos(ang);
+      im += mk * std::sin(ang);
+    }
+    const double den = re * re + im * im;
+    if (den >= 1e-7) {
+      b2[m] = 1.0 / den;
+      ok[m] = 1;
+    }
+  }
+  for (int m = 0; m < K; ++m)
+    if (!ok[m]) b2[m] = 0.5 * (b2[(m - 1 + K) % K] + b2[(m + 1) % K]);
+  return b2;
+}
+
+int exec_fft(amp_ctx* c, bool fp32, bool forward) {
+  cufftResult r;
+  if (!fp32)
+    r = forward ? cufftExecD2Z(c->plan_d2z, c->grid64, reinterpret_cast<cufftDoubleComplex*>(c->cgrid64))
+                : cufftExecZ2D(c->plan_z2d, reinterpret_cast<cufftDoubleComplex*>(c->cgrid64), c->grid64);
+  else
+    r = forward ? cufftExecR2C(c->plan_r2c, c->grid32, reinterpret_cast<cufftComplex*>(c->cgrid32))
+                : cufftExecC2R(c->plan_c2r, reinterpret_cast<cufftComplex*>(c->cgrid32), c->grid32);
+  if (r != CUFFT_SUCCESS) return fail(c, AMP_ERR_CUDA, "cuFFT exec failed (%d)", (int)r);
+  return AMP_OK;
+}
+
+}  // namespace
+
+int pme_setup(amp_ctx* c) {
+  const int K = c->cfg.pme_grid;
+  c->K = K;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  int r;
+  if ((r = dev_alloc(c, &c->grid64, ng)) || (r = dev_alloc(c, &c->cgrid64, nh)) ||
+      (r = dev_alloc(c, &c->G64, nh)))
+    return r;
+  if (c->cfg.precision == AMP_MIXED) {
+    if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
+        (r = dev_alloc(c, &c->G32, nh)))
+      return r;
+  }
+  // influence function on the half spectrum
+  const std::vector<double> b2 = moduli(K);
+  const double L = c->cfg.box, beta = c->cfg.ewald_beta, V = L * L * L;
+  std::vector<double> G(nh);
+  std::vector<float> G32(c->cfg.precision == AMP_MIXED ? nh : 0);
+  for (int mx = 0; mx < K; ++mx)
+    for (int my = 0; my < K; ++my)
+      for (int mz = 0; mz <= K / 2; ++mz) {
+        const double fx = (mx <= K / 2 ? mx : mx - K) / L, fy = (my <= K / 2 ? my : my - K) / L, fz = mz / L;
+        const double m2 = fx * fx + fy * fy + fz * fz;
+        const long long k = ((long long)mx * K + my) * (K / 2 + 1) + mz;
+        double g = 0.0;
+        if (m2 > 0.0) g = std::exp(-M_PI * M_PI * m2 / (beta * beta)) / (M_PI * V * m2) * b2[mx] * b2[my] * b2[mz];
+        G[k] = g;
+        if (!G32.empty()) G32[k] = (float)g;
+      }
+  if ((r = cuda_check(c, cudaMemcpy(c->G64, G.data(), sizeof(double) * nh, cudaMemcpyHostToDevice), "G upload")))
+    return r;
+  if (!G32.empty() &&
+      (r = cuda_check(c, cudaMemcpy(c->G32, G32.data(), sizeof(float) * nh, cudaMemcpyHostToDevice), "G upload")))
+    return r;
+  if (cufftPlan3d(&c->plan_d2z, K, K, K, CUFFT_D2Z) != CUFFT_SUCCESS ||
+      cufftPlan3d(&c->plan_z2d, K, K, K, CUFFT_Z2D) != CUFFT_SUCCESS)
+    return fail(c, AMP_ERR_CUDA, "cuFFT plan creation failed");
+  cufftSetStream(c->plan_d2z, c->stream);
+  cufftSetStream(c->plan_z2d, c->stream);
+  if (c->cfg.precision == AMP_MIXED) {
+    if (cufftPlan3d(&c->plan_r2c, K, K, K, CUFFT_R2C) != CUFFT_SUCCESS ||
+        cufftPlan3d(&c->plan_c2r, K, K, K, CUFFT_C2R) != CUFFT_SUCCESS)
+      return fail(c, AMP_ERR_CUDA, "cuFFT plan creation failed");
+    cufftSetStream(c->plan_r2c, c->stream);
+    cufftSetStream(c->plan_c2r, c->stream);
+  }
+  c->plans = true;
+  return AMP_OK;
+}
+
+int pme_alloc_atoms(amp_ctx* c, int n_cap) {
+  int r;
+  if ((r = dev_alloc(c, &c->theta, (long long)kTh * n_cap)) || (r = dev_alloc(c, &c->gbase, n_cap))) return r;
+  if (c->cfg.precision == AMP_MIXED && (r = dev_alloc(c, &c->theta32, (long long)kTh * n_cap))) return r;
+  return AMP_OK;
+}
+
+void launch_pme_theta(amp_ctx* c) {
+  c->n_launch += 1;
+  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
+                                                       c->gbase);
+}
+
+int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
+  const int K = c->K, n = c->n;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  cudaStream_t st = c->stream;
+  c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
+  int r;
+  if (c->cfg.precision == AMP_FP64) {
+    cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
+    k_spread_multipoles<double><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB,
+                                                                    c->atomC, c->atomD, K, c->grid64);
+    if ((r = exec_fft(c, false, true))) return r;
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
+    if ((r = exec_fft(c, false, false))) return r;
+    k_gather_field<double><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
+  } else {
+    cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
+    k_spread_multipoles<float><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB,
+                                                                   c->atomC, c->atomD, K, c->grid32);
+    if ((r = exec_fft(c, true, true))) return r;
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
+    if ((r = exec_fft(c, true, false))) return r;
+    k_gather_field<float><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
+  }
+  return AMP_OK;
+}
+
+int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out_add) {
+  const int K = c->K, n = c->n;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  cudaStream_t st = c->stream;
+  c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
+  int r;
+  cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
+  k_spread_dipoles<double, double4_32a><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, v, K, c->grid64);
+  if ((r = exec_fft(c, false, true))) return r;
+  k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
+  if ((r = exec_fft(c, false, false))) return r;
+  k_gather_field<double><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
+  return AMP_OK;
+}
+
+int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out_add) {
+  const int K = c->K, n = c->n;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  cudaStream_t st = c->stream;
+  c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
+  int r;
+  cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
+  k_spread_dipoles<float, float4><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, v, K, c->grid32);
+  if ((r = exec_fft(c, true, true))) return r;
+  k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
+  if ((r = exec_fft(c, true, false))) return r;
+  k_gather_field<float><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
+  return AMP_OK;
+}
+
+}  // namespace amp

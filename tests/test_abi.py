@@ -1,0 +1,46 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every declared call.
+
+These run without a GPU: they only load the shared library and look up
+symbols; nothing computes.
+"""
+import ctypes
+import os
+
+import pytest
+
+from paper_1906_01211_gb300 import build as build_mod
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return build_mod.build()
+
+
+def test_library_exports_every_declared_function(lib_path):
+    from paper_1906_01211_gb300 import amoebapol
+    names = amoebapol.header_functions()
+    assert {"amp_create", "amp_set_system", "amp_permanent_field", "amp_apply_T",
+            "amp_solve_induced", "amp_polarization_energy", "amp_destroy"} <= set(names)
+    lib = ctypes.CDLL(lib_path)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_create_rejects_bad_config(lib_path):
+    from paper_1906_01211_gb300 import amoebapol as ap
+    bad = [
+        ap.Config(box=10.0, cutoff=7.0),                  # cutoff >= box/2
+        ap.Config(box=30.0, pme_order=4),                 # order must be 5
+        ap.Config(box=30.0, pme_grid=4),
+        ap.Config(box=30.0, tol_debye=0.0),
+    ]
+    for cfg in bad:
+        with pytest.raises(ap.AmpError) as e:
+            ap.amp_create(cfg.to_c(), None)
+        assert e.value.code == ap.AMP_ERR_ARG
+
+
+def test_null_context_calls_fail_cleanly(lib_path):
+    from paper_1906_01211_gb300 import amoebapol as ap
+    assert ap._lib.amp_set_system(None, 3, None, None, None, None, None, None, None) == ap.AMP_ERR_ARG
+    assert ap.amp_last_error(None) == "null context"
