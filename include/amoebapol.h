@@ -144,6 +144,31 @@ int amp_launch_count(const amp_ctx* ctx, long long* n);
  * either may be NULL). */
 int amp_last_solve_stats(const amp_ctx* ctx, int* iters, int* fp64_checks);
 
+/* Polarization energy without any allocation. The paper has no counterpart to
+ * this entry point: it exists for callers that cannot allocate device memory
+ * when they need the energy (a host framework that owns all device memory in
+ * its own pool, or a loop that must not pay the implicit synchronisation of
+ * cudaMalloc/cudaFree). Same value as amp_polarization_energy, U = -1/2 C
+ * sum_i mu_i . E0_i (kcal/mol), but no context is needed and nothing is
+ * allocated: the only scratch (one float64 partial per 256 atoms) is a fixed
+ * 32 KiB array in device memory owned by the library, present on every GPU
+ * that loads it until the process exits.
+ *   n_atoms: 1 .. AMP_NOALLOC_MAX_ATOMS; larger returns AMP_ERR_TOO_LARGE and
+ *            launches nothing.
+ *   mu, E0:  device [N][3] float64 (caller's);  U: DEVICE pointer to one
+ *            double, written on the stream (the call does not synchronise).
+ *   cuda_stream: cudaStream_t as void* (NULL = legacy default stream).
+ * The first call on each device resolves the array's device address once;
+ * make it before any stream capture. All calls share the array: calls whose
+ * kernels overlap on the GPU race and give wrong results. Each call writes
+ * every partial it reads, so no clearing between calls is needed.
+ * Returns AMP_OK, AMP_ERR_ARG (null pointer, n_atoms < 1), AMP_ERR_TOO_LARGE
+ * or AMP_ERR_CUDA. */
+#define AMP_ERR_TOO_LARGE (-7)
+#define AMP_NOALLOC_MAX_ATOMS 1048576
+int amp_polarization_energy_noalloc(int n_atoms, const double* mu, const double* E0, double* U,
+                                    void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "amp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
         "amp_last_solve_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "amp_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+        "amp_polarization_energy_noalloc": (I, [I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -156,6 +157,21 @@ def amp_profile_read(ctx) -> dict:
     cnt = (ctypes.c_longlong * n)()
     _check(ctx, _lib.amp_profile_read(ctx, ms, cnt))
     return {name: (ms[k], cnt[k]) for k, name in enumerate(PHASES)}
+
+
+AMP_ERR_TOO_LARGE = -7
+AMP_NOALLOC_MAX_ATOMS = 1048576
+
+
+def amp_polarization_energy_noalloc(n_atoms: int, mu_ptr: int, e0_ptr: int, u_dev_ptr: int,
+                                    stream: int | None = None) -> int:
+    """Energy into a device double, no allocation and no context (returns the status code).
+
+    For callers that cannot allocate device memory when they need the energy;
+    see include/amoebapol.h for the limits and the sharing rules of its scratch.
+    """
+    return _lib.amp_polarization_energy_noalloc(int(n_atoms), mu_ptr, e0_ptr, u_dev_ptr,
+                                                ctypes.c_void_p(stream or 0))
 
 
 def amp_launch_count(ctx) -> int:
