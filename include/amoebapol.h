@@ -112,6 +112,18 @@ int amp_solve_induced(amp_ctx* ctx, const double* E0, double* mu, int use_guess,
 /* Polarization energy U = -1/2 C sum_i mu_i . E0_i (kcal/mol) into *U (host). */
 int amp_polarization_energy(amp_ctx* ctx, const double* mu, const double* E0, double* U);
 
+/* Gradients of the polarization energy at the solution mu (paper, Section
+ * "Hotspots": routine epolar1 computes the polarization energy and forces).
+ * U is stationary in mu, so no re-solve: the adjoint is mu itself.
+ *   mu    [N][3] the converged induced dipoles (caller order);
+ *   F     [N][3] forces -dU/dr (kcal/mol/Angstrom), required;
+ *   gq    [N]    dU/dq, gdip [N][3] dU/dd, gquad [N][6] dU/dTheta for the six
+ *         stored components (xx, yy, zz, xy, xz, yz; each off-diagonal stands
+ *         for two matrix entries); each may be NULL to skip it.
+ * Multipoles are global-frame, so there are no torque terms. Uses the
+ * geometry of the current system; allocates its buffers on the first call. */
+int amp_forces(amp_ctx* ctx, const double* mu, double* F, double* gq, double* gdip, double* gquad);
+
 /* Number of unique atom pairs within the cutoff of the current system. */
 int amp_pair_count(const amp_ctx* ctx, long long* n_pairs);
 
@@ -126,7 +138,8 @@ int amp_pair_count(const amp_ctx* ctx, long long* n_pairs);
 #define AMP_PHASE_PCG 6         /* fused PCG vector updates and reductions */
 #define AMP_PHASE_FP64_CHECK 7  /* mixed path: float64 residual check */
 #define AMP_PHASE_ENERGY 8      /* energy reduction */
-#define AMP_NPHASE 9
+#define AMP_PHASE_FORCES 9      /* adjoint backward: forces and moment gradients */
+#define AMP_NPHASE 10
 
 /* enable != 0: start recording (clears totals); 0: stop. */
 int amp_profile(amp_ctx* ctx, int enable);

@@ -27,7 +27,7 @@ AMP_ERR_GEOMETRY = -5
 AMP_ERR_STATE = -6
 AMP_FP64 = 0
 AMP_MIXED = 1
-PHASES = ("list", "pair", "e0_real", "e0_recip", "t_real", "t_recip", "pcg", "fp64_check", "energy")
+PHASES = ("list", "pair", "e0_real", "e0_recip", "t_real", "t_recip", "pcg", "fp64_check", "energy", "forces")
 
 
 class amp_config(ctypes.Structure):
@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "amp_solve_induced": (I, [P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "amp_polarization_energy": (I, [P, P, P, ctypes.POINTER(D)]),
         "amp_pair_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+        "amp_forces": (I, [P, P, P, P, P, P]),
         "amp_profile": (I, [P, I]),
         "amp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
         "amp_last_solve_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -138,6 +139,10 @@ def amp_polarization_energy(ctx, mu, E0) -> float:
     u = ctypes.c_double(0.0)
     _check(ctx, _lib.amp_polarization_energy(ctx, mu, E0, ctypes.byref(u)))
     return u.value
+
+
+def amp_forces(ctx, mu, F, gq=None, gdip=None, gquad=None):
+    _check(ctx, _lib.amp_forces(ctx, mu, F, gq, gdip, gquad))
 
 
 def amp_pair_count(ctx) -> int:
@@ -221,6 +226,7 @@ class Polarization:
         self.ctx = amp_create(cfg.to_c(), self.stream.cuda_stream)
         self.n = 0
         self._keep = ()
+        self.generation = 0  # bumped by every set_system
 
     def close(self):
         if self.ctx is not None:
@@ -248,6 +254,7 @@ class Polarization:
         self.n = int(arrs[0].shape[0])
         amp_set_system(self.ctx, self.n, *[a.data_ptr() for a in arrs])
         self._keep = arrs  # inputs stay alive while the stream may read them
+        self.generation += 1
 
     def set_synthetic(self, system):
         """Upload a ``synth.System`` (numpy arrays)."""
@@ -282,6 +289,18 @@ class Polarization:
         mu = self._dev(mu, torch.float64)
         E0 = self._dev(E0, torch.float64)
         return amp_polarization_energy(self.ctx, mu.data_ptr(), E0.data_ptr())
+
+    def forces(self, mu):
+        """(F, dU/dq, dU/dd, dU/dTheta6) at the converged dipoles mu."""
+        torch = self.torch
+        mu = self._dev(mu, torch.float64)
+        n = mu.shape[0]
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gq = torch.empty((n,), dtype=torch.float64, device="cuda")
+        gd = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gt = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        amp_forces(self.ctx, mu.data_ptr(), F.data_ptr(), gq.data_ptr(), gd.data_ptr(), gt.data_ptr())
+        return F, gq, gd, gt
 
     def pair_count(self) -> int:
         return amp_pair_count(self.ctx)

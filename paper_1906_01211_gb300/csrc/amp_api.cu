@@ -219,6 +219,14 @@ int amp_solve_induced(amp_ctx* c, const double* E0, double* mu, int use_guess, i
   return e ? e : r;
 }
 
+int amp_forces(amp_ctx* c, const double* mu, double* F, double* gq, double* gdip, double* gquad) {
+  if (!c) return AMP_ERR_ARG;
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!mu || !F) return fail(c, AMP_ERR_ARG, "mu and F are required");
+  launch_to_sorted(c, mu, c->tmp);
+  return forces(c, c->tmp, F, gq, gdip, gquad);
+}
+
 int amp_polarization_energy(amp_ctx* c, const double* mu, const double* E0, double* U) {
   if (!c) return AMP_ERR_ARG;
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");

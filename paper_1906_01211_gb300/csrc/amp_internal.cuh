@@ -13,6 +13,7 @@
 //   full list  CSR rows full_start[s]..full_start[s+1]: entry k holds the
 //              neighbour index full_j[k] and full_ref[k] = 2*pid + side, where
 //              pid is the unique-pair id and side = 0 if the row owns the pair;
+//              a row lists its owned pairs first, then the others by pair id;
 //   half list  (half_i[pid], half_j[pid]) for every unique pair, owned by the
 //              row for which (i < j) != ((i + j) odd) — each pair exactly once,
 //              about half of each row's neighbours.
@@ -64,7 +65,7 @@ struct amp_ctx {
 
   // neighbour lists
   int *full_cnt = nullptr, *half_cnt = nullptr, *full_start = nullptr, *half_start = nullptr;
-  int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr;
+  int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr, *tr_tmp = nullptr;
   long long n_full = 0, n_half = 0, cap_full = 0, cap_half = 0;
   int* flags = nullptr;  // [0] list overflow / search failure
 
@@ -106,6 +107,14 @@ struct amp_ctx {
   int ev_used = 0;
   double prof_ms[AMP_NPHASE] = {0};
   long long prof_cnt[AMP_NPHASE] = {0};
+
+  // backward buffers (allocated by the first amp_forces call)
+  double* force_pair = nullptr;
+  long long force_pair_cap = 0;
+  double* force_recip = nullptr;
+  int force_atom_cap = 0;
+  double* grid64b = nullptr;
+  float* grid32b = nullptr;
 
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
@@ -162,6 +171,10 @@ int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out_add);  // f
 void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst);
 void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst);
 int solve(amp_ctx* c, bool use_guess);
+void launch_to32(amp_ctx* c, const double4_32a* v, float4* o);
+
+// backward (amp_forces.cu)
+int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt);
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
 
 }  // namespace amp

@@ -17,7 +17,8 @@
 //      neighbour cells, float32 distance pre-filter with a margin, exact
 //      float64 decision d.d < rc^2 for candidates near the cutoff;
 //   5. scan the row counts; fill pass writes the full rows and the half rows;
-//   6. every non-owned full entry finds its pair id in the owner's half row.
+//   6. each pair id is scattered to its non-owner's row, which sorts that part
+//      of the row by pair id (deterministic order).
 #include <cstdarg>
 #include <cstdio>
 
@@ -205,17 +206,14 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
           bool own = in && ((i < k) != (((i + k) & 1) != 0));
           unsigned mf = __ballot_sync(0xffffffffu, in);
           unsigned mh = __ballot_sync(0xffffffffu, own);
-          if (kFill && in) {
-            int pos = fbase + nfull + __popc(mf & lt);
-            full_j[pos] = k;
-            if (own) {
-              int pid = hbase + nhalf + __popc(mh & lt);
-              full_ref[pos] = pid << 1;
-              half_i[pid] = i;
-              half_j[pid] = k;
-            } else {
-              full_ref[pos] = -1;
-            }
+          if (kFill && own) {
+            // owned pairs open the row: full slot and pair id share the rank
+            const int rank = nhalf + __popc(mh & lt);
+            const int pid = hbase + rank;
+            full_j[fbase + rank] = k;
+            full_ref[fbase + rank] = pid << 1;
+            half_i[pid] = i;
+            half_j[pid] = k;
           }
           nfull += __popc(mf);
           nhalf += __popc(mh);
@@ -229,29 +227,32 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
   }
 }
 
-// Non-owned entries of row i: find i in the owner's half row.
-__global__ void k_pid_fix(int n, const int* __restrict__ full_start, const int* __restrict__ full_j,
-                          int* __restrict__ full_ref, const int* __restrict__ half_start,
-                          const int* __restrict__ half_j, int* __restrict__ flags) {
+// The rest of row j lists the pairs owned by other rows: every pair id is
+// scattered to its non-owner's row (atomic slot), then each row sorts that part
+// by pair id, so the final order does not depend on the atomics.
+__global__ void k_transpose_scatter(long long nh, const int* __restrict__ half_j,
+                                    const int* __restrict__ full_start, const int* __restrict__ half_cnt,
+                                    int* __restrict__ tcount, int* __restrict__ tmp) {
+  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pid >= nh) return;
+  const int j = half_j[pid];
+  const int slot = full_start[j] + half_cnt[j] + atomicAdd(&tcount[j], 1);
+  tmp[slot] = (int)pid;
+}
+
+__global__ void k_transpose_sort(int n, const int* __restrict__ full_start, const int* __restrict__ half_cnt,
+                                 const int* __restrict__ tmp, const int* __restrict__ half_i,
+                                 int* __restrict__ full_j, int* __restrict__ full_ref) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
-  for (int k = full_start[i] + lane; k < full_start[i + 1]; k += 32) {
-    if (full_ref[k] >= 0) continue;
-    int j = full_j[k];
-    int pid = -1;
-    for (int m = half_start[j]; m < half_start[j + 1]; ++m) {
-      if (half_j[m] == i) {
-        pid = m;
-        break;
-      }
-    }
-    if (pid < 0) {
-      atomicOr(&flags[0], 1);
-      full_ref[k] = 0;
-    } else {
-      full_ref[k] = (pid << 1) | 1;
-    }
+  const int lo = full_start[i] + half_cnt[i], hi = full_start[i + 1];
+  for (int e = lo + lane; e < hi; e += 32) {
+    const int p = tmp[e];
+    int rank = 0;
+    for (int m = lo; m < hi; ++m) rank += tmp[m] < p;
+    full_ref[lo + rank] = (p << 1) | 1;
+    full_j[lo + rank] = half_i[p];
   }
 }
 
@@ -283,7 +284,7 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
       (r = cuda_check(c, cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * ncell, st), "memset")) ||
       (r = cuda_check(c, cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, st), "memset")))
     return r;
-  c->n_launch += 10;  // cell_assign .. pid_fix below
+  c->n_launch += 11;  // cell_assign .. transpose_sort below
   k_cell_assign<<<amp_blocks(n, 256), 256, 0, st>>>(n, xyz, L, nc, c->cell_of, c->cell_count);
   k_scan_exclusive<<<1, 1024, 0, st>>>(c->cell_count, c->cell_start, ncell);
   k_cell_scatter<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->cell_of, c->cell_start, c->cell_fill, c->slot_tmp);
@@ -317,7 +318,7 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   if (c->n_full != 2 * c->n_half) return fail(c, AMP_ERR_GEOMETRY, "inconsistent neighbour counts");
   if (c->n_full > (1LL << 30)) return fail(c, AMP_ERR_GEOMETRY, "too many pairs");
   if (c->n_full > c->cap_full || c->n_half > c->cap_half) {
-    void** bufs[] = {(void**)&c->full_j, (void**)&c->full_ref, (void**)&c->half_i, (void**)&c->half_j,
+    void** bufs[] = {(void**)&c->full_j, (void**)&c->full_ref, (void**)&c->tr_tmp, (void**)&c->half_i, (void**)&c->half_j,
                      (void**)&c->T64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32};
     for (void** b : bufs) {
       dev_free(c, *b);
@@ -326,6 +327,7 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
     const long long caph = c->n_half + c->n_half / 4 + 1024, capf = 2 * caph;
     c->cap_half = c->cap_full = 0;
     if ((r = dev_alloc(c, &c->full_j, capf)) || (r = dev_alloc(c, &c->full_ref, capf)) ||
+        (r = dev_alloc(c, &c->tr_tmp, capf)) ||
         (r = dev_alloc(c, &c->half_i, caph)) || (r = dev_alloc(c, &c->half_j, caph)) ||
         (r = dev_alloc(c, &c->Ep64, 6 * caph)))
       return r;
@@ -339,7 +341,10 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   }
   k_neighbours<true><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, nullptr, nullptr, c->full_start,
                                          c->half_start, c->full_j, c->full_ref, c->half_i, c->half_j);
-  k_pid_fix<<<lb, 256, 0, st>>>(n, c->full_start, c->full_j, c->full_ref, c->half_start, c->half_j, c->flags);
+  cudaMemsetAsync(c->full_cnt, 0, sizeof(int) * n, st);  // reused as the per-row slot counter
+  k_transpose_scatter<<<amp_blocks(c->n_half, 256), 256, 0, st>>>(c->n_half, c->half_j, c->full_start, c->half_cnt,
+                                                                  c->full_cnt, c->tr_tmp);
+  k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref);
   cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
   if ((r = cuda_check(c, cudaStreamSynchronize(st), "list fill"))) return r;
   if (c->hibuf[2] & 1) return fail(c, AMP_ERR_GEOMETRY, "neighbour list transpose failed");

@@ -210,9 +210,16 @@ __global__ void __launch_bounds__(256) k_t_real64(int n, const int* __restrict__
     const double2* t = reinterpret_cast<const double2*>(T + 6 * (long long)(full_ref[k] >> 1));
     const double2 t0 = t[0], t1 = t[1], t2 = t[2];  // (xx,yy) (zz,xy) (xz,yz)
     const double4_32a vj = v[j];
-    sx += t0.x * vj.x + t1.y * vj.y + t2.x * vj.z;
-    sy += t1.y * vj.x + t0.y * vj.y + t2.y * vj.z;
-    sz += t2.x * vj.x + t2.y * vj.y + t1.x * vj.z;
+    // three FMAs per component (the float64 pipe is the bound)
+    sx = fma(t0.x, vj.x, sx);
+    sx = fma(t1.y, vj.y, sx);
+    sx = fma(t2.x, vj.z, sx);
+    sy = fma(t1.y, vj.x, sy);
+    sy = fma(t0.y, vj.y, sy);
+    sy = fma(t2.y, vj.z, sy);
+    sz = fma(t2.x, vj.x, sz);
+    sz = fma(t2.y, vj.y, sz);
+    sz = fma(t1.x, vj.z, sz);
   }
   sx = group_sum(sx);
   sy = group_sum(sy);
@@ -240,9 +247,15 @@ __global__ void __launch_bounds__(256) k_t_real32(int n, const int* __restrict__
     const float2* t = reinterpret_cast<const float2*>(T + 6 * (long long)(full_ref[k] >> 1));
     const float2 t0 = t[0], t1 = t[1], t2 = t[2];
     const float4 vj = v32[j];
-    sx += t0.x * vj.x + t1.y * vj.y + t2.x * vj.z;
-    sy += t1.y * vj.x + t0.y * vj.y + t2.y * vj.z;
-    sz += t2.x * vj.x + t2.y * vj.y + t1.x * vj.z;
+    sx = fmaf(t0.x, vj.x, sx);
+    sx = fmaf(t1.y, vj.y, sx);
+    sx = fmaf(t2.x, vj.z, sx);
+    sy = fmaf(t1.y, vj.x, sy);
+    sy = fmaf(t0.y, vj.y, sy);
+    sy = fmaf(t2.y, vj.z, sy);
+    sz = fmaf(t2.x, vj.x, sz);
+    sz = fmaf(t2.y, vj.y, sz);
+    sz = fmaf(t1.x, vj.z, sz);
   }
   double dx = group_sum((double)sx);
   double dy = group_sum((double)sy);

@@ -98,6 +98,15 @@ __device__ __forceinline__ void load_wts(const R* __restrict__ th, int nd, Wts<R
 
 __device__ __forceinline__ int wrapk(int g, int K) { return g < 0 ? g + K : g; }
 
+// Spreading and gathering run one atom per group of kPmeGroup lanes, lane t
+// (t < 5) owning the grid plane k0x - t: five times the parallelism of one
+// thread per atom, which the float64 pipe needs to stay busy.
+constexpr int kPmeGroup = 8;
+
+__device__ __forceinline__ unsigned pme_group_mask() {
+  return ((1u << kPmeGroup) - 1u) << ((threadIdx.x & 31) & ~(kPmeGroup - 1));
+}
+
 template <typename R>
 __global__ void __launch_bounds__(128) k_spread_multipoles(int n, const R* __restrict__ theta,
                                                            const int4* __restrict__ gbase,
@@ -106,30 +115,35 @@ __global__ void __launch_bounds__(128) k_spread_multipoles(int n, const R* __res
                                                            const double4_32a* __restrict__ C,
                                                            const double4_32a* __restrict__ D, int K,
                                                            R* __restrict__ grid) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  Wts<R> w;
-  load_wts<R>(theta + (long long)kTh * s, 3, w);
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
+  if (s >= n || tx >= kOrder) return;
+  const R* th = theta + (long long)kTh * s;
+  R wx[3], wy[3][kOrder], wz[3][kOrder];
+  for (int d = 0; d < 3; ++d) {
+    wx[d] = th[(0 * 4 + d) * kOrder + tx];
+    for (int t = 0; t < kOrder; ++t) {
+      wy[d][t] = th[(1 * 4 + d) * kOrder + t];
+      wz[d][t] = th[(2 * 4 + d) * kOrder + t];
+    }
+  }
   const int4 b = gbase[s];
   const double4_32a a = A[s], bb = B[s], c = C[s], d = D[s];
   const R q = (R)a.w, dx = (R)bb.x, dy = (R)bb.y, dz = (R)bb.z;
   const R qxx = (R)c.x, qyy = (R)c.y, qzz = (R)c.z, qxy = (R)c.w, qxz = (R)d.x, qyz = (R)d.y;
   const R third = (R)(1.0 / 3.0), two3 = (R)(2.0 / 3.0);
-  for (int tx = 0; tx < kOrder; ++tx) {
-    const int gx = wrapk(b.x - tx, K);
-    for (int ty = 0; ty < kOrder; ++ty) {
-      const int gy = wrapk(b.y - ty, K);
-      const R x0y0 = w.x[0][tx] * w.y[0][ty], x1y0 = w.x[1][tx] * w.y[0][ty], x0y1 = w.x[0][tx] * w.y[1][ty];
-      const R a0 = q * x0y0 + dx * x1y0 + dy * x0y1 +
-                   third * (qxx * w.x[2][tx] * w.y[0][ty] + qyy * w.x[0][tx] * w.y[2][ty] +
-                            (R)2 * qxy * w.x[1][tx] * w.y[1][ty]);
-      const R a1 = dz * x0y0 + two3 * (qxz * x1y0 + qyz * x0y1);
-      const R a2 = third * qzz * x0y0;
-      R* row = grid + ((long long)gx * K + gy) * K;
-      for (int tz = 0; tz < kOrder; ++tz) {
-        const int gz = wrapk(b.z - tz, K);
-        atomicAdd(row + gz, a0 * w.z[0][tz] + a1 * w.z[1][tz] + a2 * w.z[2][tz]);
-      }
+  const int gx = wrapk(b.x - tx, K);
+  for (int ty = 0; ty < kOrder; ++ty) {
+    const int gy = wrapk(b.y - ty, K);
+    const R x0y0 = wx[0] * wy[0][ty], x1y0 = wx[1] * wy[0][ty], x0y1 = wx[0] * wy[1][ty];
+    const R a0 = q * x0y0 + dx * x1y0 + dy * x0y1 +
+                 third * (qxx * wx[2] * wy[0][ty] + qyy * wx[0] * wy[2][ty] + (R)2 * qxy * wx[1] * wy[1][ty]);
+    const R a1 = dz * x0y0 + two3 * (qxz * x1y0 + qyz * x0y1);
+    const R a2 = third * qzz * x0y0;
+    R* row = grid + ((long long)gx * K + gy) * K;
+    for (int tz = 0; tz < kOrder; ++tz) {
+      const int gz = wrapk(b.z - tz, K);
+      atomicAdd(row + gz, a0 * wz[0][tz] + a1 * wz[1][tz] + a2 * wz[2][tz]);
     }
   }
 }
@@ -138,24 +152,31 @@ template <typename R, typename V>
 __global__ void __launch_bounds__(128) k_spread_dipoles(int n, const R* __restrict__ theta,
                                                         const int4* __restrict__ gbase, const V* __restrict__ v,
                                                         int K, R* __restrict__ grid) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  Wts<R> w;
-  load_wts<R>(theta + (long long)kTh * s, 2, w);
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
+  if (s >= n || tx >= kOrder) return;
+  const R* th = theta + (long long)kTh * s;
+  const R wx0 = th[(0 * 4 + 0) * kOrder + tx], wx1 = th[(0 * 4 + 1) * kOrder + tx];
+  R wy0[kOrder], wy1[kOrder], wz0[kOrder], wz1[kOrder];
+  for (int t = 0; t < kOrder; ++t) {
+    wy0[t] = th[(1 * 4 + 0) * kOrder + t];
+    wy1[t] = th[(1 * 4 + 1) * kOrder + t];
+    wz0[t] = th[(2 * 4 + 0) * kOrder + t];
+    wz1[t] = th[(2 * 4 + 1) * kOrder + t];
+  }
   const int4 b = gbase[s];
   const V m = v[s];
   const R mx = (R)m.x, my = (R)m.y, mz = (R)m.z;
-  for (int tx = 0; tx < kOrder; ++tx) {
-    const int gx = wrapk(b.x - tx, K);
-    for (int ty = 0; ty < kOrder; ++ty) {
-      const int gy = wrapk(b.y - ty, K);
-      const R a0 = mx * w.x[1][tx] * w.y[0][ty] + my * w.x[0][tx] * w.y[1][ty];
-      const R a1 = mz * w.x[0][tx] * w.y[0][ty];
-      R* row = grid + ((long long)gx * K + gy) * K;
-      for (int tz = 0; tz < kOrder; ++tz) {
-        const int gz = wrapk(b.z - tz, K);
-        atomicAdd(row + gz, a0 * w.z[0][tz] + a1 * w.z[1][tz]);
-      }
+  const R cx0 = mx * wx1, cx1 = my * wx0, cz = mz * wx0;
+  const int gx = wrapk(b.x - tx, K);
+  for (int ty = 0; ty < kOrder; ++ty) {
+    const int gy = wrapk(b.y - ty, K);
+    const R a0 = cx0 * wy0[ty] + cx1 * wy1[ty];
+    const R a1 = cz * wy0[ty];
+    R* row = grid + ((long long)gx * K + gy) * K;
+    for (int tz = 0; tz < kOrder; ++tz) {
+      const int gz = wrapk(b.z - tz, K);
+      atomicAdd(row + gz, a0 * wz0[tz] + a1 * wz1[tz]);
     }
   }
 }
@@ -171,38 +192,59 @@ __global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict_
   cg[k] = v;
 }
 
-// out_i += -sum_g grad W_i(g) phi(g)
+// out_i += -sum_g grad W_i(g) phi(g); lane t of the atom's group sums plane
+// k0x - t, the group adds the five planes.
 template <typename R>
 __global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict__ theta,
                                                       const int4* __restrict__ gbase, const R* __restrict__ phi,
                                                       int K, double4_32a* __restrict__ out) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  Wts<R> w;
-  load_wts<R>(theta + (long long)kTh * s, 2, w);
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
+  if (s >= n) return;  // whole groups leave together
+  double ex = 0.0, ey = 0.0, ez = 0.0;
   const int4 b = gbase[s];
-  R ex = 0, ey = 0, ez = 0;
-  for (int tx = 0; tx < kOrder; ++tx) {
+  if (tx < kOrder) {
+    const R* th = theta + (long long)kTh * s;
+    const R wx0 = th[(0 * 4 + 0) * kOrder + tx], wx1 = th[(0 * 4 + 1) * kOrder + tx];
+    R wz0[kOrder], wz1[kOrder];
+    for (int t = 0; t < kOrder; ++t) {
+      wz0[t] = th[(2 * 4 + 0) * kOrder + t];
+      wz1[t] = th[(2 * 4 + 1) * kOrder + t];
+    }
     const int gx = wrapk(b.x - tx, K);
+    R px = 0, py = 0, pz = 0;
     for (int ty = 0; ty < kOrder; ++ty) {
+      const R wy0 = th[(1 * 4 + 0) * kOrder + ty], wy1 = th[(1 * 4 + 1) * kOrder + ty];
       const int gy = wrapk(b.y - ty, K);
       const R* row = phi + ((long long)gx * K + gy) * K;
       R s0 = 0, s1 = 0;
       for (int tz = 0; tz < kOrder; ++tz) {
         const R p = row[wrapk(b.z - tz, K)];
-        s0 += w.z[0][tz] * p;
-        s1 += w.z[1][tz] * p;
+        s0 += wz0[tz] * p;
+        s1 += wz1[tz] * p;
       }
-      ex += w.x[1][tx] * w.y[0][ty] * s0;
-      ey += w.x[0][tx] * w.y[1][ty] * s0;
-      ez += w.x[0][tx] * w.y[0][ty] * s1;
+      px += wy0 * s0;
+      py += wy1 * s0;
+      pz += wy0 * s1;
     }
+    ex = (double)(wx1 * px);
+    ey = (double)(wx0 * py);
+    ez = (double)(wx0 * pz);
   }
-  double4_32a o = out[s];
-  o.x -= (double)ex;
-  o.y -= (double)ey;
-  o.z -= (double)ez;
-  out[s] = o;
+  const unsigned mask = pme_group_mask();
+#pragma unroll
+  for (int o = kPmeGroup / 2; o > 0; o >>= 1) {
+    ex += __shfl_xor_sync(mask, ex, o, kPmeGroup);
+    ey += __shfl_xor_sync(mask, ey, o, kPmeGroup);
+    ez += __shfl_xor_sync(mask, ez, o, kPmeGroup);
+  }
+  if (tx == 0) {
+    double4_32a o = out[s];
+    o.x -= ex;
+    o.y -= ey;
+    o.z -= ez;
+    out[s] = o;
+  }
 }
 
 // Host: B-spline moduli and influence function, float64.
@@ -324,21 +366,61 @@ int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
   int r;
   if (c->cfg.precision == AMP_FP64) {
     cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
-    k_spread_multipoles<double><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB,
+    k_spread_multipoles<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB,
                                                                     c->atomC, c->atomD, K, c->grid64);
     if ((r = exec_fft(c, false, true))) return r;
     k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
     if ((r = exec_fft(c, false, false))) return r;
-    k_gather_field<double><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
+    k_gather_field<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
   } else {
     cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
-    k_spread_multipoles<float><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB,
+    k_spread_multipoles<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB,
                                                                    c->atomC, c->atomD, K, c->grid32);
     if ((r = exec_fft(c, true, true))) return r;
     k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
     if ((r = exec_fft(c, true, false))) return r;
-    k_gather_field<float><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
+    k_gather_field<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
   }
+  return AMP_OK;
+}
+
+// Grid potential phi = conv(Q) into grid_out (float64 or float32 grid), Q the
+// spread of the dipoles v (v32 in float32) or of the permanent multipoles.
+int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out) {
+  const int K = c->K, n = c->n;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  cudaStream_t st = c->stream;
+  const int blocks = amp_blocks((long long)n * kPmeGroup, 128);
+  c->n_launch += 2;
+  cufftResult fr;
+  if (!fp32) {
+    double* g = static_cast<double*>(grid_out);
+    cudaMemsetAsync(g, 0, sizeof(double) * ng, st);
+    if (multipoles)
+      k_spread_multipoles<double><<<blocks, 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB, c->atomC,
+                                                          c->atomD, K, g);
+    else
+      k_spread_dipoles<double, double4_32a><<<blocks, 128, 0, st>>>(n, c->theta, c->gbase, v, K, g);
+    fr = cufftExecD2Z(c->plan_d2z, g, reinterpret_cast<cufftDoubleComplex*>(c->cgrid64));
+    if (fr == CUFFT_SUCCESS) {
+      k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
+      fr = cufftExecZ2D(c->plan_z2d, reinterpret_cast<cufftDoubleComplex*>(c->cgrid64), g);
+    }
+  } else {
+    float* g = static_cast<float*>(grid_out);
+    cudaMemsetAsync(g, 0, sizeof(float) * ng, st);
+    if (multipoles)
+      k_spread_multipoles<float><<<blocks, 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB, c->atomC,
+                                                         c->atomD, K, g);
+    else
+      k_spread_dipoles<float, float4><<<blocks, 128, 0, st>>>(n, c->theta32, c->gbase, v32, K, g);
+    fr = cufftExecR2C(c->plan_r2c, g, reinterpret_cast<cufftComplex*>(c->cgrid32));
+    if (fr == CUFFT_SUCCESS) {
+      k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
+      fr = cufftExecC2R(c->plan_c2r, reinterpret_cast<cufftComplex*>(c->cgrid32), g);
+    }
+  }
+  if (fr != CUFFT_SUCCESS) return fail(c, AMP_ERR_CUDA, "cuFFT exec failed (%d)", (int)fr);
   return AMP_OK;
 }
 
@@ -349,11 +431,11 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out_add) {
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
   int r;
   cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
-  k_spread_dipoles<double, double4_32a><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, v, K, c->grid64);
+  k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, v, K, c->grid64);
   if ((r = exec_fft(c, false, true))) return r;
   k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
   if ((r = exec_fft(c, false, false))) return r;
-  k_gather_field<double><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
+  k_gather_field<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
   return AMP_OK;
 }
 
@@ -364,11 +446,11 @@ int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out_add) {
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
   int r;
   cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
-  k_spread_dipoles<float, float4><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, v, K, c->grid32);
+  k_spread_dipoles<float, float4><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, v, K, c->grid32);
   if ((r = exec_fft(c, true, true))) return r;
   k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
   if ((r = exec_fft(c, true, false))) return r;
-  k_gather_field<float><<<amp_blocks(n, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
+  k_gather_field<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
   return AMP_OK;
 }
 
