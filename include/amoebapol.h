@@ -59,7 +59,9 @@ extern "C" {
 typedef struct amp_ctx amp_ctx;
 
 typedef struct {
-  double box;        /* cubic box edge (Angstrom); must be > 2 * cutoff */
+  double box;        /* cubic box edge (Angstrom); must be > 2 * cutoff.
+                        0 = isolated cluster: every pair, no cutoff, no Ewald
+                        (cutoff, ewald_beta, pme_grid, pme_order ignored) */
   double cutoff;     /* real-space cutoff (Angstrom) */
   double ewald_beta; /* Ewald splitting parameter (1/Angstrom), > 0 */
   int pme_grid;      /* PME points per axis, >= 8 */
@@ -73,6 +75,13 @@ typedef struct {
  * NULL = legacy default stream). Validates cfg. Returns AMP_ERR_ARG on a bad
  * configuration (then *out is NULL). */
 int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream);
+
+/* Change box, cutoff, beta, tolerance and iteration cap of a context while
+ * keeping its buffers and cuFFT plans: the PME grid size, B-spline order,
+ * precision and cluster/periodic mode must stay those given to amp_create
+ * (else AMP_ERR_ARG). Recomputes the influence function when box or beta
+ * change (synchronises the stream); the next call must be amp_set_system. */
+int amp_reconfigure(amp_ctx* ctx, const amp_config* cfg);
 
 /* Free every device buffer and plan of the context. NULL is ignored. */
 void amp_destroy(amp_ctx* ctx);

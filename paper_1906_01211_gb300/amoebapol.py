@@ -61,6 +61,7 @@ def _load() -> ctypes.CDLL:
     sig = {
         "amp_create": (I, [ctypes.POINTER(P), ctypes.POINTER(amp_config), P]),
         "amp_destroy": (None, [P]),
+        "amp_reconfigure": (I, [P, ctypes.POINTER(amp_config)]),
         "amp_last_error": (ctypes.c_char_p, [P]),
         "amp_set_system": (I, [P, I, P, P, P, P, P, P, P]),
         "amp_permanent_field": (I, [P, P]),
@@ -109,6 +110,10 @@ def amp_create(cfg: amp_config, stream: int | None = None):
 
 def amp_destroy(ctx):
     _lib.amp_destroy(ctx)
+
+
+def amp_reconfigure(ctx, cfg: amp_config):
+    _check(ctx, _lib.amp_reconfigure(ctx, ctypes.byref(cfg)))
 
 
 def amp_last_error(ctx) -> str:
@@ -304,6 +309,12 @@ class Polarization:
 
     def pair_count(self) -> int:
         return amp_pair_count(self.ctx)
+
+    def reconfigure(self, cfg: Config):
+        """New box/cutoff/beta/tolerance with the same grid, precision and mode."""
+        amp_reconfigure(self.ctx, cfg.to_c())
+        self.cfg = cfg
+        self.n = 0
 
     def profile(self, enable: bool):
         amp_profile(self.ctx, enable)

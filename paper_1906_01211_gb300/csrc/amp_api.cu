@@ -104,13 +104,16 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
   if (!out) return AMP_ERR_ARG;
   *out = nullptr;
   if (!cfg) return AMP_ERR_ARG;
-  if (!(cfg->box > 0.0) || !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) || !(cfg->ewald_beta > 0.0) ||
-      cfg->pme_grid < 8 || cfg->pme_grid > 512 || cfg->pme_order != kOrder || !(cfg->tol_debye > 0.0) ||
-      cfg->max_iter < 1 || (cfg->precision != AMP_FP64 && cfg->precision != AMP_MIXED))
+  const bool cluster = cfg->box == 0.0;
+  if (!(cfg->tol_debye > 0.0) || cfg->max_iter < 1 || (cfg->precision != AMP_FP64 && cfg->precision != AMP_MIXED))
+    return AMP_ERR_ARG;
+  if (!cluster && (!(cfg->box > 0.0) || !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) ||
+                   !(cfg->ewald_beta > 0.0) || cfg->pme_grid < 8 || cfg->pme_grid > 512 || cfg->pme_order != kOrder))
     return AMP_ERR_ARG;
   amp_ctx* c = new (std::nothrow) amp_ctx();
   if (!c) return AMP_ERR_OOM;
   c->cfg = *cfg;
+  c->cluster = cluster;
   c->stream = (cudaStream_t)cuda_stream;
   int r;
   if ((r = dev_alloc(c, &c->flags, 4)) || (r = dev_alloc(c, &c->iflags, 4)) || (r = dev_alloc(c, &c->scal, 8)) ||
@@ -123,11 +126,27 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return AMP_ERR_OOM;
   }
-  if ((r = pme_setup(c))) {
+  if (!cluster && (r = pme_setup(c))) {
     amp_destroy(c);
     return r;
   }
   *out = c;
+  return AMP_OK;
+}
+
+int amp_reconfigure(amp_ctx* c, const amp_config* cfg) {
+  if (!c || !cfg) return AMP_ERR_ARG;
+  const bool cluster = cfg->box == 0.0;
+  if (cluster != c->cluster || cfg->precision != c->cfg.precision)
+    return fail(c, AMP_ERR_ARG, "amp_reconfigure: precision and cluster/periodic mode are fixed at creation");
+  if (!(cfg->tol_debye > 0.0) || cfg->max_iter < 1) return fail(c, AMP_ERR_ARG, "amp_reconfigure: bad tolerance");
+  if (!cluster && (cfg->pme_grid != c->cfg.pme_grid || cfg->pme_order != kOrder || !(cfg->box > 0.0) ||
+                   !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) || !(cfg->ewald_beta > 0.0)))
+    return fail(c, AMP_ERR_ARG, "amp_reconfigure: same PME grid required, cutoff < box/2, beta > 0");
+  const bool box_changed = cfg->box != c->cfg.box || cfg->ewald_beta != c->cfg.ewald_beta;
+  c->cfg = *cfg;
+  c->have_system = false;
+  if (!cluster && box_changed) return pme_influence(c);
   return AMP_OK;
 }
 
@@ -157,6 +176,11 @@ int amp_set_system(amp_ctx* c, int n, const double* xyz, const double* q, const 
   int r;
   if ((r = alloc_atoms(c, n))) return r;
   c->n = n;
+  if (c->cluster) {
+    if ((r = cluster_setup(c, xyz, q, dip, quad, alpha, thole, mol))) return r;
+    c->have_system = true;
+    return AMP_OK;
+  }
   {
     PhaseScope ps(c, AMP_PHASE_LIST);
     if ((r = build_cells_and_lists(c, xyz, q, dip, quad, alpha, thole, mol))) return r;
@@ -178,16 +202,21 @@ int amp_permanent_field(amp_ctx* c, double* E0) {
   if (!c) return AMP_ERR_ARG;
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!E0) return fail(c, AMP_ERR_ARG, "E0 is null");
-  {
+  if (c->cluster) {
     PhaseScope ps(c, AMP_PHASE_E0_REAL);
-    launch_e0_real(c, c->E0s);
+    cluster_permanent_field(c, c->E0s);
+  } else {
+    {
+      PhaseScope ps(c, AMP_PHASE_E0_REAL);
+      launch_e0_real(c, c->E0s);
+    }
+    int r;
+    {
+      PhaseScope ps(c, AMP_PHASE_E0_RECIP);
+      r = pme_permanent_field(c, c->E0s);
+    }
+    if (r) return r;
   }
-  int r;
-  {
-    PhaseScope ps(c, AMP_PHASE_E0_RECIP);
-    r = pme_permanent_field(c, c->E0s);
-  }
-  if (r) return r;
   launch_from_sorted(c, c->E0s, E0);
   return cuda_check(c, cudaGetLastError(), "permanent_field launch");
 }
@@ -223,6 +252,7 @@ int amp_forces(amp_ctx* c, const double* mu, double* F, double* gq, double* gdip
   if (!c) return AMP_ERR_ARG;
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!mu || !F) return fail(c, AMP_ERR_ARG, "mu and F are required");
+  if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_forces: not available for isolated clusters");
   launch_to_sorted(c, mu, c->tmp);
   return forces(c, c->tmp, F, gq, gdip, gquad);
 }

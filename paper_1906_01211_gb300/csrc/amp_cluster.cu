@@ -1,0 +1,223 @@
+// Isolated clusters (no periodic box): every pair interacts, no cutoff, no
+// Ewald screening (beta = 0), no reciprocal or self terms. The kernels are
+// then B1 = 1/r^3, B2 = 3/r^5, B3 = 15/r^7 with Thole damping, and the
+// permanent field skips pairs inside one molecule (their damped kernel
+// B_n - bare_n vanishes when beta = 0).
+//
+// All-pairs tiles: a block owns kTileI rows and one slice of the columns
+// (blockIdx.y); the column slice is staged through shared memory tile by
+// tile. Each thread sums a tile in the working precision R and adds the tile
+// sum to float64 accumulators. Slices are summed by a second kernel in a
+// fixed order (no atomics), so results do not depend on scheduling.
+#include "amp_internal.cuh"
+
+namespace amp {
+namespace {
+
+constexpr int kTileI = 64;  // rows per block (threads)
+constexpr int kTileJ = 64;  // columns staged per shared-memory tile
+
+template <typename R>
+struct JTile {
+  R x[kTileJ], y[kTileJ], z[kTileJ], isa[kTileJ], th[kTileJ];
+  int mol[kTileJ];
+  R v[kTileJ][3];      // dipoles (T*v) or permanent dipoles
+  R q[kTileJ];
+  R quad[kTileJ][6];
+};
+
+template <typename R, bool kPerm, typename V>
+__global__ void __launch_bounds__(kTileI) k_cluster_field(int n, int cols_per_slice, const double4_32a* __restrict__ A,
+                                                          const double4_32a* __restrict__ B,
+                                                          const double4_32a* __restrict__ C,
+                                                          const double4_32a* __restrict__ D, const V* __restrict__ v,
+                                                          double4_32a* __restrict__ part) {
+  __shared__ JTile<R> t;
+  const int i = blockIdx.x * kTileI + threadIdx.x;
+  const int j0 = blockIdx.y * cols_per_slice;
+  const int j1 = min(n, j0 + cols_per_slice);
+  R xi = 0, yi = 0, zi = 0, isai = 0, thi = 0;
+  int moli = -1;
+  if (i < n) {
+    const double4_32a a = A[i], b = B[i], d = D[i];
+    xi = (R)a.x;
+    yi = (R)a.y;
+    zi = (R)a.z;
+    isai = (R)b.w;
+    thi = (R)d.z;
+    moli = (int)d.w;
+  }
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int jt = j0; jt < j1; jt += kTileJ) {
+    const int jl = jt + threadIdx.x;
+    if (threadIdx.x < kTileJ && jl < j1) {
+      const double4_32a a = A[jl], b = B[jl], d = D[jl];
+      t.x[threadIdx.x] = (R)a.x;
+      t.y[threadIdx.x] = (R)a.y;
+      t.z[threadIdx.x] = (R)a.z;
+      t.isa[threadIdx.x] = (R)b.w;
+      t.th[threadIdx.x] = (R)d.z;
+      t.mol[threadIdx.x] = (int)d.w;
+      if (kPerm) {
+        const double4_32a c = C[jl];
+        t.q[threadIdx.x] = (R)a.w;
+        t.v[threadIdx.x][0] = (R)b.x;
+        t.v[threadIdx.x][1] = (R)b.y;
+        t.v[threadIdx.x][2] = (R)b.z;
+        t.quad[threadIdx.x][0] = (R)c.x;
+        t.quad[threadIdx.x][1] = (R)c.y;
+        t.quad[threadIdx.x][2] = (R)c.z;
+        t.quad[threadIdx.x][3] = (R)c.w;
+        t.quad[threadIdx.x][4] = (R)d.x;
+        t.quad[threadIdx.x][5] = (R)d.y;
+      } else {
+        const V m = v[jl];
+        t.v[threadIdx.x][0] = (R)m.x;
+        t.v[threadIdx.x][1] = (R)m.y;
+        t.v[threadIdx.x][2] = (R)m.z;
+      }
+    }
+    __syncthreads();
+    const int cnt = min(kTileJ, j1 - jt);
+    R sx = 0, sy = 0, sz = 0;
+    if (i < n) {
+      for (int k = 0; k < cnt; ++k) {
+        const int j = jt + k;
+        if (j == i) continue;
+        if (kPerm && t.mol[k] == moli) continue;  // excluded: damped kernel vanishes
+        const R rx = xi - t.x[k], ry = yi - t.y[k], rz = zi - t.z[k];
+        const R r2 = rx * rx + ry * ry + rz * rz;
+        const R ir = (R)1 / sqrt(r2);
+        const R ir2 = ir * ir;
+        const R x = min(thi, t.th[k]) * r2 * sqrt(r2) * isai * t.isa[k];
+        const R e = exp(-x);
+        const R b1 = ((R)1 - e) * ir * ir2;
+        const R b2 = (R)3 * ((R)1 - ((R)1 + x) * e) * ir2 * ir2 * ir;
+        if (kPerm) {
+          const R b3 = (R)15 * ((R)1 - ((R)1 + x + (R)0.6 * x * x) * e) * ir2 * ir2 * ir2 * ir;
+          const R* Q = t.quad[k];
+          const R tx = Q[0] * rx + Q[3] * ry + Q[4] * rz;
+          const R ty = Q[3] * rx + Q[1] * ry + Q[5] * rz;
+          const R tz = Q[4] * rx + Q[5] * ry + Q[2] * rz;
+          const R rtr = rx * tx + ry * ty + rz * tz;
+          const R dr = t.v[k][0] * rx + t.v[k][1] * ry + t.v[k][2] * rz;
+          const R rad = t.q[k] * b1 + b2 * dr + b3 * rtr * (R)(1.0 / 3.0);
+          const R c2 = b2 * (R)(2.0 / 3.0);
+          sx += rad * rx - b1 * t.v[k][0] - c2 * tx;
+          sy += rad * ry - b1 * t.v[k][1] - c2 * ty;
+          sz += rad * rz - b1 * t.v[k][2] - c2 * tz;
+        } else {
+          const R s = b2 * (t.v[k][0] * rx + t.v[k][1] * ry + t.v[k][2] * rz);
+          sx += s * rx - b1 * t.v[k][0];
+          sy += s * ry - b1 * t.v[k][1];
+          sz += s * rz - b1 * t.v[k][2];
+        }
+      }
+    }
+    ax += (double)sx;
+    ay += (double)sy;
+    az += (double)sz;
+    __syncthreads();
+  }
+  if (i < n) part[(long long)blockIdx.y * n + i] = make_double4_32a(ax, ay, az, 0.0);
+}
+
+__global__ void k_cluster_reduce(int n, int slices, const double4_32a* __restrict__ part, double4_32a* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = 0, y = 0, z = 0;
+  for (int s = 0; s < slices; ++s) {
+    const double4_32a p = part[(long long)s * n + i];
+    x += p.x;
+    y += p.y;
+    z += p.z;
+  }
+  out[i] = make_double4_32a(x, y, z, 0.0);
+}
+
+__global__ void k_identity_perm(int n, int* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) perm[i] = i;
+}
+
+__global__ void k_cluster_atoms(int n, const double* __restrict__ xyz, const double* __restrict__ q,
+                                const double* __restrict__ dip, const double* __restrict__ quad,
+                                const double* __restrict__ alpha, const double* __restrict__ thole,
+                                const int* __restrict__ mol, double4_32a* __restrict__ A, double4_32a* __restrict__ B,
+                                double4_32a* __restrict__ C, double4_32a* __restrict__ D, double2* __restrict__ alph,
+                                int* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double al = alpha[i];
+  if (!(al > 0.0)) atomicOr(&flags[0], 2);
+  alph[i] = make_double2(al, 1.0 / al);
+  A[i] = make_double4_32a(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], q[i]);
+  B[i] = make_double4_32a(dip[3 * i], dip[3 * i + 1], dip[3 * i + 2], 1.0 / sqrt(al));
+  C[i] = make_double4_32a(quad[6 * i], quad[6 * i + 1], quad[6 * i + 2], quad[6 * i + 3]);
+  D[i] = make_double4_32a(quad[6 * i + 4], quad[6 * i + 5], thole[i], (double)mol[i]);
+}
+
+// Column slices so that the grid covers about 2 blocks per SM.
+int slices_for(int n) {
+  const int rows = (n + kTileI - 1) / kTileI;
+  int s = (2 * 152 + rows - 1) / rows;
+  const int max_s = (n + kTileJ - 1) / kTileJ;
+  if (s > max_s) s = max_s;
+  if (s > kClusterMaxSlices) s = kClusterMaxSlices;
+  return s < 1 ? 1 : s;
+}
+
+template <bool kPerm, typename R, typename V>
+void launch_field(amp_ctx* c, const V* v, double4_32a* out) {
+  const int n = c->n;
+  const int s = slices_for(n);
+  int cols = (n + s - 1) / s;
+  cols = (cols + kTileJ - 1) / kTileJ * kTileJ;
+  dim3 grid((n + kTileI - 1) / kTileI, s);
+  c->n_launch += 2;
+  k_cluster_field<R, kPerm, V><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD, v,
+                                                                c->cluster_part);
+  k_cluster_reduce<<<amp_blocks(n, 256), 256, 0, c->stream>>>(n, s, c->cluster_part, out);
+}
+
+}  // namespace
+
+int cluster_setup(amp_ctx* c, const double* xyz, const double* q, const double* dip, const double* quad,
+                  const double* alpha, const double* thole, const int* mol) {
+  const int n = c->n;
+  cudaStream_t st = c->stream;
+  int r;
+  if (c->cluster_part_cap < (long long)kClusterMaxSlices * n) {
+    dev_free(c, c->cluster_part);
+    c->cluster_part = nullptr;
+    if ((r = dev_alloc(c, &c->cluster_part, (long long)kClusterMaxSlices * n))) return r;
+    c->cluster_part_cap = (long long)kClusterMaxSlices * n;
+  }
+  cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, st);
+  c->n_launch += 2;
+  k_identity_perm<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm);
+  k_cluster_atoms<<<amp_blocks(n, 256), 256, 0, st>>>(n, xyz, q, dip, quad, alpha, thole, mol, c->atomA, c->atomB,
+                                                      c->atomC, c->atomD, c->alph, c->flags);
+  cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if ((r = cuda_check(c, cudaStreamSynchronize(st), "cluster setup"))) return r;
+  if (c->hibuf[2] & 2) return fail(c, AMP_ERR_ARG, "alpha must be > 0 for every site");
+  c->n_half = (long long)n * (n - 1) / 2;
+  c->n_full = 2 * c->n_half;
+  return AMP_OK;
+}
+
+void cluster_permanent_field(amp_ctx* c, double4_32a* out) {
+  if (c->cfg.precision == AMP_FP64)
+    launch_field<true, double, double4_32a>(c, (const double4_32a*)nullptr, out);
+  else
+    launch_field<true, float, double4_32a>(c, (const double4_32a*)nullptr, out);
+}
+
+void cluster_t(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* out, bool fp64) {
+  if (fp64)
+    launch_field<false, double, double4_32a>(c, v, out);
+  else
+    launch_field<false, float, float4>(c, v32, out);
+}
+
+}  // namespace amp

@@ -116,6 +116,11 @@ struct amp_ctx {
   double* grid64b = nullptr;
   float* grid32b = nullptr;
 
+  // isolated cluster (box == 0): all-pairs kernels, column-slice partial sums
+  bool cluster = false;
+  double4_32a* cluster_part = nullptr;
+  long long cluster_part_cap = 0;
+
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
   amp::Stats stats;
@@ -162,6 +167,7 @@ void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* ou
 // PME (amp_pme.cu)
 int pme_setup(amp_ctx* c);
 int pme_alloc_atoms(amp_ctx* c, int n_cap);
+int pme_influence(amp_ctx* c);
 void launch_pme_theta(amp_ctx* c);
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
 int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out_add);  // float64 grid
@@ -176,6 +182,13 @@ void launch_to32(amp_ctx* c, const double4_32a* v, float4* o);
 // backward (amp_forces.cu)
 int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt);
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
+
+// isolated clusters (amp_cluster.cu)
+constexpr int kClusterMaxSlices = 16;
+int cluster_setup(amp_ctx* c, const double* xyz, const double* q, const double* dip, const double* quad,
+                  const double* alpha, const double* thole, const int* mol);
+void cluster_permanent_field(amp_ctx* c, double4_32a* out);
+void cluster_t(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* out, bool fp64);
 
 }  // namespace amp
 

@@ -287,6 +287,11 @@ void launch_to32(amp_ctx* c, const double4_32a* v, float4* o) {
 // t = T v in the solver's working precision (v32 must mirror v in mixed mode).
 int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* t) {
   const bool fp64 = c->cfg.precision == AMP_FP64;
+  if (c->cluster) {
+    PhaseScope ps(c, AMP_PHASE_T_REAL);
+    cluster_t(c, v, v32, t, fp64);
+    return AMP_OK;
+  }
   {
     PhaseScope ps(c, AMP_PHASE_T_REAL);
     if (fp64)
@@ -302,6 +307,10 @@ int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, double4_
 int apply_T_sorted_fp64(amp_ctx* c, const double4_32a* v, double4_32a* t) {
   if (c->cfg.precision == AMP_FP64) return apply_T_sorted(c, v, nullptr, t);
   PhaseScope ps(c, AMP_PHASE_FP64_CHECK);
+  if (c->cluster) {
+    cluster_t(c, v, nullptr, t, true);
+    return AMP_OK;
+  }
   launch_t_real_fp64_direct(c, v, t);
   return pme_dipole_field(c, v, t);
 }

@@ -295,20 +295,11 @@ int exec_fft(amp_ctx* c, bool fp32, bool forward) {
 
 }  // namespace
 
-int pme_setup(amp_ctx* c) {
-  const int K = c->cfg.pme_grid;
-  c->K = K;
-  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
-  int r;
-  if ((r = dev_alloc(c, &c->grid64, ng)) || (r = dev_alloc(c, &c->cgrid64, nh)) ||
-      (r = dev_alloc(c, &c->G64, nh)))
-    return r;
-  if (c->cfg.precision == AMP_MIXED) {
-    if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
-        (r = dev_alloc(c, &c->G32, nh)))
-      return r;
-  }
-  // influence function on the half spectrum
+// Influence function G(m) on the half spectrum for the current box and beta,
+// uploaded on the context stream.
+int pme_influence(amp_ctx* c) {
+  const int K = c->K;
+  const long long nh = (long long)K * K * (K / 2 + 1);
   const std::vector<double> b2 = moduli(K);
   const double L = c->cfg.box, beta = c->cfg.ewald_beta, V = L * L * L;
   std::vector<double> G(nh);
@@ -324,11 +315,31 @@ int pme_setup(amp_ctx* c) {
         G[k] = g;
         if (!G32.empty()) G32[k] = (float)g;
       }
-  if ((r = cuda_check(c, cudaMemcpy(c->G64, G.data(), sizeof(double) * nh, cudaMemcpyHostToDevice), "G upload")))
+  int r;
+  if ((r = cuda_check(c, cudaMemcpyAsync(c->G64, G.data(), sizeof(double) * nh, cudaMemcpyHostToDevice, c->stream),
+                      "G upload")))
     return r;
-  if (!G32.empty() &&
-      (r = cuda_check(c, cudaMemcpy(c->G32, G32.data(), sizeof(float) * nh, cudaMemcpyHostToDevice), "G upload")))
+  if (!G32.empty() && (r = cuda_check(c, cudaMemcpyAsync(c->G32, G32.data(), sizeof(float) * nh,
+                                                         cudaMemcpyHostToDevice, c->stream),
+                                      "G upload")))
     return r;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "G upload");
+}
+
+int pme_setup(amp_ctx* c) {
+  const int K = c->cfg.pme_grid;
+  c->K = K;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  int r;
+  if ((r = dev_alloc(c, &c->grid64, ng)) || (r = dev_alloc(c, &c->cgrid64, nh)) ||
+      (r = dev_alloc(c, &c->G64, nh)))
+    return r;
+  if (c->cfg.precision == AMP_MIXED) {
+    if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
+        (r = dev_alloc(c, &c->G32, nh)))
+      return r;
+  }
+  if ((r = pme_influence(c))) return r;
   if (cufftPlan3d(&c->plan_d2z, K, K, K, CUFFT_D2Z) != CUFFT_SUCCESS ||
       cufftPlan3d(&c->plan_z2d, K, K, K, CUFFT_Z2D) != CUFFT_SUCCESS)
     return fail(c, AMP_ERR_CUDA, "cuFFT plan creation failed");
