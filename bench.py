@@ -43,7 +43,71 @@ def parse():
     ap.add_argument("--workload", default="water-23556")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="only the serving measurement (request stream, rates) as its own JSON line")
+    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--rates", default="2.0", help="arrival rates as multiples of the float64 capacity")
     return ap.parse_args()
+
+
+# ------------------------------------------------------------------ serving
+
+def run_serving(n_requests: int, slots: int, rate_factors, warm: int = 40):
+    """Poisson stream of solve requests (sizes log-uniform 64..4096 waters, half
+    clusters, half periodic boxes; mixed precision, 1e-5 D) through the
+    continuous-batching server, against one-at-a-time float64 solves."""
+    import numpy as np
+    from paper_1906_01211_gb300.serve import Server, percentile, request_stream
+    reqs = request_stream(n_requests + warm, seed=4)
+    warm_reqs, reqs = reqs[:warm], reqs[warm:]
+    # one-at-a-time float64: one slot, each request alone, back to back
+    base = Server(n_slots=1, precision="fp64", tol_debye=1e-5)
+    for s in warm_reqs:
+        base.result(base.submit(s))
+    service = []
+    t0 = time.perf_counter()
+    for s in reqs:
+        r = base.result(base.submit(s))
+        if not r.ok:
+            raise RuntimeError(r.error)
+        service.append(r.t_done - r.t_start)
+    t_base = time.perf_counter() - t0
+    base.close()
+    cap = len(reqs) / t_base
+    out = {"requests": len(reqs), "slots": slots, "precision": "mixed", "tol_debye": 1e-5,
+           "one_at_a_time_fp64": {"throughput_per_s": cap, "p50_ms": 1e3 * percentile(service, 50),
+                                  "p99_ms": 1e3 * percentile(service, 99)},
+           "rates": []}
+    rng = np.random.Generator(np.random.PCG64(44))
+    for f in rate_factors:
+        srv = Server(n_slots=slots, precision="mixed", tol_debye=1e-5)
+        for s in warm_reqs:
+            srv.result(srv.submit(s))
+        lam = f * cap
+        gaps = rng.exponential(1.0 / lam, len(reqs))
+        t_start = time.perf_counter()
+        t_next = t_start
+        ids = []
+        for s, g in zip(reqs, gaps):
+            t_next += g
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(s))
+        res = [srv.result(i) for i in ids]
+        t_end = max(r.t_done for r in res)
+        srv.close()
+        bad = [r.error for r in res if not r.ok]
+        if bad:
+            raise RuntimeError(bad[0])
+        lat = [r.latency for r in res]
+        out["rates"].append({"arrival_per_s": lam, "rate_vs_fp64_capacity": f,
+                             "throughput_per_s": len(res) / (t_end - t_start),
+                             "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
+                             "mean_iters": float(np.mean([r.iters for r in res]))})
+    return out
 
 
 def dist_env():
@@ -157,6 +221,16 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
+    if args.serving:
+        if rank == 0:
+            rates = [float(x) for x in args.rates.split(",")]
+            sv = run_serving(args.requests, args.slots, rates)
+            print(json.dumps({"metric": "serving solves/s and p50/p99 latency", "unit": "solves/s",
+                              "value": sv["rates"][-1]["throughput_per_s"], "higher_is_better": True,
+                              "dtype": "f32+f64", "data": "synthetic",
+                              "config": {"workload": "water request stream (64..4096 waters, half clusters)"},
+                              "serving": sv}), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -293,6 +367,10 @@ def main():
                  "energy_rel_vs_fp64_gpu": abs(Um / U - 1.0)}
         pm.close()
 
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(args.requests, args.slots, [float(x) for x in args.rates.split(",")])
+
     cpu = None
     if not args.no_cpu_baseline:
         pairs_o, times, t_build = oracle_sample(w, 2, 0)
@@ -314,6 +392,7 @@ def main():
                                                / max(phases["t_real"][1], 1) / 1e3),
         "phase_ms_per_step": phase_ms,
         "mixed": mixed,
+        "serving": serving,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
