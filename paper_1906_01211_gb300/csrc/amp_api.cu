@@ -32,18 +32,26 @@ void dev_free(amp_ctx* c, void* p) {
 
 constexpr int kEvPool = 8192;
 
-void prof_begin(amp_ctx* c, int phase) {
-  if (!c->prof) return;
-  if (c->ev_used + 2 > (int)c->ev_pool.size()) prof_resolve(c);
-  cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
-  c->ev_phase[c->ev_used / 2] = phase;
+// Each scope takes an event pair at begin and records its end into the same
+// pair, so scopes may nest; events go on the stream the scope's launches use.
+int prof_begin(amp_ctx* c, int phase, cudaStream_t st) {
+  if (!c->prof) return -1;
+  if (c->ev_used + 2 > (int)c->ev_pool.size()) {
+    if (c->ev_open > 0) return -1;  // pool full inside an open scope: skip this one
+    prof_resolve(c);
+  }
+  const int k = c->ev_used;
+  c->ev_used += 2;
+  c->ev_open += 1;
+  cudaEventRecord(c->ev_pool[k], st);
+  c->ev_phase[k / 2] = phase;
+  return k;
 }
 
-void prof_end(amp_ctx* c, int phase) {
-  if (!c->prof) return;
-  (void)phase;
-  cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream);
-  c->ev_used += 2;
+void prof_end(amp_ctx* c, int slot, cudaStream_t st) {
+  if (!c->prof || slot < 0) return;
+  cudaEventRecord(c->ev_pool[slot + 1], st);
+  c->ev_open -= 1;
 }
 
 int prof_resolve(amp_ctx* c) {
@@ -61,7 +69,8 @@ int prof_resolve(amp_ctx* c) {
   return AMP_OK;
 }
 
-int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* t);
+int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* t,
+                   double4_32a* t2);
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o);
 
 static int alloc_atoms(amp_ctx* c, int n) {
@@ -71,7 +80,8 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->alph, (void**)&c->pos32, (void**)&c->full_cnt, (void**)&c->half_cnt,
                    (void**)&c->full_start, (void**)&c->half_start, (void**)&c->theta, (void**)&c->theta32,
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
-                   (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32};
+                   (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
+                   (void**)&c->trec, (void**)&c->plo};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -88,7 +98,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = pme_alloc_atoms(c, cap)) || (r = dev_alloc(c, &c->E0s, cap)) || (r = dev_alloc(c, &c->mu, cap)) ||
       (r = dev_alloc(c, &c->res, cap)) || (r = dev_alloc(c, &c->zv, cap)) || (r = dev_alloc(c, &c->pv, cap)) ||
       (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
-      (r = dev_alloc(c, &c->p32, cap)))
+      (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)))
     return r;
   c->n_cap = cap;
   return AMP_OK;
@@ -126,6 +136,12 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return AMP_ERR_OOM;
   }
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    amp_destroy(c);
+    return AMP_ERR_CUDA;
+  }
   if (!cluster && (r = pme_setup(c))) {
     amp_destroy(c);
     return r;
@@ -154,6 +170,12 @@ void amp_destroy(amp_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->plan_d2z) cufftDestroy(c->plan_d2z);
   if (c->plan_z2d) cufftDestroy(c->plan_z2d);
   if (c->plan_r2c) cufftDestroy(c->plan_r2c);
@@ -226,8 +248,9 @@ int amp_apply_T(amp_ctx* c, const double* mu, double* Tmu) {
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!mu || !Tmu) return fail(c, AMP_ERR_ARG, "null vector");
   launch_to_sorted(c, mu, c->tmp);
-  if (c->cfg.precision == AMP_MIXED) launch_to32(c, c->tmp, c->p32);
-  int r = apply_T_sorted(c, c->tmp, c->p32, c->tv);
+  float4* lo = c->cfg.precision == AMP_MIXED ? nullptr : c->plo;
+  launch_split(c, c->tmp, c->p32, lo);
+  int r = apply_T_sorted(c, c->tmp, c->p32, lo, c->tv, nullptr);
   if (r) return r;
   launch_from_sorted(c, c->tv, Tmu);
   return cuda_check(c, cudaGetLastError(), "apply_T launch");

@@ -92,7 +92,11 @@ struct amp_ctx {
   // vectors in cell order
   double4_32a *E0s = nullptr, *mu = nullptr, *res = nullptr, *zv = nullptr, *pv = nullptr;
   double4_32a *qv = nullptr, *tv = nullptr, *tmp = nullptr;
-  float4* p32 = nullptr;
+  double4_32a* trec = nullptr;  // reciprocal part of T*v, computed on the side stream
+  cudaStream_t side = nullptr;  // second stream: PME beside the real-space kernel
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  float4* p32 = nullptr;  // float part of p (mixed: p in float32; float64: hi of hi + lo)
+  float4* plo = nullptr;  // float64 path: p - hi, so that hi + lo carries p to ~48 bits
   double* partials = nullptr;  // block partial sums (two sets)
   int n_parts_cap = 0;
   double* scal = nullptr;      // device scalars of the solver: rz[2], rms, pq
@@ -105,6 +109,7 @@ struct amp_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_phase;  // phase of each begin/end pair in flight
   int ev_used = 0;
+  int ev_open = 0;
   double prof_ms[AMP_NPHASE] = {0};
   long long prof_cnt[AMP_NPHASE] = {0};
 
@@ -142,14 +147,16 @@ inline int dev_alloc(amp_ctx* c, T** p, long long count) {
 int cuda_check(amp_ctx* c, cudaError_t e, const char* what);
 
 // Phase timers: record an event pair around a phase on the context stream.
-void prof_begin(amp_ctx* c, int phase);
-void prof_end(amp_ctx* c, int phase);
+int prof_begin(amp_ctx* c, int phase, cudaStream_t st);
+void prof_end(amp_ctx* c, int slot, cudaStream_t st);
 int prof_resolve(amp_ctx* c);
 struct PhaseScope {
   amp_ctx* c;
-  int ph;
-  PhaseScope(amp_ctx* c_, int ph_) : c(c_), ph(ph_) { prof_begin(c, ph); }
-  ~PhaseScope() { prof_end(c, ph); }
+  cudaStream_t st;
+  int slot;
+  PhaseScope(amp_ctx* c_, int ph) : c(c_), st(c_->stream) { slot = prof_begin(c, ph, st); }
+  PhaseScope(amp_ctx* c_, int ph, cudaStream_t s) : c(c_), st(s) { slot = prof_begin(c, ph, st); }
+  ~PhaseScope() { prof_end(c, slot, st); }
 };
 
 // neighbour lists (amp_nblist.cu)
@@ -160,7 +167,8 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
 // pair terms and real-space sums (amp_pair.cu)
 void launch_pair_build(amp_ctx* c);
 void launch_e0_real(amp_ctx* c, double4_32a* out);  // out = real-space E0 + self
-void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out);  // out = T_real v + self v
+// out = T_real v + self v (float64 path, double-float arithmetic; vhi + vlo = v)
+void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const float4* vlo, double4_32a* out);
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out);
 void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out);
 
@@ -170,14 +178,16 @@ int pme_alloc_atoms(amp_ctx* c, int n_cap);
 int pme_influence(amp_ctx* c);
 void launch_pme_theta(amp_ctx* c);
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
-int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out_add);  // float64 grid
-int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out_add);  // float32 grid
+// reciprocal field of dipoles on stream st: out += field (set: out = field)
+int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStream_t st, bool set);
+int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream_t st, bool set);
 
 // solver (amp_pcg.cu)
 void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst);
 void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst);
 int solve(amp_ctx* c, bool use_guess);
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o);
+void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo);  // v = hi + lo
 
 // backward (amp_forces.cu)
 int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt);

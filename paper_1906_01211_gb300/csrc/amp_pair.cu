@@ -108,13 +108,24 @@ __global__ void __launch_bounds__(256) k_pair_build(long long nh, const int* __r
   const R rx = (R)rx64, ry = (R)ry64, rz = (R)rz64;
   const R r2 = rx * rx + ry * ry + rz * rz;
   const Kern<R> k = pair_kernels<R>(r2, (R)bi.w, (R)bj.w, (R)di.z, (R)dj.z, di.w == dj.w, g);
-  R* t = T + 6 * pid;
-  t[0] = k.b2u * rx * rx - k.b1u;
-  t[1] = k.b2u * ry * ry - k.b1u;
-  t[2] = k.b2u * rz * rz - k.b1u;
-  t[3] = k.b2u * rx * ry;
-  t[4] = k.b2u * rx * rz;
-  t[5] = k.b2u * ry * rz;
+  const R tv[6] = {k.b2u * rx * rx - k.b1u, k.b2u * ry * ry - k.b1u, k.b2u * rz * rz - k.b1u,
+                   k.b2u * rx * ry, k.b2u * rx * rz, k.b2u * ry * rz};
+  if constexpr (sizeof(R) == 8) {
+    // float64 path: the tensor is kept as float pairs hi + lo (hi = fl(t),
+    // lo = fl(t - hi)), read by the double-float kernel k_t_real_df
+    float hi[6], lo[6];
+    for (int a = 0; a < 6; ++a) {
+      hi[a] = __double2float_rn((double)tv[a]);
+      lo[a] = __double2float_rn((double)tv[a] - (double)hi[a]);
+    }
+    float4* o = reinterpret_cast<float4*>(T + 6 * pid);
+    o[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    o[1] = make_float4(hi[4], hi[5], lo[0], lo[1]);
+    o[2] = make_float4(lo[2], lo[3], lo[4], lo[5]);
+  } else {
+    R* t = T + 6 * pid;
+    for (int a = 0; a < 6; ++a) t[a] = tv[a];
+  }
   R ex, ey, ez;
   multipole_field<R>(rx, ry, rz, (R)aj.w, (R)bj.x, (R)bj.y, (R)bj.z, (R)cj.x, (R)cj.y, (R)cj.z, (R)cj.w,
                      (R)dj.x, (R)dj.y, k.b1e, k.b2e, k.b3e, ex, ey, ez);
@@ -195,38 +206,89 @@ __global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __res
   }
 }
 
-// out_i = sum_j T_ij v_j + selfc v_i, float64 tensors.
-__global__ void __launch_bounds__(256) k_t_real64(int n, const int* __restrict__ full_start,
-                                                  const int* __restrict__ full_j, const int* __restrict__ full_ref,
-                                                  const double* __restrict__ T, double selfc,
-                                                  const double4_32a* __restrict__ v, double4_32a* __restrict__ out) {
+// ---- double-float arithmetic (a value is hi + lo, two floats, |lo| <= ulp(hi)/2)
+// Error-free transformations with round-to-nearest intrinsics, which the
+// compiler never contracts: two-sum (Knuth) and the FMA two-product give about
+// 48 significant bits, enough for float64-level results (1e-14 relative) on a
+// GPU whose float32 rate is ~58 times its float64 rate.
+struct dflt {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dflt df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dflt df_quick(float s, float t) {  // renormalise, |s| >= |t|
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+// acc += (ahi + alo) * (bhi + blo)
+__device__ __forceinline__ void df_fma(dflt& acc, float ahi, float alo, float bhi, float blo) {
+  const float p = __fmul_rn(ahi, bhi);
+  float e = __fmaf_rn(ahi, bhi, -p);
+  e = __fmaf_rn(ahi, blo, e);
+  e = __fmaf_rn(alo, bhi, e);
+  const dflt s = df_two_sum(acc.hi, p);
+  acc = df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
+}
+
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  const dflt s = df_two_sum(a.hi, b.hi);
+  return df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dflt df_group_sum(dflt v) {
+  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
+#pragma unroll
+  for (int o = kRowGroup / 2; o > 0; o >>= 1) {
+    dflt w;
+    w.hi = __shfl_xor_sync(mask, v.hi, o, kRowGroup);
+    w.lo = __shfl_xor_sync(mask, v.lo, o, kRowGroup);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// out_i = sum_j T_ij v_j + selfc v_i for the float64 path, in double-float:
+// tensors as hi/lo float pairs (written by the pair build), v as vhi + vlo.
+__global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict__ full_start,
+                                                   const int* __restrict__ full_j, const int* __restrict__ full_ref,
+                                                   const float4* __restrict__ T, double selfc,
+                                                   const float4* __restrict__ vhi, const float4* __restrict__ vlo,
+                                                   const double4_32a* __restrict__ v64, double4_32a* __restrict__ out) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gid / kRowGroup, l = gid % kRowGroup;
   if (i >= n) return;
-  double sx = 0, sy = 0, sz = 0;
+  dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
   const int e = full_start[i + 1];
   for (int k = full_start[i] + l; k < e; k += kRowGroup) {
     const int j = full_j[k];
-    const double2* t = reinterpret_cast<const double2*>(T + 6 * (long long)(full_ref[k] >> 1));
-    const double2 t0 = t[0], t1 = t[1], t2 = t[2];  // (xx,yy) (zz,xy) (xz,yz)
-    const double4_32a vj = v[j];
-    // three FMAs per component (the float64 pipe is the bound)
-    sx = fma(t0.x, vj.x, sx);
-    sx = fma(t1.y, vj.y, sx);
-    sx = fma(t2.x, vj.z, sx);
-    sy = fma(t1.y, vj.x, sy);
-    sy = fma(t0.y, vj.y, sy);
-    sy = fma(t2.y, vj.z, sy);
-    sz = fma(t2.x, vj.x, sz);
-    sz = fma(t2.y, vj.y, sz);
-    sz = fma(t1.x, vj.z, sz);
+    const float4* t = T + 3 * (long long)(full_ref[k] >> 1);
+    const float4 a = t[0], b = t[1], c = t[2];
+    // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
+    const float4 h = vhi[j], w = vlo[j];
+    df_fma(sx, a.x, b.z, h.x, w.x);
+    df_fma(sx, a.w, c.y, h.y, w.y);
+    df_fma(sx, b.x, c.z, h.z, w.z);
+    df_fma(sy, a.w, c.y, h.x, w.x);
+    df_fma(sy, a.y, b.w, h.y, w.y);
+    df_fma(sy, b.y, c.w, h.z, w.z);
+    df_fma(sz, b.x, c.z, h.x, w.x);
+    df_fma(sz, b.y, c.w, h.y, w.y);
+    df_fma(sz, a.z, c.x, h.z, w.z);
   }
-  sx = group_sum(sx);
-  sy = group_sum(sy);
-  sz = group_sum(sz);
+  sx = df_group_sum(sx);
+  sy = df_group_sum(sy);
+  sz = df_group_sum(sz);
   if (l == 0) {
-    const double4_32a vi = v[i];
-    out[i] = make_double4_32a(sx + selfc * vi.x, sy + selfc * vi.y, sz + selfc * vi.z, 0.0);
+    const double4_32a vi = v64[i];
+    out[i] = make_double4_32a((double)sx.hi + (double)sx.lo + selfc * vi.x, (double)sy.hi + (double)sy.lo + selfc * vi.y,
+                              (double)sz.hi + (double)sz.lo + selfc * vi.z, 0.0);
   }
 }
 
@@ -305,11 +367,13 @@ void launch_e0_real(amp_ctx* c, double4_32a* out) {
                                                             c->atomB, out);
 }
 
-void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out) {
+// v must be mirrored in (vhi, vlo) = split of v into float pairs.
+void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const float4* vlo, double4_32a* out) {
   const PairGeom g = geom(c);
   c->n_launch += 1;
-  k_t_real64<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
-      c->n, c->full_start, c->full_j, c->full_ref, c->T64, g.selfc, v, out);
+  k_t_real_df<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
+      c->n, c->full_start, c->full_j, c->full_ref, reinterpret_cast<const float4*>(c->T64), g.selfc, vhi, vlo, v,
+      out);
 }
 
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out) {

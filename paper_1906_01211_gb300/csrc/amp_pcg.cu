@@ -92,22 +92,47 @@ __global__ void k_mu_from_e0(int n, const double4_32a* __restrict__ e0, const do
   }
 }
 
-// r = E0 - mu/alpha + t (t = T mu); z = alpha r; p = z; partials (r.z, z.z)
+// v = hi + lo with hi = fl32(v), lo = fl32(v - hi) (lo skipped when null)
+__device__ __forceinline__ void split_store(const double4_32a& v, float4* __restrict__ hi, float4* __restrict__ lo,
+                                            int s) {
+  if (!hi) return;
+  const float4 h = make_float4(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z), 0.f);
+  hi[s] = h;
+  if (lo)
+    lo[s] = make_float4(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y),
+                        __double2float_rn(v.z - (double)h.z), 0.f);
+}
+
+__device__ __forceinline__ double4_32a sum_t(const double4_32a* __restrict__ t, const double4_32a* __restrict__ t2,
+                                             int s) {
+  double4_32a a = t[s];
+  if (t2) {
+    const double4_32a b = t2[s];
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+  }
+  return a;
+}
+
+// r = E0 - mu/alpha + t (t (+ t2) = T mu); z = alpha r; p = z; partials (r.z, z.z)
 __global__ void __launch_bounds__(NT) k_pcg_init(int n, const double4_32a* __restrict__ e0,
                                                  const double4_32a* __restrict__ mu, const double4_32a* __restrict__ t,
+                                                 const double4_32a* __restrict__ t2,
                                                  const double2* __restrict__ al, double4_32a* __restrict__ r,
                                                  double4_32a* __restrict__ z, double4_32a* __restrict__ p,
-                                                 float4* __restrict__ p32, double* __restrict__ part) {
+                                                 float4* __restrict__ p32, float4* __restrict__ plo,
+                                                 double* __restrict__ part) {
   double rz = 0.0, zz = 0.0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const double2 a = al[s];
-    const double4_32a e = e0[s], m = mu[s], tt = t[s];
+    const double4_32a e = e0[s], m = mu[s], tt = sum_t(t, t2, s);
     const double4_32a rr = make_double4_32a(e.x - m.x * a.y + tt.x, e.y - m.y * a.y + tt.y, e.z - m.z * a.y + tt.z, 0.0);
     const double4_32a zz4 = make_double4_32a(a.x * rr.x, a.x * rr.y, a.x * rr.z, 0.0);
     r[s] = rr;
     z[s] = zz4;
     p[s] = zz4;
-    if (p32) p32[s] = make_float4((float)zz4.x, (float)zz4.y, (float)zz4.z, 0.f);
+    split_store(zz4, p32, plo, s);
     rz += dot3(rr, zz4);
     zz += dot3(zz4, zz4);
   }
@@ -135,13 +160,14 @@ __global__ void __launch_bounds__(NT) k_pcg_init_finish(int n, const double* __r
 
 // q = p/alpha - t; partials (p.q, 0)
 __global__ void __launch_bounds__(NT) k_pcg_q(int n, const double4_32a* __restrict__ p, const double4_32a* __restrict__ t,
-                                              const double2* __restrict__ al, double4_32a* __restrict__ q,
-                                              double* __restrict__ part, const int* __restrict__ fl) {
+                                              const double4_32a* __restrict__ t2, const double2* __restrict__ al,
+                                              double4_32a* __restrict__ q, double* __restrict__ part,
+                                              const int* __restrict__ fl) {
   if (fl[F_STOP]) return;
   double pq = 0.0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const double ia = al[s].y;
-    const double4_32a pp = p[s], tt = t[s];
+    const double4_32a pp = p[s], tt = sum_t(t, t2, s);
     const double4_32a qq = make_double4_32a(pp.x * ia - tt.x, pp.y * ia - tt.y, pp.z * ia - tt.z, 0.0);
     q[s] = qq;
     pq += dot3(pp, qq);
@@ -184,10 +210,11 @@ __global__ void __launch_bounds__(NT) k_pcg_update(int n, double4_32a* __restric
   write_partials(part, rz, zz);
 }
 
-// convergence test on z; beta = rz_new/rz_old; p = z + beta p
+// convergence test on z; beta = rz_new/rz_old; p = z + beta p (and its float split)
 __global__ void __launch_bounds__(NT) k_pcg_dir(int n, const double4_32a* __restrict__ z, double4_32a* __restrict__ p,
-                                                float4* __restrict__ p32, const double* __restrict__ part,
-                                                double* __restrict__ scal, int* __restrict__ fl, double tol) {
+                                                float4* __restrict__ p32, float4* __restrict__ plo,
+                                                const double* __restrict__ part, double* __restrict__ scal,
+                                                int* __restrict__ fl, double tol) {
   if (fl[F_STOP] || fl[F_CONV] < 0) return;
   double rz, zz;
   reduce_partials(part, rz, zz);
@@ -206,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_pcg_dir(int n, const double4_32a* __rest
     pp.y = zz4.y + beta * pp.y;
     pp.z = zz4.z + beta * pp.z;
     p[s] = pp;
-    if (p32) p32[s] = make_float4((float)pp.x, (float)pp.y, (float)pp.z, 0.f);
+    split_store(pp, p32, plo, s);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[(it + 1) & 1] = rz;
 }
@@ -245,11 +272,8 @@ __global__ void k_from_sorted(int n, const int* __restrict__ perm, const double4
   dst[3 * i + 2] = v.z;
 }
 
-__global__ void k_to32(int n, const double4_32a* __restrict__ v, float4* __restrict__ o) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double4_32a a = v[s];
-    o[s] = make_float4((float)a.x, (float)a.y, (float)a.z, 0.f);
-  }
+__global__ void k_split(int n, const double4_32a* __restrict__ v, float4* __restrict__ hi, float4* __restrict__ lo) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) split_store(v[s], hi, lo, s);
 }
 
 // U = -1/2 C sum mu . E0 over the caller's [N][3] arrays
@@ -281,38 +305,75 @@ void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst) {
 
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o) {
   c->n_launch += 1;
-  k_to32<<<NB, NT, 0, c->stream>>>(c->n, v, o);
+  k_split<<<NB, NT, 0, c->stream>>>(c->n, v, o, nullptr);
 }
 
-// t = T v in the solver's working precision (v32 must mirror v in mixed mode).
-int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* t) {
+void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo) {
+  c->n_launch += 1;
+  k_split<<<NB, NT, 0, c->stream>>>(c->n, v, hi, lo);
+}
+
+// T v = t (+ t2). With t2 == nullptr the whole product lands in t. With t2
+// given (periodic systems) the reciprocal part runs on the side stream into t2
+// while the real-space kernel runs on the main stream into t: the two parts
+// are independent, and the FFTs leave float64 units idle that the real-space
+// kernel uses. The main stream waits for the side stream before returning.
+static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const float4* v32, const float4* vlo,
+                       double4_32a* t, double4_32a* t2, bool fp64_real_cached, bool fp64_real_direct) {
+  int r;
+  if (t2) {
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    {
+      PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
+      r = fp64_pme ? pme_dipole_field(c, v, t2, c->side, true) : pme_dipole_field32(c, v32, t2, c->side, true);
+    }
+    cudaEventRecord(c->ev_join, c->side);
+    if (r) {
+      cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+      return r;
+    }
+  }
+  {
+    PhaseScope ps(c, AMP_PHASE_T_REAL);
+    if (fp64_real_direct)
+      launch_t_real_fp64_direct(c, v, t);
+    else if (fp64_real_cached)
+      launch_t_real(c, v, v32, vlo, t);
+    else
+      launch_t_real32(c, v32, v, t);
+  }
+  if (t2) {
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    return AMP_OK;
+  }
+  PhaseScope ps(c, AMP_PHASE_T_RECIP);
+  return fp64_pme ? pme_dipole_field(c, v, t, c->stream, false) : pme_dipole_field32(c, v32, t, c->stream, false);
+}
+
+// t (+ t2) = T v in the solver's working precision. v32 (+ vlo) must mirror
+// v: mixed, v32 = fl32(v); float64, v = v32 + vlo (double-float split).
+int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* t,
+                   double4_32a* t2) {
   const bool fp64 = c->cfg.precision == AMP_FP64;
   if (c->cluster) {
     PhaseScope ps(c, AMP_PHASE_T_REAL);
     cluster_t(c, v, v32, t, fp64);
+    if (t2) cudaMemsetAsync(t2, 0, sizeof(double4_32a) * c->n, c->stream);
     return AMP_OK;
   }
-  {
-    PhaseScope ps(c, AMP_PHASE_T_REAL);
-    if (fp64)
-      launch_t_real(c, v, t);
-    else
-      launch_t_real32(c, v32, v, t);
-  }
-  PhaseScope ps(c, AMP_PHASE_T_RECIP);
-  return fp64 ? pme_dipole_field(c, v, t) : pme_dipole_field32(c, v32, t);
+  return fork_join_T(c, fp64, v, v32, vlo, t, t2, fp64, false);
 }
 
-// t = T v with every term in float64 (mixed path: pair tensors recomputed).
-int apply_T_sorted_fp64(amp_ctx* c, const double4_32a* v, double4_32a* t) {
-  if (c->cfg.precision == AMP_FP64) return apply_T_sorted(c, v, nullptr, t);
+// Mixed path: t (+ t2) = T v with every term in float64 (pair tensors recomputed).
+static int apply_T_sorted_fp64_check(amp_ctx* c, const double4_32a* v, double4_32a* t, double4_32a* t2) {
   PhaseScope ps(c, AMP_PHASE_FP64_CHECK);
   if (c->cluster) {
     cluster_t(c, v, nullptr, t, true);
+    if (t2) cudaMemsetAsync(t2, 0, sizeof(double4_32a) * c->n, c->stream);
     return AMP_OK;
   }
-  launch_t_real_fp64_direct(c, v, t);
-  return pme_dipole_field(c, v, t);
+  return fork_join_T(c, true, v, nullptr, nullptr, t, t2, false, true);
 }
 
 static int read_flags(amp_ctx* c) {
@@ -327,14 +388,14 @@ static int enqueue_iteration(amp_ctx* c) {
   const bool mixed = c->cfg.precision == AMP_MIXED;
   double* pa = c->partials;
   double* pb = c->partials + 2 * NB;
-  int r = apply_T_sorted(c, c->pv, mixed ? c->p32 : nullptr, c->tv);
+  float4* lo = mixed ? nullptr : c->plo;
+  int r = apply_T_sorted(c, c->pv, c->p32, lo, c->tv, c->trec);
   if (r) return r;
   PhaseScope ps(c, AMP_PHASE_PCG);
   c->n_launch += 4;
-  k_pcg_q<<<NB, NT, 0, st>>>(n, c->pv, c->tv, c->alph, c->qv, pa, c->iflags);
+  k_pcg_q<<<NB, NT, 0, st>>>(n, c->pv, c->tv, c->trec, c->alph, c->qv, pa, c->iflags);
   k_pcg_update<<<NB, NT, 0, st>>>(n, c->mu, c->res, c->zv, c->pv, c->qv, c->alph, pa, pb, c->scal, c->iflags);
-  k_pcg_dir<<<NB, NT, 0, st>>>(n, c->zv, c->pv, mixed ? c->p32 : nullptr, pb, c->scal, c->iflags,
-                               c->cfg.tol_debye);
+  k_pcg_dir<<<NB, NT, 0, st>>>(n, c->zv, c->pv, c->p32, lo, pb, c->scal, c->iflags, c->cfg.tol_debye);
   k_pcg_advance<<<1, 1, 0, st>>>(c->iflags, c->cfg.max_iter);
   return AMP_OK;
 }
@@ -343,18 +404,20 @@ static int enqueue_iteration(amp_ctx* c) {
 // restart the recurrence from it.
 static int restart(amp_ctx* c, bool fp64_operator) {
   const bool mixed = c->cfg.precision == AMP_MIXED;
+  float4* lo = mixed ? nullptr : c->plo;
   int r;
-  if (fp64_operator) {
-    r = apply_T_sorted_fp64(c, c->mu, c->tv);
+  if (fp64_operator && mixed) {
+    r = apply_T_sorted_fp64_check(c, c->mu, c->tv, c->trec);
   } else {
-    if (mixed) launch_to32(c, c->mu, c->p32);
-    r = apply_T_sorted(c, c->mu, mixed ? c->p32 : nullptr, c->tv);
+    // the float split of mu goes through the p buffers, which k_pcg_init rewrites
+    launch_split(c, c->mu, c->p32, lo);
+    r = apply_T_sorted(c, c->mu, c->p32, lo, c->tv, c->trec);
   }
   if (r) return r;
   PhaseScope ps(c, AMP_PHASE_PCG);
   c->n_launch += 2;
-  k_pcg_init<<<NB, NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->alph, c->res, c->zv, c->pv,
-                                       mixed ? c->p32 : nullptr, c->partials);
+  k_pcg_init<<<NB, NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->trec, c->alph, c->res, c->zv, c->pv, c->p32,
+                                       lo, c->partials);
   k_pcg_init_finish<<<1, NT, 0, c->stream>>>(c->n, c->partials, c->cfg.tol_debye, c->scal, c->iflags);
   return AMP_OK;
 }

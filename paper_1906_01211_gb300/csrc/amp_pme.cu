@@ -192,9 +192,9 @@ __global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict_
   cg[k] = v;
 }
 
-// out_i += -sum_g grad W_i(g) phi(g); lane t of the atom's group sums plane
-// k0x - t, the group adds the five planes.
-template <typename R>
+// out_i += -sum_g grad W_i(g) phi(g) (kSet: out_i = ...); lane t of the atom's
+// group sums plane k0x - t, the group adds the five planes.
+template <typename R, bool kSet = false>
 __global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict__ theta,
                                                       const int4* __restrict__ gbase, const R* __restrict__ phi,
                                                       int K, double4_32a* __restrict__ out) {
@@ -239,11 +239,15 @@ __global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict
     ez += __shfl_xor_sync(mask, ez, o, kPmeGroup);
   }
   if (tx == 0) {
-    double4_32a o = out[s];
-    o.x -= ex;
-    o.y -= ey;
-    o.z -= ez;
-    out[s] = o;
+    if (kSet) {
+      out[s] = make_double4_32a(-ex, -ey, -ez, 0.0);
+    } else {
+      double4_32a o = out[s];
+      o.x -= ex;
+      o.y -= ey;
+      o.z -= ez;
+      out[s] = o;
+    }
   }
 }
 
@@ -435,34 +439,61 @@ int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, 
   return AMP_OK;
 }
 
-int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out_add) {
+// Reciprocal field of the dipoles v on stream st: out (+)= -grad phi. With
+// set = true the result overwrites out (used when it runs beside the real-space
+// kernel on a second stream and is summed later).
+int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStream_t st, bool set) {
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
-  cudaStream_t st = c->stream;
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  int r;
+  cufftSetStream(c->plan_d2z, st);
+  cufftSetStream(c->plan_z2d, st);
   cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
-  k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, v, K, c->grid64);
-  if ((r = exec_fft(c, false, true))) return r;
-  k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
-  if ((r = exec_fft(c, false, false))) return r;
-  k_gather_field<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
-  return AMP_OK;
+  k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+      n, c->theta, c->gbase, v, K, c->grid64);
+  int r = exec_fft(c, false, true);
+  if (!r) {
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
+    r = exec_fft(c, false, false);
+  }
+  if (!r) {
+    if (set)
+      k_gather_field<double, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+          n, c->theta, c->gbase, c->grid64, K, out);
+    else
+      k_gather_field<double, false><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+          n, c->theta, c->gbase, c->grid64, K, out);
+  }
+  cufftSetStream(c->plan_d2z, c->stream);
+  cufftSetStream(c->plan_z2d, c->stream);
+  return r;
 }
 
-int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out_add) {
+int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream_t st, bool set) {
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
-  cudaStream_t st = c->stream;
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  int r;
+  cufftSetStream(c->plan_r2c, st);
+  cufftSetStream(c->plan_c2r, st);
   cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
-  k_spread_dipoles<float, float4><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, v, K, c->grid32);
-  if ((r = exec_fft(c, true, true))) return r;
-  k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
-  if ((r = exec_fft(c, true, false))) return r;
-  k_gather_field<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
-  return AMP_OK;
+  k_spread_dipoles<float, float4><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+      n, c->theta32, c->gbase, v, K, c->grid32);
+  int r = exec_fft(c, true, true);
+  if (!r) {
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
+    r = exec_fft(c, true, false);
+  }
+  if (!r) {
+    if (set)
+      k_gather_field<float, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+          n, c->theta32, c->gbase, c->grid32, K, out);
+    else
+      k_gather_field<float, false><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+          n, c->theta32, c->gbase, c->grid32, K, out);
+  }
+  cufftSetStream(c->plan_r2c, c->stream);
+  cufftSetStream(c->plan_c2r, c->stream);
+  return r;
 }
 
 }  // namespace amp
