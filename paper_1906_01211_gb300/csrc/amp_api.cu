@@ -81,7 +81,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->full_start, (void**)&c->half_start, (void**)&c->theta, (void**)&c->theta32,
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
-                   (void**)&c->trec, (void**)&c->plo};
+                   (void**)&c->trec, (void**)&c->plo, (void**)&c->mp_df};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -98,7 +98,8 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = pme_alloc_atoms(c, cap)) || (r = dev_alloc(c, &c->E0s, cap)) || (r = dev_alloc(c, &c->mu, cap)) ||
       (r = dev_alloc(c, &c->res, cap)) || (r = dev_alloc(c, &c->zv, cap)) || (r = dev_alloc(c, &c->pv, cap)) ||
       (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
-      (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)))
+      (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)) ||
+      (r = dev_alloc(c, &c->mp_df, 5LL * cap)))
     return r;
   c->n_cap = cap;
   return AMP_OK;

@@ -61,6 +61,7 @@ struct amp_ctx {
   int *perm = nullptr, *inv_perm = nullptr, *slot_tmp = nullptr;
   double4_32a *atomA = nullptr, *atomB = nullptr, *atomC = nullptr, *atomD = nullptr;
   double2* alph = nullptr;  // (alpha, 1/alpha) per sorted atom
+  float4* mp_df = nullptr;  // float64 path: q, d, Theta as hi/lo float pairs, 5 float4 per atom
   float4* pos32 = nullptr;
 
   // neighbour lists
@@ -79,6 +80,8 @@ struct amp_ctx {
   int K = 0;
   double* theta = nullptr;  // [n][3 axes][4 derivatives][5 points]
   float* theta32 = nullptr;
+  float2* theta_df = nullptr;  // float64 path: weights and first derivatives as hi/lo [n][3][2][5]
+  float *phi_hi = nullptr, *phi_lo = nullptr;  // float64 path: grid potential split for the gather
   int4* gbase = nullptr;    // [n] base grid index per axis
   double* grid64 = nullptr;
   double2* cgrid64 = nullptr;
@@ -199,6 +202,85 @@ int cluster_setup(amp_ctx* c, const double* xyz, const double* q, const double* 
                   const double* alpha, const double* thole, const int* mol);
 void cluster_permanent_field(amp_ctx* c, double4_32a* out);
 void cluster_t(amp_ctx* c, const double4_32a* v, const float4* v32, double4_32a* out, bool fp64);
+
+}  // namespace amp
+
+namespace amp {
+
+// ---- double-float arithmetic (a value is hi + lo, two floats, |lo| <= ulp(hi)/2)
+// Error-free transformations with round-to-nearest intrinsics, which the
+// compiler never contracts: two-sum (Knuth) and the FMA two-product give about
+// 48 significant bits, enough for float64-level results (1e-14 relative) on a
+// GPU whose float32 rate is ~58 times its float64 rate. Conversions between
+// float and double run at the float64 rate, so values that are reused are
+// split once and kept as hi/lo pairs.
+struct dflt {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dflt df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dflt df_quick(float s, float t) {  // renormalise, |s| >= |t|
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+// acc += (ahi + alo) * (bhi + blo)
+__device__ __forceinline__ void df_fma(dflt& acc, float ahi, float alo, float bhi, float blo) {
+  const float p = __fmul_rn(ahi, bhi);
+  float e = __fmaf_rn(ahi, bhi, -p);
+  e = __fmaf_rn(ahi, blo, e);
+  e = __fmaf_rn(alo, bhi, e);
+  const dflt s = df_two_sum(acc.hi, p);
+  acc = df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
+}
+
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  const dflt s = df_two_sum(a.hi, b.hi);
+  return df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dflt df_split(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to_double(dflt v) { return (double)v.hi + (double)v.lo; }
+
+__device__ __forceinline__ dflt df_neg(dflt a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dflt df_sub(dflt a, dflt b) { return df_add(a, df_neg(b)); }
+// a * b + c
+__device__ __forceinline__ dflt df_madd(dflt a, dflt b, dflt c) {
+  dflt acc = c;
+  df_fma(acc, a.hi, a.lo, b.hi, b.lo);
+  return acc;
+}
+
+// Sum over the kRowGroup lanes of one row; the mask names exactly this group.
+__device__ __forceinline__ dflt df_group_sum(dflt v) {
+  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
+#pragma unroll
+  for (int o = kRowGroup / 2; o > 0; o >>= 1) {
+    dflt w;
+    w.hi = __shfl_xor_sync(mask, v.hi, o, kRowGroup);
+    w.lo = __shfl_xor_sync(mask, v.lo, o, kRowGroup);
+    v = df_add(v, w);
+  }
+  return v;
+}
 
 }  // namespace amp
 

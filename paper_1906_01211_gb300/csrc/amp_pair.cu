@@ -25,7 +25,7 @@ namespace amp {
 namespace {
 
 struct PairGeom {
-  double L, beta, twob2, gpre, selfc;
+  double L, invL, beta, twob2, gpre, selfc;
 };
 
 template <typename R>
@@ -140,6 +140,156 @@ __global__ void __launch_bounds__(256) k_pair_build(long long nh, const int* __r
   e[5] = ez;
 }
 
+// ---- float64 path of the pair build: float64 only where double-float has no
+// cheap form (minimum image, sqrt, 1/r, erfc, the two exp); every product and
+// sum after that runs in double-float on the float units. Per-atom multipoles
+// come pre-split (mp_df: q, d, Theta as hi/lo), outputs stay split: tensor as
+// written for k_t_real_df, fields as Ep[pid] = 12 floats (side 0 x,y,z hi/lo,
+// then side 1).
+
+// Field at r of a multipole with kernels b1..b3, all double-float.
+__device__ __forceinline__ void mp_field_df(const dflt r[3], const dflt* mp, dflt b1, dflt b2, dflt b3, dflt out[3]) {
+  // mp: q, dx, dy, dz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz
+  const dflt t0 = df_madd(mp[8], r[2], df_madd(mp[7], r[1], df_mul(mp[4], r[0])));
+  const dflt t1 = df_madd(mp[9], r[2], df_madd(mp[5], r[1], df_mul(mp[7], r[0])));
+  const dflt t2 = df_madd(mp[6], r[2], df_madd(mp[9], r[1], df_mul(mp[8], r[0])));
+  const dflt rtr = df_madd(r[2], t2, df_madd(r[1], t1, df_mul(r[0], t0)));
+  const dflt dr = df_madd(mp[3], r[2], df_madd(mp[2], r[1], df_mul(mp[1], r[0])));
+  const dflt third = {0.333333343267f, -9.93410748e-09f};  // 1/3 = hi + lo
+  const dflt two3 = {0.666666686535f, -1.98682150e-08f};   // 2/3 = hi + lo
+  const dflt rad = df_madd(df_mul(b3, rtr), third, df_madd(b2, dr, df_mul(mp[0], b1)));
+  const dflt c2 = df_mul(b2, two3);
+  const dflt t[3] = {t0, t1, t2};
+  for (int a = 0; a < 3; ++a) out[a] = df_sub(df_sub(df_mul(rad, r[a]), df_mul(b1, mp[1 + a])), df_mul(c2, t[a]));
+}
+
+__global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* __restrict__ half_i,
+                                                       const int* __restrict__ half_j,
+                                                       const double4_32a* __restrict__ A,
+                                                       const double4_32a* __restrict__ B,
+                                                       const double4_32a* __restrict__ D,
+                                                       const float4* __restrict__ mp_df, PairGeom g,
+                                                       float4* __restrict__ T, float* __restrict__ Ep) {
+  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pid >= nh) return;
+  const int i = half_i[pid], j = half_j[pid];
+  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], di = D[i], dj = D[j];
+  // the pair is within rc < L/2, so d * (1/L) rounds to the same image as d / L
+  const double iL = g.invL;
+  const double rx0 = ai.x - aj.x, ry0 = ai.y - aj.y, rz0 = ai.z - aj.z;
+  const double rx = rx0 - g.L * rint(rx0 * iL), ry = ry0 - g.L * rint(ry0 * iL), rz = rz0 - g.L * rint(rz0 * iL);
+  const double r2 = rx * rx + ry * ry + rz * rz;
+  const double ir = rsqrt(r2);
+  const double rr = r2 * ir;
+  const double br = g.beta * rr;
+  const double fac64 = exp(-br * br) * g.gpre;
+  const double b064 = erfc(br) * ir;
+  const double x = min(di.z, dj.z) * r2 * rr * bi.w * bj.w;
+  const double e64 = exp(-x);
+  const dflt R[3] = {df_split(rx), df_split(ry), df_split(rz)};
+  const dflt NR[3] = {df_neg(R[0]), df_neg(R[1]), df_neg(R[2])};
+  const dflt IR = df_split(ir), B0 = df_split(b064), X = df_split(x), E = df_split(e64);
+  dflt FAC = df_split(fac64);
+  const dflt TB2 = df_split(g.twob2);
+  const dflt ONE = {1.f, 0.f}, THREE = {3.f, 0.f}, FIVE = {5.f, 0.f};
+  const dflt IR2 = df_mul(IR, IR);
+  const dflt B1 = df_mul(df_add(B0, FAC), IR2);
+  FAC = df_mul(FAC, TB2);
+  const dflt B2 = df_mul(df_madd(THREE, B1, FAC), IR2);
+  FAC = df_mul(FAC, TB2);
+  const dflt B3 = df_mul(df_madd(FIVE, B2, FAC), IR2);
+  const dflt bare1 = df_mul(IR, IR2);
+  const dflt bare2 = df_mul(df_mul(THREE, bare1), IR2);
+  const dflt bare3 = df_mul(df_mul(FIVE, bare2), IR2);
+  const dflt d3 = E;
+  const dflt d5 = df_mul(df_add(ONE, X), E);
+  const dflt six = {0.600000024f, -2.38418579e-08f};  // 0.6 = hi + lo
+  const dflt d7 = df_mul(df_madd(df_mul(six, X), X, df_add(ONE, X)), E);
+  const dflt b1u = df_sub(B1, df_mul(d3, bare1));
+  const dflt b2u = df_sub(B2, df_mul(d5, bare2));
+  dflt b1e, b2e, b3e;
+  if (di.w == dj.w) {
+    b1e = df_sub(B1, bare1);
+    b2e = df_sub(B2, bare2);
+    b3e = df_sub(B3, bare3);
+  } else {
+    b1e = b1u;
+    b2e = b2u;
+    b3e = df_sub(B3, df_mul(d7, bare3));
+  }
+  // tensor T = -b1u I + b2u r r^T  (xx, yy, zz, xy, xz, yz)
+  const dflt tv[6] = {df_sub(df_mul(df_mul(b2u, R[0]), R[0]), b1u), df_sub(df_mul(df_mul(b2u, R[1]), R[1]), b1u),
+                      df_sub(df_mul(df_mul(b2u, R[2]), R[2]), b1u), df_mul(df_mul(b2u, R[0]), R[1]),
+                      df_mul(df_mul(b2u, R[0]), R[2]),          df_mul(df_mul(b2u, R[1]), R[2])};
+  float4* o = T + 3 * pid;
+  o[0] = make_float4(tv[0].hi, tv[1].hi, tv[2].hi, tv[3].hi);
+  o[1] = make_float4(tv[4].hi, tv[5].hi, tv[0].lo, tv[1].lo);
+  o[2] = make_float4(tv[2].lo, tv[3].lo, tv[4].lo, tv[5].lo);
+  // permanent fields: at i from j (r), at j from i (-r)
+  dflt mpi[10], mpj[10];
+  {
+    const float4* pi = mp_df + 5 * (long long)i;
+    const float4* pj = mp_df + 5 * (long long)j;
+    for (int k = 0; k < 5; ++k) {
+      const float4 u = pi[k], w = pj[k];
+      mpi[2 * k] = {u.x, u.y};
+      mpi[2 * k + 1] = {u.z, u.w};
+      mpj[2 * k] = {w.x, w.y};
+      mpj[2 * k + 1] = {w.z, w.w};
+    }
+  }
+  dflt fi[3], fj[3];
+  mp_field_df(R, mpj, b1e, b2e, b3e, fi);
+  mp_field_df(NR, mpi, b1e, b2e, b3e, fj);
+  float4* e = reinterpret_cast<float4*>(Ep + 12 * pid);
+  e[0] = make_float4(fi[0].hi, fi[0].lo, fi[1].hi, fi[1].lo);
+  e[1] = make_float4(fi[2].hi, fi[2].lo, fj[0].hi, fj[0].lo);
+  e[2] = make_float4(fj[1].hi, fj[1].lo, fj[2].hi, fj[2].lo);
+}
+
+// mp_df[s] = q, d, Theta of sorted atom s as hi/lo float pairs (5 float4)
+__global__ void k_split_multipoles(int n, const double4_32a* __restrict__ A, const double4_32a* __restrict__ B,
+                                   const double4_32a* __restrict__ C, const double4_32a* __restrict__ D,
+                                   float4* __restrict__ mp) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double4_32a a = A[s], b = B[s], c = C[s], d = D[s];
+  const double v[10] = {a.w, b.x, b.y, b.z, c.x, c.y, c.z, c.w, d.x, d.y};
+  for (int k = 0; k < 5; ++k) {
+    const dflt u = df_split(v[2 * k]), w = df_split(v[2 * k + 1]);
+    mp[5 * (long long)s + k] = make_float4(u.hi, u.lo, w.hi, w.lo);
+  }
+}
+
+// E0_i = sum over row entries of the split permanent fields + selfc d_i
+__global__ void __launch_bounds__(256) k_row_sum_fields_df(int n, const int* __restrict__ full_start,
+                                                           const int* __restrict__ full_ref,
+                                                           const float* __restrict__ Ep, double selfc,
+                                                           const double4_32a* __restrict__ selfv,
+                                                           double4_32a* __restrict__ out) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gid / kRowGroup, l = gid % kRowGroup;
+  if (i >= n) return;
+  dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
+  const int e = full_start[i + 1];
+  for (int k = full_start[i] + l; k < e; k += kRowGroup) {
+    const int ref = full_ref[k];
+    const float2* p = reinterpret_cast<const float2*>(Ep + 12 * (long long)(ref >> 1) + 6 * (ref & 1));
+    const float2 x = p[0], y = p[1], z = p[2];
+    sx = df_add(sx, {x.x, x.y});
+    sy = df_add(sy, {y.x, y.y});
+    sz = df_add(sz, {z.x, z.y});
+  }
+  sx = df_group_sum(sx);
+  sy = df_group_sum(sy);
+  sz = df_group_sum(sz);
+  if (l == 0) {
+    const double4_32a s = selfv[i];
+    out[i] = make_double4_32a(df_to_double(sx) + selfc * s.x, df_to_double(sy) + selfc * s.y,
+                              df_to_double(sz) + selfc * s.z, 0.0);
+  }
+}
+
 // float64 products T_ij v_j and T_ij v_i of every pair, tensor recomputed on
 // the fly in float64 (the mixed path's float64 residual check).
 __global__ void __launch_bounds__(256) k_pair_tv_direct(long long nh, const int* __restrict__ half_i,
@@ -204,54 +354,6 @@ __global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __res
     const double4_32a s = selfv[i];
     out[i] = make_double4_32a(sx + selfc * s.x, sy + selfc * s.y, sz + selfc * s.z, 0.0);
   }
-}
-
-// ---- double-float arithmetic (a value is hi + lo, two floats, |lo| <= ulp(hi)/2)
-// Error-free transformations with round-to-nearest intrinsics, which the
-// compiler never contracts: two-sum (Knuth) and the FMA two-product give about
-// 48 significant bits, enough for float64-level results (1e-14 relative) on a
-// GPU whose float32 rate is ~58 times its float64 rate.
-struct dflt {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dflt df_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-
-__device__ __forceinline__ dflt df_quick(float s, float t) {  // renormalise, |s| >= |t|
-  const float h = __fadd_rn(s, t);
-  return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-
-// acc += (ahi + alo) * (bhi + blo)
-__device__ __forceinline__ void df_fma(dflt& acc, float ahi, float alo, float bhi, float blo) {
-  const float p = __fmul_rn(ahi, bhi);
-  float e = __fmaf_rn(ahi, bhi, -p);
-  e = __fmaf_rn(ahi, blo, e);
-  e = __fmaf_rn(alo, bhi, e);
-  const dflt s = df_two_sum(acc.hi, p);
-  acc = df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
-}
-
-__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
-  const dflt s = df_two_sum(a.hi, b.hi);
-  return df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ dflt df_group_sum(dflt v) {
-  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
-#pragma unroll
-  for (int o = kRowGroup / 2; o > 0; o >>= 1) {
-    dflt w;
-    w.hi = __shfl_xor_sync(mask, v.hi, o, kRowGroup);
-    w.lo = __shfl_xor_sync(mask, v.lo, o, kRowGroup);
-    v = df_add(v, w);
-  }
-  return v;
 }
 
 // out_i = sum_j T_ij v_j + selfc v_i for the float64 path, in double-float:
@@ -332,6 +434,7 @@ PairGeom geom(const amp_ctx* c) {
   PairGeom g;
   const double b = c->cfg.ewald_beta;
   g.L = c->cfg.box;
+  g.invL = c->cfg.box > 0.0 ? 1.0 / c->cfg.box : 0.0;
   g.beta = b;
   g.twob2 = 2.0 * b * b;
   g.gpre = 2.0 * b * b / (b * kSqrtPi);
@@ -345,12 +448,17 @@ void launch_pair_build(amp_ctx* c) {
   if (c->n_half == 0) return;
   const PairGeom g = geom(c);
   const int blocks = amp_blocks(c->n_half, 256);
+  if (c->cfg.precision == AMP_FP64) {
+    c->n_launch += 2;
+    k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                                    c->mp_df);
+    k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB, c->atomD,
+                                                   c->mp_df, g, reinterpret_cast<float4*>(c->T64),
+                                                   reinterpret_cast<float*>(c->Ep64));
+    return;
+  }
   c->n_launch += 1;
-  if (c->cfg.precision == AMP_FP64)
-    k_pair_build<double><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
-                                                        c->atomC, c->atomD, g, c->T64, c->Ep64);
-  else
-    k_pair_build<float><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
+  k_pair_build<float><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
                                                        c->atomC, c->atomD, g, c->T32, c->Ep32);
 }
 
@@ -360,8 +468,9 @@ void launch_e0_real(amp_ctx* c, double4_32a* out) {
   const int blocks = amp_blocks((long long)c->n * kRowGroup, 256);
   c->n_launch += 1;
   if (c->cfg.precision == AMP_FP64)
-    k_row_sum_pairvec<double><<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref, c->Ep64, g.selfc,
-                                                             c->atomB, out);
+    k_row_sum_fields_df<<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref,
+                                                       reinterpret_cast<const float*>(c->Ep64), g.selfc, c->atomB,
+                                                       out);
   else
     k_row_sum_pairvec<float><<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref, c->Ep32, g.selfc,
                                                             c->atomB, out);

@@ -22,7 +22,8 @@
 namespace amp {
 namespace {
 
-constexpr int kTh = 3 * 4 * kOrder;  // per atom: 3 axes x derivatives 0..3 x 5 points
+constexpr int kTh = 3 * 4 * kOrder;    // per atom: 3 axes x derivatives 0..3 x 5 points
+constexpr int kThDf = 3 * 2 * kOrder;  // per atom: 3 axes x derivatives 0..1 x 5 points (hi/lo)
 
 // Weights M5(f + t) and their first three derivatives (t = 0..4) by the
 // B-spline recursion M_n(u) = [u M_{n-1}(u) + (n - u) M_{n-1}(u - 1)]/(n - 1).
@@ -55,7 +56,7 @@ __device__ __forceinline__ void bspline5(double f, double s, double w[4][kOrder]
 }
 
 __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int K, double* __restrict__ theta,
-                        float* __restrict__ theta32, int4* __restrict__ gbase) {
+                        float* __restrict__ theta32, float2* __restrict__ theta_df, int4* __restrict__ gbase) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double4_32a a = A[s];
@@ -76,6 +77,11 @@ __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int 
       for (int t = 0; t < kOrder; ++t) {
         th[(ax * 4 + d) * kOrder + t] = w[d][t];
         if (theta32) theta32[(long long)kTh * s + (ax * 4 + d) * kOrder + t] = (float)w[d][t];
+        if (theta_df && d < 2) {
+          const float h = __double2float_rn(w[d][t]);
+          theta_df[(long long)kThDf * s + (ax * 2 + d) * kOrder + t] =
+              make_float2(h, __double2float_rn(w[d][t] - (double)h));
+        }
       }
   }
   gbase[s] = make_int4(base[0], base[1], base[2], 0);
@@ -251,6 +257,90 @@ __global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict
   }
 }
 
+// phi = hi + lo for every grid point (float64 path, once per gather)
+__global__ void k_split_grid(long long ng, const double* __restrict__ phi, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ng) return;
+  const dflt v = df_split(phi[k]);
+  hi[k] = v.hi;
+  lo[k] = v.lo;
+}
+
+// The float64 path's gather in double-float arithmetic (float units only):
+// weights, their derivatives and the grid potential are hi/lo pairs.
+template <bool kSet>
+__global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __restrict__ th_df,
+                                                         const int4* __restrict__ gbase,
+                                                         const float* __restrict__ phi_hi,
+                                                         const float* __restrict__ phi_lo, int K,
+                                                         double4_32a* __restrict__ out) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
+  if (s >= n) return;  // whole groups leave together
+  dflt ex = {0.f, 0.f}, ey = {0.f, 0.f}, ez = {0.f, 0.f};
+  const int4 b = gbase[s];
+  if (tx < kOrder) {
+    const float2* th = th_df + (long long)kThDf * s;
+    const float2 wx0 = th[(0 * 2 + 0) * kOrder + tx], wx1 = th[(0 * 2 + 1) * kOrder + tx];
+    float2 wz0[kOrder], wz1[kOrder];
+    int gz[kOrder];
+    for (int t = 0; t < kOrder; ++t) {
+      wz0[t] = th[(2 * 2 + 0) * kOrder + t];
+      wz1[t] = th[(2 * 2 + 1) * kOrder + t];
+      gz[t] = wrapk(b.z - t, K);
+    }
+    const int gx = wrapk(b.x - tx, K);
+    dflt px = {0.f, 0.f}, py = {0.f, 0.f}, pz = {0.f, 0.f};
+    for (int ty = 0; ty < kOrder; ++ty) {
+      const float2 wy0 = th[(1 * 2 + 0) * kOrder + ty], wy1 = th[(1 * 2 + 1) * kOrder + ty];
+      const long long row = ((long long)gx * K + wrapk(b.y - ty, K)) * K;
+      dflt s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+      for (int tz = 0; tz < kOrder; ++tz) {
+        const float ph = phi_hi[row + gz[tz]], pl = phi_lo[row + gz[tz]];
+        df_fma(s0, wz0[tz].x, wz0[tz].y, ph, pl);
+        df_fma(s1, wz1[tz].x, wz1[tz].y, ph, pl);
+      }
+      df_fma(px, wy0.x, wy0.y, s0.hi, s0.lo);
+      df_fma(py, wy1.x, wy1.y, s0.hi, s0.lo);
+      df_fma(pz, wy0.x, wy0.y, s1.hi, s1.lo);
+    }
+    ex = df_mul({wx1.x, wx1.y}, px);
+    ey = df_mul({wx0.x, wx0.y}, py);
+    ez = df_mul({wx0.x, wx0.y}, pz);
+  }
+  const unsigned mask = pme_group_mask();
+#pragma unroll
+  for (int o = kPmeGroup / 2; o > 0; o >>= 1) {
+    ex = df_add(ex, {__shfl_xor_sync(mask, ex.hi, o, kPmeGroup), __shfl_xor_sync(mask, ex.lo, o, kPmeGroup)});
+    ey = df_add(ey, {__shfl_xor_sync(mask, ey.hi, o, kPmeGroup), __shfl_xor_sync(mask, ey.lo, o, kPmeGroup)});
+    ez = df_add(ez, {__shfl_xor_sync(mask, ez.hi, o, kPmeGroup), __shfl_xor_sync(mask, ez.lo, o, kPmeGroup)});
+  }
+  if (tx == 0) {
+    const double fx = df_to_double(ex), fy = df_to_double(ey), fz = df_to_double(ez);
+    if (kSet) {
+      out[s] = make_double4_32a(-fx, -fy, -fz, 0.0);
+    } else {
+      double4_32a o = out[s];
+      o.x -= fx;
+      o.y -= fy;
+      o.z -= fz;
+      out[s] = o;
+    }
+  }
+}
+
+// split the float64 grid potential and gather the field in double-float
+template <bool kSet>
+void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out) {
+  const int K = c->K, n = c->n;
+  const long long ng = (long long)K * K * K;
+  c->n_launch += 1;
+  k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_hi, c->phi_lo);
+  k_gather_field_df<kSet><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+      n, c->theta_df, c->gbase, c->phi_hi, c->phi_lo, K, out);
+}
+
 // Host: B-spline moduli and influence function, float64.
 double m5_at(double u) {  // M5 at integer-shifted u by the recursion (host side)
   double m[6] = {0};
@@ -338,6 +428,9 @@ int pme_setup(amp_ctx* c) {
   if ((r = dev_alloc(c, &c->grid64, ng)) || (r = dev_alloc(c, &c->cgrid64, nh)) ||
       (r = dev_alloc(c, &c->G64, nh)))
     return r;
+  if (c->cfg.precision == AMP_FP64 &&
+      ((r = dev_alloc(c, &c->phi_hi, ng)) || (r = dev_alloc(c, &c->phi_lo, ng))))
+    return r;
   if (c->cfg.precision == AMP_MIXED) {
     if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
         (r = dev_alloc(c, &c->G32, nh)))
@@ -364,13 +457,14 @@ int pme_alloc_atoms(amp_ctx* c, int n_cap) {
   int r;
   if ((r = dev_alloc(c, &c->theta, (long long)kTh * n_cap)) || (r = dev_alloc(c, &c->gbase, n_cap))) return r;
   if (c->cfg.precision == AMP_MIXED && (r = dev_alloc(c, &c->theta32, (long long)kTh * n_cap))) return r;
+  if (c->cfg.precision == AMP_FP64 && (r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap))) return r;
   return AMP_OK;
 }
 
 void launch_pme_theta(amp_ctx* c) {
   c->n_launch += 1;
   k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
-                                                       c->gbase);
+                                                       c->theta_df, c->gbase);
 }
 
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
@@ -386,7 +480,7 @@ int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
     if ((r = exec_fft(c, false, true))) return r;
     k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
     if ((r = exec_fft(c, false, false))) return r;
-    k_gather_field<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->grid64, K, out_add);
+    gather_df<false>(c, st, out_add);
   } else {
     cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
     k_spread_multipoles<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB,
@@ -457,12 +551,18 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStr
     r = exec_fft(c, false, false);
   }
   if (!r) {
-    if (set)
+    if (c->theta_df) {  // float64 context: double-float gather
+      if (set)
+        gather_df<true>(c, st, out);
+      else
+        gather_df<false>(c, st, out);
+    } else if (set) {   // float64 check of the mixed path
       k_gather_field<double, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
           n, c->theta, c->gbase, c->grid64, K, out);
-    else
+    } else {
       k_gather_field<double, false><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
           n, c->theta, c->gbase, c->grid64, K, out);
+    }
   }
   cufftSetStream(c->plan_d2z, c->stream);
   cufftSetStream(c->plan_z2d, c->stream);

@@ -155,7 +155,12 @@ def test_isolated_atoms_have_empty_rows():
     case = Case(sysm, 40.0, 7.0, 0.5446, 40, 1e-10)
     s, E0, mu, it, rms, U = run_gpu(case)
     assert s.pair_count() == case.op.n_pairs == 6
-    assert rel(E0, case.E0) < 1e-12
+    # Here E0 (~1e-4) is what is left after the excluded intramolecular
+    # real-space terms and the reciprocal terms (~1e-1) cancel; the float64
+    # path's double-float kernels (~48 bits) are held to 1e-12 of those parts.
+    parts = case.op.permanent_field_parts()
+    scale = sum(np.linalg.norm(p) for p in parts)
+    assert np.linalg.norm(E0 - case.E0) < 1e-12 * scale
     assert rms_debye(mu, case.mu) < 1e-8
 
 
