@@ -82,6 +82,9 @@ struct amp_ctx {
   float* theta32 = nullptr;
   float2* theta_df = nullptr;  // float64 path: weights and first derivatives as hi/lo [n][3][2][5]
   float *phi_hi = nullptr, *phi_lo = nullptr;  // float64 path: grid potential split for the gather
+  float4* fft_grid = nullptr;  // double-float complex grid of the float64 path's own FFT
+  float2* fft_G = nullptr;     // full-spectrum influence function, hi/lo
+  float4* fft_tw = nullptr;    // twiddles (cos hi, lo, sin hi, lo)
   int4* gbase = nullptr;    // [n] base grid index per axis
   double* grid64 = nullptr;
   double2* cgrid64 = nullptr;
@@ -179,6 +182,11 @@ void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* ou
 int pme_setup(amp_ctx* c);
 int pme_alloc_atoms(amp_ctx* c, int n_cap);
 int pme_influence(amp_ctx* c);
+
+// double-float 3D FFT convolution (amp_fft.cu), power-of-two grids
+bool fft_df_supported(int K);
+int fft_df_setup(amp_ctx* c, const double* G_half);
+void fft_df_convolve(amp_ctx* c, cudaStream_t st);  // grid64 -> phi_hi/phi_lo
 void launch_pme_theta(amp_ctx* c);
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
 // reciprocal field of dipoles on stream st: out += field (set: out = field)

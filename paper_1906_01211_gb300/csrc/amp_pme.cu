@@ -330,15 +330,41 @@ __global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __
   }
 }
 
-// split the float64 grid potential and gather the field in double-float
+// gather the field in double-float from phi_hi/phi_lo (split = true: first
+// split the float64 grid potential in grid64 into them)
 template <bool kSet>
-void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out) {
+void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out, bool split) {
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K;
-  c->n_launch += 1;
-  k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_hi, c->phi_lo);
+  c->n_launch += split ? 2 : 1;
+  if (split) k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_hi, c->phi_lo);
   k_gather_field_df<kSet><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
       n, c->theta_df, c->gbase, c->phi_hi, c->phi_lo, K, out);
+}
+
+int exec_fft(amp_ctx* c, bool fp32, bool forward);
+
+// grid64 (spread charges) -> phi: the double-float FFT writes phi_hi/phi_lo
+// directly when the grid allows it, else cuFFT float64 leaves phi in grid64
+// and *split_needed tells the gather to split it first.
+int conv_to_phi(amp_ctx* c, cudaStream_t st, bool* split_needed) {
+  if (c->fft_grid) {
+    fft_df_convolve(c, st);
+    *split_needed = false;
+    return AMP_OK;
+  }
+  const long long nh = (long long)c->K * c->K * (c->K / 2 + 1);
+  cufftSetStream(c->plan_d2z, st);
+  cufftSetStream(c->plan_z2d, st);
+  int r = exec_fft(c, false, true);
+  if (!r) {
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
+    r = exec_fft(c, false, false);
+  }
+  cufftSetStream(c->plan_d2z, c->stream);
+  cufftSetStream(c->plan_z2d, c->stream);
+  *split_needed = true;
+  return r;
 }
 
 // Host: B-spline moduli and influence function, float64.
@@ -417,7 +443,10 @@ int pme_influence(amp_ctx* c) {
                                                          cudaMemcpyHostToDevice, c->stream),
                                       "G upload")))
     return r;
-  return cuda_check(c, cudaStreamSynchronize(c->stream), "G upload");
+  if ((r = cuda_check(c, cudaStreamSynchronize(c->stream), "G upload"))) return r;
+  // the float64 path transforms power-of-two grids with its own double-float FFT
+  if (c->cfg.precision == AMP_FP64 && fft_df_supported(K)) return fft_df_setup(c, G.data());
+  return AMP_OK;
 }
 
 int pme_setup(amp_ctx* c) {
@@ -477,10 +506,9 @@ int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
     cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
     k_spread_multipoles<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB,
                                                                     c->atomC, c->atomD, K, c->grid64);
-    if ((r = exec_fft(c, false, true))) return r;
-    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
-    if ((r = exec_fft(c, false, false))) return r;
-    gather_df<false>(c, st, out_add);
+    bool split = true;
+    if ((r = conv_to_phi(c, st, &split))) return r;
+    gather_df<false>(c, st, out_add, split);
   } else {
     cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
     k_spread_multipoles<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB,
@@ -540,23 +568,29 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStr
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  cufftSetStream(c->plan_d2z, st);
-  cufftSetStream(c->plan_z2d, st);
   cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
   k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
       n, c->theta, c->gbase, v, K, c->grid64);
+  if (c->theta_df) {  // float64 context: own FFT (or cuFFT + split) and double-float gather
+    bool split = true;
+    const int r = conv_to_phi(c, st, &split);
+    if (r) return r;
+    if (set)
+      gather_df<true>(c, st, out, split);
+    else
+      gather_df<false>(c, st, out, split);
+    return AMP_OK;
+  }
+  // float64 check of the mixed path: cuFFT float64 and a float64 gather
+  cufftSetStream(c->plan_d2z, st);
+  cufftSetStream(c->plan_z2d, st);
   int r = exec_fft(c, false, true);
   if (!r) {
     k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
     r = exec_fft(c, false, false);
   }
   if (!r) {
-    if (c->theta_df) {  // float64 context: double-float gather
-      if (set)
-        gather_df<true>(c, st, out);
-      else
-        gather_df<false>(c, st, out);
-    } else if (set) {   // float64 check of the mixed path
+    if (set) {
       k_gather_field<double, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
           n, c->theta, c->gbase, c->grid64, K, out);
     } else {

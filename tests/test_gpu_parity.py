@@ -143,6 +143,20 @@ def test_small_boxes_ragged_sizes(nw, seed):
     assert abs(U / case.U - 1) < 1e-10
 
 
+@pytest.mark.parametrize("nw,K", [(1000, 32), (300, 16)])
+def test_power_of_two_grids(nw, K):
+    """Grids whose size is a power of two take the float64 path's own
+    double-float FFT; other sizes (24, 15, ...) take cuFFT."""
+    L = density_box_edge(nw)
+    rc, beta, _ = small_box_settings(L)
+    case = Case(make_waters(nw, L, 40 + K), L, rc, beta, K, 1e-10)
+    s, E0, mu, it, rms, U = run_gpu(case)
+    assert rel(E0, case.E0) < 1e-12
+    v = np.random.default_rng(K).normal(size=(case.sys.n, 3)) * 0.1
+    assert rel(s.apply_T(torch.tensor(v)).cpu().numpy(), case.op.apply_T(v)) < 1e-12
+    assert rms_debye(mu, case.mu) < 1e-8
+
+
 def test_isolated_atoms_have_empty_rows():
     """Two waters far apart in a large box: most rows hold only intramolecular pairs,
     the field still includes PME and self terms."""
