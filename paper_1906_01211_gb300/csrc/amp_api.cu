@@ -4,6 +4,7 @@
 // operator (tmatxb_pme2), solve, energy (epolar1).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -127,7 +128,7 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
   c->cluster = cluster;
   c->stream = (cudaStream_t)cuda_stream;
   int r;
-  if ((r = dev_alloc(c, &c->flags, 4)) || (r = dev_alloc(c, &c->iflags, 4)) || (r = dev_alloc(c, &c->scal, 8)) ||
+  if ((r = dev_alloc(c, &c->flags, 4)) || (r = dev_alloc(c, &c->iflags, 8)) || (r = dev_alloc(c, &c->scal, 8)) ||
       (r = dev_alloc(c, &c->partials, 4 * kReduceBlocks))) {
     amp_destroy(c);
     return r;
@@ -147,6 +148,13 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return r;
   }
+  // Fused (cooperative) PCG iteration where the device offers cooperative
+  // launches; AMOEBAPOL_PCG_SEPARATE=1 selects the four-kernel iteration.
+  int dev = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  const char* sep = std::getenv("AMOEBAPOL_PCG_SEPARATE");
+  c->coop_ok = coop != 0 && !(sep && sep[0] == '1');
   *out = c;
   return AMP_OK;
 }

@@ -132,6 +132,7 @@ struct amp_ctx {
   double4_32a* cluster_part = nullptr;
   long long cluster_part_cap = 0;
 
+  bool coop_ok = true;         // cooperative PCG iteration kernel usable on this device
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
   amp::Stats stats;

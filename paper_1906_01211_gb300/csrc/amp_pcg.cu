@@ -22,7 +22,8 @@ constexpr int NT = kReduceThreads;
 constexpr int NB = kReduceBlocks;
 
 // iflags: [0] stop, [1] iterations done, [2] converged this iteration,
-//         [3] status (0 running, 1 converged, 2 max_iter, 3 breakdown)
+//         [3] status (0 running, 1 converged, 2 max_iter, 3 breakdown,
+//             4 grid barrier gave up), [4..5] grid barrier count, generation
 // scal:   [0], [1] r.z double buffer indexed by iteration parity,
 //         [2] last RMS (Debye), [3] energy
 enum { F_STOP = 0, F_ITERS = 1, F_CONV = 2, F_STATUS = 3 };
@@ -238,6 +239,162 @@ __global__ void __launch_bounds__(NT) k_pcg_dir(int n, const double4_32a* __rest
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[(it + 1) & 1] = rz;
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
+
+// Grid-wide barrier of a cooperative launch. bar[0] counts arrivals, bar[1]
+// is the generation; both start at zero and the count returns to zero after
+// every completed barrier. The wait is bounded: false when it gave up.
+__device__ bool grid_barrier(unsigned* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire(bar + 1);
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire(bar + 1) == gen) {
+        if (global_ns() - t0 > kBarrierTimeoutNs) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok;
+}
+
+__device__ __forceinline__ void barrier_gave_up(int* fl) {
+  if (threadIdx.x == 0) {
+    atomicExch(fl + F_STATUS, 4);
+    atomicExch(fl + F_STOP, 1);
+  }
+}
+
+// Partials written by other blocks of the same launch: read through L2.
+__device__ __forceinline__ void reduce_partials_cg(const double* part, double& a, double& b) {
+  a = 0.0;
+  b = 0.0;
+  for (int k = threadIdx.x; k < NB; k += NT) {
+    a += __ldcg(part + k);
+    b += __ldcg(part + NB + k);
+  }
+  block_sum2(a, b);
+}
+
+// One PCG iteration after T p, in one cooperative launch: the three vector
+// phases of k_pcg_q, k_pcg_update and k_pcg_dir separated by grid-wide
+// barriers, then the bookkeeping of k_pcg_advance. Every block takes the same
+// branch at each decision (the reduced scalars are identical in all blocks),
+// so either all blocks reach a barrier or none does. A barrier that gives up
+// stops the solve with status 4 and the host repeats it with the four kernels.
+__global__ void __launch_bounds__(NT) k_pcg_iter(int n, double4_32a* __restrict__ mu, double4_32a* __restrict__ r,
+                                                 double4_32a* __restrict__ z, double4_32a* __restrict__ p,
+                                                 double4_32a* __restrict__ q, const double4_32a* __restrict__ t,
+                                                 const double4_32a* __restrict__ t2, const double2* __restrict__ al,
+                                                 float4* __restrict__ p32, float4* __restrict__ plo,
+                                                 double* __restrict__ pa, double* __restrict__ pb,
+                                                 double* __restrict__ scal, int* __restrict__ fl, double tol,
+                                                 int max_iter) {
+  unsigned* bar = reinterpret_cast<unsigned*>(fl + 4);
+  if (fl[F_STOP]) return;
+  const int it = fl[F_ITERS];
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  // q = p/alpha - t; partials p.q
+  double pq = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double ia = al[s].y;
+    const double4_32a pp = p[s], tt = sum_t(t, t2, s);
+    const double4_32a qq = make_double4_32a(pp.x * ia - tt.x, pp.y * ia - tt.y, pp.z * ia - tt.z, 0.0);
+    q[s] = qq;
+    pq += dot3(pp, qq);
+  }
+  write_partials(pa, pq, 0.0);
+  if (!grid_barrier(bar)) return barrier_gave_up(fl);
+  double unused;
+  reduce_partials_cg(pa, pq, unused);
+  if (!(pq > 0.0)) {  // breakdown: operator not positive definite
+    if (lead) {
+      fl[F_ITERS] = it + 1;
+      fl[F_CONV] = -1;
+      fl[F_STOP] = 1;
+      fl[F_STATUS] = 3;
+    }
+    return;
+  }
+  const double gamma = scal[it & 1] / pq;
+  double rz = 0.0, zz = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double a = al[s].x;
+    const double4_32a pp = p[s], qq = q[s];
+    double4_32a m = mu[s], rr = r[s];
+    m.x += gamma * pp.x;
+    m.y += gamma * pp.y;
+    m.z += gamma * pp.z;
+    rr.x -= gamma * qq.x;
+    rr.y -= gamma * qq.y;
+    rr.z -= gamma * qq.z;
+    const double4_32a zz4 = make_double4_32a(a * rr.x, a * rr.y, a * rr.z, 0.0);
+    mu[s] = m;
+    r[s] = rr;
+    z[s] = zz4;
+    rz += dot3(rr, zz4);
+    zz += dot3(zz4, zz4);
+  }
+  write_partials(pb, rz, zz);
+  if (!grid_barrier(bar)) return barrier_gave_up(fl);
+  reduce_partials_cg(pb, rz, zz);
+  const double rms = kDebye * sqrt(zz / (double)n);
+  if (rms < tol) {
+    if (lead) {
+      scal[2] = rms;
+      fl[F_ITERS] = it + 1;
+      fl[F_CONV] = 1;
+      fl[F_STOP] = 1;
+      fl[F_STATUS] = 1;
+    }
+    return;
+  }
+  const double beta = rz / scal[it & 1];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double4_32a zz4 = z[s];
+    double4_32a pp = p[s];
+    pp.x = zz4.x + beta * pp.x;
+    pp.y = zz4.y + beta * pp.y;
+    pp.z = zz4.z + beta * pp.z;
+    p[s] = pp;
+    split_store(pp, p32, plo, s);
+  }
+  if (lead) {
+    scal[2] = rms;
+    scal[(it + 1) & 1] = rz;
+    fl[F_ITERS] = it + 1;
+    if (it + 1 >= max_iter) {
+      fl[F_STOP] = 1;
+      fl[F_STATUS] = 2;
+    }
+  }
+}
+
 __global__ void k_pcg_advance(int* __restrict__ fl, int max_iter) {
   if (fl[F_STOP]) return;
   fl[F_ITERS] += 1;
@@ -392,6 +549,20 @@ static int enqueue_iteration(amp_ctx* c) {
   int r = apply_T_sorted(c, c->pv, c->p32, lo, c->tv, c->trec);
   if (r) return r;
   PhaseScope ps(c, AMP_PHASE_PCG);
+  if (c->coop_ok) {
+    double tol = c->cfg.tol_debye;
+    int max_iter = c->cfg.max_iter;
+    int nn = n;
+    void* args[] = {&nn, &c->mu, &c->res, &c->zv, &c->pv, &c->qv, &c->tv, &c->trec, &c->alph, &c->p32, &lo,
+                    &pa, &pb, &c->scal, &c->iflags, &tol, &max_iter};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_iter, dim3(NB), dim3(NT), args, 0, st);
+    if (e == cudaSuccess) {
+      c->n_launch += 1;
+      return AMP_OK;
+    }
+    cudaGetLastError();  // not co-resident here: use the four-kernel form from now on
+    c->coop_ok = false;
+  }
   c->n_launch += 4;
   k_pcg_q<<<NB, NT, 0, st>>>(n, c->pv, c->tv, c->trec, c->alph, c->qv, pa, c->iflags);
   k_pcg_update<<<NB, NT, 0, st>>>(n, c->mu, c->res, c->zv, c->pv, c->qv, c->alph, pa, pb, c->scal, c->iflags);
@@ -428,7 +599,7 @@ int solve(amp_ctx* c, bool use_guess) {
   int r;
   if (!use_guess) c->n_launch += 1;
   if (!use_guess) k_mu_from_e0<<<NB, NT, 0, st>>>(c->n, c->E0s, c->alph, c->mu);
-  if ((r = cuda_check(c, cudaMemsetAsync(c->iflags, 0, sizeof(int) * 4, st), "memset"))) return r;
+  if ((r = cuda_check(c, cudaMemsetAsync(c->iflags, 0, sizeof(int) * 6, st), "memset"))) return r;
   if ((r = restart(c, !mixed))) return r;
   const int chunk = 4;
   c->stats.fp64_checks = 0;
@@ -450,6 +621,10 @@ int solve(amp_ctx* c, bool use_guess) {
   c->stats.iters = c->hibuf[1];
   c->stats.rms = c->hbuf[2];
   const int status = c->hibuf[3];
+  if (status == 4) {  // the fused iteration's barrier gave up: redo with separate kernels
+    c->coop_ok = false;
+    return solve(c, false);
+  }
   if (status == 3) return fail(c, AMP_ERR_NOT_CONVERGED, "PCG breakdown: p.Ap <= 0");
   if (status != 1)
     return fail(c, AMP_ERR_NOT_CONVERGED, "PCG not converged after %d iterations (RMS %.3e D)", c->stats.iters,

@@ -369,13 +369,11 @@ int conv_to_phi(amp_ctx* c, cudaStream_t st, bool* split_needed) {
 
 // Host: B-spline moduli and influence function, float64.
 double m5_at(double u) {  // M5 at integer-shifted u by the recursion (host side)
-  double m[6] = {0};
   // M2 on [0, 2]
   auto M = [](int n, double x, auto&& self) -> double {
     if (n == 2) return x <= 0.0 || x >= 2.0 ? 0.0 : 1.0 - std::fabs(x - 1.0);
     return (x * self(n - 1, x, self) + (n - x) * self(n - 1, x - 1.0, self)) / (n - 1);
   };
-  (void)m;
   return M(5, u, M);
 }
 
