@@ -4,7 +4,6 @@
 // operator (tmatxb_pme2), solve, energy (epolar1).
 #include <cmath>
 #include <cstdio>
-#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -82,7 +81,8 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->full_start, (void**)&c->half_start, (void**)&c->theta, (void**)&c->theta32,
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
-                   (void**)&c->trec, (void**)&c->plo, (void**)&c->mp_df};
+                   (void**)&c->trec, (void**)&c->plo, (void**)&c->mp_df, (void**)&c->wv,
+                   (void**)&c->theta_df};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -100,6 +100,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = dev_alloc(c, &c->res, cap)) || (r = dev_alloc(c, &c->zv, cap)) || (r = dev_alloc(c, &c->pv, cap)) ||
       (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
       (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)) ||
+      (r = dev_alloc(c, &c->wv, cap)) ||
       (r = dev_alloc(c, &c->mp_df, 5LL * cap)))
     return r;
   c->n_cap = cap;
@@ -129,16 +130,24 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
   c->stream = (cudaStream_t)cuda_stream;
   int r;
   if ((r = dev_alloc(c, &c->flags, 4)) || (r = dev_alloc(c, &c->iflags, 8)) || (r = dev_alloc(c, &c->scal, 8)) ||
-      (r = dev_alloc(c, &c->partials, 4 * kReduceBlocks))) {
+      (r = dev_alloc(c, &c->partials, 4 * kReduceBlocks)) || (r = dev_alloc(c, &c->vmax_part, kReduceBlocks + 2))) {
     amp_destroy(c);
     return r;
+  }
+  if (cudaMemset(c->vmax_part, 0, sizeof(float) * (kReduceBlocks + 2)) != cudaSuccess) {
+    amp_destroy(c);
+    return AMP_ERR_CUDA;
   }
   if (cudaMallocHost((void**)&c->hbuf, 8 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hibuf, 8 * sizeof(int)) != cudaSuccess) {
     amp_destroy(c);
     return AMP_ERR_OOM;
   }
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+  // The reciprocal-space chain runs on the side stream beside the real-space
+  // kernel and is the longer of the two: give its blocks priority.
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     amp_destroy(c);
@@ -148,13 +157,6 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return r;
   }
-  // Fused (cooperative) PCG iteration where the device offers cooperative
-  // launches; AMOEBAPOL_PCG_SEPARATE=1 selects the four-kernel iteration.
-  int dev = 0, coop = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  const char* sep = std::getenv("AMOEBAPOL_PCG_SEPARATE");
-  c->coop_ok = coop != 0 && !(sep && sep[0] == '1');
   *out = c;
   return AMP_OK;
 }

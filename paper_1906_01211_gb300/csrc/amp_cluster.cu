@@ -31,7 +31,9 @@ __global__ void __launch_bounds__(kTileI) k_cluster_field(int n, int cols_per_sl
                                                           const double4_32a* __restrict__ B,
                                                           const double4_32a* __restrict__ C,
                                                           const double4_32a* __restrict__ D, const V* __restrict__ v,
-                                                          double4_32a* __restrict__ part) {
+                                                          double4_32a* __restrict__ part,
+                                                          const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ JTile<R> t;
   const int i = blockIdx.x * kTileI + threadIdx.x;
   const int j0 = blockIdx.y * cols_per_slice;
@@ -122,7 +124,9 @@ __global__ void __launch_bounds__(kTileI) k_cluster_field(int n, int cols_per_sl
   if (i < n) part[(long long)blockIdx.y * n + i] = make_double4_32a(ax, ay, az, 0.0);
 }
 
-__global__ void k_cluster_reduce(int n, int slices, const double4_32a* __restrict__ part, double4_32a* __restrict__ out) {
+__global__ void k_cluster_reduce(int n, int slices, const double4_32a* __restrict__ part, double4_32a* __restrict__ out,
+                                 const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = 0, y = 0, z = 0;
@@ -176,8 +180,8 @@ void launch_field(amp_ctx* c, const V* v, double4_32a* out) {
   dim3 grid((n + kTileI - 1) / kTileI, s);
   c->n_launch += 2;
   k_cluster_field<R, kPerm, V><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD, v,
-                                                                c->cluster_part);
-  k_cluster_reduce<<<amp_blocks(n, 256), 256, 0, c->stream>>>(n, s, c->cluster_part, out);
+                                                                c->cluster_part, c->op_stop);
+  k_cluster_reduce<<<amp_blocks(n, 256), 256, 0, c->stream>>>(n, s, c->cluster_part, out, c->op_stop);
 }
 
 }  // namespace

@@ -5,7 +5,7 @@
 // for one forward + inverse 64^3 pair on GB300); these passes do the same
 // arithmetic in double-float (hi + lo floats, ~48 bits) on the float units.
 // Complex transforms of length K along each axis:
-//   z forward  (DIF, real float64 input split to hi/lo, output bit-reversed)
+//   z forward  (DIF, real float64 or fixed-point input as hi/lo, output bit-reversed)
 //   y forward  (DIF)
 //   x forward, multiply by G at the bit-reversed frequencies, x inverse (DIT)
 //   y inverse  (DIT, bit-reversed input, natural output)
@@ -74,16 +74,48 @@ __device__ __forceinline__ void line_fft(float4* x, const float4* __restrict__ t
   }
 }
 
-// z forward: lines (x, y) contiguous in the real float64 grid.
-template <int K>
-__global__ void __launch_bounds__(32 * kLines) k_fft_z_fwd(const double* __restrict__ q, float4* __restrict__ out,
-                                                          const float4* __restrict__ tw) {
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }  // -126 <= e <= 127
+
+// A 64-bit fixed-point value v * 2^-s as hi/lo floats: v in three pieces of
+// at most 23 bits, each converted exactly, summed error-free.
+__device__ __forceinline__ dflt fixed_to_df(long long v, int s) {
+  const float a = (float)(int)(v >> 40), b = (float)(int)((v >> 20) & 0xFFFFF), c = (float)(int)(v & 0xFFFFF);
+  return df_add(df_two_sum(a * pow2f(40 - s), b * pow2f(20 - s)), dflt{c * pow2f(-s), 0.f});
+}
+
+// z forward: lines (x, y) contiguous in the real grid, either float64 or (kFixed)
+// 64-bit fixed point scaled by 2^fx_info[0], which is zeroed once read.
+template <int K, bool kFixed>
+__global__ void __launch_bounds__(32 * kLines) k_fft_z_fwd(const double* __restrict__ q,
+                                                          unsigned long long* __restrict__ qfx,
+                                                          const int* __restrict__ fx_info, float4* __restrict__ out,
+                                                          const float4* __restrict__ tw, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ float4 sm[kLines][K];
   const long long line0 = (long long)blockIdx.x * kLines;  // line = x*K + y
-  for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-    const int l = e / K, k = e % K;
-    const dflt v = df_split(q[(line0 + l) * K + k]);
-    sm[l][k] = make_float4(v.hi, v.lo, 0.f, 0.f);
+  // the block's kLines lines are one contiguous run of kLines * K values
+  if (kFixed) {
+    const int sfx = fx_info[0];
+    constexpr int kPer = (kLines * K + 32 * kLines - 1) / (32 * kLines);
+    long long v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = threadIdx.x + i * 32 * kLines;
+      v[i] = e < kLines * K ? (long long)qfx[line0 * K + e] : 0ll;
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = threadIdx.x + i * 32 * kLines;
+      if (e >= kLines * K) break;
+      qfx[line0 * K + e] = 0ull;
+      const dflt d = fixed_to_df(v[i], sfx);
+      sm[e / K][e % K] = make_float4(d.hi, d.lo, 0.f, 0.f);
+    }
+  } else {
+    for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
+      const dflt d = df_split(q[line0 * K + e]);
+      sm[e / K][e % K] = make_float4(d.hi, d.lo, 0.f, 0.f);
+    }
   }
   __syncthreads();
   const int w = threadIdx.x >> 5;
@@ -99,7 +131,8 @@ __global__ void __launch_bounds__(32 * kLines) k_fft_z_fwd(const double* __restr
 // 2 = x), kLines neighbouring z per block. kFusedG: forward, * G, inverse.
 template <int K, int kAxis, bool kForward, bool kFusedG>
 __global__ void __launch_bounds__(32 * kLines) k_fft_yx(float4* __restrict__ g, const float4* __restrict__ tw,
-                                                       const float2* __restrict__ Gdf) {
+                                                       const float2* __restrict__ Gdf, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ float4 sm[kLines][K];
   constexpr int kBits = __builtin_ctz(K);
   // block -> (other index o, z0): o = x for the y pass, y for the x pass
@@ -139,8 +172,9 @@ __global__ void __launch_bounds__(32 * kLines) k_fft_yx(float4* __restrict__ g, 
 
 // z inverse: real part of each point written as hi/lo floats.
 template <int K>
-__global__ void __launch_bounds__(32 * kLines) k_fft_z_inv(const float4* __restrict__ g, float* __restrict__ phi_hi,
-                                                          float* __restrict__ phi_lo, const float4* __restrict__ tw) {
+__global__ void __launch_bounds__(32 * kLines) k_fft_z_inv(const float4* __restrict__ g, float2* __restrict__ phi,
+                                                          const float4* __restrict__ tw, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ float4 sm[kLines][K];
   const long long line0 = (long long)blockIdx.x * kLines;
   for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
@@ -154,23 +188,26 @@ __global__ void __launch_bounds__(32 * kLines) k_fft_z_inv(const float4* __restr
   for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
     const int l = e / K, k = e % K;
     const float4 v = sm[l][k];
-    phi_hi[(line0 + l) * K + k] = v.x;
-    phi_lo[(line0 + l) * K + k] = v.y;
+    phi[(line0 + l) * K + k] = make_float2(v.x, v.y);
   }
 }
 
 template <int K>
-void run_conv(amp_ctx* c, cudaStream_t st) {
+void run_conv(amp_ctx* c, cudaStream_t st, bool fixed) {
   const int lines = K * K;
   const int blocks = lines / kLines;
   const float4* tw = c->fft_tw;
   float4* g = c->fft_grid;
   c->n_launch += 5;
-  k_fft_z_fwd<K><<<blocks, 32 * kLines, 0, st>>>(c->grid64, g, tw);
-  k_fft_yx<K, 1, true, false><<<blocks, 32 * kLines, 0, st>>>(g, tw, nullptr);
-  k_fft_yx<K, 2, true, true><<<blocks, 32 * kLines, 0, st>>>(g, tw, c->fft_G);
-  k_fft_yx<K, 1, false, false><<<blocks, 32 * kLines, 0, st>>>(g, tw, nullptr);
-  k_fft_z_inv<K><<<blocks, 32 * kLines, 0, st>>>(g, c->phi_hi, c->phi_lo, tw);
+  const int* stop = c->op_stop;
+  if (fixed)
+    k_fft_z_fwd<K, true><<<blocks, 32 * kLines, 0, st>>>(nullptr, c->gridfx, c->fx_info, g, tw, stop);
+  else
+    k_fft_z_fwd<K, false><<<blocks, 32 * kLines, 0, st>>>(c->grid64, nullptr, nullptr, g, tw, stop);
+  k_fft_yx<K, 1, true, false><<<blocks, 32 * kLines, 0, st>>>(g, tw, nullptr, stop);
+  k_fft_yx<K, 2, true, true><<<blocks, 32 * kLines, 0, st>>>(g, tw, c->fft_G, stop);
+  k_fft_yx<K, 1, false, false><<<blocks, 32 * kLines, 0, st>>>(g, tw, nullptr, stop);
+  k_fft_z_inv<K><<<blocks, 32 * kLines, 0, st>>>(g, c->phi_df, tw, stop);
 }
 
 }  // namespace
@@ -214,13 +251,13 @@ int fft_df_setup(amp_ctx* c, const double* G_half) {
   return cuda_check(c, cudaStreamSynchronize(c->stream), "fft tables");
 }
 
-// phi (hi/lo floats) = conv(grid64) on stream st.
-void fft_df_convolve(amp_ctx* c, cudaStream_t st) {
+// phi (hi/lo floats) = conv(grid) on stream st.
+void fft_df_convolve(amp_ctx* c, cudaStream_t st, bool fixed) {
   switch (c->K) {
-    case 16: run_conv<16>(c, st); break;
-    case 32: run_conv<32>(c, st); break;
-    case 64: run_conv<64>(c, st); break;
-    case 128: run_conv<128>(c, st); break;
+    case 16: run_conv<16>(c, st, fixed); break;
+    case 32: run_conv<32>(c, st, fixed); break;
+    case 64: run_conv<64>(c, st, fixed); break;
+    case 128: run_conv<128>(c, st, fixed); break;
     default: break;
   }
 }

@@ -81,7 +81,16 @@ struct amp_ctx {
   double* theta = nullptr;  // [n][3 axes][4 derivatives][5 points]
   float* theta32 = nullptr;
   float2* theta_df = nullptr;  // float64 path: weights and first derivatives as hi/lo [n][3][2][5]
-  float *phi_hi = nullptr, *phi_lo = nullptr;  // float64 path: grid potential split for the gather
+  float2* phi_df = nullptr;    // float64 path: grid potential as hi/lo pairs for the gather
+  // float64 path's dipole spreading: 64-bit fixed-point grid (integer
+  // atomics, exact and order-independent), scaled by 2^fx_info[0]; fx_info[1]
+  // bounds the atoms that reach one grid point; kcount = atoms per base cell.
+  unsigned long long* gridfx = nullptr;
+  int* fx_info = nullptr;
+  int* kcount = nullptr;
+  // max |hi component| of the last split vector: [0, kReduceBlocks) per block,
+  // [kReduceBlocks] the whole vector, [kReduceBlocks + 1] arrival counter
+  float* vmax_part = nullptr;
   float4* fft_grid = nullptr;  // double-float complex grid of the float64 path's own FFT
   float2* fft_G = nullptr;     // full-spectrum influence function, hi/lo
   float4* fft_tw = nullptr;    // twiddles (cos hi, lo, sin hi, lo)
@@ -99,6 +108,10 @@ struct amp_ctx {
   double4_32a *E0s = nullptr, *mu = nullptr, *res = nullptr, *zv = nullptr, *pv = nullptr;
   double4_32a *qv = nullptr, *tv = nullptr, *tmp = nullptr;
   double4_32a* trec = nullptr;  // reciprocal part of T*v, computed on the side stream
+  double4_32a* wv = nullptr;    // the solver's w = A z
+  // While the solver enqueues an iteration: its device stop flag, which the
+  // operator's kernels test on entry (null: always run).
+  const int* op_stop = nullptr;
   cudaStream_t side = nullptr;  // second stream: PME beside the real-space kernel
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   float4* p32 = nullptr;  // float part of p (mixed: p in float32; float64: hi of hi + lo)
@@ -132,7 +145,6 @@ struct amp_ctx {
   double4_32a* cluster_part = nullptr;
   long long cluster_part_cap = 0;
 
-  bool coop_ok = true;         // cooperative PCG iteration kernel usable on this device
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
   amp::Stats stats;
@@ -187,11 +199,13 @@ int pme_influence(amp_ctx* c);
 // double-float 3D FFT convolution (amp_fft.cu), power-of-two grids
 bool fft_df_supported(int K);
 int fft_df_setup(amp_ctx* c, const double* G_half);
-void fft_df_convolve(amp_ctx* c, cudaStream_t st);  // grid64 -> phi_hi/phi_lo
+// grid64 (fixed = false) or gridfx (fixed = true, zeroed on the way) -> phi_df
+void fft_df_convolve(amp_ctx* c, cudaStream_t st, bool fixed);
 void launch_pme_theta(amp_ctx* c);
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
 // reciprocal field of dipoles on stream st: out += field (set: out = field)
-int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStream_t st, bool set);
+int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* out,
+                     cudaStream_t st, bool set);
 int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream_t st, bool set);
 
 // solver (amp_pcg.cu)

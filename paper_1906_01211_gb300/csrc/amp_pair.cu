@@ -362,16 +362,19 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
                                                    const int* __restrict__ full_j, const int* __restrict__ full_ref,
                                                    const float4* __restrict__ T, double selfc,
                                                    const float4* __restrict__ vhi, const float4* __restrict__ vlo,
-                                                   const double4_32a* __restrict__ v64, double4_32a* __restrict__ out) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gid / kRowGroup, l = gid % kRowGroup;
-  if (i >= n) return;
+                                                   const double4_32a* __restrict__ v64, double4_32a* __restrict__ out,
+                                                   const int* __restrict__ stop) {
+  if (stop && *stop) return;  // the solver has stopped: nothing to compute
+  const int l = threadIdx.x % kRowGroup;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup; i < n; i += gridDim.x * (blockDim.x / kRowGroup)) {
   dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
   const int e = full_start[i + 1];
   for (int k = full_start[i] + l; k < e; k += kRowGroup) {
-    const int j = full_j[k];
-    const float4* t = T + 3 * (long long)(full_ref[k] >> 1);
-    const float4 a = t[0], b = t[1], c = t[2];
+    // pair data is read once per product: streaming loads keep it from
+    // evicting the reciprocal-space grids that run beside this kernel
+    const int j = __ldcs(full_j + k);
+    const float4* t = T + 3 * (long long)(__ldcs(full_ref + k) >> 1);
+    const float4 a = __ldcs(t), b = __ldcs(t + 1), c = __ldcs(t + 2);
     // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
     const float4 h = vhi[j], w = vlo[j];
     df_fma(sx, a.x, b.z, h.x, w.x);
@@ -392,6 +395,7 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
     out[i] = make_double4_32a((double)sx.hi + (double)sx.lo + selfc * vi.x, (double)sy.hi + (double)sy.lo + selfc * vi.y,
                               (double)sz.hi + (double)sz.lo + selfc * vi.z, 0.0);
   }
+  }
 }
 
 // Mixed precision: float32 tensors and float32 copy of v, products summed in
@@ -400,7 +404,8 @@ __global__ void __launch_bounds__(256) k_t_real32(int n, const int* __restrict__
                                                   const int* __restrict__ full_j, const int* __restrict__ full_ref,
                                                   const float* __restrict__ T, double selfc,
                                                   const float4* __restrict__ v32, const double4_32a* __restrict__ v64,
-                                                  double4_32a* __restrict__ out) {
+                                                  double4_32a* __restrict__ out, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gid / kRowGroup, l = gid % kRowGroup;
   if (i >= n) return;
@@ -482,14 +487,14 @@ void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const fl
   c->n_launch += 1;
   k_t_real_df<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
       c->n, c->full_start, c->full_j, c->full_ref, reinterpret_cast<const float4*>(c->T64), g.selfc, vhi, vlo, v,
-      out);
+      out, c->op_stop);
 }
 
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out) {
   const PairGeom g = geom(c);
   c->n_launch += 1;
   k_t_real32<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
-      c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64, out);
+      c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64, out, c->op_stop);
 }
 
 void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out) {

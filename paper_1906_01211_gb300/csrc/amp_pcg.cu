@@ -8,11 +8,22 @@
 //   loop: q = A p; gamma = r.z / p.q; mu += gamma p; r -= gamma q; z = alpha r;
 //         stop if DEBYE sqrt(sum |z_i|^2 / N) < tol;
 //         beta = (r.z)_new / (r.z)_old; p = z + beta p.
-// All scalars stay on the device in float64; the vector updates are fused
-// into three grid-stride kernels whose block partial sums are reduced again
-// by every block in a fixed order (deterministic, no host round trip). Every
-// kernel of an iteration returns at once when the device "stop" flag is set,
-// so the host can enqueue several iterations between flag reads.
+// It is run in the Chronopoulos-Gear arrangement (J. Comput. Appl. Math. 25,
+// 1989), which takes the same steps in exact arithmetic but needs one global
+// reduction per iteration instead of two: the operator is applied to z,
+// w = A z, and q = A p follows by recurrence:
+//   rho = r.z, m = z.w; beta = rho / rho_old (0 at the first step);
+//   gamma = rho / (m - beta rho / gamma_old)  [= r.z / p.q];
+//   p = z + beta p; q = w + beta q; mu += gamma p; r -= gamma q; z = alpha r.
+// On a GPU where a grid-wide synchronisation costs as much as a launch
+// (~2.5 us), this leaves two small kernels per iteration after the operator:
+// k_cg_dots (w, partial r.z and z.w) and k_cg_step (the update, the new z's
+// float split for the operator, and the convergence test by the last block
+// to finish). All scalars stay on the device in float64 and partial sums are
+// reduced in a fixed order (deterministic). Every kernel of an iteration,
+// those of the operator included, returns at once when the device "stop"
+// flag is set, so the host can enqueue several iterations between flag reads
+// without paying for the ones after convergence.
 #include "amp_internal.cuh"
 
 namespace amp {
@@ -21,12 +32,23 @@ namespace {
 constexpr int NT = kReduceThreads;
 constexpr int NB = kReduceBlocks;
 
-// iflags: [0] stop, [1] iterations done, [2] converged this iteration,
-//         [3] status (0 running, 1 converged, 2 max_iter, 3 breakdown,
-//             4 grid barrier gave up), [4..5] grid barrier count, generation
-// scal:   [0], [1] r.z double buffer indexed by iteration parity,
+// Blocks of a vector kernel over n atoms: one element per thread up to NB
+// blocks (grid-stride beyond). Blocks without elements would still pay for
+// their float64 reductions, each warp instruction of which holds the float64
+// pipe for ~64 cycles on this GPU.
+__host__ __device__ __forceinline__ int vec_blocks(int n) {
+  const int b = (n + NT - 1) / NT;
+  return b < 1 ? 1 : (b > NB ? NB : b);
+}
+
+// iflags: [0] stop, [1] iterations done, [2] first step pending (beta = 0),
+//         [3] status (0 running, 1 converged, 2 max_iter, 3 breakdown),
+//         [4] arrival counter of the last-block reductions
+// scal:   [0] rho = r.z of the current z, [1] gamma of the last step,
 //         [2] last RMS (Debye), [3] energy
-enum { F_STOP = 0, F_ITERS = 1, F_CONV = 2, F_STATUS = 3 };
+// partials: [0, NB) r.z and [NB, 2 NB) z.w per block (k_cg_dots);
+//           [2 NB, 3 NB) z.z per block (k_cg_init, k_cg_step)
+enum { F_STOP = 0, F_ITERS = 1, F_FIRST = 2, F_STATUS = 3, F_COUNT = 4 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -61,15 +83,27 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __syncthreads();
 }
 
-// Every block re-reduces the NB partials in the same order.
-__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, double& a, double& b) {
-  a = 0.0;
-  b = 0.0;
-  for (int k = threadIdx.x; k < NB; k += NT) {
-    a += part[k];
-    b += part[NB + k];
+// Every block re-reduces the nb partials in the same order (one warp, then
+// broadcast).
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int nb, double& a, double& b) {
+  __shared__ double ra, rb;
+  if (threadIdx.x < 32) {
+    double x = 0.0, y = 0.0;
+    for (int k = threadIdx.x; k < nb; k += 32) {
+      x += part[k];
+      y += part[NB + k];
+    }
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (threadIdx.x == 0) {
+      ra = x;
+      rb = y;
+    }
   }
-  block_sum2(a, b);
+  __syncthreads();
+  a = ra;
+  b = rb;
+  __syncthreads();
 }
 
 __device__ __forceinline__ void write_partials(double* __restrict__ part, double a, double b) {
@@ -93,15 +127,50 @@ __global__ void k_mu_from_e0(int n, const double4_32a* __restrict__ e0, const do
   }
 }
 
-// v = hi + lo with hi = fl32(v), lo = fl32(v - hi) (lo skipped when null)
-__device__ __forceinline__ void split_store(const double4_32a& v, float4* __restrict__ hi, float4* __restrict__ lo,
-                                            int s) {
-  if (!hi) return;
+// v = hi + lo with hi = fl32(v), lo = fl32(v - hi) (lo skipped when null);
+// returns max |hi component| for the block maxima of the split vector.
+__device__ __forceinline__ float split_store(const double4_32a& v, float4* __restrict__ hi, float4* __restrict__ lo,
+                                             int s) {
+  if (!hi) return 0.f;
   const float4 h = make_float4(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z), 0.f);
   hi[s] = h;
   if (lo)
     lo[s] = make_float4(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y),
                         __double2float_rn(v.z - (double)h.z), 0.f);
+  return fmaxf(fabsf(h.x), fmaxf(fabsf(h.y), fabsf(h.z)));
+}
+
+// Max of m over the whole grid into vmax[NB] (the float64 path's reciprocal
+// spreading scales its fixed-point grid by it): every block stores its max in
+// vmax[blockIdx.x]; the last block to arrive (counter in vmax[NB + 1], back to
+// zero afterwards) reduces them. Called by every block of the launch.
+__device__ __forceinline__ void write_max_partial(float* __restrict__ vmax, float m) {
+  __shared__ float sm[NT / 32];
+  __shared__ bool last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = sm[0];
+    for (int w = 1; w < NT / 32; ++w) r = fmaxf(r, sm[w]);
+    vmax[blockIdx.x] = r;
+    __threadfence();
+    unsigned* count = reinterpret_cast<unsigned*>(vmax + NB + 1);
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x < 32) {
+    __threadfence();
+    float r = 0.f;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) r = fmaxf(r, __ldcg(vmax + k));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (threadIdx.x == 0) {
+      vmax[NB] = r;
+      *reinterpret_cast<unsigned*>(vmax + NB + 1) = 0u;
+    }
+  }
 }
 
 __device__ __forceinline__ double4_32a sum_t(const double4_32a* __restrict__ t, const double4_32a* __restrict__ t2,
@@ -116,297 +185,178 @@ __device__ __forceinline__ double4_32a sum_t(const double4_32a* __restrict__ t, 
   return a;
 }
 
-// r = E0 - mu/alpha + t (t (+ t2) = T mu); z = alpha r; p = z; partials (r.z, z.z)
-__global__ void __launch_bounds__(NT) k_pcg_init(int n, const double4_32a* __restrict__ e0,
-                                                 const double4_32a* __restrict__ mu, const double4_32a* __restrict__ t,
-                                                 const double4_32a* __restrict__ t2,
-                                                 const double2* __restrict__ al, double4_32a* __restrict__ r,
-                                                 double4_32a* __restrict__ z, double4_32a* __restrict__ p,
-                                                 float4* __restrict__ p32, float4* __restrict__ plo,
-                                                 double* __restrict__ part) {
-  double rz = 0.0, zz = 0.0;
+// Called once by every block after it stored its partials; true in the block
+// that arrived last (every partial is then visible to it). The counter goes
+// back to zero for the next launch.
+__device__ __forceinline__ bool last_block(int* fl) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned* count = reinterpret_cast<unsigned*>(fl + F_COUNT);
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+    if (last) *count = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Block partials of z.z (into part[2 NB + block]) and of max |z32| (into
+// vmax[block]); the last block reduces both. Returns true in that block, with
+// rms (Debye) in its thread 0, which runs the convergence test.
+__device__ __forceinline__ bool finish_z(int n, double zz, float vm, double* __restrict__ part,
+                                         float* __restrict__ vmax, int* __restrict__ fl, double& rms) {
+  double unused = 0.0;
+  block_sum2(zz, unused);
+  __shared__ float sm[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = vm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = sm[0];
+    for (int w = 1; w < NT / 32; ++w) m = fmaxf(m, sm[w]);
+    part[2 * NB + blockIdx.x] = zz;
+    vmax[blockIdx.x] = m;
+  }
+  if (!last_block(fl)) return false;
+  if (threadIdx.x < 32) {
+    double tot = 0.0;
+    float m = 0.f;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) {
+      tot += __ldcg(part + 2 * NB + k);
+      m = fmaxf(m, __ldcg(vmax + k));
+    }
+    tot = warp_sum(tot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      vmax[NB] = m;
+      rms = kDebye * sqrt(tot / (double)(n > 0 ? n : 1));
+    }
+  }
+  return true;
+}
+
+// r = E0 - mu/alpha + t (t (+ t2) = T mu); z = alpha r and its float split
+// (z32, zlo: the operator's input); convergence test on z. Starts (or
+// restarts) the recurrence: the next step has beta = 0.
+__global__ void __launch_bounds__(NT) k_cg_init(int n, const double4_32a* __restrict__ e0,
+                                                const double4_32a* __restrict__ mu, const double4_32a* __restrict__ t,
+                                                const double4_32a* __restrict__ t2, const double2* __restrict__ al,
+                                                double4_32a* __restrict__ r, double4_32a* __restrict__ z,
+                                                float4* __restrict__ z32, float4* __restrict__ zlo,
+                                                double* __restrict__ part, float* __restrict__ vmax,
+                                                double* __restrict__ scal, int* __restrict__ fl, double tol) {
+  double zz = 0.0;
+  float vm = 0.f;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const double2 a = al[s];
     const double4_32a e = e0[s], m = mu[s], tt = sum_t(t, t2, s);
     const double4_32a rr = make_double4_32a(e.x - m.x * a.y + tt.x, e.y - m.y * a.y + tt.y, e.z - m.z * a.y + tt.z, 0.0);
-    const double4_32a zz4 = make_double4_32a(a.x * rr.x, a.x * rr.y, a.x * rr.z, 0.0);
+    const double4_32a zv = make_double4_32a(a.x * rr.x, a.x * rr.y, a.x * rr.z, 0.0);
     r[s] = rr;
-    z[s] = zz4;
-    p[s] = zz4;
-    split_store(zz4, p32, plo, s);
-    rz += dot3(rr, zz4);
-    zz += dot3(zz4, zz4);
+    z[s] = zv;
+    vm = fmaxf(vm, split_store(zv, z32, zlo, s));
+    zz += dot3(zv, zv);
   }
-  write_partials(part, rz, zz);
+  double rms = 0.0;
+  if (finish_z(n, zz, vm, part, vmax, fl, rms) && threadIdx.x == 0) {
+    scal[2] = rms;
+    fl[F_FIRST] = 1;
+    const bool conv = rms < tol;
+    fl[F_STOP] = conv ? 1 : 0;
+    fl[F_STATUS] = conv ? 1 : 0;
+  }
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_init_finish(int n, const double* __restrict__ part, double tol,
-                                                        double* __restrict__ scal, int* __restrict__ fl) {
-  double rz, zz;
-  reduce_partials(part, rz, zz);
+// After w's operator part t (+ t2) = T z: w = z/alpha - t; partials r.z, z.w.
+__global__ void __launch_bounds__(NT) k_cg_dots(int n, const double4_32a* __restrict__ r,
+                                                const double4_32a* __restrict__ z, const double4_32a* __restrict__ t,
+                                                const double4_32a* __restrict__ t2, const double2* __restrict__ al,
+                                                double4_32a* __restrict__ w, double* __restrict__ part,
+                                                const int* __restrict__ fl) {
+  if (fl[F_STOP]) return;
+  double rz = 0.0, zw = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double ia = al[s].y;
+    const double4_32a zv = z[s], tt = sum_t(t, t2, s);
+    const double4_32a wv = make_double4_32a(zv.x * ia - tt.x, zv.y * ia - tt.y, zv.z * ia - tt.z, 0.0);
+    w[s] = wv;
+    rz += dot3(r[s], zv);
+    zw += dot3(zv, wv);
+  }
+  write_partials(part, rz, zw);
+}
+
+// One step: scalars from the partials of k_cg_dots, the vector update, the
+// new z (and its split), and the convergence / iteration-limit test.
+__global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__ mu, double4_32a* __restrict__ r,
+                                                double4_32a* __restrict__ z, double4_32a* __restrict__ p,
+                                                double4_32a* __restrict__ q, const double4_32a* __restrict__ w,
+                                                const double2* __restrict__ al, float4* __restrict__ z32,
+                                                float4* __restrict__ zlo, double* __restrict__ part,
+                                                float* __restrict__ vmax, double* __restrict__ scal,
+                                                int* __restrict__ fl, double tol, int max_iter) {
+  if (fl[F_STOP]) return;
+  double rho, m;
+  reduce_partials(part, vec_blocks(n), rho, m);
+  __shared__ double sbeta, sgamma;
+  __shared__ bool bad;
   if (threadIdx.x == 0) {
-    const double rms = kDebye * sqrt(zz / (double)n);
-    scal[fl[F_ITERS] & 1] = rz;
+    double beta = 0.0, den = m;
+    if (!fl[F_FIRST]) {
+      beta = rho / scal[0];
+      den = m - beta * rho / scal[1];
+    }
+    bad = !(den > 0.0);  // p.Ap <= 0: the operator is not positive definite
+    sbeta = beta;
+    sgamma = rho / den;
+  }
+  __syncthreads();
+  const double beta = sbeta, gamma = sgamma;
+  double zz = 0.0;
+  float vm = 0.f;
+  if (!bad) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+      const double a = al[s].x;
+      const double4_32a zv = z[s], wv = w[s];
+      double4_32a pp = p[s], qq = q[s], x = mu[s], rr = r[s];
+      pp = make_double4_32a(zv.x + beta * pp.x, zv.y + beta * pp.y, zv.z + beta * pp.z, 0.0);
+      qq = make_double4_32a(wv.x + beta * qq.x, wv.y + beta * qq.y, wv.z + beta * qq.z, 0.0);
+      x = make_double4_32a(x.x + gamma * pp.x, x.y + gamma * pp.y, x.z + gamma * pp.z, 0.0);
+      rr = make_double4_32a(rr.x - gamma * qq.x, rr.y - gamma * qq.y, rr.z - gamma * qq.z, 0.0);
+      const double4_32a zn = make_double4_32a(a * rr.x, a * rr.y, a * rr.z, 0.0);
+      p[s] = pp;
+      q[s] = qq;
+      mu[s] = x;
+      r[s] = rr;
+      z[s] = zn;
+      vm = fmaxf(vm, split_store(zn, z32, zlo, s));
+      zz += dot3(zn, zn);
+    }
+  }
+  double rms = 0.0;
+  if (finish_z(n, zz, vm, part, vmax, fl, rms) && threadIdx.x == 0) {
+    const int it = fl[F_ITERS] + 1;
+    fl[F_ITERS] = it;
+    fl[F_FIRST] = 0;
+    if (bad) {
+      fl[F_STOP] = 1;
+      fl[F_STATUS] = 3;
+      return;
+    }
+    scal[0] = rho;
+    scal[1] = gamma;
     scal[2] = rms;
-    fl[F_CONV] = 0;
     if (rms < tol) {
       fl[F_STOP] = 1;
       fl[F_STATUS] = 1;
-    } else {
-      fl[F_STOP] = 0;
-      fl[F_STATUS] = 0;
-    }
-  }
-}
-
-// q = p/alpha - t; partials (p.q, 0)
-__global__ void __launch_bounds__(NT) k_pcg_q(int n, const double4_32a* __restrict__ p, const double4_32a* __restrict__ t,
-                                              const double4_32a* __restrict__ t2, const double2* __restrict__ al,
-                                              double4_32a* __restrict__ q, double* __restrict__ part,
-                                              const int* __restrict__ fl) {
-  if (fl[F_STOP]) return;
-  double pq = 0.0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double ia = al[s].y;
-    const double4_32a pp = p[s], tt = sum_t(t, t2, s);
-    const double4_32a qq = make_double4_32a(pp.x * ia - tt.x, pp.y * ia - tt.y, pp.z * ia - tt.z, 0.0);
-    q[s] = qq;
-    pq += dot3(pp, qq);
-  }
-  write_partials(part, pq, 0.0);
-}
-
-// gamma = r.z / p.q; mu += gamma p; r -= gamma q; z = alpha r; partials (r.z, z.z)
-__global__ void __launch_bounds__(NT) k_pcg_update(int n, double4_32a* __restrict__ mu, double4_32a* __restrict__ r,
-                                                   double4_32a* __restrict__ z, const double4_32a* __restrict__ p,
-                                                   const double4_32a* __restrict__ q, const double2* __restrict__ al,
-                                                   const double* __restrict__ part_in, double* __restrict__ part,
-                                                   const double* __restrict__ scal, int* __restrict__ fl) {
-  if (fl[F_STOP]) return;
-  double pq, unused;
-  reduce_partials(part_in, pq, unused);
-  if (!(pq > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) fl[F_CONV] = -1;  // breakdown: operator not SPD
-    return;
-  }
-  const double gamma = scal[fl[F_ITERS] & 1] / pq;
-  double rz = 0.0, zz = 0.0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double a = al[s].x;
-    const double4_32a pp = p[s], qq = q[s];
-    double4_32a m = mu[s], rr = r[s];
-    m.x += gamma * pp.x;
-    m.y += gamma * pp.y;
-    m.z += gamma * pp.z;
-    rr.x -= gamma * qq.x;
-    rr.y -= gamma * qq.y;
-    rr.z -= gamma * qq.z;
-    const double4_32a zz4 = make_double4_32a(a * rr.x, a * rr.y, a * rr.z, 0.0);
-    mu[s] = m;
-    r[s] = rr;
-    z[s] = zz4;
-    rz += dot3(rr, zz4);
-    zz += dot3(zz4, zz4);
-  }
-  write_partials(part, rz, zz);
-}
-
-// convergence test on z; beta = rz_new/rz_old; p = z + beta p (and its float split)
-__global__ void __launch_bounds__(NT) k_pcg_dir(int n, const double4_32a* __restrict__ z, double4_32a* __restrict__ p,
-                                                float4* __restrict__ p32, float4* __restrict__ plo,
-                                                const double* __restrict__ part, double* __restrict__ scal,
-                                                int* __restrict__ fl, double tol) {
-  if (fl[F_STOP] || fl[F_CONV] < 0) return;
-  double rz, zz;
-  reduce_partials(part, rz, zz);
-  const double rms = kDebye * sqrt(zz / (double)n);
-  const int it = fl[F_ITERS];
-  if (blockIdx.x == 0 && threadIdx.x == 0) scal[2] = rms;
-  if (rms < tol) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) fl[F_CONV] = 1;
-    return;
-  }
-  const double beta = rz / scal[it & 1];
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double4_32a zz4 = z[s];
-    double4_32a pp = p[s];
-    pp.x = zz4.x + beta * pp.x;
-    pp.y = zz4.y + beta * pp.y;
-    pp.z = zz4.z + beta * pp.z;
-    p[s] = pp;
-    split_store(pp, p32, plo, s);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) scal[(it + 1) & 1] = rz;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
-
-// Grid-wide barrier of a cooperative launch. bar[0] counts arrivals, bar[1]
-// is the generation; both start at zero and the count returns to zero after
-// every completed barrier. The wait is bounded: false when it gave up.
-__device__ bool grid_barrier(unsigned* bar) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned gen = ld_acquire(bar + 1);
-    __threadfence();
-    ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire(bar + 1) == gen) {
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok;
-}
-
-__device__ __forceinline__ void barrier_gave_up(int* fl) {
-  if (threadIdx.x == 0) {
-    atomicExch(fl + F_STATUS, 4);
-    atomicExch(fl + F_STOP, 1);
-  }
-}
-
-// Partials written by other blocks of the same launch: read through L2.
-__device__ __forceinline__ void reduce_partials_cg(const double* part, double& a, double& b) {
-  a = 0.0;
-  b = 0.0;
-  for (int k = threadIdx.x; k < NB; k += NT) {
-    a += __ldcg(part + k);
-    b += __ldcg(part + NB + k);
-  }
-  block_sum2(a, b);
-}
-
-// One PCG iteration after T p, in one cooperative launch: the three vector
-// phases of k_pcg_q, k_pcg_update and k_pcg_dir separated by grid-wide
-// barriers, then the bookkeeping of k_pcg_advance. Every block takes the same
-// branch at each decision (the reduced scalars are identical in all blocks),
-// so either all blocks reach a barrier or none does. A barrier that gives up
-// stops the solve with status 4 and the host repeats it with the four kernels.
-__global__ void __launch_bounds__(NT) k_pcg_iter(int n, double4_32a* __restrict__ mu, double4_32a* __restrict__ r,
-                                                 double4_32a* __restrict__ z, double4_32a* __restrict__ p,
-                                                 double4_32a* __restrict__ q, const double4_32a* __restrict__ t,
-                                                 const double4_32a* __restrict__ t2, const double2* __restrict__ al,
-                                                 float4* __restrict__ p32, float4* __restrict__ plo,
-                                                 double* __restrict__ pa, double* __restrict__ pb,
-                                                 double* __restrict__ scal, int* __restrict__ fl, double tol,
-                                                 int max_iter) {
-  unsigned* bar = reinterpret_cast<unsigned*>(fl + 4);
-  if (fl[F_STOP]) return;
-  const int it = fl[F_ITERS];
-  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-  // q = p/alpha - t; partials p.q
-  double pq = 0.0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double ia = al[s].y;
-    const double4_32a pp = p[s], tt = sum_t(t, t2, s);
-    const double4_32a qq = make_double4_32a(pp.x * ia - tt.x, pp.y * ia - tt.y, pp.z * ia - tt.z, 0.0);
-    q[s] = qq;
-    pq += dot3(pp, qq);
-  }
-  write_partials(pa, pq, 0.0);
-  if (!grid_barrier(bar)) return barrier_gave_up(fl);
-  double unused;
-  reduce_partials_cg(pa, pq, unused);
-  if (!(pq > 0.0)) {  // breakdown: operator not positive definite
-    if (lead) {
-      fl[F_ITERS] = it + 1;
-      fl[F_CONV] = -1;
-      fl[F_STOP] = 1;
-      fl[F_STATUS] = 3;
-    }
-    return;
-  }
-  const double gamma = scal[it & 1] / pq;
-  double rz = 0.0, zz = 0.0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double a = al[s].x;
-    const double4_32a pp = p[s], qq = q[s];
-    double4_32a m = mu[s], rr = r[s];
-    m.x += gamma * pp.x;
-    m.y += gamma * pp.y;
-    m.z += gamma * pp.z;
-    rr.x -= gamma * qq.x;
-    rr.y -= gamma * qq.y;
-    rr.z -= gamma * qq.z;
-    const double4_32a zz4 = make_double4_32a(a * rr.x, a * rr.y, a * rr.z, 0.0);
-    mu[s] = m;
-    r[s] = rr;
-    z[s] = zz4;
-    rz += dot3(rr, zz4);
-    zz += dot3(zz4, zz4);
-  }
-  write_partials(pb, rz, zz);
-  if (!grid_barrier(bar)) return barrier_gave_up(fl);
-  reduce_partials_cg(pb, rz, zz);
-  const double rms = kDebye * sqrt(zz / (double)n);
-  if (rms < tol) {
-    if (lead) {
-      scal[2] = rms;
-      fl[F_ITERS] = it + 1;
-      fl[F_CONV] = 1;
-      fl[F_STOP] = 1;
-      fl[F_STATUS] = 1;
-    }
-    return;
-  }
-  const double beta = rz / scal[it & 1];
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double4_32a zz4 = z[s];
-    double4_32a pp = p[s];
-    pp.x = zz4.x + beta * pp.x;
-    pp.y = zz4.y + beta * pp.y;
-    pp.z = zz4.z + beta * pp.z;
-    p[s] = pp;
-    split_store(pp, p32, plo, s);
-  }
-  if (lead) {
-    scal[2] = rms;
-    scal[(it + 1) & 1] = rz;
-    fl[F_ITERS] = it + 1;
-    if (it + 1 >= max_iter) {
+    } else if (it >= max_iter) {
       fl[F_STOP] = 1;
       fl[F_STATUS] = 2;
     }
-  }
-}
-
-__global__ void k_pcg_advance(int* __restrict__ fl, int max_iter) {
-  if (fl[F_STOP]) return;
-  fl[F_ITERS] += 1;
-  if (fl[F_CONV] == 1) {
-    fl[F_STOP] = 1;
-    fl[F_STATUS] = 1;
-  } else if (fl[F_CONV] < 0) {
-    fl[F_STOP] = 1;
-    fl[F_STATUS] = 3;
-  } else if (fl[F_ITERS] >= max_iter) {
-    fl[F_STOP] = 1;
-    fl[F_STATUS] = 2;
   }
 }
 
@@ -429,8 +379,12 @@ __global__ void k_from_sorted(int n, const int* __restrict__ perm, const double4
   dst[3 * i + 2] = v.z;
 }
 
-__global__ void k_split(int n, const double4_32a* __restrict__ v, float4* __restrict__ hi, float4* __restrict__ lo) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) split_store(v[s], hi, lo, s);
+__global__ void __launch_bounds__(NT) k_split(int n, const double4_32a* __restrict__ v, float4* __restrict__ hi,
+                                             float4* __restrict__ lo, float* __restrict__ vmax) {
+  float vm = 0.f;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+    vm = fmaxf(vm, split_store(v[s], hi, lo, s));
+  write_max_partial(vmax, vm);
 }
 
 // U = -1/2 C sum mu . E0 over the caller's [N][3] arrays
@@ -444,7 +398,7 @@ __global__ void __launch_bounds__(NT) k_energy_partial(long long m, const double
 
 __global__ void __launch_bounds__(NT) k_energy_finish(const double* __restrict__ part, double* __restrict__ out) {
   double s, unused;
-  reduce_partials(part, s, unused);
+  reduce_partials(part, NB, s, unused);
   if (threadIdx.x == 0) *out = -0.5 * kCoulomb * s;
 }
 
@@ -462,12 +416,12 @@ void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst) {
 
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o) {
   c->n_launch += 1;
-  k_split<<<NB, NT, 0, c->stream>>>(c->n, v, o, nullptr);
+  k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, o, nullptr, c->vmax_part);
 }
 
 void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo) {
   c->n_launch += 1;
-  k_split<<<NB, NT, 0, c->stream>>>(c->n, v, hi, lo);
+  k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, hi, lo, c->vmax_part);
 }
 
 // T v = t (+ t2). With t2 == nullptr the whole product lands in t. With t2
@@ -483,7 +437,8 @@ static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const fl
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     {
       PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
-      r = fp64_pme ? pme_dipole_field(c, v, t2, c->side, true) : pme_dipole_field32(c, v32, t2, c->side, true);
+      r = fp64_pme ? pme_dipole_field(c, v, v32, vlo, t2, c->side, true)
+                   : pme_dipole_field32(c, v32, t2, c->side, true);
     }
     cudaEventRecord(c->ev_join, c->side);
     if (r) {
@@ -505,7 +460,8 @@ static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const fl
     return AMP_OK;
   }
   PhaseScope ps(c, AMP_PHASE_T_RECIP);
-  return fp64_pme ? pme_dipole_field(c, v, t, c->stream, false) : pme_dipole_field32(c, v32, t, c->stream, false);
+  return fp64_pme ? pme_dipole_field(c, v, v32, vlo, t, c->stream, false)
+                  : pme_dipole_field32(c, v32, t, c->stream, false);
 }
 
 // t (+ t2) = T v in the solver's working precision. v32 (+ vlo) must mirror
@@ -539,35 +495,22 @@ static int read_flags(amp_ctx* c) {
   return cuda_check(c, cudaStreamSynchronize(c->stream), "solver flag read");
 }
 
+// One iteration: w's operator part T z (skipped on the device once the solve
+// has stopped), then k_cg_dots and k_cg_step.
 static int enqueue_iteration(amp_ctx* c) {
   const int n = c->n;
   cudaStream_t st = c->stream;
-  const bool mixed = c->cfg.precision == AMP_MIXED;
-  double* pa = c->partials;
-  double* pb = c->partials + 2 * NB;
-  float4* lo = mixed ? nullptr : c->plo;
-  int r = apply_T_sorted(c, c->pv, c->p32, lo, c->tv, c->trec);
+  float4* lo = c->cfg.precision == AMP_MIXED ? nullptr : c->plo;
+  c->op_stop = c->iflags + F_STOP;
+  int r = apply_T_sorted(c, c->zv, c->p32, lo, c->tv, c->trec);
+  c->op_stop = nullptr;
   if (r) return r;
   PhaseScope ps(c, AMP_PHASE_PCG);
-  if (c->coop_ok) {
-    double tol = c->cfg.tol_debye;
-    int max_iter = c->cfg.max_iter;
-    int nn = n;
-    void* args[] = {&nn, &c->mu, &c->res, &c->zv, &c->pv, &c->qv, &c->tv, &c->trec, &c->alph, &c->p32, &lo,
-                    &pa, &pb, &c->scal, &c->iflags, &tol, &max_iter};
-    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_iter, dim3(NB), dim3(NT), args, 0, st);
-    if (e == cudaSuccess) {
-      c->n_launch += 1;
-      return AMP_OK;
-    }
-    cudaGetLastError();  // not co-resident here: use the four-kernel form from now on
-    c->coop_ok = false;
-  }
-  c->n_launch += 4;
-  k_pcg_q<<<NB, NT, 0, st>>>(n, c->pv, c->tv, c->trec, c->alph, c->qv, pa, c->iflags);
-  k_pcg_update<<<NB, NT, 0, st>>>(n, c->mu, c->res, c->zv, c->pv, c->qv, c->alph, pa, pb, c->scal, c->iflags);
-  k_pcg_dir<<<NB, NT, 0, st>>>(n, c->zv, c->pv, c->p32, lo, pb, c->scal, c->iflags, c->cfg.tol_debye);
-  k_pcg_advance<<<1, 1, 0, st>>>(c->iflags, c->cfg.max_iter);
+  c->n_launch += 2;
+  const int nb = vec_blocks(n);
+  k_cg_dots<<<nb, NT, 0, st>>>(n, c->res, c->zv, c->tv, c->trec, c->alph, c->wv, c->partials, c->iflags);
+  k_cg_step<<<nb, NT, 0, st>>>(n, c->mu, c->res, c->zv, c->pv, c->qv, c->wv, c->alph, c->p32, lo, c->partials,
+                               c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye, c->cfg.max_iter);
   return AMP_OK;
 }
 
@@ -580,16 +523,15 @@ static int restart(amp_ctx* c, bool fp64_operator) {
   if (fp64_operator && mixed) {
     r = apply_T_sorted_fp64_check(c, c->mu, c->tv, c->trec);
   } else {
-    // the float split of mu goes through the p buffers, which k_pcg_init rewrites
+    // the float split of mu goes through the operator-input buffers, which k_cg_init rewrites
     launch_split(c, c->mu, c->p32, lo);
     r = apply_T_sorted(c, c->mu, c->p32, lo, c->tv, c->trec);
   }
   if (r) return r;
   PhaseScope ps(c, AMP_PHASE_PCG);
-  c->n_launch += 2;
-  k_pcg_init<<<NB, NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->trec, c->alph, c->res, c->zv, c->pv, c->p32,
-                                       lo, c->partials);
-  k_pcg_init_finish<<<1, NT, 0, c->stream>>>(c->n, c->partials, c->cfg.tol_debye, c->scal, c->iflags);
+  c->n_launch += 1;
+  k_cg_init<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->trec, c->alph, c->res, c->zv, c->p32, lo,
+                                      c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye);
   return AMP_OK;
 }
 
@@ -598,8 +540,8 @@ int solve(amp_ctx* c, bool use_guess) {
   cudaStream_t st = c->stream;
   int r;
   if (!use_guess) c->n_launch += 1;
-  if (!use_guess) k_mu_from_e0<<<NB, NT, 0, st>>>(c->n, c->E0s, c->alph, c->mu);
-  if ((r = cuda_check(c, cudaMemsetAsync(c->iflags, 0, sizeof(int) * 6, st), "memset"))) return r;
+  if (!use_guess) k_mu_from_e0<<<vec_blocks(c->n), NT, 0, st>>>(c->n, c->E0s, c->alph, c->mu);
+  if ((r = cuda_check(c, cudaMemsetAsync(c->iflags, 0, sizeof(int) * 5, st), "memset"))) return r;
   if ((r = restart(c, !mixed))) return r;
   const int chunk = 4;
   c->stats.fp64_checks = 0;
@@ -608,23 +550,19 @@ int solve(amp_ctx* c, bool use_guess) {
       for (int k = 0; k < chunk; ++k)
         if ((r = enqueue_iteration(c))) return r;
       if ((r = read_flags(c))) return r;
-      if (c->hibuf[0]) break;
+      if (c->hibuf[F_STOP]) break;
     }
-    if (!mixed || c->hibuf[3] != 1) break;
+    if (!mixed || c->hibuf[F_STATUS] != 1) break;
     // mixed: check the converged dipoles with the float64 operator
     if ((r = restart(c, true))) return r;
     c->stats.fp64_checks++;
     if ((r = read_flags(c))) return r;
-    if (c->hibuf[3] == 1 || c->hibuf[1] >= c->cfg.max_iter) break;
+    if (c->hibuf[F_STATUS] == 1 || c->hibuf[F_ITERS] >= c->cfg.max_iter) break;
   }
   if ((r = cuda_check(c, cudaGetLastError(), "solver launch"))) return r;
-  c->stats.iters = c->hibuf[1];
+  c->stats.iters = c->hibuf[F_ITERS];
   c->stats.rms = c->hbuf[2];
-  const int status = c->hibuf[3];
-  if (status == 4) {  // the fused iteration's barrier gave up: redo with separate kernels
-    c->coop_ok = false;
-    return solve(c, false);
-  }
+  const int status = c->hibuf[F_STATUS];
   if (status == 3) return fail(c, AMP_ERR_NOT_CONVERGED, "PCG breakdown: p.Ap <= 0");
   if (status != 1)
     return fail(c, AMP_ERR_NOT_CONVERGED, "PCG not converged after %d iterations (RMS %.3e D)", c->stats.iters,

@@ -10,8 +10,11 @@
 //   phi = unnormalised C2R( G . R2C(Q) ),
 //   G(m) = exp(-pi^2 m~^2/beta^2) / (pi V m~^2) |b1 b2 b3|^2, G(0) = 0;
 //   E_i = -sum_g grad W_i(g) phi(g).
-// The 3D FFTs are cuFFT (library call). Spreading uses float64 (or float32 in
-// the mixed path) atomics into the grid; gathering is one thread per atom.
+// The 3D FFTs are cuFFT (library call) or, for the float64 path on
+// power-of-two grids, the double-float FFT of amp_fft.cu. Spreading of the
+// permanent multipoles uses float64 (float32 in the mixed path) atomics; the
+// float64 path spreads dipoles in double-float into a 64-bit fixed-point grid.
+// Gathering runs one group of lanes per atom.
 // |b(m)|^2 = 1/|sum_{k=0}^{3} M5(k+1) e^{2 pi i m k/K}|^2; where that sum
 // vanishes (m = K/2, even K) the mean of the neighbours m-1, m+1 is used.
 #include <cmath>
@@ -55,8 +58,10 @@ __device__ __forceinline__ void bspline5(double f, double s, double w[4][kOrder]
   }
 }
 
+// kcount (float64 path): atoms per base cell k0, and fx_info[1] = the largest count.
 __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int K, double* __restrict__ theta,
-                        float* __restrict__ theta32, float2* __restrict__ theta_df, int4* __restrict__ gbase) {
+                        float* __restrict__ theta32, float2* __restrict__ theta_df, int4* __restrict__ gbase,
+                        int* __restrict__ kcount, int* __restrict__ fx_info) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double4_32a a = A[s];
@@ -85,6 +90,12 @@ __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int 
       }
   }
   gbase[s] = make_int4(base[0], base[1], base[2], 0);
+  if (kcount) {
+    const int cnt = atomicAdd(kcount + ((long long)base[0] * K + base[1]) * K + base[2], 1) + 1;
+    const unsigned active = __activemask();
+    const int m = __reduce_max_sync(active, cnt);
+    if ((threadIdx.x & 31) == __ffs(active) - 1) atomicMax(fx_info + 1, m);
+  }
 }
 
 template <typename R>
@@ -157,7 +168,9 @@ __global__ void __launch_bounds__(128) k_spread_multipoles(int n, const R* __res
 template <typename R, typename V>
 __global__ void __launch_bounds__(128) k_spread_dipoles(int n, const R* __restrict__ theta,
                                                         const int4* __restrict__ gbase, const V* __restrict__ v,
-                                                        int K, R* __restrict__ grid) {
+                                                        int K, R* __restrict__ grid,
+                                                        const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
   if (s >= n || tx >= kOrder) return;
@@ -187,8 +200,93 @@ __global__ void __launch_bounds__(128) k_spread_dipoles(int n, const R* __restri
   }
 }
 
+// ---- float64 path: dipoles spread in double-float, accumulated in 64-bit fixed point.
+// Integer atomics are exact, so the grid does not depend on the order in which
+// atoms arrive, and nothing of the spreading runs on the float64 pipe.
+
+// Scale exponent s for the fixed-point grid. One atom's weight at a grid point
+// is at most 1 and a derivative weight at most sc = K/L in magnitude, so
+// |grid value| <= 3 sc m cmax, with m = max |dipole component| and cmax the
+// number of atoms that reach one point; s keeps that below 2^61.
+__device__ __forceinline__ int fixed_scale(float m, float sc, int cmax) {
+  const float bound = 3.f * sc * m * (float)cmax;
+  if (!(bound > 0.f) || !(bound < 1e30f)) return 0;  // zero (or non-finite) vector
+  int e;
+  frexpf(bound, &e);  // bound < 2^e
+  return max(-60, min(120, 61 - e));
+}
+
+// round(f * 2^s) as a 64-bit integer, by integer operations on the bits of f.
+// Finite f only; zero and subnormals (below the grid's resolution) give 0.
+__device__ __forceinline__ long long to_fixed(float f, int s) {
+  const unsigned u = __float_as_uint(f);
+  const int e = (int)((u >> 23) & 0xffu);
+  const long long m = e ? (long long)((u & 0x7fffffu) | 0x800000u) : 0ll;
+  const int sh = e - 150 + s;
+  long long r;
+  if (sh >= 0)
+    r = m << min(sh, 39);
+  else if (sh > -25)
+    r = (m + (1ll << (-sh - 1))) >> -sh;
+  else
+    r = 0;
+  return (u >> 31) ? -r : r;
+}
+
+// Q(g) = sum_i mu_i . grad W_i(g) with mu = v32 + vlo. One thread per
+// (atom, x plane, y row): its five z points. vmax[kReduceBlocks] holds max
+// |v32| as left by the kernel that split v; every block derives the same
+// scale from it and block 0 stores it in fx_info[0] for the FFT.
+constexpr int kSpreadThreads = 256;
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, const float2* __restrict__ th_df,
+                                                                      const int4* __restrict__ gbase,
+                                                                      const float4* __restrict__ v32,
+                                                                      const float4* __restrict__ vlo,
+                                                                      const float* __restrict__ vmax,
+                                                                      int* __restrict__ fx_info, float sc, int K,
+                                                                      unsigned long long* __restrict__ grid,
+                                                                      const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  const int sfx = fixed_scale(vmax[kReduceBlocks], sc, kOrder * kOrder * kOrder * fx_info[1]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) fx_info[0] = sfx;
+  const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
+  if (item >= (long long)n * (kOrder * kOrder)) return;
+  const int s = (int)(item / (kOrder * kOrder)), txy = (int)(item - (long long)s * (kOrder * kOrder));
+  const int tx = txy / kOrder, ty = txy - tx * kOrder;
+  const float2* th = th_df + (long long)kThDf * s;
+  const float4 h = v32[s], l = vlo[s];
+  const float2 x0 = th[(0 * 2 + 0) * kOrder + tx], x1 = th[(0 * 2 + 1) * kOrder + tx];
+  const float2 y0 = th[(1 * 2 + 0) * kOrder + ty], y1 = th[(1 * 2 + 1) * kOrder + ty];
+  // A = mu_x w'_x w_y + mu_y w_x w'_y, B = mu_z w_x w_y: the point's value is A w_z + B w'_z
+  const dflt A = df_madd(df_mul({h.y, l.y}, {x0.x, x0.y}), {y1.x, y1.y},
+                         df_mul(df_mul({h.x, l.x}, {x1.x, x1.y}), {y0.x, y0.y}));
+  const dflt B = df_mul(df_mul({h.z, l.z}, {x0.x, x0.y}), {y0.x, y0.y});
+  const int4 b = gbase[s];
+  unsigned long long* row = grid + ((long long)wrapk(b.x - tx, K) * K + wrapk(b.y - ty, K)) * K;
+#pragma unroll
+  for (int tz = 0; tz < kOrder; ++tz) {
+    const float2 z0 = th[(2 * 2 + 0) * kOrder + tz], z1 = th[(2 * 2 + 1) * kOrder + tz];
+    const dflt val = df_madd(B, {z1.x, z1.y}, df_mul(A, {z0.x, z0.y}));
+    const long long q = to_fixed(val.hi, sfx) + to_fixed(val.lo, sfx);
+    atomicAdd(row + wrapk(b.z - tz, K), (unsigned long long)q);
+  }
+}
+
+// fixed-point grid -> float64 grid (for cuFFT), zeroing the fixed-point grid
+__global__ void k_fixed_to_double(long long ng, unsigned long long* __restrict__ qfx, const int* __restrict__ fx_info,
+                                  double* __restrict__ out, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ng) return;
+  const long long v = (long long)qfx[k];
+  qfx[k] = 0ull;
+  out[k] = ldexp((double)v, -fx_info[0]);
+}
+
 template <typename C, typename R>
-__global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict__ G) {
+__global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict__ G,
+                           const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= m) return;
   const R g = G[k];
@@ -203,7 +301,9 @@ __global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict_
 template <typename R, bool kSet = false>
 __global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict__ theta,
                                                       const int4* __restrict__ gbase, const R* __restrict__ phi,
-                                                      int K, double4_32a* __restrict__ out) {
+                                                      int K, double4_32a* __restrict__ out,
+                                                      const int* __restrict__ stop = nullptr) {
+  if (stop && *stop) return;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
   if (s >= n) return;  // whole groups leave together
@@ -258,13 +358,13 @@ __global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict
 }
 
 // phi = hi + lo for every grid point (float64 path, once per gather)
-__global__ void k_split_grid(long long ng, const double* __restrict__ phi, float* __restrict__ hi,
-                             float* __restrict__ lo) {
+__global__ void k_split_grid(long long ng, const double* __restrict__ phi, float2* __restrict__ out,
+                             const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ng) return;
   const dflt v = df_split(phi[k]);
-  hi[k] = v.hi;
-  lo[k] = v.lo;
+  out[k] = make_float2(v.hi, v.lo);
 }
 
 // The float64 path's gather in double-float arithmetic (float units only):
@@ -272,9 +372,9 @@ __global__ void k_split_grid(long long ng, const double* __restrict__ phi, float
 template <bool kSet>
 __global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __restrict__ th_df,
                                                          const int4* __restrict__ gbase,
-                                                         const float* __restrict__ phi_hi,
-                                                         const float* __restrict__ phi_lo, int K,
-                                                         double4_32a* __restrict__ out) {
+                                                         const float2* __restrict__ phi, int K,
+                                                         double4_32a* __restrict__ out, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
   if (s >= n) return;  // whole groups leave together
@@ -297,9 +397,9 @@ __global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __
       const long long row = ((long long)gx * K + wrapk(b.y - ty, K)) * K;
       dflt s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
       for (int tz = 0; tz < kOrder; ++tz) {
-        const float ph = phi_hi[row + gz[tz]], pl = phi_lo[row + gz[tz]];
-        df_fma(s0, wz0[tz].x, wz0[tz].y, ph, pl);
-        df_fma(s1, wz1[tz].x, wz1[tz].y, ph, pl);
+        const float2 ph = phi[row + gz[tz]];
+        df_fma(s0, wz0[tz].x, wz0[tz].y, ph.x, ph.y);
+        df_fma(s1, wz1[tz].x, wz1[tz].y, ph.x, ph.y);
       }
       df_fma(px, wy0.x, wy0.y, s0.hi, s0.lo);
       df_fma(py, wy1.x, wy1.y, s0.hi, s0.lo);
@@ -337,28 +437,34 @@ void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out, bool split) {
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K;
   c->n_launch += split ? 2 : 1;
-  if (split) k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_hi, c->phi_lo);
+  if (split) k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_df, c->op_stop);
   k_gather_field_df<kSet><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-      n, c->theta_df, c->gbase, c->phi_hi, c->phi_lo, K, out);
+      n, c->theta_df, c->gbase, c->phi_df, K, out, c->op_stop);
 }
 
 int exec_fft(amp_ctx* c, bool fp32, bool forward);
 
-// grid64 (spread charges) -> phi: the double-float FFT writes phi_hi/phi_lo
-// directly when the grid allows it, else cuFFT float64 leaves phi in grid64
-// and *split_needed tells the gather to split it first.
-int conv_to_phi(amp_ctx* c, cudaStream_t st, bool* split_needed) {
+// Spread grid -> phi. The grid is grid64 (float64) or, with fixed = true,
+// gridfx (fixed point, zeroed on the way). The double-float FFT writes phi_df
+// directly when the grid size allows it, else cuFFT float64 leaves phi in
+// grid64 and *split_needed tells the gather to split it first.
+int conv_to_phi(amp_ctx* c, cudaStream_t st, bool* split_needed, bool fixed) {
   if (c->fft_grid) {
-    fft_df_convolve(c, st);
+    fft_df_convolve(c, st, fixed);
     *split_needed = false;
     return AMP_OK;
   }
+  const long long ng = (long long)c->K * c->K * c->K;
   const long long nh = (long long)c->K * c->K * (c->K / 2 + 1);
+  if (fixed) {
+    c->n_launch += 1;
+    k_fixed_to_double<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->gridfx, c->fx_info, c->grid64, c->op_stop);
+  }
   cufftSetStream(c->plan_d2z, st);
   cufftSetStream(c->plan_z2d, st);
   int r = exec_fft(c, false, true);
   if (!r) {
-    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64, c->op_stop);
     r = exec_fft(c, false, false);
   }
   cufftSetStream(c->plan_d2z, c->stream);
@@ -455,9 +561,15 @@ int pme_setup(amp_ctx* c) {
   if ((r = dev_alloc(c, &c->grid64, ng)) || (r = dev_alloc(c, &c->cgrid64, nh)) ||
       (r = dev_alloc(c, &c->G64, nh)))
     return r;
-  if (c->cfg.precision == AMP_FP64 &&
-      ((r = dev_alloc(c, &c->phi_hi, ng)) || (r = dev_alloc(c, &c->phi_lo, ng))))
-    return r;
+  if (c->cfg.precision == AMP_FP64) {
+    if ((r = dev_alloc(c, &c->phi_df, ng)) || (r = dev_alloc(c, &c->gridfx, ng)) ||
+        (r = dev_alloc(c, &c->kcount, ng)) || (r = dev_alloc(c, &c->fx_info, 2)))
+      return r;
+    // the fixed-point grid starts at zero; the kernel that reads it zeroes it again
+    if ((r = cuda_check(c, cudaMemsetAsync(c->gridfx, 0, sizeof(unsigned long long) * ng, c->stream),
+                        "grid memset")))
+      return r;
+  }
   if (c->cfg.precision == AMP_MIXED) {
     if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
         (r = dev_alloc(c, &c->G32, nh)))
@@ -490,8 +602,12 @@ int pme_alloc_atoms(amp_ctx* c, int n_cap) {
 
 void launch_pme_theta(amp_ctx* c) {
   c->n_launch += 1;
+  if (c->kcount) {
+    cudaMemsetAsync(c->kcount, 0, sizeof(int) * (long long)c->K * c->K * c->K, c->stream);
+    cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 2, c->stream);
+  }
   k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
-                                                       c->theta_df, c->gbase);
+                                                       c->theta_df, c->gbase, c->kcount, c->fx_info);
 }
 
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
@@ -505,7 +621,7 @@ int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
     k_spread_multipoles<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB,
                                                                     c->atomC, c->atomD, K, c->grid64);
     bool split = true;
-    if ((r = conv_to_phi(c, st, &split))) return r;
+    if ((r = conv_to_phi(c, st, &split, false))) return r;
     gather_df<false>(c, st, out_add, split);
   } else {
     cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
@@ -561,17 +677,21 @@ int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, 
 
 // Reciprocal field of the dipoles v on stream st: out (+)= -grad phi. With
 // set = true the result overwrites out (used when it runs beside the real-space
-// kernel on a second stream and is summed later).
-int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStream_t st, bool set) {
+// kernel on a second stream and is summed later). In a float64 context v must
+// come with its double-float split (v32, vlo) and the per-block maxima that the
+// splitting kernel left in vmax_part.
+int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* out,
+                     cudaStream_t st, bool set) {
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
-  k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-      n, c->theta, c->gbase, v, K, c->grid64);
-  if (c->theta_df) {  // float64 context: own FFT (or cuFFT + split) and double-float gather
+  if (c->theta_df) {  // float64 context: fixed-point spread, own FFT (or cuFFT + split), double-float gather
+    if (!v32 || !vlo) return fail(c, AMP_ERR_STATE, "float64 reciprocal field needs the split vector");
+    k_spread_dipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
+        n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info, (float)((double)K / c->cfg.box), K,
+        c->gridfx, c->op_stop);
     bool split = true;
-    const int r = conv_to_phi(c, st, &split);
+    const int r = conv_to_phi(c, st, &split, true);
     if (r) return r;
     if (set)
       gather_df<true>(c, st, out, split);
@@ -579,7 +699,10 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, double4_32a* out, cudaStr
       gather_df<false>(c, st, out, split);
     return AMP_OK;
   }
-  // float64 check of the mixed path: cuFFT float64 and a float64 gather
+  // float64 check of the mixed path: float64 spread, cuFFT float64 and a float64 gather
+  cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
+  k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
+      n, c->theta, c->gbase, v, K, c->grid64);
   cufftSetStream(c->plan_d2z, st);
   cufftSetStream(c->plan_z2d, st);
   int r = exec_fft(c, false, true);
@@ -609,19 +732,19 @@ int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream
   cufftSetStream(c->plan_c2r, st);
   cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
   k_spread_dipoles<float, float4><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-      n, c->theta32, c->gbase, v, K, c->grid32);
+      n, c->theta32, c->gbase, v, K, c->grid32, c->op_stop);
   int r = exec_fft(c, true, true);
   if (!r) {
-    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
+    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32, c->op_stop);
     r = exec_fft(c, true, false);
   }
   if (!r) {
     if (set)
       k_gather_field<float, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-          n, c->theta32, c->gbase, c->grid32, K, out);
+          n, c->theta32, c->gbase, c->grid32, K, out, c->op_stop);
     else
       k_gather_field<float, false><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-          n, c->theta32, c->gbase, c->grid32, K, out);
+          n, c->theta32, c->gbase, c->grid32, K, out, c->op_stop);
   }
   cufftSetStream(c->plan_r2c, c->stream);
   cufftSetStream(c->plan_c2r, c->stream);

@@ -194,19 +194,3 @@ def test_sampled_rows_match_direct_scan(w23556):
     parts = w23556.op.apply_T_parts(v)
     ref_t = dipole_field_real_rows(w23556.sys, w23556.setup, v, rows)
     assert rel((t - parts[1] - parts[2])[rows], ref_t) < 1e-12
-
-
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_separate_kernel_iteration_matches_fused(w648, monkeypatch, precision):
-    """The four-kernel PCG iteration (used where cooperative launches are not
-    available) and the fused one take the same steps to the same dipoles."""
-    fused = run_gpu(w648, precision)
-    monkeypatch.setenv("AMOEBAPOL_PCG_SEPARATE", "1")
-    sep = run_gpu(w648, precision)
-    if precision == "fp64":
-        assert fused[3] == sep[3]
-        assert rms_debye(sep[2], w648.mu) < 1e-8
-        assert rms_debye(sep[2], fused[2]) < 1e-10
-    else:  # float32 PME spreading atomics add in a different order each run
-        assert rms_debye(sep[2], w648.mu) < 1e-5
-        assert rms_debye(sep[2], fused[2]) < 1e-6
