@@ -1,25 +1,33 @@
 // Double-float 3D FFT convolution for the float64 path's PME (power-of-two
-// grids): phi = unnormalised inverse DFT of G(m) * forward DFT(Q).
+// grids up to 64): phi = unnormalised C2R( G(m) * R2C(Q) ), the same
+// transform pair as cuFFT's D2Z / Z2D, with G given on the half spectrum
+// mz = 0 .. K/2.
 //
 // cuFFT's float64 transforms keep the scarce float64 pipe busy (about 90 us
-// for one forward + inverse 64^3 pair on GB300); these passes do the same
-// arithmetic in double-float (hi + lo floats, ~48 bits) on the float units.
-// Complex transforms of length K along each axis:
-//   z forward  (DIF, real float64 or fixed-point input as hi/lo, output bit-reversed)
-//   y forward  (DIF)
-//   x forward, multiply by G at the bit-reversed frequencies, x inverse (DIT)
-//   y inverse  (DIT, bit-reversed input, natural output)
-//   z inverse  (DIT), real part written as the hi/lo potential for the gather
+// for one forward + inverse 64^3 pair on GB300); these kernels do the same
+// arithmetic in double-float (hi + lo floats, ~48 bits) on the float units,
+// in three launches over the half spectrum:
+//   A (one block per x plane): two real z lines packed as one complex line
+//     (rows y and y + K/2), forward z transforms, the two half spectra
+//     separated, then forward y transforms; the plane's half spectrum goes
+//     to H[x][mz][my] (my in bit-reversed order);
+//   B (lines along x, eight neighbouring my per block): forward x transform,
+//     times G, inverse x transform, in place;
+//   C (one block per x plane): inverse y transforms, the two real z lines
+//     rebuilt from their half spectra as one complex line, inverse z
+//     transform; real part -> row y, imaginary part -> row y + K/2 of phi.
 // Forward: X(m) = sum_n x(n) exp(-2 pi i m n / K); inverse: exp(+...), no 1/K.
-// Each block stages kLines lines of one axis in shared memory (coalesced
-// loads: for the y and x passes the kLines lines are neighbours along z), one
-// warp transforms one line with radix-2 butterflies between __syncwarp()s.
+// A warp transforms one line in shared memory with radix-2 butterflies
+// between __syncwarp()s (decimation in frequency for the forward transforms,
+// natural in / bit-reversed out; decimation in time for the inverse ones).
+// Two real lines a, b packed as c = a + i b have spectra
+//   A(m) = (C(m) + conj C(K - m)) / 2,  B(m) = (C(m) - conj C(K - m)) / (2i),
+// and back, C(m) = A(m) + i B(m) with A(K - m) = conj A(m) (likewise B); the
+// imaginary parts of A and B at m = 0 and m = K/2 are dropped, as C2R does.
 #include "amp_internal.cuh"
 
 namespace amp {
 namespace {
-
-constexpr int kLines = 8;  // lines per block, one warp each
 
 struct cdf {
   dflt re, im;
@@ -35,6 +43,7 @@ __device__ __forceinline__ cdf c_mul_fwd(const cdf& a, dflt c, dflt s) {
 __device__ __forceinline__ cdf c_mul_inv(const cdf& a, dflt c, dflt s) {
   return {df_sub(df_mul(a.re, c), df_mul(a.im, s)), df_madd(a.re, s, df_mul(a.im, c))};
 }
+__device__ __forceinline__ dflt df_half(dflt a) { return {a.hi * 0.5f, a.lo * 0.5f}; }
 
 __device__ __forceinline__ cdf ld(const float4* p) {
   const float4 v = *p;
@@ -47,9 +56,10 @@ __device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((un
 // In-place transform of one line x[0..K) in shared memory by the 32 lanes of a warp.
 // tw[k] = (cos_hi, cos_lo, sin_hi, sin_lo) of 2 pi k / K, k < K/2.
 template <int K, bool kForward>
-__device__ __forceinline__ void line_fft(float4* x, const float4* __restrict__ tw) {
+__device__ __forceinline__ void line_fft(float4* x, const float4* tw) {
   const int lane = threadIdx.x & 31;
   if (kForward) {  // decimation in frequency: natural in, bit-reversed out
+#pragma unroll
     for (int s = K / 2; s >= 1; s >>= 1) {
       for (int b = lane; b < K / 2; b += 32) {
         const int i = (b / s) * 2 * s + (b % s), j = i + s;
@@ -61,6 +71,7 @@ __device__ __forceinline__ void line_fft(float4* x, const float4* __restrict__ t
       __syncwarp();
     }
   } else {  // decimation in time: bit-reversed in, natural out
+#pragma unroll
     for (int s = 1; s <= K / 2; s <<= 1) {
       for (int b = lane; b < K / 2; b += 32) {
         const int i = (b / s) * 2 * s + (b % s), j = i + s;
@@ -83,145 +94,191 @@ __device__ __forceinline__ dflt fixed_to_df(long long v, int s) {
   return df_add(df_two_sum(a * pow2f(40 - s), b * pow2f(20 - s)), dflt{c * pow2f(-s), 0.f});
 }
 
-// z forward: lines (x, y) contiguous in the real grid, either float64 or (kFixed)
-// 64-bit fixed point scaled by 2^fx_info[0], which is zeroed once read.
-template <int K, bool kFixed>
-__global__ void __launch_bounds__(32 * kLines) k_fft_z_fwd(const double* __restrict__ q,
-                                                          unsigned long long* __restrict__ qfx,
-                                                          const int* __restrict__ fx_info, float4* __restrict__ out,
-                                                          const float4* __restrict__ tw, const int* __restrict__ stop) {
-  if (stop && *stop) return;
-  __shared__ float4 sm[kLines][K];
-  const long long line0 = (long long)blockIdx.x * kLines;  // line = x*K + y
-  // the block's kLines lines are one contiguous run of kLines * K values
-  if (kFixed) {
-    const int sfx = fx_info[0];
-    constexpr int kPer = (kLines * K + 32 * kLines - 1) / (32 * kLines);
-    long long v[kPer];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int e = threadIdx.x + i * 32 * kLines;
-      v[i] = e < kLines * K ? (long long)qfx[line0 * K + e] : 0ll;
-    }
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int e = threadIdx.x + i * 32 * kLines;
-      if (e >= kLines * K) break;
-      qfx[line0 * K + e] = 0ull;
-      const dflt d = fixed_to_df(v[i], sfx);
-      sm[e / K][e % K] = make_float4(d.hi, d.lo, 0.f, 0.f);
-    }
-  } else {
-    for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-      const dflt d = df_split(q[line0 * K + e]);
-      sm[e / K][e % K] = make_float4(d.hi, d.lo, 0.f, 0.f);
-    }
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5;
-  line_fft<K, true>(sm[w], tw);
-  __syncthreads();
-  for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-    const int l = e / K, k = e % K;
-    out[(line0 + l) * K + k] = sm[l][k];
-  }
-}
-
-// y or x pass over the complex grid g[x][y][z]: lines along axis (1 = y,
-// 2 = x), kLines neighbouring z per block. kFusedG: forward, * G, inverse.
-template <int K, int kAxis, bool kForward, bool kFusedG>
-__global__ void __launch_bounds__(32 * kLines) k_fft_yx(float4* __restrict__ g, const float4* __restrict__ tw,
-                                                       const float2* __restrict__ Gdf, const int* __restrict__ stop) {
-  if (stop && *stop) return;
-  __shared__ float4 sm[kLines][K];
-  constexpr int kBits = __builtin_ctz(K);
-  // block -> (other index o, z0): o = x for the y pass, y for the x pass
-  const int zb = blockIdx.x % (K / kLines), o = blockIdx.x / (K / kLines);
-  const int z0 = zb * kLines;
-  auto index = [&](int t, int l) -> long long {  // t along the line, l = z offset
-    const int z = z0 + l;
-    return kAxis == 1 ? ((long long)o * K + t) * K + z : ((long long)t * K + o) * K + z;
-  };
-  for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-    const int t = e / kLines, l = e % kLines;  // consecutive threads: consecutive z
-    sm[l][t] = g[index(t, l)];
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5;
-  if (kFusedG) {
-    line_fft<K, true>(sm[w], tw);
-    // position t along x holds frequency bitrev(t); y and z are bit-reversed too
-    const int lane = threadIdx.x & 31;
-    const int my = bitrev(o, kBits), mz = bitrev(z0 + w, kBits);
-    for (int t = lane; t < K; t += 32) {
-      const float2 gv = Gdf[((long long)bitrev(t, kBits) * K + my) * K + mz];
-      const cdf a = ld(&sm[w][t]);
-      st(&sm[w][t], {df_mul(a.re, {gv.x, gv.y}), df_mul(a.im, {gv.x, gv.y})});
-    }
-    __syncwarp();
-    line_fft<K, false>(sm[w], tw);
-  } else {
-    line_fft<K, kForward>(sm[w], tw);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-    const int t = e / kLines, l = e % kLines;
-    g[index(t, l)] = sm[l][t];
-  }
-}
-
-// z inverse: real part of each point written as hi/lo floats.
 template <int K>
-__global__ void __launch_bounds__(32 * kLines) k_fft_z_inv(const float4* __restrict__ g, float2* __restrict__ phi,
-                                                          const float4* __restrict__ tw, const int* __restrict__ stop) {
+__host__ __device__ constexpr int plane_threads() {
+  return K >= 64 ? 1024 : (K >= 32 ? 512 : 256);
+}
+
+// shared memory of the plane kernels: twiddles, K/2 packed z lines, K/2 + 1 y lines
+template <int K>
+__host__ __device__ constexpr size_t plane_smem() {
+  return sizeof(float4) * (K / 2 + (K / 2) * K + (K / 2 + 1) * K);
+}
+
+// Pass A. Input plane x of the real grid, float64 or (kFixed) 64-bit fixed
+// point scaled by 2^fx_info[0], which is zeroed once read.
+template <int K, bool kFixed>
+__global__ void __launch_bounds__(plane_threads<K>()) k_fft_plane_fwd(const double* __restrict__ q,
+                                                                      unsigned long long* __restrict__ qfx,
+                                                                      const int* __restrict__ fx_info,
+                                                                      float4* __restrict__ H,
+                                                                      const float4* __restrict__ tw_g,
+                                                                      const int* __restrict__ stop) {
   if (stop && *stop) return;
-  __shared__ float4 sm[kLines][K];
-  const long long line0 = (long long)blockIdx.x * kLines;
-  for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-    const int l = e / K, k = e % K;
-    sm[l][k] = g[(line0 + l) * K + k];
+  constexpr int kBits = __builtin_ctz(K), kH = K / 2 + 1, NT = plane_threads<K>(), NW = NT / 32;
+  extern __shared__ float4 smem[];
+  float4* tw = smem;             // [K/2]
+  float4* zl = tw + K / 2;       // [K/2][K]: line y' = row y' + i row y' + K/2
+  float4* P = zl + (K / 2) * K;  // [K/2 + 1][K]: for each mz, the line over y
+  const int x = blockIdx.x, w = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < K / 2; k += NT) tw[k] = tw_g[k];
+  const long long base = (long long)x * K * K;
+  const int sfx = kFixed ? fx_info[0] : 0;
+  for (int e = threadIdx.x; e < K * K; e += NT) {
+    const dflt d = kFixed ? fixed_to_df((long long)qfx[base + e], sfx) : df_split(q[base + e]);
+    const int y = e / K, z = e % K;
+    float4* p = &zl[(y % (K / 2)) * K + z];
+    if (y < K / 2) {
+      p->x = d.hi;
+      p->y = d.lo;
+    } else {
+      p->z = d.hi;
+      p->w = d.lo;
+    }
   }
   __syncthreads();
-  const int w = threadIdx.x >> 5;
+  if (kFixed)  // every value of the plane is in shared memory: zero it for the next spreading
+    for (int e = threadIdx.x; e < K * K / 2; e += NT)
+      reinterpret_cast<ulonglong2*>(qfx + base)[e] = make_ulonglong2(0ull, 0ull);
+  for (int l = w; l < K / 2; l += NW) line_fft<K, true>(zl + l * K, tw);
+  __syncthreads();
+  // separate the two real lines' half spectra into P[mz][y]
+  for (int e = threadIdx.x; e < (K / 2) * kH; e += NT) {
+    const int yp = e / kH, mz = e % kH;
+    const cdf ck = ld(&zl[yp * K + bitrev(mz & (K - 1), kBits)]);
+    const cdf cm = ld(&zl[yp * K + bitrev((K - mz) & (K - 1), kBits)]);
+    const cdf a = {df_half(df_add(ck.re, cm.re)), df_half(df_sub(ck.im, cm.im))};
+    const cdf b = {df_half(df_add(ck.im, cm.im)), df_half(df_sub(cm.re, ck.re))};
+    st(&P[mz * K + yp], a);
+    st(&P[mz * K + yp + K / 2], b);
+  }
+  __syncthreads();
+  for (int l = w; l < kH; l += NW) line_fft<K, true>(P + l * K, tw);
+  __syncthreads();
+  float4* out = H + (long long)x * kH * K;
+  for (int e = threadIdx.x; e < kH * K; e += NT) out[e] = P[e];
+}
+
+// Pass B: lines along x of H[x][mz][my], kLinesB neighbouring my per block;
+// forward, times G(mx, my, mz), inverse. Position t along x holds
+// mx = bitrev(t); position p along y holds my = bitrev(p).
+constexpr int kLinesB = 8;
+template <int K>
+__global__ void __launch_bounds__(32 * kLinesB) k_fft_x_conv(float4* __restrict__ H, const float4* __restrict__ tw_g,
+                                                            const float2* __restrict__ Gh,
+                                                            const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  constexpr int kBits = __builtin_ctz(K), kH = K / 2 + 1;
+  constexpr int kGroups = K >= kLinesB ? K / kLinesB : 1;
+  __shared__ float4 tw[K / 2];
+  __shared__ float4 sm[kLinesB][K];
+  const int mz = blockIdx.x / kGroups, p0 = (blockIdx.x % kGroups) * kLinesB;
+  for (int k = threadIdx.x; k < K / 2; k += blockDim.x) tw[k] = tw_g[k];
+  for (int e = threadIdx.x; e < kLinesB * K; e += blockDim.x) {
+    const int t = e / kLinesB, l = e % kLinesB;  // consecutive threads: consecutive my
+    sm[l][t] = H[((long long)t * kH + mz) * K + p0 + l];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  line_fft<K, true>(sm[w], tw);
+  const int my = bitrev(p0 + w, kBits);
+  for (int t = lane; t < K; t += 32) {
+    const float2 g = Gh[((long long)bitrev(t, kBits) * K + my) * kH + mz];
+    const cdf a = ld(&sm[w][t]);
+    st(&sm[w][t], {df_mul(a.re, {g.x, g.y}), df_mul(a.im, {g.x, g.y})});
+  }
+  __syncwarp();
   line_fft<K, false>(sm[w], tw);
   __syncthreads();
-  for (int e = threadIdx.x; e < kLines * K; e += blockDim.x) {
-    const int l = e / K, k = e % K;
-    const float4 v = sm[l][k];
-    phi[(line0 + l) * K + k] = make_float2(v.x, v.y);
+  for (int e = threadIdx.x; e < kLinesB * K; e += blockDim.x) {
+    const int t = e / kLinesB, l = e % kLinesB;
+    H[((long long)t * kH + mz) * K + p0 + l] = sm[l][t];
+  }
+}
+
+// Pass C: inverse y transforms of plane x, the real z lines rebuilt pairwise,
+// inverse z transforms; phi[x][y][z] as hi/lo floats.
+template <int K>
+__global__ void __launch_bounds__(plane_threads<K>()) k_fft_plane_inv(const float4* __restrict__ H,
+                                                                      float2* __restrict__ phi,
+                                                                      const float4* __restrict__ tw_g,
+                                                                      const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  constexpr int kBits = __builtin_ctz(K), kH = K / 2 + 1, NT = plane_threads<K>(), NW = NT / 32;
+  extern __shared__ float4 smem[];
+  float4* tw = smem;
+  float4* zl = tw + K / 2;
+  float4* P = zl + (K / 2) * K;
+  const int x = blockIdx.x, w = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < K / 2; k += NT) tw[k] = tw_g[k];
+  const float4* in = H + (long long)x * kH * K;
+  for (int e = threadIdx.x; e < kH * K; e += NT) P[e] = in[e];
+  __syncthreads();
+  for (int l = w; l < kH; l += NW) line_fft<K, false>(P + l * K, tw);
+  __syncthreads();
+  // C(m) = A(m) + i B(m); A = row y', B = row y' + K/2; stored bit-reversed for the DIT
+  for (int e = threadIdx.x; e < (K / 2) * K; e += NT) {
+    const int yp = e / K, m = e % K;
+    const int mh = m <= K / 2 ? m : K - m;
+    cdf a = ld(&P[mh * K + yp]), b = ld(&P[mh * K + yp + K / 2]);
+    if (mh == 0 || mh == K / 2) {
+      a.im = {0.f, 0.f};
+      b.im = {0.f, 0.f};
+    }
+    cdf c;
+    if (m <= K / 2)
+      c = {df_sub(a.re, b.im), df_add(a.im, b.re)};
+    else
+      c = {df_add(a.re, b.im), df_sub(b.re, a.im)};
+    st(&zl[yp * K + bitrev(m, kBits)], c);
+  }
+  __syncthreads();
+  for (int l = w; l < K / 2; l += NW) line_fft<K, false>(zl + l * K, tw);
+  __syncthreads();
+  float2* out = phi + (long long)x * K * K;
+  for (int e = threadIdx.x; e < K * K; e += NT) {
+    const int y = e / K, z = e % K;
+    const float4 v = zl[(y % (K / 2)) * K + z];
+    out[e] = y < K / 2 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
   }
 }
 
 template <int K>
 void run_conv(amp_ctx* c, cudaStream_t st, bool fixed) {
-  const int lines = K * K;
-  const int blocks = lines / kLines;
+  constexpr size_t smem = plane_smem<K>();
+  constexpr int NT = plane_threads<K>();
+  static const bool attr = [] {  // opt in to more than 48 KB of dynamic shared memory, once per process
+    cudaFuncSetAttribute(k_fft_plane_fwd<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fft_plane_fwd<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fft_plane_inv<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return true;
+  }();
+  (void)attr;
+  constexpr int kGroups = K >= kLinesB ? K / kLinesB : 1;
   const float4* tw = c->fft_tw;
-  float4* g = c->fft_grid;
-  c->n_launch += 5;
+  float4* H = c->fft_grid;
   const int* stop = c->op_stop;
+  c->n_launch += 3;
   if (fixed)
-    k_fft_z_fwd<K, true><<<blocks, 32 * kLines, 0, st>>>(nullptr, c->gridfx, c->fx_info, g, tw, stop);
+    k_fft_plane_fwd<K, true><<<K, NT, smem, st>>>(nullptr, c->gridfx, c->fx_info, H, tw, stop);
   else
-    k_fft_z_fwd<K, false><<<blocks, 32 * kLines, 0, st>>>(c->grid64, nullptr, nullptr, g, tw, stop);
-  k_fft_yx<K, 1, true, false><<<blocks, 32 * kLines, 0, st>>>(g, tw, nullptr, stop);
-  k_fft_yx<K, 2, true, true><<<blocks, 32 * kLines, 0, st>>>(g, tw, c->fft_G, stop);
-  k_fft_yx<K, 1, false, false><<<blocks, 32 * kLines, 0, st>>>(g, tw, nullptr, stop);
-  k_fft_z_inv<K><<<blocks, 32 * kLines, 0, st>>>(g, c->phi_df, tw, stop);
+    k_fft_plane_fwd<K, false><<<K, NT, smem, st>>>(c->grid64, nullptr, nullptr, H, tw, stop);
+  k_fft_x_conv<K><<<(K / 2 + 1) * kGroups, 32 * kLinesB, 0, st>>>(H, tw, c->fft_G, stop);
+  k_fft_plane_inv<K><<<K, NT, smem, st>>>(H, c->phi_df, tw, stop);
 }
 
 }  // namespace
 
-bool fft_df_supported(int K) { return K == 16 || K == 32 || K == 64 || K == 128; }
+bool fft_df_supported(int K) { return K == 16 || K == 32 || K == 64; }
 
-// Tables for the double-float FFT: twiddles of length K and the full-spectrum
-// influence function as hi/lo pairs (G(mx, my, mz) = G_half at min(mz, K - mz)).
+// Tables for the double-float FFT: twiddles of length K and the influence
+// function on the half spectrum as hi/lo pairs, G_half[(mx K + my)(K/2+1) + mz].
 int fft_df_setup(amp_ctx* c, const double* G_half) {
   const int K = c->K;
-  const long long ng = (long long)K * K * K;
+  const long long nh = (long long)K * K * (K / 2 + 1);
   int r;
   if (!c->fft_grid) {
-    if ((r = dev_alloc(c, &c->fft_grid, ng)) || (r = dev_alloc(c, &c->fft_G, ng)) ||
+    if ((r = dev_alloc(c, &c->fft_grid, nh)) || (r = dev_alloc(c, &c->fft_G, nh)) ||
         (r = dev_alloc(c, &c->fft_tw, K / 2)))
       return r;
   }
@@ -232,20 +289,15 @@ int fft_df_setup(amp_ctx* c, const double* G_half) {
     const float ch = (float)cs, sh = (float)sn;
     tw[k] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(sn - (double)sh));
   }
-  std::vector<float2> G(ng);
-  const int kh = K / 2 + 1;
-  for (int mx = 0; mx < K; ++mx)
-    for (int my = 0; my < K; ++my)
-      for (int mz = 0; mz < K; ++mz) {
-        const int mzh = mz <= K / 2 ? mz : K - mz;
-        const double v = G_half[((long long)mx * K + my) * kh + mzh];
-        const float h = (float)v;
-        G[((long long)mx * K + my) * K + mz] = make_float2(h, (float)(v - (double)h));
-      }
+  std::vector<float2> G(nh);
+  for (long long k = 0; k < nh; ++k) {
+    const float h = (float)G_half[k];
+    G[k] = make_float2(h, (float)(G_half[k] - (double)h));
+  }
   if ((r = cuda_check(c, cudaMemcpyAsync(c->fft_tw, tw.data(), sizeof(float4) * tw.size(), cudaMemcpyHostToDevice,
                                          c->stream),
                       "twiddle upload")) ||
-      (r = cuda_check(c, cudaMemcpyAsync(c->fft_G, G.data(), sizeof(float2) * ng, cudaMemcpyHostToDevice, c->stream),
+      (r = cuda_check(c, cudaMemcpyAsync(c->fft_G, G.data(), sizeof(float2) * nh, cudaMemcpyHostToDevice, c->stream),
                       "G upload")))
     return r;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "fft tables");
@@ -257,7 +309,6 @@ void fft_df_convolve(amp_ctx* c, cudaStream_t st, bool fixed) {
     case 16: run_conv<16>(c, st, fixed); break;
     case 32: run_conv<32>(c, st, fixed); break;
     case 64: run_conv<64>(c, st, fixed); break;
-    case 128: run_conv<128>(c, st, fixed); break;
     default: break;
   }
 }
