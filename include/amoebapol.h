@@ -63,7 +63,7 @@ typedef struct {
                         0 = isolated cluster: every pair, no cutoff, no Ewald
                         (cutoff, ewald_beta, pme_grid, pme_order ignored) */
   double cutoff;     /* real-space cutoff (Angstrom) */
-  double ewald_beta; /* Ewald splitting parameter (1/Angstrom), > 0 */
+  double ewald_beta; /* Ewald splitting parameter (1/Angstrom), > 0, with ewald_beta * cutoff <= 8 */
   int pme_grid;      /* PME points per axis, >= 8 */
   int pme_order;     /* B-spline order; must be 5 */
   double tol_debye;  /* PCG stop: RMS of alpha*residual in Debye < tol */

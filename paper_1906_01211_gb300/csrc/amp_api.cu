@@ -82,7 +82,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
                    (void**)&c->trec, (void**)&c->plo, (void**)&c->mp_df, (void**)&c->wv,
-                   (void**)&c->theta_df};
+                   (void**)&c->theta_df, (void**)&c->pd};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -101,7 +101,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
       (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)) ||
       (r = dev_alloc(c, &c->wv, cap)) ||
-      (r = dev_alloc(c, &c->mp_df, 5LL * cap)))
+      (r = dev_alloc(c, &c->mp_df, 5LL * cap)) || (r = dev_alloc(c, &c->pd, 3LL * cap)))
     return r;
   c->n_cap = cap;
   return AMP_OK;
@@ -121,7 +121,8 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
   if (!(cfg->tol_debye > 0.0) || cfg->max_iter < 1 || (cfg->precision != AMP_FP64 && cfg->precision != AMP_MIXED))
     return AMP_ERR_ARG;
   if (!cluster && (!(cfg->box > 0.0) || !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) ||
-                   !(cfg->ewald_beta > 0.0) || cfg->pme_grid < 8 || cfg->pme_grid > 512 || cfg->pme_order != kOrder))
+                   !(cfg->ewald_beta > 0.0) || cfg->pme_grid < 8 || cfg->pme_grid > 512 || cfg->pme_order != kOrder ||
+                   !(cfg->ewald_beta * cfg->cutoff <= (double)kErfcxMax)))
     return AMP_ERR_ARG;
   amp_ctx* c = new (std::nothrow) amp_ctx();
   if (!c) return AMP_ERR_OOM;
@@ -153,7 +154,7 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return AMP_ERR_CUDA;
   }
-  if (!cluster && (r = pme_setup(c))) {
+  if (!cluster && ((r = pme_setup(c)) || (cfg->precision == AMP_FP64 && (r = dfm_setup(c))))) {
     amp_destroy(c);
     return r;
   }
@@ -168,8 +169,9 @@ int amp_reconfigure(amp_ctx* c, const amp_config* cfg) {
     return fail(c, AMP_ERR_ARG, "amp_reconfigure: precision and cluster/periodic mode are fixed at creation");
   if (!(cfg->tol_debye > 0.0) || cfg->max_iter < 1) return fail(c, AMP_ERR_ARG, "amp_reconfigure: bad tolerance");
   if (!cluster && (cfg->pme_grid != c->cfg.pme_grid || cfg->pme_order != kOrder || !(cfg->box > 0.0) ||
-                   !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) || !(cfg->ewald_beta > 0.0)))
-    return fail(c, AMP_ERR_ARG, "amp_reconfigure: same PME grid required, cutoff < box/2, beta > 0");
+                   !(cfg->cutoff > 0.0) || !(2.0 * cfg->cutoff < cfg->box) || !(cfg->ewald_beta > 0.0) ||
+                   !(cfg->ewald_beta * cfg->cutoff <= (double)kErfcxMax)))
+    return fail(c, AMP_ERR_ARG, "amp_reconfigure: same PME grid required, cutoff < box/2, 0 < beta cutoff <= 8");
   const bool box_changed = cfg->box != c->cfg.box || cfg->ewald_beta != c->cfg.ewald_beta;
   c->cfg = *cfg;
   c->have_system = false;

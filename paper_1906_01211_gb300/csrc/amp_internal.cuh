@@ -62,6 +62,9 @@ struct amp_ctx {
   double4_32a *atomA = nullptr, *atomB = nullptr, *atomC = nullptr, *atomD = nullptr;
   double2* alph = nullptr;  // (alpha, 1/alpha) per sorted atom
   float4* mp_df = nullptr;  // float64 path: q, d, Theta as hi/lo float pairs, 5 float4 per atom
+  // float64 path, per atom: (x, y, z, 1/sqrt(alpha)) hi, the same lo, (thole hi, lo, molecule, 0)
+  float4* pd = nullptr;
+  float2* dfm = nullptr;    // float64 path: table of the double-float elementary functions
   float4* pos32 = nullptr;
 
   // neighbour lists
@@ -185,6 +188,7 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
 
 // pair terms and real-space sums (amp_pair.cu)
 void launch_pair_build(amp_ctx* c);
+int dfm_setup(amp_ctx* c);  // builds c->dfm
 void launch_e0_real(amp_ctx* c, double4_32a* out);  // out = real-space E0 + self
 // out = T_real v + self v (float64 path, double-float arithmetic; vhi + vlo = v)
 void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const float4* vlo, double4_32a* out);
@@ -290,6 +294,70 @@ __device__ __forceinline__ dflt df_madd(dflt a, dflt b, dflt c) {
   dflt acc = c;
   df_fma(acc, a.hi, a.lo, b.hi, b.lo);
   return acc;
+}
+
+// ---- double-float elementary functions (float units only)
+
+// 1/sqrt(a), a > 0: float estimate, then two Newton steps y += y (1 - a y^2) / 2
+// in double-float (each step doubles the correct bits, up to the format's ~48).
+__device__ __forceinline__ dflt df_rsqrt(dflt a) {
+  dflt y = {rsqrtf(a.hi), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const dflt e = df_sub({1.f, 0.f}, df_mul(a, df_mul(y, y)));
+    y = df_madd(df_mul(y, {0.5f, 0.f}), e, y);
+  }
+  return y;
+}
+
+// Table of the double-float elementary functions (kDfmTableSize float2, hi/lo):
+// [0, kErfcxIntervals * kErfcxTerms): Taylor coefficients of erfcx(x) =
+// exp(x^2) erfc(x) at the centres of the intervals [i h, (i+1) h), h = 1/8;
+// then exp(j/32) for j = -11 .. 11.
+constexpr int kErfcxIntervals = 64, kErfcxTerms = 12;
+constexpr float kErfcxMax = 8.f;  // x range covered: [0, 8]
+constexpr int kExpTable = kErfcxIntervals * kErfcxTerms;
+constexpr int kDfmTableSize = kExpTable + 23;
+
+// exp(-y), y >= 0, by table-driven reduction (Tang, ACM TOMS 15, 1989):
+// k = round(y / ln 2), t = k ln 2 - y (ln 2 split three ways, Cody & Waite, so
+// k C1 is exact), j = round(32 t), s = t - j/32 (|s| <= 1/64);
+// exp(-y) = 2^-k exp(j/32) exp(s), exp(s) by its Taylor series to s^7
+// (remainder < 1e-19). Results below 2^-126 (y >= 87) are returned as 0.
+__device__ __forceinline__ dflt df_exp_neg(dflt y, const float2* __restrict__ tab) {
+  if (!(y.hi < 87.f)) return {0.f, 0.f};
+  constexpr float kC1 = 6.931457520e-01f, kC2 = 1.428606765e-06f, kC3 = 5.495603972e-14f;
+  const float k = rintf(y.hi * 1.44269502f);
+  dflt t = df_add({k * kC1, 0.f}, df_neg(y));
+  t = df_add(t, df_mul({k, 0.f}, {kC2, 0.f}));
+  t = df_add(t, {k * kC3, 0.f});
+  const float jf = rintf(t.hi * 32.f);
+  const dflt s = df_add(t, {-jf * 0.03125f, 0.f});
+  dflt p = {1.984127011e-04f, -2.725596875e-12f};                // 1/7!
+  p = df_madd(p, s, {1.388888923e-03f, -3.363109444e-11f});      // 1/6!
+  p = df_madd(p, s, {8.333333768e-03f, -4.346172033e-10f});      // 1/5!
+  p = df_madd(p, s, {4.166666791e-02f, -1.241763470e-09f});      // 1/4!
+  p = df_madd(p, s, {1.666666716e-01f, -4.967053879e-09f});      // 1/3!
+  p = df_madd(p, s, {0.5f, 0.f});
+  p = df_madd(p, s, {1.f, 0.f});
+  p = df_madd(p, s, {1.f, 0.f});
+  const float2 e = tab[kExpTable + 11 + (int)jf];
+  const dflt r = df_mul(p, {e.x, e.y});
+  const float sc = __int_as_float((127 - (int)k) << 23);  // 2^-k, k <= 126
+  return {r.hi * sc, r.lo * sc};
+}
+
+// erfcx(x) = exp(x^2) erfc(x), 0 <= x <= 8: Taylor polynomial of the interval
+// holding x (coefficients from the ODE y' = 2 x y - 2/sqrt(pi); see the host
+// table builder), evaluated by Horner in double-float at t = x - centre.
+__device__ __forceinline__ dflt df_erfcx(dflt x, const float2* __restrict__ tab) {
+  const int i = max(0, min(kErfcxIntervals - 1, (int)(x.hi * 8.f)));
+  const dflt t = df_add(x, {-((float)i + 0.5f) * 0.125f, 0.f});
+  const float2* c = tab + i * kErfcxTerms;
+  dflt p = {c[kErfcxTerms - 1].x, c[kErfcxTerms - 1].y};
+#pragma unroll
+  for (int n = kErfcxTerms - 2; n >= 0; --n) p = df_madd(p, t, {c[n].x, c[n].y});
+  return p;
 }
 
 // Sum over the kRowGroup lanes of one row; the mask names exactly this group.

@@ -19,6 +19,9 @@
 //
 // Each iteration then reduces over the full neighbour rows: a group of
 // kRowGroup lanes per atom sums T_ij v_j, no atomics, fixed order.
+#include <cmath>
+#include <vector>
+
 #include "amp_internal.cuh"
 
 namespace amp {
@@ -140,12 +143,18 @@ __global__ void __launch_bounds__(256) k_pair_build(long long nh, const int* __r
   e[5] = ez;
 }
 
-// ---- float64 path of the pair build: float64 only where double-float has no
-// cheap form (minimum image, sqrt, 1/r, erfc, the two exp); every product and
-// sum after that runs in double-float on the float units. Per-atom multipoles
-// come pre-split (mp_df: q, d, Theta as hi/lo), outputs stay split: tensor as
-// written for k_t_real_df, fields as Ep[pid] = 12 floats (side 0 x,y,z hi/lo,
-// then side 1).
+// ---- float64 path of the pair build, entirely in double-float on the float
+// units: the minimum image from split positions, 1/r by Newton steps,
+// exp(-beta^2 r^2) and the Thole exponential by table-driven reduction, and
+// erfc(beta r) = erfcx(beta r) exp(-beta^2 r^2) with erfcx from a per-interval
+// Taylor table (df_rsqrt, df_exp_neg, df_erfcx). Per-atom inputs come
+// pre-split (pd: position, 1/sqrt(alpha), Thole a, molecule; mp_df: q, d,
+// Theta); outputs stay split: the tensor as read by k_t_real_df, the fields
+// as Ep[pid] = 12 floats (side 0 x,y,z hi/lo, then side 1).
+struct PairGeomDf {
+  dflt L, beta, twob2, gpre;
+  float invL;
+};
 
 // Field at r of a multipole with kernels b1..b3, all double-float.
 __device__ __forceinline__ void mp_field_df(const dflt r[3], const dflt* mp, dflt b1, dflt b2, dflt b3, dflt out[3]) {
@@ -163,40 +172,46 @@ __device__ __forceinline__ void mp_field_df(const dflt r[3], const dflt* mp, dfl
   for (int a = 0; a < 3; ++a) out[a] = df_sub(df_sub(df_mul(rad, r[a]), df_mul(b1, mp[1 + a])), df_mul(c2, t[a]));
 }
 
+// minimum-image component: the pair lies within rc < L/2, so rounding d/L
+// from the hi part picks the same image as exact arithmetic would
+__device__ __forceinline__ dflt min_image_df(dflt d, const PairGeomDf& g) {
+  const float sh = rintf(d.hi * g.invL);
+  return sh == 0.f ? d : df_sub(d, df_mul({sh, 0.f}, g.L));
+}
+
 __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* __restrict__ half_i,
                                                        const int* __restrict__ half_j,
-                                                       const double4_32a* __restrict__ A,
-                                                       const double4_32a* __restrict__ B,
-                                                       const double4_32a* __restrict__ D,
-                                                       const float4* __restrict__ mp_df, PairGeom g,
-                                                       float4* __restrict__ T, float* __restrict__ Ep) {
+                                                       const float4* __restrict__ pd,
+                                                       const float4* __restrict__ mp_df, PairGeomDf g,
+                                                       const float2* __restrict__ tab, float4* __restrict__ T,
+                                                       float* __restrict__ Ep) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
-  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], di = D[i], dj = D[j];
-  // the pair is within rc < L/2, so d * (1/L) rounds to the same image as d / L
-  const double iL = g.invL;
-  const double rx0 = ai.x - aj.x, ry0 = ai.y - aj.y, rz0 = ai.z - aj.z;
-  const double rx = rx0 - g.L * rint(rx0 * iL), ry = ry0 - g.L * rint(ry0 * iL), rz = rz0 - g.L * rint(rz0 * iL);
-  const double r2 = rx * rx + ry * ry + rz * rz;
-  const double ir = rsqrt(r2);
-  const double rr = r2 * ir;
-  const double br = g.beta * rr;
-  const double fac64 = exp(-br * br) * g.gpre;
-  const double b064 = erfc(br) * ir;
-  const double x = min(di.z, dj.z) * r2 * rr * bi.w * bj.w;
-  const double e64 = exp(-x);
-  const dflt R[3] = {df_split(rx), df_split(ry), df_split(rz)};
+  const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
+  const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
+  const dflt R[3] = {min_image_df(df_sub({hi_i.x, lo_i.x}, {hi_j.x, lo_j.x}), g),
+                     min_image_df(df_sub({hi_i.y, lo_i.y}, {hi_j.y, lo_j.y}), g),
+                     min_image_df(df_sub({hi_i.z, lo_i.z}, {hi_j.z, lo_j.z}), g)};
   const dflt NR[3] = {df_neg(R[0]), df_neg(R[1]), df_neg(R[2])};
-  const dflt IR = df_split(ir), B0 = df_split(b064), X = df_split(x), E = df_split(e64);
-  dflt FAC = df_split(fac64);
-  const dflt TB2 = df_split(g.twob2);
+  const dflt R2 = df_madd(R[2], R[2], df_madd(R[1], R[1], df_mul(R[0], R[0])));
+  const dflt IR = df_rsqrt(R2);
+  const dflt RR = df_mul(R2, IR);
+  const dflt BR = df_mul(g.beta, RR);
+  const dflt E2 = df_exp_neg(df_mul(BR, BR), tab);  // exp(-beta^2 r^2)
+  const dflt B0 = df_mul(df_mul(df_erfcx(BR, tab), E2), IR);
+  dflt FAC = df_mul(E2, g.gpre);
+  // Thole: x = a r^3 / sqrt(alpha_i alpha_j), a = min(a_i, a_j)
+  const dflt A = th_i.x < th_j.x || (th_i.x == th_j.x && th_i.y <= th_j.y) ? dflt{th_i.x, th_i.y}
+                                                                           : dflt{th_j.x, th_j.y};
+  const dflt X = df_mul(df_mul(A, df_mul(R2, RR)), df_mul({hi_i.w, lo_i.w}, {hi_j.w, lo_j.w}));
+  const dflt E = df_exp_neg(X, tab);
   const dflt ONE = {1.f, 0.f}, THREE = {3.f, 0.f}, FIVE = {5.f, 0.f};
   const dflt IR2 = df_mul(IR, IR);
   const dflt B1 = df_mul(df_add(B0, FAC), IR2);
-  FAC = df_mul(FAC, TB2);
+  FAC = df_mul(FAC, g.twob2);
   const dflt B2 = df_mul(df_madd(THREE, B1, FAC), IR2);
-  FAC = df_mul(FAC, TB2);
+  FAC = df_mul(FAC, g.twob2);
   const dflt B3 = df_mul(df_madd(FIVE, B2, FAC), IR2);
   const dflt bare1 = df_mul(IR, IR2);
   const dflt bare2 = df_mul(df_mul(THREE, bare1), IR2);
@@ -208,7 +223,7 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
   const dflt b1u = df_sub(B1, df_mul(d3, bare1));
   const dflt b2u = df_sub(B2, df_mul(d5, bare2));
   dflt b1e, b2e, b3e;
-  if (di.w == dj.w) {
+  if (__float_as_int(th_i.z) == __float_as_int(th_j.z)) {  // same molecule
     b1e = df_sub(B1, bare1);
     b2e = df_sub(B2, bare2);
     b3e = df_sub(B3, bare3);
@@ -247,10 +262,11 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
   e[2] = make_float4(fj[1].hi, fj[1].lo, fj[2].hi, fj[2].lo);
 }
 
-// mp_df[s] = q, d, Theta of sorted atom s as hi/lo float pairs (5 float4)
+// Per sorted atom s: mp_df[s] = q, d, Theta as hi/lo float pairs (5 float4);
+// pd[s] = (x, y, z, 1/sqrt(alpha)) hi, the same lo, (Thole a hi, lo, molecule, 0).
 __global__ void k_split_multipoles(int n, const double4_32a* __restrict__ A, const double4_32a* __restrict__ B,
                                    const double4_32a* __restrict__ C, const double4_32a* __restrict__ D,
-                                   float4* __restrict__ mp) {
+                                   float4* __restrict__ mp, float4* __restrict__ pd) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double4_32a a = A[s], b = B[s], c = C[s], d = D[s];
@@ -258,6 +274,12 @@ __global__ void k_split_multipoles(int n, const double4_32a* __restrict__ A, con
   for (int k = 0; k < 5; ++k) {
     const dflt u = df_split(v[2 * k]), w = df_split(v[2 * k + 1]);
     mp[5 * (long long)s + k] = make_float4(u.hi, u.lo, w.hi, w.lo);
+  }
+  if (pd) {
+    const dflt x = df_split(a.x), y = df_split(a.y), z = df_split(a.z), is = df_split(b.w), th = df_split(d.z);
+    pd[3 * (long long)s] = make_float4(x.hi, y.hi, z.hi, is.hi);
+    pd[3 * (long long)s + 1] = make_float4(x.lo, y.lo, z.lo, is.lo);
+    pd[3 * (long long)s + 2] = make_float4(th.hi, th.lo, __int_as_float((int)d.w), 0.f);
   }
 }
 
@@ -447,7 +469,43 @@ PairGeom geom(const amp_ctx* c) {
   return g;
 }
 
+dflt dsplit_host(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
 }  // namespace
+
+// Table for df_erfcx and df_exp_neg, built in long double on the host.
+// erfcx(x0 + t) = sum_n a_n t^n at the centre x0 of each interval, from the
+// differential equation y' = 2 x y - 2/sqrt(pi) of erfcx:
+//   a_0 = erfc(x0) exp(x0^2), a_1 = 2 x0 a_0 - 2/sqrt(pi),
+//   (n + 1) a_{n+1} = 2 x0 a_n + 2 a_{n-1}  (n >= 1);
+// with |t| <= 1/16 the series is cut after t^11 (remainder below 1e-17).
+int dfm_setup(amp_ctx* c) {
+  std::vector<float2> tab(kDfmTableSize);
+  auto put = [&](int k, long double v) {
+    const float h = (float)v;
+    tab[k] = make_float2(h, (float)(v - (long double)h));
+  };
+  const long double two_rsqrtpi = 2.0L / std::sqrt(std::acos(-1.0L));
+  for (int i = 0; i < kErfcxIntervals; ++i) {
+    const long double x0 = ((long double)i + 0.5L) / 8.0L;
+    long double a[kErfcxTerms];
+    a[0] = std::erfc(x0) * std::exp(x0 * x0);
+    a[1] = 2.0L * x0 * a[0] - two_rsqrtpi;
+    for (int n = 1; n + 1 < kErfcxTerms; ++n) a[n + 1] = (2.0L * x0 * a[n] + 2.0L * a[n - 1]) / (long double)(n + 1);
+    for (int n = 0; n < kErfcxTerms; ++n) put(i * kErfcxTerms + n, a[n]);
+  }
+  for (int j = -11; j <= 11; ++j) put(kExpTable + 11 + j, std::exp((long double)j / 32.0L));
+  int r;
+  if (!c->dfm && (r = dev_alloc(c, &c->dfm, kDfmTableSize))) return r;
+  if ((r = cuda_check(c, cudaMemcpyAsync(c->dfm, tab.data(), sizeof(float2) * kDfmTableSize, cudaMemcpyHostToDevice,
+                                         c->stream),
+                      "function table upload")))
+    return r;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "function table upload");
+}
 
 void launch_pair_build(amp_ctx* c) {
   if (c->n_half == 0) return;
@@ -455,10 +513,16 @@ void launch_pair_build(amp_ctx* c) {
   const int blocks = amp_blocks(c->n_half, 256);
   if (c->cfg.precision == AMP_FP64) {
     c->n_launch += 2;
+    PairGeomDf gd;
+    gd.L = dsplit_host(g.L);
+    gd.beta = dsplit_host(g.beta);
+    gd.twob2 = dsplit_host(g.twob2);
+    gd.gpre = dsplit_host(g.gpre);
+    gd.invL = (float)g.invL;
     k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
-                                                                    c->mp_df);
-    k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB, c->atomD,
-                                                   c->mp_df, g, reinterpret_cast<float4*>(c->T64),
+                                                                    c->mp_df, c->pd);
+    k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, gd, c->dfm,
+                                                   reinterpret_cast<float4*>(c->T64),
                                                    reinterpret_cast<float*>(c->Ep64));
     return;
   }
