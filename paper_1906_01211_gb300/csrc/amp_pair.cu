@@ -391,11 +391,23 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup; i < n; i += gridDim.x * (blockDim.x / kRowGroup)) {
   dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
   const int e = full_start[i + 1];
-  for (int k = full_start[i] + l; k < e; k += kRowGroup) {
-    // pair data is read once per product: streaming loads keep it from
-    // evicting the reciprocal-space grids that run beside this kernel
-    const int j = __ldcs(full_j + k);
-    const float4* t = T + 3 * (long long)(__ldcs(full_ref + k) >> 1);
+  // pair data is read once per product: streaming loads keep it from evicting
+  // the reciprocal-space grids that run beside this kernel. The next entry's
+  // indices are fetched one iteration ahead, so that each iteration waits for
+  // one round of loads (tensor, v_j) instead of two.
+  int k = full_start[i] + l;
+  int jn = 0, refn = 0;
+  if (k < e) {
+    jn = __ldcs(full_j + k);
+    refn = __ldcs(full_ref + k);
+  }
+  for (; k < e; k += kRowGroup) {
+    const int j = jn, ref = refn;
+    if (k + kRowGroup < e) {
+      jn = __ldcs(full_j + k + kRowGroup);
+      refn = __ldcs(full_ref + k + kRowGroup);
+    }
+    const float4* t = T + 3 * (long long)(ref >> 1);
     const float4 a = __ldcs(t), b = __ldcs(t + 1), c = __ldcs(t + 2);
     // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
     const float4 h = vhi[j], w = vlo[j];
@@ -412,10 +424,16 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
   sx = df_group_sum(sx);
   sy = df_group_sum(sy);
   sz = df_group_sum(sz);
-  if (l == 0) {
-    const double4_32a vi = v64[i];
-    out[i] = make_double4_32a((double)sx.hi + (double)sx.lo + selfc * vi.x, (double)sy.hi + (double)sy.lo + selfc * vi.y,
-                              (double)sz.hi + (double)sz.lo + selfc * vi.z, 0.0);
+  // lanes 0..2 convert one component each: a float64 instruction holds the
+  // float64 pipe as long for one active lane as for 32
+  if (l < 4) {
+    double* o = reinterpret_cast<double*>(out + i);
+    if (l < 3) {
+      const dflt sc = l == 0 ? sx : (l == 1 ? sy : sz);
+      o[l] = (double)sc.hi + (double)sc.lo + selfc * reinterpret_cast<const double*>(v64 + i)[l];
+    } else {
+      o[3] = 0.0;
+    }
   }
   }
 }

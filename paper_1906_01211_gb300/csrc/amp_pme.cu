@@ -416,17 +416,17 @@ __global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __
     ey = df_add(ey, {__shfl_xor_sync(mask, ey.hi, o, kPmeGroup), __shfl_xor_sync(mask, ey.lo, o, kPmeGroup)});
     ez = df_add(ez, {__shfl_xor_sync(mask, ez.hi, o, kPmeGroup), __shfl_xor_sync(mask, ez.lo, o, kPmeGroup)});
   }
-  if (tx == 0) {
-    const double fx = df_to_double(ex), fy = df_to_double(ey), fz = df_to_double(ez);
-    if (kSet) {
-      out[s] = make_double4_32a(-fx, -fy, -fz, 0.0);
-    } else {
-      double4_32a o = out[s];
-      o.x -= fx;
-      o.y -= fy;
-      o.z -= fz;
-      out[s] = o;
-    }
+  // lanes 0..2 finish one component each (float64 instructions cost the same
+  // for one active lane as for 32)
+  double* o = reinterpret_cast<double*>(out + s);
+  if (tx < 3) {
+    const double f = df_to_double(tx == 0 ? ex : (tx == 1 ? ey : ez));
+    if (kSet)
+      o[tx] = -f;
+    else
+      o[tx] -= f;
+  } else if (kSet && tx == 3) {
+    o[3] = 0.0;
   }
 }
 
