@@ -71,7 +71,9 @@ struct amp_ctx {
   int *full_cnt = nullptr, *half_cnt = nullptr, *full_start = nullptr, *half_start = nullptr;
   int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr, *tr_tmp = nullptr;
   long long n_full = 0, n_half = 0, cap_full = 0, cap_half = 0;
-  int* flags = nullptr;  // [0] list overflow / search failure
+  int* flags = nullptr;  // [0] bit 1 list transpose failure, bit 2 bad alpha, bit 4 slab overflow
+  int* slab = nullptr;   // single-pass list: owned neighbours per atom, fixed row capacity
+  long long slab_cap = 0;
 
   // pair data
   double* T64 = nullptr;

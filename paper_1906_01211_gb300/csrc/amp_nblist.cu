@@ -13,12 +13,17 @@
 //   2. exclusive scan -> cell_start; scatter; stable sort inside each cell by
 //      the caller's index, so the cell order does not depend on atomics;
 //   3. gather the atom records into cell order (float64 + wrapped float32);
-//   4. count pass: one warp per atom, candidates from the (distinct) 27
-//      neighbour cells, float32 distance pre-filter with a margin, exact
-//      float64 decision d.d < rc^2 for candidates near the cutoff;
-//   5. scan the row counts; fill pass writes the full rows and the half rows;
+//   4. one warp per atom scans the candidates in the cells within two cells
+//      per axis (cell edge >= rc/2), as runs of consecutive atoms along z:
+//      float32 distance pre-filter with a margin, exact float64 decision
+//      d.d < rc^2 for candidates near the cutoff; counts, and the owned
+//      neighbours into a slab row;
+//   5. scan the row counts; copy the slab rows into the full rows and the half
+//      list (or, if a slab row overflowed, scan the candidates again and write
+//      them at the row offsets);
 //   6. each pair id is scattered to its non-owner's row, which sorts that part
 //      of the row by pair id (deterministic order).
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 
@@ -66,8 +71,14 @@ __global__ void k_cell_assign(int n, const double* __restrict__ xyz, double L, i
   atomicAdd(&cell_count[id], 1);
 }
 
-// Single-block exclusive scan: out[k] = sum_{m<k} in[k], out[n] = total.
-__global__ void k_scan_exclusive(const int* __restrict__ in, int* __restrict__ out, int n) {
+// Single-block exclusive scan: out[k] = sum_{m<k} in[k], out[n] = total. A
+// second block, if launched, scans (in2, out2) the same way.
+__global__ void k_scan_exclusive(const int* __restrict__ in, int* __restrict__ out, int n,
+                                 const int* __restrict__ in2 = nullptr, int* __restrict__ out2 = nullptr) {
+  if (blockIdx.x == 1) {
+    in = in2;
+    out = out2;
+  }
   __shared__ int warp_sums[32];
   __shared__ int carry;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -150,7 +161,8 @@ __global__ void k_gather_atoms(int n, const int* __restrict__ perm, const double
 }
 
 struct ListParams {
-  int n, nc, nof;
+  int n, nc;  // atoms, cells per axis (edge >= rc / 2)
+  int slab;   // slab row capacity (kMode 2)
   double L, rc2;
   float Lf, invLf, lo2, hi2;
 };
@@ -166,54 +178,79 @@ __device__ __forceinline__ bool exact_in_range(const double4_32a& a, const doubl
   return r2 < rc2;
 }
 
-template <bool kFill>
+// Candidates of atom i: cells within two cells per axis (cell edge >= rc/2;
+// every cell when there are fewer than five per axis). For each (x, y) cell
+// column the z cells form one or two runs of consecutive cells, hence of
+// consecutive atoms, scanned 32 at a time. kMode 0 counts the full and owned
+// neighbours; 1 writes them at the row offsets; 2 counts and writes the owned
+// neighbours into a slab row of P.slab entries (flag bit 4 if one overflows),
+// so that a single scan of the candidates suffices.
+template <int kMode>
 __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, const double4_32a* __restrict__ A,
-                             const int* __restrict__ cell_sorted, const int* __restrict__ cell_start, int* __restrict__ full_cnt,
-                             int* __restrict__ half_cnt, const int* __restrict__ full_start,
-                             const int* __restrict__ half_start, int* __restrict__ full_j,
-                             int* __restrict__ full_ref, int* __restrict__ half_i, int* __restrict__ half_j) {
+                             const int* __restrict__ cell_sorted, const int* __restrict__ cell_start,
+                             int* __restrict__ full_cnt, int* __restrict__ half_cnt,
+                             const int* __restrict__ full_start, const int* __restrict__ half_start,
+                             int* __restrict__ full_j, int* __restrict__ full_ref, int* __restrict__ half_i,
+                             int* __restrict__ half_j, int* __restrict__ slab, int* __restrict__ flags) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= P.n) return;
   const unsigned lt = (1u << lane) - 1u;
   const float4 pi = pos32[i];
   const double4_32a ai = A[i];
+  const int nc = P.nc;
   const int cself = cell_sorted[i];  // the cell the atom was binned in (float64 wrap)
-  const int ci[3] = {cself / (P.nc * P.nc), (cself / P.nc) % P.nc, cself % P.nc};
+  const int ci[3] = {cself / (nc * nc), (cself / nc) % nc, cself % nc};
+  const bool all = nc < 5;
+  const int span = all ? nc : 5;
+  int zr[2][2], nr;  // z runs [zr[r][0], zr[r][1]]
+  if (all) {
+    zr[0][0] = 0, zr[0][1] = nc - 1, nr = 1;
+  } else if (ci[2] - 2 < 0) {
+    zr[0][0] = 0, zr[0][1] = ci[2] + 2, zr[1][0] = ci[2] - 2 + nc, zr[1][1] = nc - 1, nr = 2;
+  } else if (ci[2] + 2 >= nc) {
+    zr[0][0] = ci[2] - 2, zr[0][1] = nc - 1, zr[1][0] = 0, zr[1][1] = ci[2] + 2 - nc, nr = 2;
+  } else {
+    zr[0][0] = ci[2] - 2, zr[0][1] = ci[2] + 2, nr = 1;
+  }
   int nfull = 0, nhalf = 0;
-  const int fbase = kFill ? full_start[i] : 0;
-  const int hbase = kFill ? half_start[i] : 0;
-  for (int ox = 0; ox < P.nof; ++ox) {
-    int cx = (ci[0] + (P.nof == 3 ? ox - 1 : ox) + P.nc) % P.nc;
-    for (int oy = 0; oy < P.nof; ++oy) {
-      int cy = (ci[1] + (P.nof == 3 ? oy - 1 : oy) + P.nc) % P.nc;
-      for (int oz = 0; oz < P.nof; ++oz) {
-        int cz = (ci[2] + (P.nof == 3 ? oz - 1 : oz) + P.nc) % P.nc;
-        int cell = (cx * P.nc + cy) * P.nc + cz;
-        int s = cell_start[cell], e = cell_start[cell + 1];
+  const int fbase = kMode == 1 ? full_start[i] : 0;
+  const int hbase = kMode == 1 ? half_start[i] : 0;
+  int* srow = kMode == 2 ? slab + (long long)i * P.slab : nullptr;
+  for (int ox = 0; ox < span; ++ox) {
+    const int cx = all ? ox : (ci[0] + ox - 2 + nc) % nc;
+    for (int oy = 0; oy < span; ++oy) {
+      const int cy = all ? oy : (ci[1] + oy - 2 + nc) % nc;
+      const int base = (cx * nc + cy) * nc;
+      for (int r = 0; r < nr; ++r) {
+        const int s = cell_start[base + zr[r][0]], e = cell_start[base + zr[r][1] + 1];
         for (int k0 = s; k0 < e; k0 += 32) {
-          int k = k0 + lane;
+          const int k = k0 + lane;
           bool in = false;
           if (k < e && k != i) {
-            float4 pj = pos32[k];
+            const float4 pj = pos32[k];
             float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             dx -= P.Lf * rintf(dx * P.invLf);
             dy -= P.Lf * rintf(dy * P.invLf);
             dz -= P.Lf * rintf(dz * P.invLf);
-            float r2 = dx * dx + dy * dy + dz * dz;
+            const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
           }
-          bool own = in && ((i < k) != (((i + k) & 1) != 0));
-          unsigned mf = __ballot_sync(0xffffffffu, in);
-          unsigned mh = __ballot_sync(0xffffffffu, own);
-          if (kFill && own) {
+          const bool own = in && ((i < k) != (((i + k) & 1) != 0));
+          const unsigned mf = __ballot_sync(0xffffffffu, in);
+          const unsigned mh = __ballot_sync(0xffffffffu, own);
+          if (own) {
             // owned pairs open the row: full slot and pair id share the rank
             const int rank = nhalf + __popc(mh & lt);
-            const int pid = hbase + rank;
-            full_j[fbase + rank] = k;
-            full_ref[fbase + rank] = pid << 1;
-            half_i[pid] = i;
-            half_j[pid] = k;
+            if (kMode == 1) {
+              const int pid = hbase + rank;
+              full_j[fbase + rank] = k;
+              full_ref[fbase + rank] = pid << 1;
+              half_i[pid] = i;
+              half_j[pid] = k;
+            } else if (kMode == 2 && rank < P.slab) {
+              srow[rank] = k;
+            }
           }
           nfull += __popc(mf);
           nhalf += __popc(mh);
@@ -221,9 +258,29 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
       }
     }
   }
-  if (!kFill && lane == 0) {
+  if (kMode != 1 && lane == 0) {
     full_cnt[i] = nfull;
     half_cnt[i] = nhalf;
+    if (kMode == 2 && nhalf > P.slab) atomicOr(flags, 4);
+  }
+}
+
+// Slab rows -> owned part of the full rows and the half list.
+__global__ void k_slab_copy(int n, int slab_cap, const int* __restrict__ slab, const int* __restrict__ half_cnt,
+                            const int* __restrict__ full_start, const int* __restrict__ half_start,
+                            int* __restrict__ full_j, int* __restrict__ full_ref, int* __restrict__ half_i,
+                            int* __restrict__ half_j) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int m = half_cnt[i], fb = full_start[i], hb = half_start[i];
+  const int* row = slab + (long long)i * slab_cap;
+  for (int r = lane; r < m; r += 32) {
+    const int k = row[r], pid = hb + r;
+    full_j[fb + r] = k;
+    full_ref[fb + r] = pid << 1;
+    half_i[pid] = i;
+    half_j[pid] = k;
   }
 }
 
@@ -263,8 +320,10 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   const int n = c->n;
   const double L = c->cfg.box, rc = c->cfg.cutoff;
   cudaStream_t st = c->stream;
-  int nc = (int)floor(L / (rc + 1e-6));
+  // cells of edge >= rc / 2 (the neighbour search spans two cells per axis)
+  int nc = (int)floor(2.0 * L / (rc + 1e-6));
   if (nc < 1) nc = 1;
+  if (nc > 1024) nc = 1024;
   const int ncell = nc * nc * nc;
   if (ncell > c->ncell_cap) {
     dev_free(c, c->cell_count);
@@ -284,7 +343,7 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
       (r = cuda_check(c, cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * ncell, st), "memset")) ||
       (r = cuda_check(c, cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, st), "memset")))
     return r;
-  c->n_launch += 11;  // cell_assign .. transpose_sort below
+  c->n_launch += 10;  // cell_assign .. transpose_sort below
   k_cell_assign<<<amp_blocks(n, 256), 256, 0, st>>>(n, xyz, L, nc, c->cell_of, c->cell_count);
   k_scan_exclusive<<<1, 1024, 0, st>>>(c->cell_count, c->cell_start, ncell);
   k_cell_scatter<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->cell_of, c->cell_start, c->cell_fill, c->slot_tmp);
@@ -292,10 +351,24 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   k_gather_atoms<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, q, dip, quad, alpha, thole, mol, L,
                                                      c->inv_perm, c->atomA, c->atomB, c->atomC, c->atomD,
                                                      c->pos32, c->cell_of, c->slot_tmp, c->alph, c->flags);
+  // slab rows for the single-pass list: four times the mean number of owned
+  // neighbours (half of 4/3 pi rc^3 n / L^3), at least 64; a row that would
+  // overflow sends the build through the two-pass count / fill path instead
+  const double mean_full = 4.0 / 3.0 * M_PI * rc * rc * rc * (double)n / (L * L * L);
+  int slab = (int)std::ceil(2.0 * mean_full / 32.0) * 32;
+  if (slab < 64) slab = 64;
+  if (slab > 4096) slab = 4096;
+  if ((long long)n * slab > c->slab_cap) {
+    dev_free(c, c->slab);
+    c->slab = nullptr;
+    c->slab_cap = 0;
+    if ((r = dev_alloc(c, &c->slab, (long long)n * slab))) return r;
+    c->slab_cap = (long long)n * slab;
+  }
   ListParams P;
   P.n = n;
   P.nc = nc;
-  P.nof = nc >= 3 ? 3 : nc;
+  P.slab = slab;
   P.L = L;
   P.rc2 = rc * rc;
   P.Lf = (float)L;
@@ -303,10 +376,9 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   P.lo2 = (float)(rc * rc - 0.01);
   P.hi2 = (float)(rc * rc + 0.01);
   const int lb = amp_blocks((long long)n * 32, 256);
-  k_neighbours<false><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, c->full_cnt, c->half_cnt,
-                                          nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
-  k_scan_exclusive<<<1, 1024, 0, st>>>(c->full_cnt, c->full_start, n);
-  k_scan_exclusive<<<1, 1024, 0, st>>>(c->half_cnt, c->half_start, n);
+  k_neighbours<2><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, c->full_cnt, c->half_cnt,
+                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->slab, c->flags);
+  k_scan_exclusive<<<2, 1024, 0, st>>>(c->full_cnt, c->full_start, n, c->half_cnt, c->half_start);
   if ((r = cuda_check(c, cudaGetLastError(), "list count launch"))) return r;
   cudaMemcpyAsync(&c->hibuf[0], c->full_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&c->hibuf[1], c->half_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -339,8 +411,13 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
     c->cap_half = caph;
     c->cap_full = capf;
   }
-  k_neighbours<true><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, nullptr, nullptr, c->full_start,
-                                         c->half_start, c->full_j, c->full_ref, c->half_i, c->half_j);
+  if (c->hibuf[2] & 4)  // a slab row overflowed: second scan of the candidates
+    k_neighbours<1><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, nullptr, nullptr,
+                                        c->full_start, c->half_start, c->full_j, c->full_ref, c->half_i, c->half_j,
+                                        nullptr, nullptr);
+  else
+    k_slab_copy<<<lb, 256, 0, st>>>(n, slab, c->slab, c->half_cnt, c->full_start, c->half_start, c->full_j,
+                                    c->full_ref, c->half_i, c->half_j);
   cudaMemsetAsync(c->full_cnt, 0, sizeof(int) * n, st);  // reused as the per-row slot counter
   k_transpose_scatter<<<amp_blocks(c->n_half, 256), 256, 0, st>>>(c->n_half, c->half_j, c->full_start, c->half_cnt,
                                                                   c->full_cnt, c->tr_tmp);
