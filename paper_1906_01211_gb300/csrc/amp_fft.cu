@@ -7,13 +7,13 @@
 // for one forward + inverse 64^3 pair on GB300); these kernels do the same
 // arithmetic in double-float (hi + lo floats, ~48 bits) on the float units,
 // in three launches over the half spectrum:
-//   A (one block per x plane): two real z lines packed as one complex line
+//   A (one cluster of CTAs per x plane): two real z lines packed as one complex line
 //     (rows y and y + K/2), forward z transforms, the two half spectra
 //     separated, then forward y transforms; the plane's half spectrum goes
 //     to H[x][mz][my] (my in bit-reversed order);
 //   B (lines along x, eight neighbouring my per block): forward x transform,
 //     times G, inverse x transform, in place;
-//   C (one block per x plane): inverse y transforms, the two real z lines
+//   C (one cluster of CTAs per x plane): inverse y transforms, the two real z lines
 //     rebuilt from their half spectra as one complex line, inverse z
 //     transform; real part -> row y, imaginary part -> row y + K/2 of phi.
 // Forward: X(m) = sum_n x(n) exp(-2 pi i m n / K); inverse: exp(+...), no 1/K.
@@ -24,6 +24,8 @@
 //   A(m) = (C(m) + conj C(K - m)) / 2,  B(m) = (C(m) - conj C(K - m)) / (2i),
 // and back, C(m) = A(m) + i B(m) with A(K - m) = conj A(m) (likewise B); the
 // imaginary parts of A and B at m = 0 and m = K/2 are dropped, as C2R does.
+#include <cooperative_groups.h>
+
 #include "amp_internal.cuh"
 
 namespace amp {
@@ -94,41 +96,57 @@ __device__ __forceinline__ dflt fixed_to_df(long long v, int s) {
   return df_add(df_two_sum(a * pow2f(40 - s), b * pow2f(20 - s)), dflt{c * pow2f(-s), 0.f});
 }
 
-template <int K>
-__host__ __device__ constexpr int plane_threads() {
-  return K >= 64 ? 1024 : (K >= 32 ? 512 : 256);
-}
+// The plane passes run one cluster of kClus CTAs per x plane: CTA r owns the
+// packed rows y' in [r R, (r + 1) R) (R = K / (2 kClus)) for the z
+// transforms and the half-spectrum lines mz in [mz_lo(r), mz_lo(r + 1)) for
+// the y transforms; the values that cross over are read from the other CTAs'
+// shared memory (distributed shared memory) between two cluster barriers.
+constexpr int kClus = 4;
 
-// shared memory of the plane kernels: twiddles, K/2 packed z lines, K/2 + 1 y lines
 template <int K>
-__host__ __device__ constexpr size_t plane_smem() {
-  return sizeof(float4) * (K / 2 + (K / 2) * K + (K / 2 + 1) * K);
+struct Plane {
+  static constexpr int kH = K / 2 + 1;              // half-spectrum lines
+  static constexpr int R = K / 2 / kClus;           // packed rows per CTA
+  static constexpr int M = (kH + kClus - 1) / kClus;  // at most this many mz lines per CTA
+  static constexpr int kWarps = R > M ? R : M;
+  static constexpr int NT = 32 * kWarps;
+  static constexpr int kBits = __builtin_ctz(K);
+};
+
+__host__ __device__ __forceinline__ int mz_lo(int r, int kH) { return r * kH / kClus; }
+__device__ __forceinline__ int mz_owner(int mz, int kH) {
+  int r = 0;
+  while (r + 1 < kClus && mz_lo(r + 1, kH) <= mz) ++r;
+  return r;
 }
 
 // Pass A. Input plane x of the real grid, float64 or (kFixed) 64-bit fixed
 // point scaled by 2^fx_info[0], which is zeroed once read.
 template <int K, bool kFixed>
-__global__ void __launch_bounds__(plane_threads<K>()) k_fft_plane_fwd(const double* __restrict__ q,
-                                                                      unsigned long long* __restrict__ qfx,
-                                                                      const int* __restrict__ fx_info,
-                                                                      float4* __restrict__ H,
-                                                                      const float4* __restrict__ tw_g,
-                                                                      const int* __restrict__ stop) {
-  if (stop && *stop) return;
-  constexpr int kBits = __builtin_ctz(K), kH = K / 2 + 1, NT = plane_threads<K>(), NW = NT / 32;
-  extern __shared__ float4 smem[];
-  float4* tw = smem;             // [K/2]
-  float4* zl = tw + K / 2;       // [K/2][K]: line y' = row y' + i row y' + K/2
-  float4* P = zl + (K / 2) * K;  // [K/2 + 1][K]: for each mz, the line over y
-  const int x = blockIdx.x, w = threadIdx.x >> 5;
+__global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
+    k_fft_plane_fwd(const double* __restrict__ q, unsigned long long* __restrict__ qfx,
+                    const int* __restrict__ fx_info, float4* __restrict__ H, const float4* __restrict__ tw_g,
+                    const int* __restrict__ stop) {
+  namespace cg = cooperative_groups;
+  using PL = Plane<K>;
+  constexpr int kH = PL::kH, R = PL::R, NT = PL::NT;
+  if (stop && *stop) return;  // the same for every CTA of the cluster
+  __shared__ float4 tw[K / 2];
+  __shared__ float4 zl[R][K];        // packed line y' = row y' + i row y' + K/2
+  __shared__ float4 Ploc[kH][2 * R]; // separated half spectra of this CTA's rows
+  __shared__ float4 yl[PL::M][K];    // this CTA's mz lines over all y
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank(), x = blockIdx.x / kClus, w = threadIdx.x >> 5;
+  const int y0 = r * R;
   for (int k = threadIdx.x; k < K / 2; k += NT) tw[k] = tw_g[k];
   const long long base = (long long)x * K * K;
   const int sfx = kFixed ? fx_info[0] : 0;
-  for (int e = threadIdx.x; e < K * K; e += NT) {
-    const dflt d = kFixed ? fixed_to_df((long long)qfx[base + e], sfx) : df_split(q[base + e]);
-    const int y = e / K, z = e % K;
-    float4* p = &zl[(y % (K / 2)) * K + z];
-    if (y < K / 2) {
+  for (int e = threadIdx.x; e < 2 * R * K; e += NT) {
+    const int li = e / K % R, half = e / (R * K), z = e % K;
+    const long long g = base + (long long)(y0 + li + half * (K / 2)) * K + z;
+    const dflt d = kFixed ? fixed_to_df((long long)qfx[g], sfx) : df_split(q[g]);
+    float4* p = &zl[li][z];
+    if (half == 0) {
       p->x = d.hi;
       p->y = d.lo;
     } else {
@@ -137,26 +155,33 @@ __global__ void __launch_bounds__(plane_threads<K>()) k_fft_plane_fwd(const doub
     }
   }
   __syncthreads();
-  if (kFixed)  // every value of the plane is in shared memory: zero it for the next spreading
-    for (int e = threadIdx.x; e < K * K / 2; e += NT)
-      reinterpret_cast<ulonglong2*>(qfx + base)[e] = make_ulonglong2(0ull, 0ull);
-  for (int l = w; l < K / 2; l += NW) line_fft<K, true>(zl + l * K, tw);
+  if (kFixed)  // every value read is in shared memory: zero it for the next spreading
+    for (int e = threadIdx.x; e < 2 * R * K; e += NT) {
+      const int li = e / K % R, half = e / (R * K), z = e % K;
+      qfx[base + (long long)(y0 + li + half * (K / 2)) * K + z] = 0ull;
+    }
+  if (w < R) line_fft<K, true>(zl[w], tw);
   __syncthreads();
-  // separate the two real lines' half spectra into P[mz][y]
-  for (int e = threadIdx.x; e < (K / 2) * kH; e += NT) {
-    const int yp = e / kH, mz = e % kH;
-    const cdf ck = ld(&zl[yp * K + bitrev(mz & (K - 1), kBits)]);
-    const cdf cm = ld(&zl[yp * K + bitrev((K - mz) & (K - 1), kBits)]);
-    const cdf a = {df_half(df_add(ck.re, cm.re)), df_half(df_sub(ck.im, cm.im))};
-    const cdf b = {df_half(df_add(ck.im, cm.im)), df_half(df_sub(cm.re, ck.re))};
-    st(&P[mz * K + yp], a);
-    st(&P[mz * K + yp + K / 2], b);
+  for (int e = threadIdx.x; e < R * kH; e += NT) {
+    const int li = e / kH, mz = e % kH;
+    const cdf ck = ld(&zl[li][bitrev(mz & (K - 1), PL::kBits)]);
+    const cdf cm = ld(&zl[li][bitrev((K - mz) & (K - 1), PL::kBits)]);
+    st(&Ploc[mz][li], {df_half(df_add(ck.re, cm.re)), df_half(df_sub(ck.im, cm.im))});
+    st(&Ploc[mz][R + li], {df_half(df_add(ck.im, cm.im)), df_half(df_sub(cm.re, ck.re))});
   }
-  __syncthreads();
-  for (int l = w; l < kH; l += NW) line_fft<K, true>(P + l * K, tw);
+  cluster.sync();
+  const int m0 = mz_lo(r, kH), nm = mz_lo(r + 1, kH) - m0;
+  for (int e = threadIdx.x; e < nm * K; e += NT) {
+    const int t = e / K, y = e % K;
+    const int yp = y % (K / 2), owner = yp / R;
+    const float4* src = cluster.map_shared_rank(&Ploc[0][0], owner);
+    yl[t][y] = src[(m0 + t) * (2 * R) + (y < K / 2 ? 0 : R) + yp % R];
+  }
+  cluster.sync();  // no CTA leaves while another still reads its shared memory
+  if (w < nm) line_fft<K, true>(yl[w], tw);
   __syncthreads();
   float4* out = H + (long long)x * kH * K;
-  for (int e = threadIdx.x; e < kH * K; e += NT) out[e] = P[e];
+  for (int e = threadIdx.x; e < nm * K; e += NT) out[(long long)(m0 + e / K) * K + e % K] = yl[e / K][e % K];
 }
 
 // Pass B: lines along x of H[x][mz][my], kLinesB neighbouring my per block;
@@ -199,72 +224,69 @@ __global__ void __launch_bounds__(32 * kLinesB) k_fft_x_conv(float4* __restrict_
 // Pass C: inverse y transforms of plane x, the real z lines rebuilt pairwise,
 // inverse z transforms; phi[x][y][z] as hi/lo floats.
 template <int K>
-__global__ void __launch_bounds__(plane_threads<K>()) k_fft_plane_inv(const float4* __restrict__ H,
-                                                                      float2* __restrict__ phi,
-                                                                      const float4* __restrict__ tw_g,
-                                                                      const int* __restrict__ stop) {
+__global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
+    k_fft_plane_inv(const float4* __restrict__ H, float2* __restrict__ phi, const float4* __restrict__ tw_g,
+                    const int* __restrict__ stop) {
+  namespace cg = cooperative_groups;
+  using PL = Plane<K>;
+  constexpr int kH = PL::kH, R = PL::R, NT = PL::NT;
   if (stop && *stop) return;
-  constexpr int kBits = __builtin_ctz(K), kH = K / 2 + 1, NT = plane_threads<K>(), NW = NT / 32;
-  extern __shared__ float4 smem[];
-  float4* tw = smem;
-  float4* zl = tw + K / 2;
-  float4* P = zl + (K / 2) * K;
-  const int x = blockIdx.x, w = threadIdx.x >> 5;
+  __shared__ float4 tw[K / 2];
+  __shared__ float4 yl[PL::M][K];  // this CTA's mz lines, then over natural y
+  __shared__ float4 zl[R][K];      // packed lines, bit-reversed for the DIT
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank(), x = blockIdx.x / kClus, w = threadIdx.x >> 5;
+  const int y0 = r * R;
   for (int k = threadIdx.x; k < K / 2; k += NT) tw[k] = tw_g[k];
+  const int m0 = mz_lo(r, kH), nm = mz_lo(r + 1, kH) - m0;
   const float4* in = H + (long long)x * kH * K;
-  for (int e = threadIdx.x; e < kH * K; e += NT) P[e] = in[e];
+  for (int e = threadIdx.x; e < nm * K; e += NT) yl[e / K][e % K] = in[(long long)(m0 + e / K) * K + e % K];
   __syncthreads();
-  for (int l = w; l < kH; l += NW) line_fft<K, false>(P + l * K, tw);
-  __syncthreads();
-  // C(m) = A(m) + i B(m); A = row y', B = row y' + K/2; stored bit-reversed for the DIT
-  for (int e = threadIdx.x; e < (K / 2) * K; e += NT) {
-    const int yp = e / K, m = e % K;
+  if (w < nm) line_fft<K, false>(yl[w], tw);
+  cluster.sync();
+  // C(m) = A(m) + i B(m); A = row y', B = row y' + K/2
+  for (int e = threadIdx.x; e < R * K; e += NT) {
+    const int li = e / K, m = e % K;
     const int mh = m <= K / 2 ? m : K - m;
-    cdf a = ld(&P[mh * K + yp]), b = ld(&P[mh * K + yp + K / 2]);
+    const int owner = mz_owner(mh, kH);
+    const float4* src = cluster.map_shared_rank(&yl[0][0], owner);
+    const int row = (mh - mz_lo(owner, kH)) * K;
+    cdf a = ld(&src[row + y0 + li]), b = ld(&src[row + y0 + li + K / 2]);
     if (mh == 0 || mh == K / 2) {
       a.im = {0.f, 0.f};
       b.im = {0.f, 0.f};
     }
-    cdf c;
+    cdf cc;
     if (m <= K / 2)
-      c = {df_sub(a.re, b.im), df_add(a.im, b.re)};
+      cc = {df_sub(a.re, b.im), df_add(a.im, b.re)};
     else
-      c = {df_add(a.re, b.im), df_sub(b.re, a.im)};
-    st(&zl[yp * K + bitrev(m, kBits)], c);
+      cc = {df_add(a.re, b.im), df_sub(b.re, a.im)};
+    st(&zl[li][bitrev(m, PL::kBits)], cc);
   }
-  __syncthreads();
-  for (int l = w; l < K / 2; l += NW) line_fft<K, false>(zl + l * K, tw);
+  cluster.sync();  // no CTA leaves while another still reads its shared memory
+  if (w < R) line_fft<K, false>(zl[w], tw);
   __syncthreads();
   float2* out = phi + (long long)x * K * K;
-  for (int e = threadIdx.x; e < K * K; e += NT) {
-    const int y = e / K, z = e % K;
-    const float4 v = zl[(y % (K / 2)) * K + z];
-    out[e] = y < K / 2 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+  for (int e = threadIdx.x; e < 2 * R * K; e += NT) {
+    const int li = e / K % R, half = e / (R * K), z = e % K;
+    const float4 v = zl[li][z];
+    out[(long long)(y0 + li + half * (K / 2)) * K + z] = half == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
   }
 }
 
 template <int K>
 void run_conv(amp_ctx* c, cudaStream_t st, bool fixed) {
-  constexpr size_t smem = plane_smem<K>();
-  constexpr int NT = plane_threads<K>();
-  static const bool attr = [] {  // opt in to more than 48 KB of dynamic shared memory, once per process
-    cudaFuncSetAttribute(k_fft_plane_fwd<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_fft_plane_fwd<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_fft_plane_inv<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return true;
-  }();
-  (void)attr;
   constexpr int kGroups = K >= kLinesB ? K / kLinesB : 1;
   const float4* tw = c->fft_tw;
   float4* H = c->fft_grid;
   const int* stop = c->op_stop;
   c->n_launch += 3;
   if (fixed)
-    k_fft_plane_fwd<K, true><<<K, NT, smem, st>>>(nullptr, c->gridfx, c->fx_info, H, tw, stop);
+    k_fft_plane_fwd<K, true><<<K * kClus, Plane<K>::NT, 0, st>>>(nullptr, c->gridfx, c->fx_info, H, tw, stop);
   else
-    k_fft_plane_fwd<K, false><<<K, NT, smem, st>>>(c->grid64, nullptr, nullptr, H, tw, stop);
+    k_fft_plane_fwd<K, false><<<K * kClus, Plane<K>::NT, 0, st>>>(c->grid64, nullptr, nullptr, H, tw, stop);
   k_fft_x_conv<K><<<(K / 2 + 1) * kGroups, 32 * kLinesB, 0, st>>>(H, tw, c->fft_G, stop);
-  k_fft_plane_inv<K><<<K, NT, smem, st>>>(H, c->phi_df, tw, stop);
+  k_fft_plane_inv<K><<<K * kClus, Plane<K>::NT, 0, st>>>(H, c->phi_df, tw, stop);
 }
 
 }  // namespace
