@@ -170,14 +170,25 @@ def run_reference(args):
 # exp, sqrt and 1/r counted as one operation (their internal polynomials are
 # not algorithmic work).
 PAIR_BUILD_FLOPS = 130
+# The pair build runs in double-float on the float32 pipe; one float64
+# operation of the formulas costs about DF_FP32_PER_FP64 float32 operations
+# (the df_* helpers: a double-float multiply-add is one multiply, three fused
+# multiply-adds and about nine adds).
+DF_FP32_PER_FP64 = 13
+# DRAM traffic (read + write) per launch of k_t_real_df, from one ncu capture of
+# the current kernel on this workload (profiles/k_t_real_df_water23556.md).
+T_REAL_TRAFFIC = {"water-23556": 111.8e6}
 
 
-def kernel_rooflines(phases, n_pairs, n_atoms, steps=None):
+def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
     """Roofline entries from the live phase timers (one kernel per phase).
 
-    pair build: float64 ALU, PAIR_BUILD_FLOPS per unique pair, peak derived
-    from 152 SMs x 2 float64 FMA/clk x 2 flop x max SM clock.
-    real-space T*v (double-float): HBM, algorithmic bytes per launch = 48 B
+    pair build (k_pair_build_df): bound "alu" on the float32 pipe, which runs
+    it in double-float; achieved = PAIR_BUILD_FLOPS float64 operations per
+    unique pair / launch time, peak = the float32 pipe's rate divided by
+    DF_FP32_PER_FP64 (152 SMs x 128 lanes x 2 flop x max SM clock / 13), the
+    float64-equivalent rate of double-float arithmetic on this GPU.
+    real-space T*v (k_t_real_df): HBM, algorithmic bytes per launch = 48 B
     tensor per unique pair + 8 B index per directed entry + 96 B per atom
     (v as float hi/lo + float64 v, and the float64 output), peak =
     MEASURED_PEAKS.json hbm_gbs.
@@ -188,17 +199,18 @@ def kernel_rooflines(phases, n_pairs, n_atoms, steps=None):
     except Exception:
         pass
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+    df_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 / DF_FP32_PER_FP64
     hbm = peaks.get("hbm_gbs")
+    steps_seen = max(1, phases["pair"][1])
     out = []
     ms, cnt = phases["pair"]
     if cnt:
         per = ms / cnt
         ach = PAIR_BUILD_FLOPS * n_pairs / (per / 1e3) / 1e12
-        out.append({"kernel": "k_pair_build<double> (tensors + permanent fields per unique pair)", "bound": "alu",
-                    "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                    "traffic": None, "launch_ms": per, "ms_per_step": ms / max(1, cnt),
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x max SM clock"})
+        out.append({"kernel": "k_pair_build_df (tensors + permanent fields per unique pair, double-float)",
+                    "bound": "alu", "achieved": ach, "peak": df_peak, "unit": "TFLOP/s", "frac": ach / df_peak,
+                    "traffic": None, "launch_ms": per, "ms_per_step": ms / steps_seen,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock / 13 (double-float cost)"})
     ms, cnt = phases["t_real"]
     if cnt:
         per = ms / cnt
@@ -206,14 +218,9 @@ def kernel_rooflines(phases, n_pairs, n_atoms, steps=None):
         ach = nbytes / (per / 1e3) / 1e9
         peak = hbm if hbm else 6800.0
         out.append({"kernel": "k_t_real_df (real-space T*v, double-float)", "bound": "hbm", "achieved": ach,
-                    "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None, "launch_ms": per,
-                    "ms_per_step": ms * (cnt / max(1, phases["pair"][1])) / max(1, cnt),
-                    "peak_source": "measured" if hbm else "fallback"})
-    # per-step totals for choosing the dominant kernel
-    steps_seen = max(1, phases["pair"][1])
-    for r in out:
-        key = "pair" if r["kernel"].startswith("k_pair_build") else "t_real"
-        r["ms_per_step"] = phases[key][0] / steps_seen
+                    "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": T_REAL_TRAFFIC.get(workload), "algorithmic_bytes": nbytes, "launch_ms": per,
+                    "ms_per_step": ms / steps_seen, "peak_source": "measured" if hbm else "fallback"})
     return out
 
 
@@ -380,7 +387,7 @@ def main():
         return
 
     # ---- rooflines of our two largest kernels; the dominant one is "roofline"
-    rooflines = kernel_rooflines(phases, n_pairs, n)
+    rooflines = kernel_rooflines(phases, n_pairs, n, w.name)
     roofline = max(rooflines, key=lambda r: r["ms_per_step"])
     phase_ms = {k: round(v[0] / args.steps, 4) for k, v in phases.items()}
 
