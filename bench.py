@@ -398,6 +398,9 @@ def main():
         pm = solver("mixed")
         ms_m = []
         for k in range(args.warmup + 3):
+            if k == args.warmup:
+                torch.cuda.synchronize()
+                pm.profile(True)
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -409,8 +412,12 @@ def main():
             e1.synchronize()
             if k >= args.warmup:
                 ms_m.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        phases_m = pm.profile_read()
+        pm.profile(False)
         d = (mum - mu64).double()
         mixed = {"solve_ms": statistics.mean(ms_m), "iters": itm, "fp64_checks": pm.last_solve_stats()[1],
+                 "phase_ms_per_step": {k: round(v[0] / len(ms_m), 4) for k, v in phases_m.items()},
                  "rms_vs_fp64_gpu_debye": float(4.8032047 * torch.sqrt((d * d).sum() / n)),
                  "energy_rel_vs_fp64_gpu": abs(Um / U - 1.0)}
         pm.close()

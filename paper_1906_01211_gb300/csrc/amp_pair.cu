@@ -179,6 +179,45 @@ __device__ __forceinline__ dflt min_image_df(dflt d, const PairGeomDf& g) {
   return sh == 0.f ? d : df_sub(d, df_mul({sh, 0.f}, g.L));
 }
 
+// The geometry-only terms of pair (i, j) in double-float: r = x_i - x_j
+// (minimum image), 1/r, the screened kernels B1..B3, the bare kernels and the
+// Thole exponent x with e^-x.
+struct PairTermsDf {
+  dflt R[3], IR2, B1, B2, B3, bare1, bare2, bare3, X, E;
+};
+
+__device__ __forceinline__ PairTermsDf pair_terms_df(const float4& hi_i, const float4& lo_i, const float4& th_i,
+                                                     const float4& hi_j, const float4& lo_j, const float4& th_j,
+                                                     const PairGeomDf& g, const float2* __restrict__ tab) {
+  PairTermsDf p;
+  p.R[0] = min_image_df(df_sub({hi_i.x, lo_i.x}, {hi_j.x, lo_j.x}), g);
+  p.R[1] = min_image_df(df_sub({hi_i.y, lo_i.y}, {hi_j.y, lo_j.y}), g);
+  p.R[2] = min_image_df(df_sub({hi_i.z, lo_i.z}, {hi_j.z, lo_j.z}), g);
+  const dflt R2 = df_madd(p.R[2], p.R[2], df_madd(p.R[1], p.R[1], df_mul(p.R[0], p.R[0])));
+  const dflt IR = df_rsqrt(R2);
+  const dflt RR = df_mul(R2, IR);
+  const dflt BR = df_mul(g.beta, RR);
+  const dflt E2 = df_exp_neg(df_mul(BR, BR), tab);  // exp(-beta^2 r^2)
+  const dflt B0 = df_mul(df_mul(df_erfcx(BR, tab), E2), IR);
+  dflt FAC = df_mul(E2, g.gpre);
+  // Thole: x = a r^3 / sqrt(alpha_i alpha_j), a = min(a_i, a_j)
+  const dflt A = th_i.x < th_j.x || (th_i.x == th_j.x && th_i.y <= th_j.y) ? dflt{th_i.x, th_i.y}
+                                                                           : dflt{th_j.x, th_j.y};
+  p.X = df_mul(df_mul(A, df_mul(R2, RR)), df_mul({hi_i.w, lo_i.w}, {hi_j.w, lo_j.w}));
+  p.E = df_exp_neg(p.X, tab);
+  const dflt THREE = {3.f, 0.f}, FIVE = {5.f, 0.f};
+  p.IR2 = df_mul(IR, IR);
+  p.B1 = df_mul(df_add(B0, FAC), p.IR2);
+  FAC = df_mul(FAC, g.twob2);
+  p.B2 = df_mul(df_madd(THREE, p.B1, FAC), p.IR2);
+  FAC = df_mul(FAC, g.twob2);
+  p.B3 = df_mul(df_madd(FIVE, p.B2, FAC), p.IR2);
+  p.bare1 = df_mul(IR, p.IR2);
+  p.bare2 = df_mul(df_mul(THREE, p.bare1), p.IR2);
+  p.bare3 = df_mul(df_mul(FIVE, p.bare2), p.IR2);
+  return p;
+}
+
 __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* __restrict__ half_i,
                                                        const int* __restrict__ half_j,
                                                        const float4* __restrict__ pd,
@@ -190,32 +229,12 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
   const int i = half_i[pid], j = half_j[pid];
   const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
   const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
-  const dflt R[3] = {min_image_df(df_sub({hi_i.x, lo_i.x}, {hi_j.x, lo_j.x}), g),
-                     min_image_df(df_sub({hi_i.y, lo_i.y}, {hi_j.y, lo_j.y}), g),
-                     min_image_df(df_sub({hi_i.z, lo_i.z}, {hi_j.z, lo_j.z}), g)};
+  const PairTermsDf p = pair_terms_df(hi_i, lo_i, th_i, hi_j, lo_j, th_j, g, tab);
+  const dflt(&R)[3] = p.R;
   const dflt NR[3] = {df_neg(R[0]), df_neg(R[1]), df_neg(R[2])};
-  const dflt R2 = df_madd(R[2], R[2], df_madd(R[1], R[1], df_mul(R[0], R[0])));
-  const dflt IR = df_rsqrt(R2);
-  const dflt RR = df_mul(R2, IR);
-  const dflt BR = df_mul(g.beta, RR);
-  const dflt E2 = df_exp_neg(df_mul(BR, BR), tab);  // exp(-beta^2 r^2)
-  const dflt B0 = df_mul(df_mul(df_erfcx(BR, tab), E2), IR);
-  dflt FAC = df_mul(E2, g.gpre);
-  // Thole: x = a r^3 / sqrt(alpha_i alpha_j), a = min(a_i, a_j)
-  const dflt A = th_i.x < th_j.x || (th_i.x == th_j.x && th_i.y <= th_j.y) ? dflt{th_i.x, th_i.y}
-                                                                           : dflt{th_j.x, th_j.y};
-  const dflt X = df_mul(df_mul(A, df_mul(R2, RR)), df_mul({hi_i.w, lo_i.w}, {hi_j.w, lo_j.w}));
-  const dflt E = df_exp_neg(X, tab);
-  const dflt ONE = {1.f, 0.f}, THREE = {3.f, 0.f}, FIVE = {5.f, 0.f};
-  const dflt IR2 = df_mul(IR, IR);
-  const dflt B1 = df_mul(df_add(B0, FAC), IR2);
-  FAC = df_mul(FAC, g.twob2);
-  const dflt B2 = df_mul(df_madd(THREE, B1, FAC), IR2);
-  FAC = df_mul(FAC, g.twob2);
-  const dflt B3 = df_mul(df_madd(FIVE, B2, FAC), IR2);
-  const dflt bare1 = df_mul(IR, IR2);
-  const dflt bare2 = df_mul(df_mul(THREE, bare1), IR2);
-  const dflt bare3 = df_mul(df_mul(FIVE, bare2), IR2);
+  const dflt X = p.X, E = p.E, B1 = p.B1, B2 = p.B2, B3 = p.B3;
+  const dflt bare1 = p.bare1, bare2 = p.bare2, bare3 = p.bare3;
+  const dflt ONE = {1.f, 0.f};
   const dflt d3 = E;
   const dflt d5 = df_mul(df_add(ONE, X), E);
   const dflt six = {0.600000024f, -2.38418579e-08f};  // 0.6 = hi + lo
@@ -312,35 +331,37 @@ __global__ void __launch_bounds__(256) k_row_sum_fields_df(int n, const int* __r
   }
 }
 
-// float64 products T_ij v_j and T_ij v_i of every pair, tensor recomputed on
-// the fly in float64 (the mixed path's float64 residual check).
-__global__ void __launch_bounds__(256) k_pair_tv_direct(long long nh, const int* __restrict__ half_i,
-                                                        const int* __restrict__ half_j,
-                                                        const double4_32a* __restrict__ A,
-                                                        const double4_32a* __restrict__ B,
-                                                        const double4_32a* __restrict__ D, PairGeom g,
-                                                        const double4_32a* __restrict__ v, double* __restrict__ out) {
+// The mixed path's float64 residual check: T_ij v_j and T_ij v_i of every
+// pair with the tensor recomputed on the fly in double-float (the terms of
+// pair_terms_df), v given as hi/lo floats; written in the layout of the
+// permanent fields (12 floats per pair) for k_row_sum_fields_df.
+__global__ void __launch_bounds__(256) k_pair_tv_df(long long nh, const int* __restrict__ half_i,
+                                                    const int* __restrict__ half_j, const float4* __restrict__ pd,
+                                                    PairGeomDf g, const float2* __restrict__ tab,
+                                                    const float4* __restrict__ vh, const float4* __restrict__ vl,
+                                                    float* __restrict__ out) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
-  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], di = D[i], dj = D[j];
-  const double rx = min_image(ai.x - aj.x, g.L), ry = min_image(ai.y - aj.y, g.L), rz = min_image(ai.z - aj.z, g.L);
-  const double r2 = rx * rx + ry * ry + rz * rz;
-  const Kern<double> k = pair_kernels<double>(r2, bi.w, bj.w, di.z, dj.z, true, g);
-  const double4_32a vi = v[i], vj = v[j];
-  double s = k.b2u * (rx * vj.x + ry * vj.y + rz * vj.z);
-  double* o = out + 6 * pid;
-  o[0] = s * rx - k.b1u * vj.x;
-  o[1] = s * ry - k.b1u * vj.y;
-  o[2] = s * rz - k.b1u * vj.z;
-  s = k.b2u * (rx * vi.x + ry * vi.y + rz * vi.z);
-  o[3] = s * rx - k.b1u * vi.x;
-  o[4] = s * ry - k.b1u * vi.y;
-  o[5] = s * rz - k.b1u * vi.z;
+  const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
+  const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
+  const PairTermsDf p = pair_terms_df(hi_i, lo_i, th_i, hi_j, lo_j, th_j, g, tab);
+  const dflt b1u = df_sub(p.B1, df_mul(p.E, p.bare1));
+  const dflt b2u = df_sub(p.B2, df_mul(df_mul(df_add({1.f, 0.f}, p.X), p.E), p.bare2));
+  dflt f[2][3];
+  for (int side = 0; side < 2; ++side) {  // field at i from v_j, at j from v_i
+    const int o = side == 0 ? j : i;
+    const float4 h = vh[o], l = vl[o];
+    const dflt v[3] = {{h.x, l.x}, {h.y, l.y}, {h.z, l.z}};
+    const dflt s = df_mul(b2u, df_madd(p.R[2], v[2], df_madd(p.R[1], v[1], df_mul(p.R[0], v[0]))));
+    for (int a = 0; a < 3; ++a) f[side][a] = df_sub(df_mul(s, p.R[a]), df_mul(b1u, v[a]));
+  }
+  float4* e = reinterpret_cast<float4*>(out + 12 * pid);
+  e[0] = make_float4(f[0][0].hi, f[0][0].lo, f[0][1].hi, f[0][1].lo);
+  e[1] = make_float4(f[0][2].hi, f[0][2].lo, f[1][0].hi, f[1][0].lo);
+  e[2] = make_float4(f[1][1].hi, f[1][1].lo, f[1][2].hi, f[1][2].lo);
 }
 
-// Sum over the kRowGroup lanes of one row. The mask names exactly the lanes
-// of this group, so groups past the last row may exit early.
 __device__ __forceinline__ double group_sum(double v) {
   const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
 #pragma unroll
@@ -492,6 +513,16 @@ dflt dsplit_host(double v) {
   return {h, (float)(v - (double)h)};
 }
 
+PairGeomDf geom_df(const PairGeom& g) {
+  PairGeomDf gd;
+  gd.L = dsplit_host(g.L);
+  gd.beta = dsplit_host(g.beta);
+  gd.twob2 = dsplit_host(g.twob2);
+  gd.gpre = dsplit_host(g.gpre);
+  gd.invL = (float)g.invL;
+  return gd;
+}
+
 }  // namespace
 
 // Table for df_erfcx and df_exp_neg, built in long double on the host.
@@ -531,12 +562,7 @@ void launch_pair_build(amp_ctx* c) {
   const int blocks = amp_blocks(c->n_half, 256);
   if (c->cfg.precision == AMP_FP64) {
     c->n_launch += 2;
-    PairGeomDf gd;
-    gd.L = dsplit_host(g.L);
-    gd.beta = dsplit_host(g.beta);
-    gd.twob2 = dsplit_host(g.twob2);
-    gd.gpre = dsplit_host(g.gpre);
-    gd.invL = (float)g.invL;
+    const PairGeomDf gd = geom_df(g);
     k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
                                                                     c->mp_df, c->pd);
     k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, gd, c->dfm,
@@ -544,7 +570,10 @@ void launch_pair_build(amp_ctx* c) {
                                                    reinterpret_cast<float*>(c->Ep64));
     return;
   }
-  c->n_launch += 1;
+  // mixed path: float32 pair terms; the split positions serve its float64 check
+  c->n_launch += 2;
+  k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                                  c->mp_df, c->pd);
   k_pair_build<float><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
                                                        c->atomC, c->atomD, g, c->T32, c->Ep32);
 }
@@ -579,15 +608,18 @@ void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, doub
       c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64, out, c->op_stop);
 }
 
+// v's split goes through p32/plo (free during the check: k_cg_init rewrites them).
 void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out) {
   const PairGeom g = geom(c);
+  const int blocks = amp_blocks((long long)c->n * kRowGroup, 256);
+  launch_split(c, v, c->p32, c->plo);
   c->n_launch += c->n_half > 0 ? 2 : 1;
   if (c->n_half > 0)
-    k_pair_tv_direct<<<amp_blocks(c->n_half, 256), 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j,
-                                                                        c->atomA, c->atomB, c->atomD, g, v,
-                                                                        c->Ep64);
-  k_row_sum_pairvec<double><<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
-      c->n, c->full_start, c->full_ref, c->Ep64, g.selfc, v, out);
+    k_pair_tv_df<<<amp_blocks(c->n_half, 256), 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd,
+                                                                    geom_df(g), c->dfm, c->p32, c->plo,
+                                                                    reinterpret_cast<float*>(c->Ep64));
+  k_row_sum_fields_df<<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref,
+                                                     reinterpret_cast<const float*>(c->Ep64), g.selfc, v, out);
 }
 
 }  // namespace amp
