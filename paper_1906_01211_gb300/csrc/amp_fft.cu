@@ -131,6 +131,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
   using PL = Plane<K>;
   constexpr int kH = PL::kH, R = PL::R, NT = PL::NT;
   if (stop && *stop) return;  // the same for every CTA of the cluster
+  pdl_wait();
+  pdl_trigger();
   __shared__ float4 tw[K / 2];
   __shared__ float4 zl[R][K];        // packed line y' = row y' + i row y' + K/2
   __shared__ float4 Ploc[kH][2 * R]; // separated half spectra of this CTA's rows
@@ -193,6 +195,8 @@ __global__ void __launch_bounds__(32 * kLinesB) k_fft_x_conv(float4* __restrict_
                                                             const float2* __restrict__ Gh,
                                                             const int* __restrict__ stop) {
   if (stop && *stop) return;
+  pdl_wait();
+  pdl_trigger();
   constexpr int kBits = __builtin_ctz(K), kH = K / 2 + 1;
   constexpr int kGroups = K >= kLinesB ? K / kLinesB : 1;
   __shared__ float4 tw[K / 2];
@@ -231,6 +235,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
   using PL = Plane<K>;
   constexpr int kH = PL::kH, R = PL::R, NT = PL::NT;
   if (stop && *stop) return;
+  pdl_wait();
+  pdl_trigger();
   __shared__ float4 tw[K / 2];
   __shared__ float4 yl[PL::M][K];  // this CTA's mz lines, then over natural y
   __shared__ float4 zl[R][K];      // packed lines, bit-reversed for the DIT
@@ -281,12 +287,17 @@ void run_conv(amp_ctx* c, cudaStream_t st, bool fixed) {
   float4* H = c->fft_grid;
   const int* stop = c->op_stop;
   c->n_launch += 3;
+  const double* qnull = nullptr;
+  unsigned long long* fxnull = nullptr;
+  const int* infonull = nullptr;
   if (fixed)
-    k_fft_plane_fwd<K, true><<<K * kClus, Plane<K>::NT, 0, st>>>(nullptr, c->gridfx, c->fx_info, H, tw, stop);
+    launch_pdl(k_fft_plane_fwd<K, true>, dim3(K * kClus), dim3(Plane<K>::NT), 0, st, qnull, c->gridfx, c->fx_info, H,
+               tw, stop);
   else
-    k_fft_plane_fwd<K, false><<<K * kClus, Plane<K>::NT, 0, st>>>(c->grid64, nullptr, nullptr, H, tw, stop);
-  k_fft_x_conv<K><<<(K / 2 + 1) * kGroups, 32 * kLinesB, 0, st>>>(H, tw, c->fft_G, stop);
-  k_fft_plane_inv<K><<<K * kClus, Plane<K>::NT, 0, st>>>(H, c->phi_df, tw, stop);
+    launch_pdl(k_fft_plane_fwd<K, false>, dim3(K * kClus), dim3(Plane<K>::NT), 0, st, c->grid64, fxnull, infonull,
+               H, tw, stop);
+  launch_pdl(k_fft_x_conv<K>, dim3((K / 2 + 1) * kGroups), dim3(32 * kLinesB), 0, st, H, tw, c->fft_G, stop);
+  launch_pdl(k_fft_plane_inv<K>, dim3(K * kClus), dim3(Plane<K>::NT), 0, st, H, c->phi_df, tw, stop);
 }
 
 }  // namespace

@@ -377,6 +377,31 @@ __device__ __forceinline__ dflt df_group_sum(dflt v) {
 
 }  // namespace amp
 
+// ---- programmatic dependent launch (sm_90+): a kernel launched with
+// launch_pdl may start while the previous kernel of its stream finishes; it
+// calls pdl_wait() before touching anything that kernel writes (the wait
+// returns once the previous grid has completed and its writes are visible),
+// and pdl_trigger() to let its own successor be launched early. Kernels
+// launched the ordinary way pass through pdl_wait() at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // launch geometry helpers
 static inline int amp_blocks(long long work, int threads) {
   long long b = (work + threads - 1) / threads;

@@ -278,6 +278,8 @@ __global__ void __launch_bounds__(NT) k_cg_dots(int n, const double4_32a* __rest
                                                 double4_32a* __restrict__ w, double* __restrict__ part,
                                                 const int* __restrict__ fl) {
   if (fl[F_STOP]) return;
+  pdl_wait();
+  pdl_trigger();
   double rz = 0.0, zw = 0.0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const double ia = al[s].y;
@@ -300,6 +302,8 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
                                                 float* __restrict__ vmax, double* __restrict__ scal,
                                                 int* __restrict__ fl, double tol, int max_iter) {
   if (fl[F_STOP]) return;
+  pdl_wait();
+  pdl_trigger();
   double rho, m;
   reduce_partials(part, vec_blocks(n), rho, m);
   __shared__ double sbeta, sgamma;
@@ -508,9 +512,10 @@ static int enqueue_iteration(amp_ctx* c) {
   PhaseScope ps(c, AMP_PHASE_PCG);
   c->n_launch += 2;
   const int nb = vec_blocks(n);
-  k_cg_dots<<<nb, NT, 0, st>>>(n, c->res, c->zv, c->tv, c->trec, c->alph, c->wv, c->partials, c->iflags);
-  k_cg_step<<<nb, NT, 0, st>>>(n, c->mu, c->res, c->zv, c->pv, c->qv, c->wv, c->alph, c->p32, lo, c->partials,
-                               c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye, c->cfg.max_iter);
+  launch_pdl(k_cg_dots, dim3(nb), dim3(NT), 0, st, n, c->res, c->zv, c->tv, c->trec, c->alph, c->wv, c->partials,
+             c->iflags);
+  launch_pdl(k_cg_step, dim3(nb), dim3(NT), 0, st, n, c->mu, c->res, c->zv, c->pv, c->qv, c->wv, c->alph, c->p32,
+             lo, c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye, c->cfg.max_iter);
   return AMP_OK;
 }
 

@@ -247,6 +247,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, con
                                                                       unsigned long long* __restrict__ grid,
                                                                       const int* __restrict__ stop) {
   if (stop && *stop) return;
+  pdl_wait();
+  pdl_trigger();
   const int sfx = fixed_scale(vmax[kReduceBlocks], sc, kOrder * kOrder * kOrder * fx_info[1]);
   if (blockIdx.x == 0 && threadIdx.x == 0) fx_info[0] = sfx;
   const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
@@ -375,6 +377,8 @@ __global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __
                                                          const float2* __restrict__ phi, int K,
                                                          double4_32a* __restrict__ out, const int* __restrict__ stop) {
   if (stop && *stop) return;
+  pdl_wait();
+  pdl_trigger();
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
   if (s >= n) return;  // whole groups leave together
@@ -438,8 +442,8 @@ void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out, bool split) {
   const long long ng = (long long)K * K * K;
   c->n_launch += split ? 2 : 1;
   if (split) k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_df, c->op_stop);
-  k_gather_field_df<kSet><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-      n, c->theta_df, c->gbase, c->phi_df, K, out, c->op_stop);
+  launch_pdl(k_gather_field_df<kSet>, dim3(amp_blocks((long long)n * kPmeGroup, 128)), dim3(128), 0, st, n,
+             c->theta_df, c->gbase, c->phi_df, K, out, c->op_stop);
 }
 
 int exec_fft(amp_ctx* c, bool fp32, bool forward);
@@ -687,9 +691,9 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
   if (c->theta_df) {  // float64 context: fixed-point spread, own FFT (or cuFFT + split), double-float gather
     if (!v32 || !vlo) return fail(c, AMP_ERR_STATE, "float64 reciprocal field needs the split vector");
-    k_spread_dipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
-        n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info, (float)((double)K / c->cfg.box), K,
-        c->gridfx, c->op_stop);
+    launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
+               dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
+               (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
     bool split = true;
     const int r = conv_to_phi(c, st, &split, true);
     if (r) return r;
