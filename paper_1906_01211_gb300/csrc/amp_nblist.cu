@@ -217,44 +217,53 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
   const int fbase = kMode == 1 ? full_start[i] : 0;
   const int hbase = kMode == 1 ? half_start[i] : 0;
   int* srow = kMode == 2 ? slab + (long long)i * P.slab : nullptr;
-  for (int ox = 0; ox < span; ++ox) {
+  // lane c < span^2 fetches the atom ranges of (x, y) column c up front, so
+  // the scan below waits on no cell_start load
+  const int ncol = span * span;
+  int rs[2] = {0, 0}, re[2] = {0, 0};
+  if (lane < ncol) {
+    const int ox = lane / span, oy = lane % span;
     const int cx = all ? ox : (ci[0] + ox - 2 + nc) % nc;
-    for (int oy = 0; oy < span; ++oy) {
-      const int cy = all ? oy : (ci[1] + oy - 2 + nc) % nc;
-      const int base = (cx * nc + cy) * nc;
-      for (int r = 0; r < nr; ++r) {
-        const int s = cell_start[base + zr[r][0]], e = cell_start[base + zr[r][1] + 1];
-        for (int k0 = s; k0 < e; k0 += 32) {
-          const int k = k0 + lane;
-          bool in = false;
-          if (k < e && k != i) {
-            const float4 pj = pos32[k];
-            float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            dx -= P.Lf * rintf(dx * P.invLf);
-            dy -= P.Lf * rintf(dy * P.invLf);
-            dz -= P.Lf * rintf(dz * P.invLf);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
-          }
-          const bool own = in && ((i < k) != (((i + k) & 1) != 0));
-          const unsigned mf = __ballot_sync(0xffffffffu, in);
-          const unsigned mh = __ballot_sync(0xffffffffu, own);
-          if (own) {
-            // owned pairs open the row: full slot and pair id share the rank
-            const int rank = nhalf + __popc(mh & lt);
-            if (kMode == 1) {
-              const int pid = hbase + rank;
-              full_j[fbase + rank] = k;
-              full_ref[fbase + rank] = pid << 1;
-              half_i[pid] = i;
-              half_j[pid] = k;
-            } else if (kMode == 2 && rank < P.slab) {
-              srow[rank] = k;
-            }
-          }
-          nfull += __popc(mf);
-          nhalf += __popc(mh);
+    const int cy = all ? oy : (ci[1] + oy - 2 + nc) % nc;
+    const int base = (cx * nc + cy) * nc;
+    for (int r = 0; r < nr; ++r) {
+      rs[r] = cell_start[base + zr[r][0]];
+      re[r] = cell_start[base + zr[r][1] + 1];
+    }
+  }
+  for (int col = 0; col < ncol; ++col) {
+    for (int r = 0; r < nr; ++r) {
+      const int s = __shfl_sync(0xffffffffu, rs[r], col), e = __shfl_sync(0xffffffffu, re[r], col);
+      for (int k0 = s; k0 < e; k0 += 32) {
+        const int k = k0 + lane;
+        bool in = false;
+        if (k < e && k != i) {
+          const float4 pj = pos32[k];
+          float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+          dx -= P.Lf * rintf(dx * P.invLf);
+          dy -= P.Lf * rintf(dy * P.invLf);
+          dz -= P.Lf * rintf(dz * P.invLf);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
         }
+        const bool own = in && ((i < k) != (((i + k) & 1) != 0));
+        const unsigned mf = __ballot_sync(0xffffffffu, in);
+        const unsigned mh = __ballot_sync(0xffffffffu, own);
+        if (own) {
+          // owned pairs open the row: full slot and pair id share the rank
+          const int rank = nhalf + __popc(mh & lt);
+          if (kMode == 1) {
+            const int pid = hbase + rank;
+            full_j[fbase + rank] = k;
+            full_ref[fbase + rank] = pid << 1;
+            half_i[pid] = i;
+            half_j[pid] = k;
+          } else if (kMode == 2 && rank < P.slab) {
+            srow[rank] = k;
+          }
+        }
+        nfull += __popc(mf);
+        nhalf += __popc(mh);
       }
     }
   }
@@ -297,17 +306,28 @@ __global__ void k_transpose_scatter(long long nh, const int* __restrict__ half_j
   tmp[slot] = (int)pid;
 }
 
-__global__ void k_transpose_sort(int n, const int* __restrict__ full_start, const int* __restrict__ half_cnt,
-                                 const int* __restrict__ tmp, const int* __restrict__ half_i,
-                                 int* __restrict__ full_j, int* __restrict__ full_ref) {
+constexpr int kSortCap = 256;  // transposed entries per row staged in shared memory
+
+__global__ void __launch_bounds__(256) k_transpose_sort(int n, const int* __restrict__ full_start,
+                                                        const int* __restrict__ half_cnt,
+                                                        const int* __restrict__ tmp, const int* __restrict__ half_i,
+                                                        int* __restrict__ full_j, int* __restrict__ full_ref) {
+  __shared__ int stage[256 / 32][kSortCap];
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  const int lo = full_start[i] + half_cnt[i], hi = full_start[i + 1];
-  for (int e = lo + lane; e < hi; e += 32) {
-    const int p = tmp[e];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (i >= n) return;  // whole warps leave together
+  const int lo = full_start[i] + half_cnt[i], hi = full_start[i + 1], m = hi - lo;
+  const bool staged = m <= kSortCap;
+  if (staged)
+    for (int e = lane; e < m; e += 32) stage[w][e] = tmp[lo + e];
+  __syncwarp();
+  for (int e = lane; e < m; e += 32) {
+    const int p = staged ? stage[w][e] : tmp[lo + e];
     int rank = 0;
-    for (int m = lo; m < hi; ++m) rank += tmp[m] < p;
+    if (staged)
+      for (int q = 0; q < m; ++q) rank += stage[w][q] < p;
+    else
+      for (int q = lo; q < hi; ++q) rank += tmp[q] < p;
     full_ref[lo + rank] = (p << 1) | 1;
     full_j[lo + rank] = half_i[p];
   }
