@@ -54,31 +54,34 @@ __device__ __forceinline__ void multipole_field(R rx, R ry, R rz, R q, R dx, R d
   ez = rad * rz - b1 * dz - c2 * tz;
 }
 
-// Kernel coefficients of one pair in precision R (float64 or float32).
-template <typename R>
-__device__ __forceinline__ Kern<R> pair_kernels(R r2, R ai_isa, R aj_isa, R thi, R thj, bool same_mol,
-                                                const PairGeom& g) {
-  Kern<R> k;
-  const R r = sqrt(r2);
-  const R ir = (R)1 / r;
-  const R ir2 = ir * ir;
-  const R beta = (R)g.beta;
-  const R br = beta * r;
-  const R ex2 = exp(-br * br);
-  const R b0 = erfc(br) * ir;
-  R fac = ex2 * (R)g.gpre;  // e^{-b^2 r^2} / (beta sqrt(pi)) * (2 beta^2)
-  const R tb2 = (R)g.twob2;
-  const R b1 = (b0 + fac) * ir2;
-  fac *= tb2;
-  const R b2 = ((R)3 * b1 + fac) * ir2;
-  fac *= tb2;
-  const R b3 = ((R)5 * b2 + fac) * ir2;
-  const R bare1 = ir * ir2;
-  const R bare2 = (R)3 * bare1 * ir2;
-  const R bare3 = (R)5 * bare2 * ir2;
-  const R x = min(thi, thj) * r2 * r * ai_isa * aj_isa;
-  const R e = exp(-x);
-  const R d3 = e, d5 = ((R)1 + x) * e, d7 = ((R)1 + x + (R)0.6 * x * x) * e;
+// ---- mixed path: pair terms in float32
+
+struct PairGeom32 {
+  float beta, twob2, gpre;
+};
+
+// Kernel coefficients of one pair in float32.
+__device__ __forceinline__ Kern<float> pair_kernels32(float r2, float ai_isa, float aj_isa, float thi, float thj,
+                                                      bool same_mol, const PairGeom32& g) {
+  Kern<float> k;
+  const float r = sqrtf(r2);
+  const float ir = 1.f / r;
+  const float ir2 = ir * ir;
+  const float br = g.beta * r;
+  const float ex2 = expf(-br * br);
+  const float b0 = erfcf(br) * ir;
+  float fac = ex2 * g.gpre;  // e^{-b^2 r^2} / (beta sqrt(pi)) * (2 beta^2)
+  const float b1 = (b0 + fac) * ir2;
+  fac *= g.twob2;
+  const float b2 = (3.f * b1 + fac) * ir2;
+  fac *= g.twob2;
+  const float b3 = (5.f * b2 + fac) * ir2;
+  const float bare1 = ir * ir2;
+  const float bare2 = 3.f * bare1 * ir2;
+  const float bare3 = 5.f * bare2 * ir2;
+  const float x = fminf(thi, thj) * r2 * r * ai_isa * aj_isa;
+  const float e = expf(-x);
+  const float d3 = e, d5 = (1.f + x) * e, d7 = (1.f + x + 0.6f * x * x) * e;
   k.b1u = b1 - d3 * bare1;
   k.b2u = b2 - d5 * bare2;
   if (same_mol) {
@@ -91,56 +94,6 @@ __device__ __forceinline__ Kern<R> pair_kernels(R r2, R ai_isa, R aj_isa, R thi,
     k.b3e = b3 - d7 * bare3;
   }
   return k;
-}
-
-__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_pair_build(long long nh, const int* __restrict__ half_i,
-                                                    const int* __restrict__ half_j, const double4_32a* __restrict__ A,
-                                                    const double4_32a* __restrict__ B, const double4_32a* __restrict__ C,
-                                                    const double4_32a* __restrict__ D, PairGeom g, R* __restrict__ T,
-                                                    R* __restrict__ Ep) {
-  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pid >= nh) return;
-  const int i = half_i[pid], j = half_j[pid];
-  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], ci = C[i], cj = C[j], di = D[i], dj = D[j];
-  // geometry in float64 (exact minimum image), then the precision of the path
-  const double rx64 = min_image(ai.x - aj.x, g.L), ry64 = min_image(ai.y - aj.y, g.L),
-               rz64 = min_image(ai.z - aj.z, g.L);
-  const R rx = (R)rx64, ry = (R)ry64, rz = (R)rz64;
-  const R r2 = rx * rx + ry * ry + rz * rz;
-  const Kern<R> k = pair_kernels<R>(r2, (R)bi.w, (R)bj.w, (R)di.z, (R)dj.z, di.w == dj.w, g);
-  const R tv[6] = {k.b2u * rx * rx - k.b1u, k.b2u * ry * ry - k.b1u, k.b2u * rz * rz - k.b1u,
-                   k.b2u * rx * ry, k.b2u * rx * rz, k.b2u * ry * rz};
-  if constexpr (sizeof(R) == 8) {
-    // float64 path: the tensor is kept as float pairs hi + lo (hi = fl(t),
-    // lo = fl(t - hi)), read by the double-float kernel k_t_real_df
-    float hi[6], lo[6];
-    for (int a = 0; a < 6; ++a) {
-      hi[a] = __double2float_rn((double)tv[a]);
-      lo[a] = __double2float_rn((double)tv[a] - (double)hi[a]);
-    }
-    float4* o = reinterpret_cast<float4*>(T + 6 * pid);
-    o[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
-    o[1] = make_float4(hi[4], hi[5], lo[0], lo[1]);
-    o[2] = make_float4(lo[2], lo[3], lo[4], lo[5]);
-  } else {
-    R* t = T + 6 * pid;
-    for (int a = 0; a < 6; ++a) t[a] = tv[a];
-  }
-  R ex, ey, ez;
-  multipole_field<R>(rx, ry, rz, (R)aj.w, (R)bj.x, (R)bj.y, (R)bj.z, (R)cj.x, (R)cj.y, (R)cj.z, (R)cj.w,
-                     (R)dj.x, (R)dj.y, k.b1e, k.b2e, k.b3e, ex, ey, ez);
-  R* e = Ep + 6 * pid;
-  e[0] = ex;
-  e[1] = ey;
-  e[2] = ez;
-  multipole_field<R>(-rx, -ry, -rz, (R)ai.w, (R)bi.x, (R)bi.y, (R)bi.z, (R)ci.x, (R)ci.y, (R)ci.z, (R)ci.w,
-                     (R)di.x, (R)di.y, k.b1e, k.b2e, k.b3e, ex, ey, ez);
-  e[3] = ex;
-  e[4] = ey;
-  e[5] = ez;
 }
 
 // ---- float64 path of the pair build, entirely in double-float on the float
@@ -177,6 +130,53 @@ __device__ __forceinline__ void mp_field_df(const dflt r[3], const dflt* mp, dfl
 __device__ __forceinline__ dflt min_image_df(dflt d, const PairGeomDf& g) {
   const float sh = rintf(d.hi * g.invL);
   return sh == 0.f ? d : df_sub(d, df_mul({sh, 0.f}, g.L));
+}
+
+// Mixed path pair build: the displacement from the split positions (minimum
+// image in double-float, then rounded to float), every other quantity in
+// float32 from the float parts of the per-atom records (pd, mp_df), so that
+// no float64 instruction is issued. Writes the tensor and both permanent
+// fields in float32, 6 + 6 per pair.
+__global__ void __launch_bounds__(256) k_pair_build32(long long nh, const int* __restrict__ half_i,
+                                                      const int* __restrict__ half_j, const float4* __restrict__ pd,
+                                                      const float4* __restrict__ mp_df, PairGeomDf gd, PairGeom32 g,
+                                                      float* __restrict__ T, float* __restrict__ Ep) {
+  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pid >= nh) return;
+  const int i = half_i[pid], j = half_j[pid];
+  const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
+  const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
+  const dflt dx = min_image_df(df_sub({hi_i.x, lo_i.x}, {hi_j.x, lo_j.x}), gd);
+  const dflt dy = min_image_df(df_sub({hi_i.y, lo_i.y}, {hi_j.y, lo_j.y}), gd);
+  const dflt dz = min_image_df(df_sub({hi_i.z, lo_i.z}, {hi_j.z, lo_j.z}), gd);
+  const float rx = dx.hi + dx.lo, ry = dy.hi + dy.lo, rz = dz.hi + dz.lo;
+  const float r2 = rx * rx + ry * ry + rz * rz;
+  const Kern<float> k = pair_kernels32(r2, hi_i.w, hi_j.w, th_i.x, th_j.x,
+                                       __float_as_int(th_i.z) == __float_as_int(th_j.z), g);
+  float* t = T + 6 * pid;
+  t[0] = k.b2u * rx * rx - k.b1u;
+  t[1] = k.b2u * ry * ry - k.b1u;
+  t[2] = k.b2u * rz * rz - k.b1u;
+  t[3] = k.b2u * rx * ry;
+  t[4] = k.b2u * rx * rz;
+  t[5] = k.b2u * ry * rz;
+  // float parts of q, d, Theta (mp_df: (q, dx), (dy, dz), (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz) as hi/lo)
+  const float4* mi = mp_df + 5 * (long long)i;
+  const float4* mj = mp_df + 5 * (long long)j;
+  const float4 i0 = mi[0], i1 = mi[1], i2 = mi[2], i3 = mi[3], i4 = mi[4];
+  const float4 j0 = mj[0], j1 = mj[1], j2 = mj[2], j3 = mj[3], j4 = mj[4];
+  float ex, ey, ez;
+  multipole_field<float>(rx, ry, rz, j0.x, j0.z, j1.x, j1.z, j2.x, j2.z, j3.x, j3.z, j4.x, j4.z, k.b1e, k.b2e,
+                         k.b3e, ex, ey, ez);
+  float* e = Ep + 6 * pid;
+  e[0] = ex;
+  e[1] = ey;
+  e[2] = ez;
+  multipole_field<float>(-rx, -ry, -rz, i0.x, i0.z, i1.x, i1.z, i2.x, i2.z, i3.x, i3.z, i4.x, i4.z, k.b1e, k.b2e,
+                         k.b3e, ex, ey, ez);
+  e[3] = ex;
+  e[4] = ey;
+  e[5] = ez;
 }
 
 // The geometry-only terms of pair (i, j) in double-float: r = x_i - x_j
@@ -570,12 +570,16 @@ void launch_pair_build(amp_ctx* c) {
                                                    reinterpret_cast<float*>(c->Ep64));
     return;
   }
-  // mixed path: float32 pair terms; the split positions serve its float64 check
+  // mixed path: float32 pair terms from the split records, which also serve its float64 check
   c->n_launch += 2;
   k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
                                                                   c->mp_df, c->pd);
-  k_pair_build<float><<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
-                                                       c->atomC, c->atomD, g, c->T32, c->Ep32);
+  PairGeom32 g32;
+  g32.beta = (float)g.beta;
+  g32.twob2 = (float)g.twob2;
+  g32.gpre = (float)g.gpre;
+  k_pair_build32<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, geom_df(g), g32,
+                                                c->T32, c->Ep32);
 }
 
 // Self term of the permanent field: +4 beta^3/(3 sqrt(pi)) d_i, d_i from atomB.
