@@ -154,7 +154,7 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return AMP_ERR_CUDA;
   }
-  if (!cluster && ((r = pme_setup(c)) || (r = dfm_setup(c)))) {
+  if ((!cluster && (r = pme_setup(c))) || (r = dfm_setup(c))) {
     amp_destroy(c);
     return r;
   }

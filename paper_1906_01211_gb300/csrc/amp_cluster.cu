@@ -124,6 +124,127 @@ __global__ void __launch_bounds__(kTileI) k_cluster_field(int n, int cols_per_sl
   if (i < n) part[(long long)blockIdx.y * n + i] = make_double4_32a(ax, ay, az, 0.0);
 }
 
+// The float64 path of the same sums in double-float (hi + lo floats, float
+// units only): positions, moments and v are split as they are staged, the
+// kernels and the Thole exponential come from df_rsqrt / df_exp_neg, and each
+// thread keeps its row sum in double-float across all tiles.
+struct JTileDf {
+  float xh[kTileJ], xl[kTileJ], yh[kTileJ], yl[kTileJ], zh[kTileJ], zl[kTileJ];
+  float ish[kTileJ], isl[kTileJ], thh[kTileJ], thl[kTileJ];
+  int mol[kTileJ];
+  float mp[kTileJ][20];  // v (or q, d, Theta) as hi/lo pairs in the order of mp_field_df
+};
+
+__device__ __forceinline__ dflt df_min(dflt a, dflt b) { return (a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo)) ? a : b; }
+
+template <bool kPerm>
+__global__ void __launch_bounds__(kTileI) k_cluster_field_df(int n, int cols_per_slice,
+                                                             const double4_32a* __restrict__ A,
+                                                             const double4_32a* __restrict__ B,
+                                                             const double4_32a* __restrict__ C,
+                                                             const double4_32a* __restrict__ D,
+                                                             const double4_32a* __restrict__ v,
+                                                             const float2* __restrict__ tab,
+                                                             double4_32a* __restrict__ part,
+                                                             const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ JTileDf t;
+  const int i = blockIdx.x * kTileI + threadIdx.x;
+  const int j0 = blockIdx.y * cols_per_slice;
+  const int j1 = min(n, j0 + cols_per_slice);
+  dflt xi = {0.f, 0.f}, yi = xi, zi = xi, isai = xi, thi = xi;
+  int moli = -1;
+  if (i < n) {
+    const double4_32a a = A[i], b = B[i], d = D[i];
+    xi = df_split(a.x);
+    yi = df_split(a.y);
+    zi = df_split(a.z);
+    isai = df_split(b.w);
+    thi = df_split(d.z);
+    moli = (int)d.w;
+  }
+  const dflt ONE = {1.f, 0.f}, THREE = {3.f, 0.f}, FIFTEEN = {15.f, 0.f};
+  const dflt six = {0.600000024f, -2.38418579e-08f};  // 0.6 = hi + lo
+  dflt sx = {0.f, 0.f}, sy = sx, sz = sx;
+  for (int jt = j0; jt < j1; jt += kTileJ) {
+    const int jl = jt + threadIdx.x;
+    if (threadIdx.x < kTileJ && jl < j1) {
+      const double4_32a a = A[jl], b = B[jl], d = D[jl];
+      dflt u = df_split(a.x);
+      t.xh[threadIdx.x] = u.hi, t.xl[threadIdx.x] = u.lo;
+      u = df_split(a.y);
+      t.yh[threadIdx.x] = u.hi, t.yl[threadIdx.x] = u.lo;
+      u = df_split(a.z);
+      t.zh[threadIdx.x] = u.hi, t.zl[threadIdx.x] = u.lo;
+      u = df_split(b.w);
+      t.ish[threadIdx.x] = u.hi, t.isl[threadIdx.x] = u.lo;
+      u = df_split(d.z);
+      t.thh[threadIdx.x] = u.hi, t.thl[threadIdx.x] = u.lo;
+      t.mol[threadIdx.x] = (int)d.w;
+      float* m = t.mp[threadIdx.x];
+      if (kPerm) {
+        const double4_32a c = C[jl];
+        const double vals[10] = {a.w, b.x, b.y, b.z, c.x, c.y, c.z, c.w, d.x, d.y};
+        for (int k = 0; k < 10; ++k) {
+          const dflt w = df_split(vals[k]);
+          m[2 * k] = w.hi;
+          m[2 * k + 1] = w.lo;
+        }
+      } else {
+        const double4_32a vv = v[jl];
+        const double vals[3] = {vv.x, vv.y, vv.z};
+        for (int k = 0; k < 3; ++k) {
+          const dflt w = df_split(vals[k]);
+          m[2 * k] = w.hi;
+          m[2 * k + 1] = w.lo;
+        }
+      }
+    }
+    __syncthreads();
+    const int cnt = min(kTileJ, j1 - jt);
+    if (i < n) {
+      for (int k = 0; k < cnt; ++k) {
+        const int j = jt + k;
+        if (j == i) continue;
+        if (kPerm && t.mol[k] == moli) continue;  // excluded: damped kernel vanishes
+        const dflt R[3] = {df_sub(xi, {t.xh[k], t.xl[k]}), df_sub(yi, {t.yh[k], t.yl[k]}),
+                           df_sub(zi, {t.zh[k], t.zl[k]})};
+        const dflt r2 = df_madd(R[2], R[2], df_madd(R[1], R[1], df_mul(R[0], R[0])));
+        const dflt ir = df_rsqrt(r2);
+        const dflt ir2 = df_mul(ir, ir);
+        const dflt x = df_mul(df_mul(df_min(thi, {t.thh[k], t.thl[k]}), df_mul(r2, df_mul(r2, ir))),
+                              df_mul(isai, {t.ish[k], t.isl[k]}));
+        const dflt e = df_exp_neg(x, tab);
+        const dflt ir3 = df_mul(ir, ir2), ir5 = df_mul(ir3, ir2);
+        const dflt b1 = df_mul(df_sub(ONE, e), ir3);
+        const dflt b2 = df_mul(df_mul(THREE, df_sub(ONE, df_mul(df_add(ONE, x), e))), ir5);
+        const float* m = t.mp[k];
+        if (kPerm) {
+          const dflt x1 = df_add(ONE, x);
+          const dflt b3 = df_mul(df_mul(FIFTEEN, df_sub(ONE, df_mul(df_madd(df_mul(six, x), x, x1), e))),
+                                 df_mul(ir5, ir2));
+          dflt mp[10];
+          for (int q = 0; q < 10; ++q) mp[q] = {m[2 * q], m[2 * q + 1]};
+          dflt f[3];
+          mp_field_df(R, mp, b1, b2, b3, f);
+          sx = df_add(sx, f[0]);
+          sy = df_add(sy, f[1]);
+          sz = df_add(sz, f[2]);
+        } else {
+          const dflt vx = {m[0], m[1]}, vy = {m[2], m[3]}, vz = {m[4], m[5]};
+          const dflt s = df_mul(b2, df_madd(R[2], vz, df_madd(R[1], vy, df_mul(R[0], vx))));
+          sx = df_add(sx, df_sub(df_mul(s, R[0]), df_mul(b1, vx)));
+          sy = df_add(sy, df_sub(df_mul(s, R[1]), df_mul(b1, vy)));
+          sz = df_add(sz, df_sub(df_mul(s, R[2]), df_mul(b1, vz)));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (i < n)
+    part[(long long)blockIdx.y * n + i] = make_double4_32a(df_to_double(sx), df_to_double(sy), df_to_double(sz), 0.0);
+}
+
 __global__ void k_cluster_reduce(int n, int slices, const double4_32a* __restrict__ part, double4_32a* __restrict__ out,
                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
@@ -179,8 +300,13 @@ void launch_field(amp_ctx* c, const V* v, double4_32a* out) {
   cols = (cols + kTileJ - 1) / kTileJ * kTileJ;
   dim3 grid((n + kTileI - 1) / kTileI, s);
   c->n_launch += 2;
-  k_cluster_field<R, kPerm, V><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD, v,
-                                                                c->cluster_part, c->op_stop);
+  if constexpr (sizeof(R) == 8)  // float64 path: double-float arithmetic
+    k_cluster_field_df<kPerm><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                               reinterpret_cast<const double4_32a*>(v), c->dfm,
+                                                               c->cluster_part, c->op_stop);
+  else
+    k_cluster_field<R, kPerm, V><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                                  v, c->cluster_part, c->op_stop);
   k_cluster_reduce<<<amp_blocks(n, 256), 256, 0, c->stream>>>(n, s, c->cluster_part, out, c->op_stop);
 }
 

@@ -362,6 +362,22 @@ __device__ __forceinline__ dflt df_erfcx(dflt x, const float2* __restrict__ tab)
   return p;
 }
 
+// Field at r of a multipole with kernels b1..b3, all double-float.
+__device__ __forceinline__ void mp_field_df(const dflt r[3], const dflt* mp, dflt b1, dflt b2, dflt b3, dflt out[3]) {
+  // mp: q, dx, dy, dz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz
+  const dflt t0 = df_madd(mp[8], r[2], df_madd(mp[7], r[1], df_mul(mp[4], r[0])));
+  const dflt t1 = df_madd(mp[9], r[2], df_madd(mp[5], r[1], df_mul(mp[7], r[0])));
+  const dflt t2 = df_madd(mp[6], r[2], df_madd(mp[9], r[1], df_mul(mp[8], r[0])));
+  const dflt rtr = df_madd(r[2], t2, df_madd(r[1], t1, df_mul(r[0], t0)));
+  const dflt dr = df_madd(mp[3], r[2], df_madd(mp[2], r[1], df_mul(mp[1], r[0])));
+  const dflt third = {0.333333343267f, -9.93410748e-09f};  // 1/3 = hi + lo
+  const dflt two3 = {0.666666686535f, -1.98682150e-08f};   // 2/3 = hi + lo
+  const dflt rad = df_madd(df_mul(b3, rtr), third, df_madd(b2, dr, df_mul(mp[0], b1)));
+  const dflt c2 = df_mul(b2, two3);
+  const dflt t[3] = {t0, t1, t2};
+  for (int a = 0; a < 3; ++a) out[a] = df_sub(df_sub(df_mul(rad, r[a]), df_mul(b1, mp[1 + a])), df_mul(c2, t[a]));
+}
+
 // Sum over the kRowGroup lanes of one row; the mask names exactly this group.
 __device__ __forceinline__ dflt df_group_sum(dflt v) {
   const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
