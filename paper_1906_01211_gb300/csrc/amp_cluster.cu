@@ -245,6 +245,76 @@ __global__ void __launch_bounds__(kTileI) k_cluster_field_df(int n, int cols_per
     part[(long long)blockIdx.y * n + i] = make_double4_32a(df_to_double(sx), df_to_double(sy), df_to_double(sz), 0.0);
 }
 
+// The mixed path's T*v over all pairs in float32: positions, 1/sqrt(alpha),
+// Thole a and molecule as float records (clu32, made once per geometry), v
+// as floats, so the tiles are staged without float64 conversions.
+struct JTile32 {
+  float4 p[kTileJ];  // x, y, z, 1/sqrt(alpha)
+  float th[kTileJ];
+  float4 v[kTileJ];
+};
+
+__global__ void __launch_bounds__(kTileI) k_cluster_tv32(int n, int cols_per_slice, const float4* __restrict__ clu32,
+                                                         const float4* __restrict__ v32,
+                                                         double4_32a* __restrict__ part,
+                                                         const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ JTile32 t;
+  const int i = blockIdx.x * kTileI + threadIdx.x;
+  const int j0 = blockIdx.y * cols_per_slice;
+  const int j1 = min(n, j0 + cols_per_slice);
+  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+  float thi = 0.f;
+  if (i < n) {
+    pi = clu32[2 * (long long)i];
+    thi = clu32[2 * (long long)i + 1].x;
+  }
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int jt = j0; jt < j1; jt += kTileJ) {
+    const int jl = jt + threadIdx.x;
+    if (threadIdx.x < kTileJ && jl < j1) {
+      t.p[threadIdx.x] = clu32[2 * (long long)jl];
+      t.th[threadIdx.x] = clu32[2 * (long long)jl + 1].x;
+      t.v[threadIdx.x] = v32[jl];
+    }
+    __syncthreads();
+    const int cnt = min(kTileJ, j1 - jt);
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    if (i < n) {
+      for (int k = 0; k < cnt; ++k) {
+        if (jt + k == i) continue;
+        const float4 pj = t.p[k], vj = t.v[k];
+        const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float ir = rsqrtf(r2);
+        const float ir2 = ir * ir;
+        const float x = fminf(thi, t.th[k]) * r2 * r2 * ir * pi.w * pj.w;
+        const float e = expf(-x);
+        const float b1 = (1.f - e) * ir * ir2;
+        const float b2 = 3.f * (1.f - (1.f + x) * e) * ir2 * ir2 * ir;
+        const float sv = b2 * (vj.x * rx + vj.y * ry + vj.z * rz);
+        sx += sv * rx - b1 * vj.x;
+        sy += sv * ry - b1 * vj.y;
+        sz += sv * rz - b1 * vj.z;
+      }
+    }
+    ax += (double)sx;
+    ay += (double)sy;
+    az += (double)sz;
+    __syncthreads();
+  }
+  if (i < n) part[(long long)blockIdx.y * n + i] = make_double4_32a(ax, ay, az, 0.0);
+}
+
+__global__ void k_cluster_records32(int n, const double4_32a* __restrict__ A, const double4_32a* __restrict__ B,
+                                    const double4_32a* __restrict__ D, float4* __restrict__ clu32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double4_32a a = A[i], b = B[i], d = D[i];
+  clu32[2 * (long long)i] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)b.w);
+  clu32[2 * (long long)i + 1] = make_float4((float)d.z, 0.f, 0.f, 0.f);
+}
+
 __global__ void k_cluster_reduce(int n, int slices, const double4_32a* __restrict__ part, double4_32a* __restrict__ out,
                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
@@ -304,6 +374,9 @@ void launch_field(amp_ctx* c, const V* v, double4_32a* out) {
     k_cluster_field_df<kPerm><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD,
                                                                reinterpret_cast<const double4_32a*>(v), c->dfm,
                                                                c->cluster_part, c->op_stop);
+  else if constexpr (!kPerm)
+    k_cluster_tv32<<<grid, kTileI, 0, c->stream>>>(n, cols, c->clu32, reinterpret_cast<const float4*>(v),
+                                                    c->cluster_part, c->op_stop);
   else
     k_cluster_field<R, kPerm, V><<<grid, kTileI, 0, c->stream>>>(n, cols, c->atomA, c->atomB, c->atomC, c->atomD,
                                                                   v, c->cluster_part, c->op_stop);
@@ -323,11 +396,21 @@ int cluster_setup(amp_ctx* c, const double* xyz, const double* q, const double* 
     if ((r = dev_alloc(c, &c->cluster_part, (long long)kClusterMaxSlices * n))) return r;
     c->cluster_part_cap = (long long)kClusterMaxSlices * n;
   }
+  if (c->cfg.precision == AMP_MIXED && c->clu32_cap < n) {
+    dev_free(c, c->clu32);
+    c->clu32 = nullptr;
+    if ((r = dev_alloc(c, &c->clu32, 2LL * n))) return r;
+    c->clu32_cap = n;
+  }
   cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, st);
   c->n_launch += 2;
   k_identity_perm<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm);
   k_cluster_atoms<<<amp_blocks(n, 256), 256, 0, st>>>(n, xyz, q, dip, quad, alpha, thole, mol, c->atomA, c->atomB,
                                                       c->atomC, c->atomD, c->alph, c->flags);
+  if (c->clu32) {
+    c->n_launch += 1;
+    k_cluster_records32<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->atomA, c->atomB, c->atomD, c->clu32);
+  }
   cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
   if ((r = cuda_check(c, cudaStreamSynchronize(st), "cluster setup"))) return r;
   if (c->hibuf[2] & 2) return fail(c, AMP_ERR_ARG, "alpha must be > 0 for every site");

@@ -148,6 +148,8 @@ struct amp_ctx {
   // isolated cluster (box == 0): all-pairs kernels, column-slice partial sums
   bool cluster = false;
   double4_32a* cluster_part = nullptr;
+  float4* clu32 = nullptr;  // mixed clusters: (x, y, z, 1/sqrt(alpha)), (thole, 0, 0, 0) per atom
+  int clu32_cap = 0;
   long long cluster_part_cap = 0;
 
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
