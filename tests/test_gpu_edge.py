@@ -1,0 +1,98 @@
+"""Edge cases of the float64 path through the C ABI: the smallest inputs, an
+iteration cap that stops the solve early (the partial iterate must equal the
+oracle's PCG iterate after the same number of steps), a zero right-hand side,
+and bitwise reproducibility of T*v (integer accumulation of the reciprocal
+grid, fixed-order sums elsewhere)."""
+import numpy as np
+import pytest
+
+from oracle import Setup
+from oracle.setup import DEBYE
+from oracle.solver import Operator, pcg
+from paper_1906_01211_gb300.synth import WATER_648, System, make_waters
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def solver(w, max_iter=100, tol=None):
+    from paper_1906_01211_gb300 import amoebapol as ap
+    return ap.Polarization(ap.Config(box=w.L, cutoff=w.cutoff, ewald_beta=w.beta, pme_grid=w.grid,
+                                     tol_debye=tol or w.tol_debye, max_iter=max_iter))
+
+
+def test_one_atom_is_rejected():
+    from paper_1906_01211_gb300 import amoebapol as ap
+    w = WATER_648
+    s = solver(w)
+    one = w.system()
+    sub = System(xyz=one.xyz[:1], q=one.q[:1], dip=one.dip[:1], quad=one.quad[:1], alpha=one.alpha[:1],
+                 thole=one.thole[:1], mol=one.mol[:1], box=one.box)
+    with pytest.raises(ap.AmpError) as e:
+        s.set_synthetic(sub)
+    assert e.value.code == ap.AMP_ERR_ARG
+
+
+@pytest.mark.parametrize("cap", [1, 2, 3])
+def test_iteration_cap_returns_the_pcg_iterate(cap):
+    from paper_1906_01211_gb300 import amoebapol as ap
+    w = WATER_648
+    sysm = w.system()
+    setup = Setup(box=w.L, cutoff=w.cutoff, beta=w.beta, grid=w.grid, order=5)
+    op = Operator(sysm, setup)
+    E0 = op.permanent_field()
+    mu_o, it_o, rms_o = pcg(op.apply_A, sysm.alpha, E0, w.tol_debye, max_iter=cap)
+    assert it_o == cap
+    s = solver(w, max_iter=cap)
+    s.set_synthetic(sysm)
+    E0g = s.permanent_field()
+    with pytest.raises(ap.AmpError) as e:
+        s.solve(E0g)
+    assert e.value.code == ap.AMP_ERR_NOT_CONVERGED
+    mu, it, rms = s.solve(E0g, check=False)
+    assert it == cap
+    d = mu.cpu().numpy() - mu_o
+    assert DEBYE * np.sqrt((d * d).sum() / sysm.n) < 1e-9
+    assert abs(rms / rms_o - 1) < 1e-8
+
+
+def test_zero_field_converges_at_once():
+    w = WATER_648
+    base = w.system()
+    sysm = System(xyz=base.xyz, q=np.zeros_like(base.q), dip=np.zeros_like(base.dip),
+                  quad=np.zeros_like(base.quad), alpha=base.alpha, thole=base.thole, mol=base.mol, box=base.box)
+    s = solver(w)
+    s.set_synthetic(sysm)
+    E0 = s.permanent_field()
+    assert float(torch.abs(E0).max()) == 0.0
+    mu, it, rms = s.solve(E0)
+    assert it == 0 and float(torch.abs(mu).max()) == 0.0
+
+
+def test_two_atom_box_matches_oracle():
+    L = 16.0
+    base = make_waters(2, L, 3)
+    sysm = System(xyz=base.xyz[:2], q=base.q[:2], dip=base.dip[:2], quad=base.quad[:2], alpha=base.alpha[:2],
+                  thole=base.thole[:2], mol=base.mol[:2], box=L)
+    setup = Setup(box=L, cutoff=7.0, beta=0.5446, grid=16, order=5)
+    op = Operator(sysm, setup)
+    from paper_1906_01211_gb300 import amoebapol as ap
+    s = ap.Polarization(ap.Config(box=L, cutoff=7.0, ewald_beta=0.5446, pme_grid=16, tol_debye=1e-10))
+    s.set_synthetic(sysm)
+    E0 = s.permanent_field().cpu().numpy()
+    ref = op.permanent_field()
+    assert np.linalg.norm(E0 - ref) < 1e-12 * sum(np.linalg.norm(p) for p in op.permanent_field_parts())
+    v = np.random.default_rng(2).normal(size=(2, 3))
+    t = s.apply_T(torch.tensor(v)).cpu().numpy()
+    assert np.linalg.norm(t - op.apply_T(v)) < 1e-12 * sum(np.linalg.norm(p) for p in op.apply_T_parts(v))
+
+
+def test_apply_T_is_bitwise_reproducible():
+    w = WATER_648
+    s = solver(w)
+    s.set_synthetic(w.system())
+    v = torch.tensor(np.random.default_rng(11).normal(size=(w.n_waters * 3, 3)) * 0.1)
+    a = s.apply_T(v).clone()
+    b = s.apply_T(v).clone()
+    assert torch.equal(a, b)
