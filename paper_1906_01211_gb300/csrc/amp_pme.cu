@@ -234,9 +234,11 @@ __device__ __forceinline__ long long to_fixed(float f, int s) {
 }
 
 // Q(g) = sum_i mu_i . grad W_i(g) with mu = v32 + vlo. One thread per
-// (atom, x plane, y row): its five z points. vmax[kReduceBlocks] holds max
-// |v32| as left by the kernel that split v; every block derives the same
-// scale from it and block 0 stores it in fx_info[0] for the FFT.
+// (atom, y row, z point) adds the atom's value at the five x planes, so the
+// lanes of a warp that share (atom, y row) hit five consecutive z points:
+// the atomics of one row coalesce. vmax[kReduceBlocks] holds max |v32| as left
+// by the kernel that split v; every block derives the same scale from it and
+// block 0 stores it in fx_info[0] for the FFT.
 constexpr int kSpreadThreads = 256;
 __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, const float2* __restrict__ th_df,
                                                                       const int4* __restrict__ gbase,
@@ -253,24 +255,25 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, con
   if (blockIdx.x == 0 && threadIdx.x == 0) fx_info[0] = sfx;
   const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
   if (item >= (long long)n * (kOrder * kOrder)) return;
-  const int s = (int)(item / (kOrder * kOrder)), txy = (int)(item - (long long)s * (kOrder * kOrder));
-  const int tx = txy / kOrder, ty = txy - tx * kOrder;
+  const int s = (int)(item / (kOrder * kOrder)), tyz = (int)(item - (long long)s * (kOrder * kOrder));
+  const int ty = tyz / kOrder, tz = tyz - ty * kOrder;
   const float2* th = th_df + (long long)kThDf * s;
   const float4 h = v32[s], l = vlo[s];
-  const float2 x0 = th[(0 * 2 + 0) * kOrder + tx], x1 = th[(0 * 2 + 1) * kOrder + tx];
   const float2 y0 = th[(1 * 2 + 0) * kOrder + ty], y1 = th[(1 * 2 + 1) * kOrder + ty];
-  // A = mu_x w'_x w_y + mu_y w_x w'_y, B = mu_z w_x w_y: the point's value is A w_z + B w'_z
-  const dflt A = df_madd(df_mul({h.y, l.y}, {x0.x, x0.y}), {y1.x, y1.y},
-                         df_mul(df_mul({h.x, l.x}, {x1.x, x1.y}), {y0.x, y0.y}));
-  const dflt B = df_mul(df_mul({h.z, l.z}, {x0.x, x0.y}), {y0.x, y0.y});
+  const float2 z0 = th[(2 * 2 + 0) * kOrder + tz], z1 = th[(2 * 2 + 1) * kOrder + tz];
+  // P = mu_y w'_y w_z + mu_z w_y w'_z, Q = mu_x w_y w_z: the point's value is P w_x + Q w'_x
+  const dflt P = df_madd(df_mul({h.z, l.z}, {y0.x, y0.y}), {z1.x, z1.y},
+                         df_mul(df_mul({h.y, l.y}, {y1.x, y1.y}), {z0.x, z0.y}));
+  const dflt Q = df_mul(df_mul({h.x, l.x}, {y0.x, y0.y}), {z0.x, z0.y});
   const int4 b = gbase[s];
-  unsigned long long* row = grid + ((long long)wrapk(b.x - tx, K) * K + wrapk(b.y - ty, K)) * K;
+  unsigned long long* col = grid + (long long)wrapk(b.y - ty, K) * K + wrapk(b.z - tz, K);
+  const long long plane = (long long)K * K;
 #pragma unroll
-  for (int tz = 0; tz < kOrder; ++tz) {
-    const float2 z0 = th[(2 * 2 + 0) * kOrder + tz], z1 = th[(2 * 2 + 1) * kOrder + tz];
-    const dflt val = df_madd(B, {z1.x, z1.y}, df_mul(A, {z0.x, z0.y}));
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const float2 x0 = th[(0 * 2 + 0) * kOrder + tx], x1 = th[(0 * 2 + 1) * kOrder + tx];
+    const dflt val = df_madd(Q, {x1.x, x1.y}, df_mul(P, {x0.x, x0.y}));
     const long long q = to_fixed(val.hi, sfx) + to_fixed(val.lo, sfx);
-    atomicAdd(row + wrapk(b.z - tz, K), (unsigned long long)q);
+    atomicAdd(col + wrapk(b.x - tx, K) * plane, (unsigned long long)q);
   }
 }
 
@@ -370,21 +373,37 @@ __global__ void k_split_grid(long long ng, const double* __restrict__ phi, float
 }
 
 // The float64 path's gather in double-float arithmetic (float units only):
-// weights, their derivatives and the grid potential are hi/lo pairs.
+// weights, their derivatives and the grid potential are hi/lo pairs. Six
+// atoms per warp, five lanes each (lanes 30 and 31 idle): lane t of an atom
+// sums x plane k0x - t, the five lanes then add their sums in a fixed order.
+constexpr int kGatherAtomsPerWarp = 6;
+constexpr int kGatherThreads = 128;
+
+__device__ __forceinline__ dflt sum_five(dflt v, int base) {  // same order in all five lanes
+  dflt t = {__shfl_sync(0xffffffffu, v.hi, base), __shfl_sync(0xffffffffu, v.lo, base)};
+#pragma unroll
+  for (int k = 1; k < kOrder; ++k)
+    t = df_add(t, {__shfl_sync(0xffffffffu, v.hi, base + k), __shfl_sync(0xffffffffu, v.lo, base + k)});
+  return t;
+}
+
 template <bool kSet>
-__global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __restrict__ th_df,
-                                                         const int4* __restrict__ gbase,
-                                                         const float2* __restrict__ phi, int K,
-                                                         double4_32a* __restrict__ out, const int* __restrict__ stop) {
+__global__ void __launch_bounds__(kGatherThreads) k_gather_field_df(int n, const float2* __restrict__ th_df,
+                                                                    const int4* __restrict__ gbase,
+                                                                    const float2* __restrict__ phi, int K,
+                                                                    double4_32a* __restrict__ out,
+                                                                    const int* __restrict__ stop) {
   if (stop && *stop) return;
   pdl_wait();
   pdl_trigger();
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
-  if (s >= n) return;  // whole groups leave together
+  const int lane = threadIdx.x & 31, seg = lane / kOrder, tx = lane - seg * kOrder;
+  const int warp = (blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
+  const int s = warp * kGatherAtomsPerWarp + seg;
+  if (warp * kGatherAtomsPerWarp >= n) return;  // whole warp
+  const bool active = seg < kGatherAtomsPerWarp && s < n;
   dflt ex = {0.f, 0.f}, ey = {0.f, 0.f}, ez = {0.f, 0.f};
-  const int4 b = gbase[s];
-  if (tx < kOrder) {
+  if (active) {
+    const int4 b = gbase[s];
     const float2* th = th_df + (long long)kThDf * s;
     const float2 wx0 = th[(0 * 2 + 0) * kOrder + tx], wx1 = th[(0 * 2 + 1) * kOrder + tx];
     float2 wz0[kOrder], wz1[kOrder];
@@ -413,15 +432,13 @@ __global__ void __launch_bounds__(128) k_gather_field_df(int n, const float2* __
     ey = df_mul({wx0.x, wx0.y}, py);
     ez = df_mul({wx0.x, wx0.y}, pz);
   }
-  const unsigned mask = pme_group_mask();
-#pragma unroll
-  for (int o = kPmeGroup / 2; o > 0; o >>= 1) {
-    ex = df_add(ex, {__shfl_xor_sync(mask, ex.hi, o, kPmeGroup), __shfl_xor_sync(mask, ex.lo, o, kPmeGroup)});
-    ey = df_add(ey, {__shfl_xor_sync(mask, ey.hi, o, kPmeGroup), __shfl_xor_sync(mask, ey.lo, o, kPmeGroup)});
-    ez = df_add(ez, {__shfl_xor_sync(mask, ez.hi, o, kPmeGroup), __shfl_xor_sync(mask, ez.lo, o, kPmeGroup)});
-  }
-  // lanes 0..2 finish one component each (float64 instructions cost the same
-  // for one active lane as for 32)
+  const int base = min(seg, kGatherAtomsPerWarp - 1) * kOrder;
+  ex = sum_five(ex, base);
+  ey = sum_five(ey, base);
+  ez = sum_five(ez, base);
+  // lanes 0..2 of each atom finish one component each (float64 instructions
+  // cost the same for one active lane as for 32)
+  if (!active) return;
   double* o = reinterpret_cast<double*>(out + s);
   if (tx < 3) {
     const double f = df_to_double(tx == 0 ? ex : (tx == 1 ? ey : ez));
@@ -442,7 +459,8 @@ void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out, bool split) {
   const long long ng = (long long)K * K * K;
   c->n_launch += split ? 2 : 1;
   if (split) k_split_grid<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->grid64, c->phi_df, c->op_stop);
-  launch_pdl(k_gather_field_df<kSet>, dim3(amp_blocks((long long)n * kPmeGroup, 128)), dim3(128), 0, st, n,
+  const long long warps = (n + kGatherAtomsPerWarp - 1) / kGatherAtomsPerWarp;
+  launch_pdl(k_gather_field_df<kSet>, dim3(amp_blocks(warps * 32, kGatherThreads)), dim3(kGatherThreads), 0, st, n,
              c->theta_df, c->gbase, c->phi_df, K, out, c->op_stop);
 }
 
