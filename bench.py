@@ -177,7 +177,7 @@ PAIR_BUILD_FLOPS = 130
 DF_FP32_PER_FP64 = 13
 # DRAM traffic (read + write) per launch of k_t_real_df, from one ncu capture of
 # the current kernel on this workload (profiles/k_t_real_df_water23556.md).
-T_REAL_TRAFFIC = {"water-23556": 111.8e6}
+T_REAL_TRAFFIC = {}
 
 
 def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
@@ -189,8 +189,9 @@ def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
     DF_FP32_PER_FP64 (152 SMs x 128 lanes x 2 flop x max SM clock / 13), the
     float64-equivalent rate of double-float arithmetic on this GPU.
     real-space T*v (k_t_real_df): HBM, algorithmic bytes per launch = 48 B
-    tensor per unique pair + 8 B index per directed entry + 96 B per atom
-    (v as float hi/lo + float64 v, and the float64 output), peak =
+    tensor + 4 B neighbour index per directed entry (the tensor is stored
+    once per entry, in row order) + 92 B per atom (row start, v as float
+    hi/lo, float64 v for the self term, the float64 output), peak =
     MEASURED_PEAKS.json hbm_gbs.
     """
     peaks = {}
@@ -214,7 +215,7 @@ def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
     ms, cnt = phases["t_real"]
     if cnt:
         per = ms / cnt
-        nbytes = 48 * n_pairs + 8 * 2 * n_pairs + 96 * n_atoms
+        nbytes = (48 + 4) * 2 * n_pairs + 92 * n_atoms
         ach = nbytes / (per / 1e3) / 1e9
         peak = hbm if hbm else 6800.0
         out.append({"kernel": "k_t_real_df (real-space T*v, double-float)", "bound": "hbm", "achieved": ach,

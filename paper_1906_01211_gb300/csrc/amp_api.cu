@@ -81,7 +81,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->full_start, (void**)&c->half_start, (void**)&c->theta, (void**)&c->theta32,
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
-                   (void**)&c->trec, (void**)&c->plo, (void**)&c->mp_df, (void**)&c->wv,
+                   (void**)&c->trec, (void**)&c->plo, (void**)&c->vhl, (void**)&c->mp_df, (void**)&c->wv,
                    (void**)&c->theta_df, (void**)&c->pd};
   for (void** b : bufs) {
     dev_free(c, *b);
@@ -100,7 +100,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = dev_alloc(c, &c->res, cap)) || (r = dev_alloc(c, &c->zv, cap)) || (r = dev_alloc(c, &c->pv, cap)) ||
       (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
       (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)) ||
-      (r = dev_alloc(c, &c->wv, cap)) ||
+      (r = dev_alloc(c, &c->wv, cap)) || (r = dev_alloc(c, &c->vhl, 2LL * cap)) ||
       (r = dev_alloc(c, &c->mp_df, 5LL * cap)) || (r = dev_alloc(c, &c->pd, 3LL * cap)))
     return r;
   c->n_cap = cap;
@@ -146,8 +146,11 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
   }
   // The reciprocal-space chain runs on the side stream beside the real-space
   // kernel and is the longer of the two: give its blocks priority.
-  int prio_lo = 0, prio_hi = 0;
+  int prio_lo = 0, prio_hi = 0, dev = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c->n_sm < 1)
+    c->n_sm = 1;
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {

@@ -18,7 +18,10 @@
 //              row for which (i < j) != ((i + j) odd) — each pair exactly once,
 //              about half of each row's neighbours.
 // Pair data indexed by pid (computed once per geometry):
-//   T64/T32[pid*6 + {xx,yy,zz,xy,xz,yz}]  damped dipole-field tensor
+//   T32[pid*6 + {xx,yy,zz,xy,xz,yz}]  damped dipole-field tensor (mixed path)
+//   T64: the float64 path's tensor once per full-list entry, in entry order:
+//     32 bytes per entry (hi xx yy zz xy xz yz, lo xx yy) from the start,
+//     then 16 bytes per entry (lo zz xy xz yz) after cap_full entries
 //   Ep64/Ep32[pid*6 + side*3 + a]         permanent field at the side's atom
 #pragma once
 
@@ -70,6 +73,7 @@ struct amp_ctx {
   // neighbour lists
   int *full_cnt = nullptr, *half_cnt = nullptr, *full_start = nullptr, *half_start = nullptr;
   int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr, *tr_tmp = nullptr;
+  int* pos_tr = nullptr;  // full-list position of each pair's entry in its non-owner's row
   long long n_full = 0, n_half = 0, cap_full = 0, cap_half = 0;
   int* flags = nullptr;  // [0] bit 1 list transpose failure, bit 2 bad alpha, bit 4 slab overflow
   int* slab = nullptr;   // single-pass list: owned neighbours per atom, fixed row capacity
@@ -118,9 +122,11 @@ struct amp_ctx {
   // operator's kernels test on entry (null: always run).
   const int* op_stop = nullptr;
   cudaStream_t side = nullptr;  // second stream: PME beside the real-space kernel
+  int n_sm = 1;                 // streaming multiprocessors of the device
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   float4* p32 = nullptr;  // float part of p (mixed: p in float32; float64: hi of hi + lo)
   float4* plo = nullptr;  // float64 path: p - hi, so that hi + lo carries p to ~48 bits
+  float4* vhl = nullptr;  // float64 path: (p32[s], plo[s]) side by side, one 32-byte record per atom
   double* partials = nullptr;  // block partial sums (two sets)
   int n_parts_cap = 0;
   double* scal = nullptr;      // device scalars of the solver: rz[2], rms, pq
@@ -401,6 +407,20 @@ __device__ __forceinline__ dflt df_group_sum(dflt v) {
 // returns once the previous grid has completed and its writes are visible),
 // and pdl_trigger() to let its own successor be launched early. Kernels
 // launched the ordinary way pass through pdl_wait() at once.
+// 32-byte vector loads (sm_100 and later); p must be 32-byte aligned. The
+// streaming form marks the lines evict-first; the read-only form goes
+// through the non-coherent path (data the kernel does not write).
+__device__ __forceinline__ void ld8_stream(const float4* p, float4& a, float4& b) {
+  asm("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+__device__ __forceinline__ void ld8_ro(const float4* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 

@@ -311,7 +311,8 @@ constexpr int kSortCap = 256;  // transposed entries per row staged in shared me
 __global__ void __launch_bounds__(256) k_transpose_sort(int n, const int* __restrict__ full_start,
                                                         const int* __restrict__ half_cnt,
                                                         const int* __restrict__ tmp, const int* __restrict__ half_i,
-                                                        int* __restrict__ full_j, int* __restrict__ full_ref) {
+                                                        int* __restrict__ full_j, int* __restrict__ full_ref,
+                                                        int* __restrict__ pos_tr) {
   __shared__ int stage[256 / 32][kSortCap];
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -330,6 +331,7 @@ __global__ void __launch_bounds__(256) k_transpose_sort(int n, const int* __rest
       for (int q = lo; q < hi; ++q) rank += tmp[q] < p;
     full_ref[lo + rank] = (p << 1) | 1;
     full_j[lo + rank] = half_i[p];
+    pos_tr[p] = lo + rank;
   }
 }
 
@@ -411,7 +413,8 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   if (c->n_full > (1LL << 30)) return fail(c, AMP_ERR_GEOMETRY, "too many pairs");
   if (c->n_full > c->cap_full || c->n_half > c->cap_half) {
     void** bufs[] = {(void**)&c->full_j, (void**)&c->full_ref, (void**)&c->tr_tmp, (void**)&c->half_i, (void**)&c->half_j,
-                     (void**)&c->T64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32};
+                     (void**)&c->T64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32,
+                     (void**)&c->pos_tr};
     for (void** b : bufs) {
       dev_free(c, *b);
       *b = nullptr;
@@ -421,10 +424,10 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
     if ((r = dev_alloc(c, &c->full_j, capf)) || (r = dev_alloc(c, &c->full_ref, capf)) ||
         (r = dev_alloc(c, &c->tr_tmp, capf)) ||
         (r = dev_alloc(c, &c->half_i, caph)) || (r = dev_alloc(c, &c->half_j, caph)) ||
-        (r = dev_alloc(c, &c->Ep64, 6 * caph)))
+        (r = dev_alloc(c, &c->pos_tr, caph)) || (r = dev_alloc(c, &c->Ep64, 6 * caph)))
       return r;
     if (c->cfg.precision == AMP_FP64) {
-      if ((r = dev_alloc(c, &c->T64, 6 * caph))) return r;
+      if ((r = dev_alloc(c, &c->T64, 6 * capf))) return r;
     } else {
       if ((r = dev_alloc(c, &c->T32, 6 * caph)) || (r = dev_alloc(c, &c->Ep32, 6 * caph))) return r;
     }
@@ -441,7 +444,8 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   cudaMemsetAsync(c->full_cnt, 0, sizeof(int) * n, st);  // reused as the per-row slot counter
   k_transpose_scatter<<<amp_blocks(c->n_half, 256), 256, 0, st>>>(c->n_half, c->half_j, c->full_start, c->half_cnt,
                                                                   c->full_cnt, c->tr_tmp);
-  k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref);
+  k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref,
+                                      c->pos_tr);
   cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
   if ((r = cuda_check(c, cudaStreamSynchronize(st), "list fill"))) return r;
   if (c->hibuf[2] & 1) return fail(c, AMP_ERR_GEOMETRY, "neighbour list transpose failed");

@@ -19,6 +19,7 @@
 //
 // Each iteration then reduces over the full neighbour rows: a group of
 // kRowGroup lanes per atom sums T_ij v_j, no atomics, fixed order.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -206,8 +207,11 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
                                                        const int* __restrict__ half_j,
                                                        const float4* __restrict__ pd,
                                                        const float4* __restrict__ mp_df, PairGeomDf g,
-                                                       const float2* __restrict__ tab, float4* __restrict__ T,
-                                                       float* __restrict__ Ep) {
+                                                       const float2* __restrict__ tab,
+                                                       const int* __restrict__ full_start,
+                                                       const int* __restrict__ half_start,
+                                                       const int* __restrict__ pos_tr, float4* __restrict__ T8,
+                                                       float4* __restrict__ T4, float* __restrict__ Ep) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
@@ -239,10 +243,21 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
   const dflt tv[6] = {df_sub(df_mul(df_mul(b2u, R[0]), R[0]), b1u), df_sub(df_mul(df_mul(b2u, R[1]), R[1]), b1u),
                       df_sub(df_mul(df_mul(b2u, R[2]), R[2]), b1u), df_mul(df_mul(b2u, R[0]), R[1]),
                       df_mul(df_mul(b2u, R[0]), R[2]),          df_mul(df_mul(b2u, R[1]), R[2])};
-  float4* o = T + 3 * pid;
-  o[0] = make_float4(tv[0].hi, tv[1].hi, tv[2].hi, tv[3].hi);
-  o[1] = make_float4(tv[4].hi, tv[5].hi, tv[0].lo, tv[1].lo);
-  o[2] = make_float4(tv[2].lo, tv[3].lo, tv[4].lo, tv[5].lo);
+  // the tensor goes to both full-list entries of the pair (the owner's entry
+  // and the transposed one), so that the product kernel reads every row's
+  // tensors contiguously: 32 bytes (one load there) + 16 bytes in a second array
+  {
+    const float4 t0 = make_float4(tv[0].hi, tv[1].hi, tv[2].hi, tv[3].hi);
+    const float4 t1 = make_float4(tv[4].hi, tv[5].hi, tv[0].lo, tv[1].lo);
+    const float4 t2 = make_float4(tv[2].lo, tv[3].lo, tv[4].lo, tv[5].lo);
+    const long long k1 = full_start[i] + (pid - half_start[i]), k2 = pos_tr[pid];
+    T8[2 * k1] = t0;
+    T8[2 * k1 + 1] = t1;
+    T4[k1] = t2;
+    T8[2 * k2] = t0;
+    T8[2 * k2 + 1] = t1;
+    T4[k2] = t2;
+  }
   // permanent fields: at i from j (r), at j from i (-r)
   dflt mpi[10], mpj[10];
   {
@@ -383,63 +398,75 @@ __global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __res
   }
 }
 
+__device__ __forceinline__ void t_entry(dflt& sx, dflt& sy, dflt& sz, float4 a, float4 b, float4 c, float4 h,
+                                        float4 w) {
+  // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
+  df_fma(sx, a.x, b.z, h.x, w.x);
+  df_fma(sx, a.w, c.y, h.y, w.y);
+  df_fma(sx, b.x, c.z, h.z, w.z);
+  df_fma(sy, a.w, c.y, h.x, w.x);
+  df_fma(sy, a.y, b.w, h.y, w.y);
+  df_fma(sy, b.y, c.w, h.z, w.z);
+  df_fma(sz, b.x, c.z, h.x, w.x);
+  df_fma(sz, b.y, c.w, h.y, w.y);
+  df_fma(sz, a.z, c.x, h.z, w.z);
+}
+
+constexpr int kTRealBlocksPerSm = 4;  // of the 5 that its registers would allow
+
 // out_i = sum_j T_ij v_j + selfc v_i for the float64 path, in double-float:
-// tensors as hi/lo float pairs (written by the pair build), v as vhi + vlo.
+// tensors as hi/lo float pairs, stored by the pair build once per full-list
+// entry in entry order (32 bytes in T8, 16 in T4), v as (hi, lo) records
+// vhl. The lanes of a row read consecutive entries, so the tensor loads are
+// contiguous; only v_j is a gather. Tensors are read once per product:
+// streaming loads keep them from evicting the reciprocal-space grids that run
+// beside this kernel. The next entry's neighbour index is fetched one
+// iteration ahead.
 __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict__ full_start,
-                                                   const int* __restrict__ full_j, const int* __restrict__ full_ref,
-                                                   const float4* __restrict__ T, double selfc,
-                                                   const float4* __restrict__ vhi, const float4* __restrict__ vlo,
+                                                   const int* __restrict__ full_j, const float4* __restrict__ T8,
+                                                   const float4* __restrict__ T4, double selfc,
+                                                   const float4* __restrict__ vhl,
                                                    const double4_32a* __restrict__ v64, double4_32a* __restrict__ out,
                                                    const int* __restrict__ stop) {
   if (stop && *stop) return;  // the solver has stopped: nothing to compute
   const int l = threadIdx.x % kRowGroup;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup; i < n; i += gridDim.x * (blockDim.x / kRowGroup)) {
-  dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
-  const int e = full_start[i + 1];
-  // pair data is read once per product: streaming loads keep it from evicting
-  // the reciprocal-space grids that run beside this kernel. The next entry's
-  // indices are fetched one iteration ahead, so that each iteration waits for
-  // one round of loads (tensor, v_j) instead of two.
-  int k = full_start[i] + l;
-  int jn = 0, refn = 0;
-  if (k < e) {
-    jn = __ldcs(full_j + k);
-    refn = __ldcs(full_ref + k);
-  }
-  for (; k < e; k += kRowGroup) {
-    const int j = jn, ref = refn;
-    if (k + kRowGroup < e) {
-      jn = __ldcs(full_j + k + kRowGroup);
-      refn = __ldcs(full_ref + k + kRowGroup);
+    dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
+    const int e = full_start[i + 1];
+    int k = full_start[i] + l;
+    int jn = k < e ? __ldcs(full_j + k) : 0;
+    for (; k < e; k += kRowGroup) {
+      const int j = jn;
+      if (k + kRowGroup < e) jn = __ldcs(full_j + k + kRowGroup);
+      float4 a, b, h, w;
+      ld8_stream(T8 + 2 * (long long)k, a, b);
+      const float4 c = __ldcs(T4 + k);
+      ld8_ro(vhl + 2 * (long long)j, h, w);
+      // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
+      df_fma(sx, a.x, b.z, h.x, w.x);
+      df_fma(sx, a.w, c.y, h.y, w.y);
+      df_fma(sx, b.x, c.z, h.z, w.z);
+      df_fma(sy, a.w, c.y, h.x, w.x);
+      df_fma(sy, a.y, b.w, h.y, w.y);
+      df_fma(sy, b.y, c.w, h.z, w.z);
+      df_fma(sz, b.x, c.z, h.x, w.x);
+      df_fma(sz, b.y, c.w, h.y, w.y);
+      df_fma(sz, a.z, c.x, h.z, w.z);
     }
-    const float4* t = T + 3 * (long long)(ref >> 1);
-    const float4 a = __ldcs(t), b = __ldcs(t + 1), c = __ldcs(t + 2);
-    // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
-    const float4 h = vhi[j], w = vlo[j];
-    df_fma(sx, a.x, b.z, h.x, w.x);
-    df_fma(sx, a.w, c.y, h.y, w.y);
-    df_fma(sx, b.x, c.z, h.z, w.z);
-    df_fma(sy, a.w, c.y, h.x, w.x);
-    df_fma(sy, a.y, b.w, h.y, w.y);
-    df_fma(sy, b.y, c.w, h.z, w.z);
-    df_fma(sz, b.x, c.z, h.x, w.x);
-    df_fma(sz, b.y, c.w, h.y, w.y);
-    df_fma(sz, a.z, c.x, h.z, w.z);
-  }
-  sx = df_group_sum(sx);
-  sy = df_group_sum(sy);
-  sz = df_group_sum(sz);
-  // lanes 0..2 convert one component each: a float64 instruction holds the
-  // float64 pipe as long for one active lane as for 32
-  if (l < 4) {
-    double* o = reinterpret_cast<double*>(out + i);
-    if (l < 3) {
-      const dflt sc = l == 0 ? sx : (l == 1 ? sy : sz);
-      o[l] = (double)sc.hi + (double)sc.lo + selfc * reinterpret_cast<const double*>(v64 + i)[l];
-    } else {
-      o[3] = 0.0;
+    sx = df_group_sum(sx);
+    sy = df_group_sum(sy);
+    sz = df_group_sum(sz);
+    // lanes 0..2 convert one component each: a float64 instruction holds the
+    // float64 pipe as long for one active lane as for 32
+    if (l < 4) {
+      double* o = reinterpret_cast<double*>(out + i);
+      if (l < 3) {
+        const dflt sc = l == 0 ? sx : (l == 1 ? sy : sz);
+        o[l] = (double)sc.hi + (double)sc.lo + selfc * reinterpret_cast<const double*>(v64 + i)[l];
+      } else {
+        o[3] = 0.0;
+      }
     }
-  }
   }
 }
 
@@ -550,7 +577,9 @@ void launch_pair_build(amp_ctx* c) {
     k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
                                                                     c->mp_df, c->pd);
     k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, gd, c->dfm,
+                                                   c->full_start, c->half_start, c->pos_tr,
                                                    reinterpret_cast<float4*>(c->T64),
+                                                   reinterpret_cast<float4*>(c->T64) + 2 * c->cap_full,
                                                    reinterpret_cast<float*>(c->Ep64));
     return;
   }
@@ -580,13 +609,19 @@ void launch_e0_real(amp_ctx* c, double4_32a* out) {
                                                             c->atomB, out);
 }
 
-// v must be mirrored in (vhi, vlo) = split of v into float pairs.
+// v must be mirrored in its float-pair split (vhi, vlo) = (p32, plo); the
+// kernel reads the same split from vhl, which every split kernel writes beside.
 void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const float4* vlo, double4_32a* out) {
   const PairGeom g = geom(c);
   c->n_launch += 1;
-  k_t_real_df<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
-      c->n, c->full_start, c->full_j, c->full_ref, reinterpret_cast<const float4*>(c->T64), g.selfc, vhi, vlo, v,
-      out, c->op_stop);
+  // At most kTRealBlocksPerSm blocks per SM (the rows are grid-strided): the
+  // register file then keeps room for the reciprocal-space chain's blocks,
+  // which run beside this kernel on the higher-priority stream and would
+  // otherwise wait for whole blocks of this kernel to finish.
+  const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256), (long long)kTRealBlocksPerSm * c->n_sm);
+  k_t_real_df<<<tb, 256, 0, c->stream>>>(
+      c->n, c->full_start, c->full_j, reinterpret_cast<const float4*>(c->T64),
+      reinterpret_cast<const float4*>(c->T64) + 2 * c->cap_full, g.selfc, c->vhl, v, out, c->op_stop);
 }
 
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out) {

@@ -127,16 +127,21 @@ __global__ void k_mu_from_e0(int n, const double4_32a* __restrict__ e0, const do
   }
 }
 
-// v = hi + lo with hi = fl32(v), lo = fl32(v - hi) (lo skipped when null);
-// returns max |hi component| for the block maxima of the split vector.
+// v = hi + lo with hi = fl32(v), lo = fl32(v - hi) (lo skipped when null),
+// with lo also (hi, lo) side by side in hl[2 s], hl[2 s + 1]; returns max |hi
+// component| for the block maxima of the split vector.
 __device__ __forceinline__ float split_store(const double4_32a& v, float4* __restrict__ hi, float4* __restrict__ lo,
-                                             int s) {
+                                             float4* __restrict__ hl, int s) {
   if (!hi) return 0.f;
   const float4 h = make_float4(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z), 0.f);
   hi[s] = h;
-  if (lo)
-    lo[s] = make_float4(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y),
-                        __double2float_rn(v.z - (double)h.z), 0.f);
+  if (lo) {
+    const float4 l = make_float4(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y),
+                                 __double2float_rn(v.z - (double)h.z), 0.f);
+    lo[s] = l;
+    hl[2 * (long long)s] = h;
+    hl[2 * (long long)s + 1] = l;
+  }
   return fmaxf(fabsf(h.x), fmaxf(fabsf(h.y), fabsf(h.z)));
 }
 
@@ -247,8 +252,9 @@ __global__ void __launch_bounds__(NT) k_cg_init(int n, const double4_32a* __rest
                                                 const double4_32a* __restrict__ t2, const double2* __restrict__ al,
                                                 double4_32a* __restrict__ r, double4_32a* __restrict__ z,
                                                 float4* __restrict__ z32, float4* __restrict__ zlo,
-                                                double* __restrict__ part, float* __restrict__ vmax,
-                                                double* __restrict__ scal, int* __restrict__ fl, double tol) {
+                                                float4* __restrict__ zhl, double* __restrict__ part,
+                                                float* __restrict__ vmax, double* __restrict__ scal,
+                                                int* __restrict__ fl, double tol) {
   double zz = 0.0;
   float vm = 0.f;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(int n, const double4_32a* __rest
     const double4_32a zv = make_double4_32a(a.x * rr.x, a.x * rr.y, a.x * rr.z, 0.0);
     r[s] = rr;
     z[s] = zv;
-    vm = fmaxf(vm, split_store(zv, z32, zlo, s));
+    vm = fmaxf(vm, split_store(zv, z32, zlo, zhl, s));
     zz += dot3(zv, zv);
   }
   double rms = 0.0;
@@ -298,7 +304,8 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
                                                 double4_32a* __restrict__ z, double4_32a* __restrict__ p,
                                                 double4_32a* __restrict__ q, const double4_32a* __restrict__ w,
                                                 const double2* __restrict__ al, float4* __restrict__ z32,
-                                                float4* __restrict__ zlo, double* __restrict__ part,
+                                                float4* __restrict__ zlo, float4* __restrict__ zhl,
+                                                double* __restrict__ part,
                                                 float* __restrict__ vmax, double* __restrict__ scal,
                                                 int* __restrict__ fl, double tol, int max_iter) {
   if (fl[F_STOP]) return;
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
       mu[s] = x;
       r[s] = rr;
       z[s] = zn;
-      vm = fmaxf(vm, split_store(zn, z32, zlo, s));
+      vm = fmaxf(vm, split_store(zn, z32, zlo, zhl, s));
       zz += dot3(zn, zn);
     }
   }
@@ -384,10 +391,11 @@ __global__ void k_from_sorted(int n, const int* __restrict__ perm, const double4
 }
 
 __global__ void __launch_bounds__(NT) k_split(int n, const double4_32a* __restrict__ v, float4* __restrict__ hi,
-                                             float4* __restrict__ lo, float* __restrict__ vmax) {
+                                             float4* __restrict__ lo, float4* __restrict__ hl,
+                                             float* __restrict__ vmax) {
   float vm = 0.f;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-    vm = fmaxf(vm, split_store(v[s], hi, lo, s));
+    vm = fmaxf(vm, split_store(v[s], hi, lo, hl, s));
   write_max_partial(vmax, vm);
 }
 
@@ -420,12 +428,12 @@ void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst) {
 
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o) {
   c->n_launch += 1;
-  k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, o, nullptr, c->vmax_part);
+  k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, o, nullptr, nullptr, c->vmax_part);
 }
 
 void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo) {
   c->n_launch += 1;
-  k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, hi, lo, c->vmax_part);
+  k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, hi, lo, lo ? c->vhl : nullptr, c->vmax_part);
 }
 
 // T v = t (+ t2). With t2 == nullptr the whole product lands in t. With t2
@@ -515,7 +523,7 @@ static int enqueue_iteration(amp_ctx* c) {
   launch_pdl(k_cg_dots, dim3(nb), dim3(NT), 0, st, n, c->res, c->zv, c->tv, c->trec, c->alph, c->wv, c->partials,
              c->iflags);
   launch_pdl(k_cg_step, dim3(nb), dim3(NT), 0, st, n, c->mu, c->res, c->zv, c->pv, c->qv, c->wv, c->alph, c->p32,
-             lo, c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye, c->cfg.max_iter);
+             lo, lo ? c->vhl : nullptr, c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye, c->cfg.max_iter);
   return AMP_OK;
 }
 
@@ -536,7 +544,7 @@ static int restart(amp_ctx* c, bool fp64_operator) {
   PhaseScope ps(c, AMP_PHASE_PCG);
   c->n_launch += 1;
   k_cg_init<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->trec, c->alph, c->res, c->zv, c->p32, lo,
-                                      c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye);
+                                      lo ? c->vhl : nullptr, c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye);
   return AMP_OK;
 }
 
