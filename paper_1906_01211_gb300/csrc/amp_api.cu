@@ -153,7 +153,8 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     c->n_sm = 1;
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_spread, cudaEventDisableTiming) != cudaSuccess) {
     amp_destroy(c);
     return AMP_ERR_CUDA;
   }
@@ -192,6 +193,7 @@ void amp_destroy(amp_ctx* c) {
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_spread) cudaEventDestroy(c->ev_spread);
   if (c->plan_d2z) cufftDestroy(c->plan_d2z);
   if (c->plan_z2d) cufftDestroy(c->plan_z2d);
   if (c->plan_r2c) cufftDestroy(c->plan_r2c);

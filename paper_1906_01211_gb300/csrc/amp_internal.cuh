@@ -124,6 +124,10 @@ struct amp_ctx {
   cudaStream_t side = nullptr;  // second stream: PME beside the real-space kernel
   int n_sm = 1;                 // streaming multiprocessors of the device
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // recorded after the dipole spreading when spread_event is set: the
+  // real-space kernel waits for it, so it runs beside the FFTs only
+  cudaEvent_t ev_spread = nullptr;
+  bool spread_event = false;
   float4* p32 = nullptr;  // float part of p (mixed: p in float32; float64: hi of hi + lo)
   float4* plo = nullptr;  // float64 path: p - hi, so that hi + lo carries p to ~48 bits
   float4* vhl = nullptr;  // float64 path: (p32[s], plo[s]) side by side, one 32-byte record per atom

@@ -618,7 +618,8 @@ void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const fl
   // register file then keeps room for the reciprocal-space chain's blocks,
   // which run beside this kernel on the higher-priority stream and would
   // otherwise wait for whole blocks of this kernel to finish.
-  const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256), (long long)kTRealBlocksPerSm * c->n_sm);
+  const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256),
+                                          (long long)kTRealBlocksPerSm * c->n_sm);
   k_t_real_df<<<tb, 256, 0, c->stream>>>(
       c->n, c->full_start, c->full_j, reinterpret_cast<const float4*>(c->T64),
       reinterpret_cast<const float4*>(c->T64) + 2 * c->cap_full, g.selfc, c->vhl, v, out, c->op_stop);

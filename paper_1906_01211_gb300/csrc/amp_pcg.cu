@@ -439,8 +439,11 @@ void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo) {
 // T v = t (+ t2). With t2 == nullptr the whole product lands in t. With t2
 // given (periodic systems) the reciprocal part runs on the side stream into t2
 // while the real-space kernel runs on the main stream into t: the two parts
-// are independent, and the FFTs leave float64 units idle that the real-space
-// kernel uses. The main stream waits for the side stream before returning.
+// are independent. In the float64 path the real-space kernel starts once the
+// dipoles are spread: the spreading keeps every SM busy by itself, while the
+// three FFT passes that follow are latency bound and leave most of the GPU to
+// the real-space kernel. The main stream waits for the side stream before
+// returning.
 static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const float4* v32, const float4* vlo,
                        double4_32a* t, double4_32a* t2, bool fp64_real_cached, bool fp64_real_direct) {
   int r;
@@ -449,8 +452,11 @@ static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const fl
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     {
       PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
+      c->spread_event = fp64_pme && fp64_real_cached;
       r = fp64_pme ? pme_dipole_field(c, v, v32, vlo, t2, c->side, true)
                    : pme_dipole_field32(c, v32, t2, c->side, true);
+      if (c->spread_event) cudaStreamWaitEvent(c->stream, c->ev_spread, 0);
+      c->spread_event = false;
     }
     cudaEventRecord(c->ev_join, c->side);
     if (r) {

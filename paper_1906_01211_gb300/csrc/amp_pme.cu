@@ -712,6 +712,7 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
     launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
                dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
                (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
+    if (c->spread_event) cudaEventRecord(c->ev_spread, st);
     bool split = true;
     const int r = conv_to_phi(c, st, &split, true);
     if (r) return r;
