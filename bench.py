@@ -177,7 +177,7 @@ PAIR_BUILD_FLOPS = 130
 DF_FP32_PER_FP64 = 13
 # DRAM traffic (read + write) per launch of k_t_real_df, from one ncu capture of
 # the current kernel on this workload (profiles/k_t_real_df_water23556.md).
-T_REAL_TRAFFIC = {}
+T_REAL_TRAFFIC = {"water-23556": 182.5e6}
 
 
 def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
