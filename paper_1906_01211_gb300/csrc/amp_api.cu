@@ -82,7 +82,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
                    (void**)&c->trec, (void**)&c->plo, (void**)&c->vhl, (void**)&c->mp_df, (void**)&c->wv,
-                   (void**)&c->theta_df, (void**)&c->pd};
+                   (void**)&c->theta_df, (void**)&c->theta_df2, (void**)&c->pd};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;

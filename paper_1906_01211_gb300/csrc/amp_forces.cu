@@ -351,6 +351,7 @@ int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, 
 int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt) {
   const bool fp32 = c->cfg.precision == AMP_MIXED;
   int r;
+  pme_theta64(c);  // the float64 B-spline weights (float64 path: built on first use)
   // per-pair and per-atom buffers, sized with the lists
   if (c->force_pair_cap < c->cap_half) {
     dev_free(c, c->force_pair);

@@ -90,12 +90,15 @@ struct amp_ctx {
   double* theta = nullptr;  // [n][3 axes][4 derivatives][5 points]
   float* theta32 = nullptr;
   float2* theta_df = nullptr;  // float64 path: weights and first derivatives as hi/lo [n][3][2][5]
+  float2* theta_df2 = nullptr;  // float64 path: second derivatives as hi/lo [n][3][5]
+  bool theta64_valid = false;   // theta (float64) matches the current system (float64 path: built on demand)
   float2* phi_df = nullptr;    // float64 path: grid potential as hi/lo pairs for the gather
   // float64 path's dipole spreading: 64-bit fixed-point grid (integer
   // atomics, exact and order-independent), scaled by 2^fx_info[0]; fx_info[1]
   // bounds the atoms that reach one grid point; kcount = atoms per base cell.
   unsigned long long* gridfx = nullptr;
-  int* fx_info = nullptr;
+  int* fx_info = nullptr;  // [0] scale exponent of the last spread, [1] atoms per base cell (max),
+                           // [2] float bits of the largest per-atom multipole bound
   int* kcount = nullptr;
   // max |hi component| of the last split vector: [0, kReduceBlocks) per block,
   // [kReduceBlocks] the whole vector, [kReduceBlocks + 1] arrival counter
@@ -220,6 +223,7 @@ int fft_df_setup(amp_ctx* c, const double* G_half);
 // grid64 (fixed = false) or gridfx (fixed = true, zeroed on the way) -> phi_df
 void fft_df_convolve(amp_ctx* c, cudaStream_t st, bool fixed);
 void launch_pme_theta(amp_ctx* c);
+void pme_theta64(amp_ctx* c);  // float64 B-spline weights for the force kernels (float64 path: on demand)
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
 // reciprocal field of dipoles on stream st: out += field (set: out = field)
 int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* out,

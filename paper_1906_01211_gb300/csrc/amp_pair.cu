@@ -568,14 +568,17 @@ int dfm_setup(amp_ctx* c) {
 }
 
 void launch_pair_build(amp_ctx* c) {
+  // the split multipoles also feed the float64 path's reciprocal spreading,
+  // so they are made even when there are no pairs
+  c->n_launch += 1;
+  k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                                  c->mp_df, c->pd);
   if (c->n_half == 0) return;
   const PairGeom g = geom(c);
   const int blocks = amp_blocks(c->n_half, 256);
+  c->n_launch += 1;
   if (c->cfg.precision == AMP_FP64) {
-    c->n_launch += 2;
     const PairGeomDf gd = geom_df(g);
-    k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
-                                                                    c->mp_df, c->pd);
     k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, gd, c->dfm,
                                                    c->full_start, c->half_start, c->pos_tr,
                                                    reinterpret_cast<float4*>(c->T64),
@@ -584,9 +587,6 @@ void launch_pair_build(amp_ctx* c) {
     return;
   }
   // mixed path: float32 pair terms from the split records, which also serve its float64 check
-  c->n_launch += 2;
-  k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
-                                                                  c->mp_df, c->pd);
   PairGeom32 g32;
   g32.beta = (float)g.beta;
   g32.twob2 = (float)g.twob2;

@@ -98,6 +98,111 @@ __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int 
   }
 }
 
+// The weights of bspline5 (derivatives 0..2) in double-float, from f as hi/lo
+// floats and s = K/L: the same recursion (Essmann et al. 1995, Eq. 4.1-4.4),
+// about 48 significant bits, on the float units.
+__device__ __forceinline__ dflt df_scale(dflt a, float c) { return {a.hi * c, a.lo * c}; }  // c a power of two
+
+__device__ __forceinline__ void bspline5_df(dflt f, dflt s, dflt w[3][kOrder]) {
+  const dflt one = {1.f, 0.f}, third = {0.333333343f, -9.93410776e-09f};  // 1/3 = hi + lo
+  dflt m2[2] = {f, df_sub(one, f)};
+  dflt m3[3], m4[4], m5[5];
+  for (int t = 0; t < 3; ++t) {  // M3(f + t) = ((f + t) M2(f + t) + (3 - f - t) M2(f + t - 1)) / 2
+    const dflt ft = df_add(f, {(float)t, 0.f}), gt = df_sub({3.f - (float)t, 0.f}, f);
+    dflt v = {0.f, 0.f};
+    if (t < 2) v = df_mul(ft, m2[t]);
+    if (t >= 1) v = df_madd(gt, m2[t - 1], v);
+    m3[t] = df_scale(v, 0.5f);
+  }
+  for (int t = 0; t < 4; ++t) {
+    const dflt ft = df_add(f, {(float)t, 0.f}), gt = df_sub({4.f - (float)t, 0.f}, f);
+    dflt v = {0.f, 0.f};
+    if (t < 3) v = df_mul(ft, m3[t]);
+    if (t >= 1) v = df_madd(gt, m3[t - 1], v);
+    m4[t] = df_mul(v, third);
+  }
+  for (int t = 0; t < 5; ++t) {
+    const dflt ft = df_add(f, {(float)t, 0.f}), gt = df_sub({5.f - (float)t, 0.f}, f);
+    dflt v = {0.f, 0.f};
+    if (t < 4) v = df_mul(ft, m4[t]);
+    if (t >= 1) v = df_madd(gt, m4[t - 1], v);
+    m5[t] = df_scale(v, 0.25f);
+  }
+  const dflt s2 = df_mul(s, s);
+  for (int t = 0; t < 5; ++t) {
+    const dflt a4 = t < 4 ? m4[t] : dflt{0.f, 0.f}, b4 = t >= 1 ? m4[t - 1] : dflt{0.f, 0.f};
+    const dflt a3 = t < 3 ? m3[t] : dflt{0.f, 0.f}, b3 = (t >= 1 && t - 1 < 3) ? m3[t - 1] : dflt{0.f, 0.f},
+               c3 = (t >= 2 && t - 2 < 3) ? m3[t - 2] : dflt{0.f, 0.f};
+    w[0][t] = m5[t];
+    w[1][t] = df_mul(df_sub(a4, b4), s);
+    w[2][t] = df_mul(df_add(df_sub(a3, df_scale(b3, 2.f)), c3), s2);
+  }
+}
+
+// Float64 path, one group of four lanes per atom: lane ax < 3 builds axis
+// ax's weights in double-float (theta_df: derivatives 0 and 1, theta_df2:
+// derivative 2) and its base index; lane 3 bounds the atom's multipole
+// contribution to one grid point for the fixed-point spreading,
+//   |q| + s (|dx| + |dy| + |dz|) + s^2 (|Qxx| + |Qyy| + |Qzz| + |Qxy| + |Qxz| + |Qyz|),
+// which covers |w| <= 1, |w'| <= s and |w''| <= 1.5 s^2 with the 1/3 and
+// 2/3 factors of the quadrupole terms. Lane 0 stores the base indices and
+// counts the atom in kcount; fx_info[1] = the largest count, fx_info[2] =
+// the largest bound (float bits, non-negative).
+__global__ void __launch_bounds__(128) k_theta_df(int n, const double4_32a* __restrict__ A,
+                                                   const double4_32a* __restrict__ B,
+                                                   const double4_32a* __restrict__ C,
+                                                   const double4_32a* __restrict__ D, double L, int K, float2 s_df,
+                                                   float2* __restrict__ theta_df, float2* __restrict__ theta_df2,
+                                                   int4* __restrict__ gbase, int* __restrict__ kcount,
+                                                   int* __restrict__ fx_info) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gid >> 2, lane4 = gid & 3;
+  const bool valid = s < n;
+  int base = 0;
+  float bound = 0.f;
+  if (valid && lane4 < 3) {
+    const double4_32a a = A[s];
+    const double x = lane4 == 0 ? a.x : (lane4 == 1 ? a.y : a.z);
+    const double sc = (double)K / L;
+    double u = x * sc;
+    u = u - (double)K * floor(u / (double)K);
+    if (u >= (double)K) u -= (double)K;
+    if (u < 0.0) u += (double)K;
+    const double k0 = floor(u);
+    base = (int)k0;
+    dflt w[3][kOrder];
+    bspline5_df(df_split(u - k0), {s_df.x, s_df.y}, w);
+    float2* o = theta_df + (long long)kThDf * s + lane4 * 2 * kOrder;
+    float2* o2 = theta_df2 + 3LL * kOrder * s + lane4 * kOrder;
+    for (int t = 0; t < kOrder; ++t) {
+      o[t] = make_float2(w[0][t].hi, w[0][t].lo);
+      o[kOrder + t] = make_float2(w[1][t].hi, w[1][t].lo);
+      o2[t] = make_float2(w[2][t].hi, w[2][t].lo);
+    }
+  } else if (valid) {
+    const double4_32a a = A[s], b = B[s], c = C[s], d = D[s];
+    const float sc = (float)((double)K / L);
+    const float dip = fabsf((float)b.x) + fabsf((float)b.y) + fabsf((float)b.z);
+    const float quad = fabsf((float)c.x) + fabsf((float)c.y) + fabsf((float)c.z) + fabsf((float)c.w) +
+                       fabsf((float)d.x) + fabsf((float)d.y);
+    bound = 1.01f * (fabsf((float)a.w) + sc * dip + sc * sc * quad);
+  }
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int by = __shfl_sync(full, base, lane + 1), bz = __shfl_sync(full, base, lane + 2);
+  const int b4 = __shfl_sync(full, __float_as_int(bound), lane + 3);
+  int cnt = 0;
+  if (valid && lane4 == 0) {
+    gbase[s] = make_int4(base, by, bz, 0);
+    cnt = atomicAdd(kcount + ((long long)base * K + by) * K + bz, 1) + 1;
+  }
+  const int mc = __reduce_max_sync(full, cnt), mb = __reduce_max_sync(full, lane4 == 0 ? b4 : 0);
+  if (lane == 0) {
+    atomicMax(fx_info + 1, mc);
+    atomicMax(fx_info + 2, mb);
+  }
+}
+
 template <typename R>
 struct Wts {
   R x[3][kOrder], y[3][kOrder], z[3][kOrder];
@@ -208,29 +313,30 @@ __global__ void __launch_bounds__(128) k_spread_dipoles(int n, const R* __restri
 // is at most 1 and a derivative weight at most sc = K/L in magnitude, so
 // |grid value| <= 3 sc m cmax, with m = max |dipole component| and cmax the
 // number of atoms that reach one point; s keeps that below 2^61.
-__device__ __forceinline__ int fixed_scale(float m, float sc, int cmax) {
-  const float bound = 3.f * sc * m * (float)cmax;
-  if (!(bound > 0.f) || !(bound < 1e30f)) return 0;  // zero (or non-finite) vector
+__device__ __forceinline__ int fixed_scale_bound(float bound) {  // |grid value| <= bound
+  if (!(bound > 0.f) || !(bound < 1e30f)) return 0;  // zero (or non-finite) input
   int e;
   frexpf(bound, &e);  // bound < 2^e
   return max(-60, min(120, 61 - e));
 }
 
-// round(f * 2^s) as a 64-bit integer, by integer operations on the bits of f.
+__device__ __forceinline__ int fixed_scale(float m, float sc, int cmax) {
+  return fixed_scale_bound(3.f * sc * m * (float)cmax);
+}
+
+// round(f * 2^s) (ties toward +infinity) as a 64-bit integer, by integer
+// operations on the bits of f: the signed significand m (24 bits) times 2^sh,
+// shifted left when sh >= 0 and otherwise rounded off in 32-bit arithmetic.
 // Finite f only; zero and subnormals (below the grid's resolution) give 0.
 __device__ __forceinline__ long long to_fixed(float f, int s) {
   const unsigned u = __float_as_uint(f);
   const int e = (int)((u >> 23) & 0xffu);
-  const long long m = e ? (long long)((u & 0x7fffffu) | 0x800000u) : 0ll;
+  const int m0 = e ? (int)((u & 0x7fffffu) | 0x800000u) : 0;
+  const int m = (u >> 31) ? -m0 : m0;
   const int sh = e - 150 + s;
-  long long r;
-  if (sh >= 0)
-    r = m << min(sh, 39);
-  else if (sh > -25)
-    r = (m + (1ll << (-sh - 1))) >> -sh;
-  else
-    r = 0;
-  return (u >> 31) ? -r : r;
+  if (sh >= 0) return (long long)m << min(sh, 39);
+  const int k = min(-sh, 30);  // |m| < 2^24: from 2^-30 on the value rounds to 0
+  return (long long)((m + (1 << (k - 1))) >> k);
 }
 
 // Q(g) = sum_i mu_i . grad W_i(g) with mu = v32 + vlo. One thread per
@@ -274,6 +380,55 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, con
     const dflt val = df_madd(Q, {x1.x, x1.y}, df_mul(P, {x0.x, x0.y}));
     const long long q = to_fixed(val.hi, sfx) + to_fixed(val.lo, sfx);
     atomicAdd(col + wrapk(b.x - tx, K) * plane, (unsigned long long)q);
+  }
+}
+
+// Permanent multipoles into the fixed-point grid (float64 path): the charge,
+// dipole and quadrupole terms of Q(g) (Sagui, Pedersen and Darden 2004,
+// Eq. 11, quadrupoles with the 1/3 of the traceless form) in double-float
+// from the split multipoles (mp: q dx | dy dz | Qxx Qyy | Qzz Qxy | Qxz Qyz
+// as hi/lo pairs). One thread per (atom, y row, z point) adds the point
+// values of the five x planes, P0 w_x + P1 w'_x + P2 w''_x with
+//   P0 = q w_y w_z + dy w'_y w_z + dz w_y w'_z + (Qyy w''_y w_z + Qzz w_y w''_z + 2 Qyz w'_y w'_z) / 3,
+//   P1 = dx w_y w_z + 2 (Qxy w'_y w_z + Qxz w_y w'_z) / 3,   P2 = Qxx w_y w_z / 3.
+// The scale comes from the per-atom bound of k_theta_df (fx_info[2]) times the
+// atoms that reach one point; block 0 stores it in fx_info[0].
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_multipoles_fx(
+    int n, const float2* __restrict__ th_df, const float2* __restrict__ th_df2, const int4* __restrict__ gbase,
+    const float4* __restrict__ mp, int* __restrict__ fx_info, int K, unsigned long long* __restrict__ grid) {
+  const int sfx = fixed_scale_bound(__int_as_float(fx_info[2]) * (float)(kOrder * kOrder * kOrder * fx_info[1]));
+  if (blockIdx.x == 0 && threadIdx.x == 0) fx_info[0] = sfx;
+  const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
+  if (item >= (long long)n * (kOrder * kOrder)) return;
+  const int s = (int)(item / (kOrder * kOrder)), tyz = (int)(item - (long long)s * (kOrder * kOrder));
+  const int ty = tyz / kOrder, tz = tyz - ty * kOrder;
+  const float2* th = th_df + (long long)kThDf * s;
+  const float2* th2 = th_df2 + 3LL * kOrder * s;
+  const float4* m = mp + 5LL * s;
+  const float4 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3], m4 = m[4];
+  const dflt q = {m0.x, m0.y}, dx = {m0.z, m0.w}, dy = {m1.x, m1.y}, dz = {m1.z, m1.w};
+  const dflt qxx = {m2.x, m2.y}, qyy = {m2.z, m2.w}, qzz = {m3.x, m3.y}, qxy = {m3.z, m3.w};
+  const dflt qxz = {m4.x, m4.y}, qyz = {m4.z, m4.w};
+  const float2 y0f = th[(1 * 2 + 0) * kOrder + ty], y1f = th[(1 * 2 + 1) * kOrder + ty], y2f = th2[1 * kOrder + ty];
+  const float2 z0f = th[(2 * 2 + 0) * kOrder + tz], z1f = th[(2 * 2 + 1) * kOrder + tz], z2f = th2[2 * kOrder + tz];
+  const dflt y0 = {y0f.x, y0f.y}, y1 = {y1f.x, y1f.y}, y2 = {y2f.x, y2f.y};
+  const dflt z0 = {z0f.x, z0f.y}, z1 = {z1f.x, z1f.y}, z2 = {z2f.x, z2f.y};
+  const dflt third = {0.333333343f, -9.93410776e-09f}, two3 = {0.666666687f, -1.98682155e-08f};
+  const dflt y0z0 = df_mul(y0, z0), y1z0 = df_mul(y1, z0), y0z1 = df_mul(y0, z1);
+  const dflt quad0 = df_madd(df_add(qyz, qyz), df_mul(y1, z1),
+                             df_madd(qzz, df_mul(y0, z2), df_mul(qyy, df_mul(y2, z0))));
+  const dflt P0 = df_madd(third, quad0, df_madd(dz, y0z1, df_madd(dy, y1z0, df_mul(q, y0z0))));
+  const dflt P1 = df_madd(two3, df_madd(qxz, y0z1, df_mul(qxy, y1z0)), df_mul(dx, y0z0));
+  const dflt P2 = df_mul(df_mul(third, qxx), y0z0);
+  const int4 b = gbase[s];
+  unsigned long long* col = grid + (long long)wrapk(b.y - ty, K) * K + wrapk(b.z - tz, K);
+  const long long plane = (long long)K * K;
+#pragma unroll
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const float2 x0 = th[(0 * 2 + 0) * kOrder + tx], x1 = th[(0 * 2 + 1) * kOrder + tx], x2 = th2[tx];
+    const dflt val = df_madd(P2, {x2.x, x2.y}, df_madd(P1, {x1.x, x1.y}, df_mul(P0, {x0.x, x0.y})));
+    const long long qv = to_fixed(val.hi, sfx) + to_fixed(val.lo, sfx);
+    atomicAdd(col + wrapk(b.x - tx, K) * plane, (unsigned long long)qv);
   }
 }
 
@@ -585,7 +740,7 @@ int pme_setup(amp_ctx* c) {
     return r;
   if (c->cfg.precision == AMP_FP64) {
     if ((r = dev_alloc(c, &c->phi_df, ng)) || (r = dev_alloc(c, &c->gridfx, ng)) ||
-        (r = dev_alloc(c, &c->kcount, ng)) || (r = dev_alloc(c, &c->fx_info, 2)))
+        (r = dev_alloc(c, &c->kcount, ng)) || (r = dev_alloc(c, &c->fx_info, 4)))
       return r;
     // the fixed-point grid starts at zero; the kernel that reads it zeroes it again
     if ((r = cuda_check(c, cudaMemsetAsync(c->gridfx, 0, sizeof(unsigned long long) * ng, c->stream),
@@ -618,18 +773,39 @@ int pme_alloc_atoms(amp_ctx* c, int n_cap) {
   int r;
   if ((r = dev_alloc(c, &c->theta, (long long)kTh * n_cap)) || (r = dev_alloc(c, &c->gbase, n_cap))) return r;
   if (c->cfg.precision == AMP_MIXED && (r = dev_alloc(c, &c->theta32, (long long)kTh * n_cap))) return r;
-  if (c->cfg.precision == AMP_FP64 && (r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap))) return r;
+  if (c->cfg.precision == AMP_FP64 && ((r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap)) ||
+                                        (r = dev_alloc(c, &c->theta_df2, 3LL * kOrder * n_cap))))
+    return r;
   return AMP_OK;
 }
 
+// B-spline weights of the current system. Float64 path: double-float weights
+// (k_theta_df); the float64 copy, which only the force kernels read, is built
+// on demand by pme_theta64. Mixed path: float64 and float32 weights.
 void launch_pme_theta(amp_ctx* c) {
   c->n_launch += 1;
-  if (c->kcount) {
+  if (c->theta_df) {
     cudaMemsetAsync(c->kcount, 0, sizeof(int) * (long long)c->K * c->K * c->K, c->stream);
-    cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 2, c->stream);
+    cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 4, c->stream);
+    const double sc = (double)c->K / c->cfg.box;
+    const float sh = (float)sc;
+    k_theta_df<<<amp_blocks(4LL * c->n, 128), 128, 0, c->stream>>>(
+        c->n, c->atomA, c->atomB, c->atomC, c->atomD, c->cfg.box, c->K, make_float2(sh, (float)(sc - (double)sh)),
+        c->theta_df, c->theta_df2, c->gbase, c->kcount, c->fx_info);
+    c->theta64_valid = false;
+    return;
   }
   k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
-                                                       c->theta_df, c->gbase, c->kcount, c->fx_info);
+                                                       nullptr, c->gbase, nullptr, nullptr);
+  c->theta64_valid = true;
+}
+
+void pme_theta64(amp_ctx* c) {
+  if (c->theta64_valid) return;
+  c->n_launch += 1;
+  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, nullptr,
+                                                       nullptr, c->gbase, nullptr, nullptr);
+  c->theta64_valid = true;
 }
 
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
@@ -638,12 +814,11 @@ int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
   cudaStream_t st = c->stream;
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
   int r;
-  if (c->cfg.precision == AMP_FP64) {
-    cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
-    k_spread_multipoles<double><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB,
-                                                                    c->atomC, c->atomD, K, c->grid64);
+  if (c->cfg.precision == AMP_FP64) {  // double-float, fixed-point grid (zero on entry), as for the dipoles
+    k_spread_multipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
+        n, c->theta_df, c->theta_df2, c->gbase, c->mp_df, c->fx_info, K, c->gridfx);
     bool split = true;
-    if ((r = conv_to_phi(c, st, &split, false))) return r;
+    if ((r = conv_to_phi(c, st, &split, true))) return r;
     gather_df<false>(c, st, out_add, split);
   } else {
     cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
