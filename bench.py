@@ -337,7 +337,6 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    p.profile(True)
     launches0 = p.launch_count()
     step_ms, applications = [], []
     for _ in range(args.steps):
@@ -351,8 +350,6 @@ def main():
         applications.append(1 + it)
     torch.cuda.synchronize()
     launches = p.launch_count() - launches0
-    phases = p.profile_read()
-    p.profile(False)
     clk = clocks.stop() if clocks else None
     t_total = sum(step_ms)
     if world > 1:
@@ -387,10 +384,23 @@ def main():
             torch.distributed.barrier()
         return
 
+    # ---- phase timers (library events around each phase) on separate steps:
+    # the event records cost ~0.1 ms per step, so the timed steps above run
+    # without them
+    prof_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    p.profile(True)
+    for _ in range(prof_steps):
+        flush.zero_()
+        step(dev_in)
+    torch.cuda.synchronize()
+    phases = p.profile_read()
+    p.profile(False)
+
     # ---- rooflines of our two largest kernels; the dominant one is "roofline"
     rooflines = kernel_rooflines(phases, n_pairs, n, w.name)
     roofline = max(rooflines, key=lambda r: r["ms_per_step"])
-    phase_ms = {k: round(v[0] / args.steps, 4) for k, v in phases.items()}
+    phase_ms = {k: round(v[0] / prof_steps, 4) for k, v in phases.items()}
 
     # ---- mixed precision on the same workload, against the float64 result
     mixed = None
@@ -399,9 +409,6 @@ def main():
         pm = solver("mixed")
         ms_m = []
         for k in range(args.warmup + 3):
-            if k == args.warmup:
-                torch.cuda.synchronize()
-                pm.profile(True)
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -414,11 +421,19 @@ def main():
             if k >= args.warmup:
                 ms_m.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
+        pm.profile(True)
+        for _ in range(3):
+            flush.zero_()
+            pm.set_system(*dev_in)
+            E0p = pm.permanent_field()
+            mup, _, _ = pm.solve(E0p)
+            pm.energy(mup, E0p)
+        torch.cuda.synchronize()
         phases_m = pm.profile_read()
         pm.profile(False)
         d = (mum - mu64).double()
         mixed = {"solve_ms": statistics.mean(ms_m), "iters": itm, "fp64_checks": pm.last_solve_stats()[1],
-                 "phase_ms_per_step": {k: round(v[0] / len(ms_m), 4) for k, v in phases_m.items()},
+                 "phase_ms_per_step": {k: round(v[0] / 3, 4) for k, v in phases_m.items()},
                  "rms_vs_fp64_gpu_debye": float(4.8032047 * torch.sqrt((d * d).sum() / n)),
                  "energy_rel_vs_fp64_gpu": abs(Um / U - 1.0)}
         pm.close()

@@ -168,6 +168,7 @@ struct amp_ctx {
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
   amp::Stats stats;
+  int last_iters = 0;  // iterations of the last solve (first chunk of the next one)
   bool have_system = false;
 };
 

@@ -24,11 +24,14 @@
 // those of the operator included, returns at once when the device "stop"
 // flag is set, so the host can enqueue several iterations between flag reads
 // without paying for the ones after convergence.
+#include <algorithm>
+
 #include "amp_internal.cuh"
 
 namespace amp {
 namespace {
 
+constexpr int kPcgChunk = 4;  // iterations enqueued per flag read after the first chunk
 constexpr int NT = kReduceThreads;
 constexpr int NB = kReduceBlocks;
 
@@ -562,15 +565,23 @@ int solve(amp_ctx* c, bool use_guess) {
   if (!use_guess) k_mu_from_e0<<<vec_blocks(c->n), NT, 0, st>>>(c->n, c->E0s, c->alph, c->mu);
   if ((r = cuda_check(c, cudaMemsetAsync(c->iflags, 0, sizeof(int) * 5, st), "memset"))) return r;
   if ((r = restart(c, !mixed))) return r;
-  const int chunk = 4;
+  // Iterations are enqueued in chunks between reads of the device flags; a
+  // read is a host round trip (~30 us on GB300, with the GPU idle). The first
+  // chunk is the iteration count that the previous solve on this context
+  // needed, so that a run of similar solves reads the flags once; later
+  // chunks are kPcgChunk. Iterations enqueued after convergence cost only
+  // their launches (every kernel returns at once on the stop flag).
+  int chunk = c->last_iters > 0 ? c->last_iters : kPcgChunk;
   c->stats.fp64_checks = 0;
   for (int round = 0; round < 8; ++round) {
     while (true) {
       for (int k = 0; k < chunk; ++k)
         if ((r = enqueue_iteration(c))) return r;
       if ((r = read_flags(c))) return r;
+      chunk = kPcgChunk;
       if (c->hibuf[F_STOP]) break;
     }
+    if (round == 0) c->last_iters = std::max(1, std::min(c->hibuf[F_ITERS], c->cfg.max_iter));
     if (!mixed || c->hibuf[F_STATUS] != 1) break;
     // mixed: check the converged dipoles with the float64 operator
     if ((r = restart(c, true))) return r;

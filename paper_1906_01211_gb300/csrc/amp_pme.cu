@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) k_theta_df(int n, const double4_32a* __re
     const double x = lane4 == 0 ? a.x : (lane4 == 1 ? a.y : a.z);
     const double sc = (double)K / L;
     double u = x * sc;
-    u = u - (double)K * floor(u / (double)K);
+    u = u - (double)K * floor(u * (1.0 / (double)K));  // the two tests below fix an off-by-one wrap
     if (u >= (double)K) u -= (double)K;
     if (u < 0.0) u += (double)K;
     const double k0 = floor(u);
@@ -196,10 +196,20 @@ __global__ void __launch_bounds__(128) k_theta_df(int n, const double4_32a* __re
     gbase[s] = make_int4(base, by, bz, 0);
     cnt = atomicAdd(kcount + ((long long)base * K + by) * K + bz, 1) + 1;
   }
+  // block maxima first: two atomics per block, skipped when the stored value
+  // is already as large (it only grows)
+  __shared__ int wmax[2][128 / 32];
   const int mc = __reduce_max_sync(full, cnt), mb = __reduce_max_sync(full, lane4 == 0 ? b4 : 0);
   if (lane == 0) {
-    atomicMax(fx_info + 1, mc);
-    atomicMax(fx_info + 2, mb);
+    wmax[0][threadIdx.x >> 5] = mc;
+    wmax[1][threadIdx.x >> 5] = mb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    int m = 0;
+    for (int w = 0; w < 128 / 32; ++w) m = max(m, wmax[threadIdx.x][w]);
+    int* dst = fx_info + 1 + threadIdx.x;
+    if (m > __ldcg(dst)) atomicMax(dst, m);
   }
 }
 
