@@ -412,7 +412,7 @@ __device__ __forceinline__ void t_entry(dflt& sx, dflt& sy, dflt& sz, float4 a, 
   df_fma(sz, a.z, c.x, h.z, w.z);
 }
 
-constexpr int kTRealBlocksPerSm = 4;  // of the 5 that its registers would allow
+constexpr int kTRealBlocksPerSm = 4;  // of the 5 (float64) or 6 (mixed) that the registers would allow
 
 // out_i = sum_j T_ij v_j + selfc v_i for the float64 path, in double-float:
 // tensors as hi/lo float pairs, stored by the pair build once per full-list
@@ -471,39 +471,45 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
 }
 
 // Mixed precision: float32 tensors and float32 copy of v, products summed in
-// float32 per lane over its share of the row, then the row total in float64.
+// float32 per lane over its share of the row; the row total in double-float
+// across the lanes, then lanes 0..2 finish one component each in float64 (a
+// float64 instruction holds the float64 pipe as long for one active lane as
+// for 32). Rows are grid-strided.
 __global__ void __launch_bounds__(256) k_t_real32(int n, const int* __restrict__ full_start,
                                                   const int* __restrict__ full_j, const int* __restrict__ full_ref,
                                                   const float* __restrict__ T, double selfc,
                                                   const float4* __restrict__ v32, const double4_32a* __restrict__ v64,
                                                   double4_32a* __restrict__ out, const int* __restrict__ stop) {
   if (stop && *stop) return;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gid / kRowGroup, l = gid % kRowGroup;
-  if (i >= n) return;
-  float sx = 0.f, sy = 0.f, sz = 0.f;
-  const int e = full_start[i + 1];
-  for (int k = full_start[i] + l; k < e; k += kRowGroup) {
-    const int j = full_j[k];
-    const float2* t = reinterpret_cast<const float2*>(T + 6 * (long long)(full_ref[k] >> 1));
-    const float2 t0 = t[0], t1 = t[1], t2 = t[2];
-    const float4 vj = v32[j];
-    sx = fmaf(t0.x, vj.x, sx);
-    sx = fmaf(t1.y, vj.y, sx);
-    sx = fmaf(t2.x, vj.z, sx);
-    sy = fmaf(t1.y, vj.x, sy);
-    sy = fmaf(t0.y, vj.y, sy);
-    sy = fmaf(t2.y, vj.z, sy);
-    sz = fmaf(t2.x, vj.x, sz);
-    sz = fmaf(t2.y, vj.y, sz);
-    sz = fmaf(t1.x, vj.z, sz);
-  }
-  double dx = group_sum((double)sx);
-  double dy = group_sum((double)sy);
-  double dz = group_sum((double)sz);
-  if (l == 0) {
-    const double4_32a vi = v64[i];
-    out[i] = make_double4_32a(dx + selfc * vi.x, dy + selfc * vi.y, dz + selfc * vi.z, 0.0);
+  const int l = threadIdx.x % kRowGroup;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup; i < n; i += gridDim.x * (blockDim.x / kRowGroup)) {
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    const int e = full_start[i + 1];
+    for (int k = full_start[i] + l; k < e; k += kRowGroup) {
+      const int j = full_j[k];
+      const float2* t = reinterpret_cast<const float2*>(T + 6 * (long long)(full_ref[k] >> 1));
+      const float2 t0 = t[0], t1 = t[1], t2 = t[2];
+      const float4 vj = v32[j];
+      sx = fmaf(t0.x, vj.x, sx);
+      sx = fmaf(t1.y, vj.y, sx);
+      sx = fmaf(t2.x, vj.z, sx);
+      sy = fmaf(t1.y, vj.x, sy);
+      sy = fmaf(t0.y, vj.y, sy);
+      sy = fmaf(t2.y, vj.z, sy);
+      sz = fmaf(t2.x, vj.x, sz);
+      sz = fmaf(t2.y, vj.y, sz);
+      sz = fmaf(t1.x, vj.z, sz);
+    }
+    const dflt dx = df_group_sum({sx, 0.f}), dy = df_group_sum({sy, 0.f}), dz = df_group_sum({sz, 0.f});
+    if (l < 4) {
+      double* o = reinterpret_cast<double*>(out + i);
+      if (l < 3) {
+        const dflt d = l == 0 ? dx : (l == 1 ? dy : dz);
+        o[l] = df_to_double(d) + selfc * reinterpret_cast<const double*>(v64 + i)[l];
+      } else {
+        o[3] = 0.0;
+      }
+    }
   }
 }
 
@@ -628,8 +634,10 @@ void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const fl
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out) {
   const PairGeom g = geom(c);
   c->n_launch += 1;
-  k_t_real32<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, c->stream>>>(
-      c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64, out, c->op_stop);
+  const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256),
+                                          (long long)kTRealBlocksPerSm * c->n_sm);
+  k_t_real32<<<tb, 256, 0, c->stream>>>(c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64,
+                                        out, c->op_stop);
 }
 
 // v's split goes through p32/plo (free during the check: k_cg_init rewrites them).

@@ -455,7 +455,7 @@ static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const fl
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     {
       PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
-      c->spread_event = fp64_pme && fp64_real_cached;
+      c->spread_event = fp64_pme == fp64_real_cached && !fp64_real_direct;
       r = fp64_pme ? pme_dipole_field(c, v, v32, vlo, t2, c->side, true)
                    : pme_dipole_field32(c, v32, t2, c->side, true);
       if (c->spread_event) cudaStreamWaitEvent(c->stream, c->ev_spread, 0);

@@ -540,7 +540,8 @@ __global__ void k_split_grid(long long ng, const double* __restrict__ phi, float
 // The float64 path's gather in double-float arithmetic (float units only):
 // weights, their derivatives and the grid potential are hi/lo pairs. Six
 // atoms per warp, five lanes each (lanes 30 and 31 idle): lane t of an atom
-// sums x plane k0x - t, the five lanes then add their sums in a fixed order.
+// sums z plane k0z - t, so the five lanes read five consecutive z points of a
+// grid row at a time; they then add their sums in a fixed order.
 constexpr int kGatherAtomsPerWarp = 6;
 constexpr int kGatherThreads = 128;
 
@@ -554,64 +555,62 @@ __device__ __forceinline__ dflt sum_five(dflt v, int base) {  // same order in a
 
 template <bool kSet>
 __global__ void __launch_bounds__(kGatherThreads) k_gather_field_df(int n, const float2* __restrict__ th_df,
-                                                                    const int4* __restrict__ gbase,
-                                                                    const float2* __restrict__ phi, int K,
-                                                                    double4_32a* __restrict__ out,
-                                                                    const int* __restrict__ stop) {
+                                                                     const int4* __restrict__ gbase,
+                                                                     const float2* __restrict__ phi, int K,
+                                                                     double4_32a* __restrict__ out,
+                                                                     const int* __restrict__ stop) {
   if (stop && *stop) return;
   pdl_wait();
   pdl_trigger();
-  const int lane = threadIdx.x & 31, seg = lane / kOrder, tx = lane - seg * kOrder;
+  const int lane = threadIdx.x & 31, seg = lane / kOrder, tz = lane - seg * kOrder;
   const int warp = (blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
   const int s = warp * kGatherAtomsPerWarp + seg;
-  if (warp * kGatherAtomsPerWarp >= n) return;  // whole warp
+  if (warp * kGatherAtomsPerWarp >= n) return;
   const bool active = seg < kGatherAtomsPerWarp && s < n;
   dflt ex = {0.f, 0.f}, ey = {0.f, 0.f}, ez = {0.f, 0.f};
   if (active) {
     const int4 b = gbase[s];
     const float2* th = th_df + (long long)kThDf * s;
-    const float2 wx0 = th[(0 * 2 + 0) * kOrder + tx], wx1 = th[(0 * 2 + 1) * kOrder + tx];
-    float2 wz0[kOrder], wz1[kOrder];
-    int gz[kOrder];
+    const float2 wz0 = th[(2 * 2 + 0) * kOrder + tz], wz1 = th[(2 * 2 + 1) * kOrder + tz];
+    float2 wx0[kOrder], wx1[kOrder];
+    int gx[kOrder];
     for (int t = 0; t < kOrder; ++t) {
-      wz0[t] = th[(2 * 2 + 0) * kOrder + t];
-      wz1[t] = th[(2 * 2 + 1) * kOrder + t];
-      gz[t] = wrapk(b.z - t, K);
+      wx0[t] = th[(0 * 2 + 0) * kOrder + t];
+      wx1[t] = th[(0 * 2 + 1) * kOrder + t];
+      gx[t] = wrapk(b.x - t, K) * K * K;
     }
-    const int gx = wrapk(b.x - tx, K);
-    dflt px = {0.f, 0.f}, py = {0.f, 0.f}, pz = {0.f, 0.f};
+    const float2* pz = phi + wrapk(b.z - tz, K);
+    dflt px = {0.f, 0.f}, py = {0.f, 0.f}, pzz = {0.f, 0.f};
     for (int ty = 0; ty < kOrder; ++ty) {
       const float2 wy0 = th[(1 * 2 + 0) * kOrder + ty], wy1 = th[(1 * 2 + 1) * kOrder + ty];
-      const long long row = ((long long)gx * K + wrapk(b.y - ty, K)) * K;
+      const float2* col = pz + wrapk(b.y - ty, K) * K;
       dflt s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
-      for (int tz = 0; tz < kOrder; ++tz) {
-        const float2 ph = phi[row + gz[tz]];
-        df_fma(s0, wz0[tz].x, wz0[tz].y, ph.x, ph.y);
-        df_fma(s1, wz1[tz].x, wz1[tz].y, ph.x, ph.y);
+      for (int tx = 0; tx < kOrder; ++tx) {
+        const float2 ph = col[gx[tx]];
+        df_fma(s0, wx0[tx].x, wx0[tx].y, ph.x, ph.y);
+        df_fma(s1, wx1[tx].x, wx1[tx].y, ph.x, ph.y);
       }
-      df_fma(px, wy0.x, wy0.y, s0.hi, s0.lo);
+      df_fma(px, wy0.x, wy0.y, s1.hi, s1.lo);
       df_fma(py, wy1.x, wy1.y, s0.hi, s0.lo);
-      df_fma(pz, wy0.x, wy0.y, s1.hi, s1.lo);
+      df_fma(pzz, wy0.x, wy0.y, s0.hi, s0.lo);
     }
-    ex = df_mul({wx1.x, wx1.y}, px);
-    ey = df_mul({wx0.x, wx0.y}, py);
-    ez = df_mul({wx0.x, wx0.y}, pz);
+    ex = df_mul({wz0.x, wz0.y}, px);
+    ey = df_mul({wz0.x, wz0.y}, py);
+    ez = df_mul({wz1.x, wz1.y}, pzz);
   }
   const int base = min(seg, kGatherAtomsPerWarp - 1) * kOrder;
   ex = sum_five(ex, base);
   ey = sum_five(ey, base);
   ez = sum_five(ez, base);
-  // lanes 0..2 of each atom finish one component each (float64 instructions
-  // cost the same for one active lane as for 32)
   if (!active) return;
   double* o = reinterpret_cast<double*>(out + s);
-  if (tx < 3) {
-    const double f = df_to_double(tx == 0 ? ex : (tx == 1 ? ey : ez));
+  if (tz < 3) {
+    const double f = df_to_double(tz == 0 ? ex : (tz == 1 ? ey : ez));
     if (kSet)
-      o[tx] = -f;
+      o[tz] = -f;
     else
-      o[tx] -= f;
-  } else if (kSet && tx == 3) {
+      o[tz] -= f;
+  } else if (kSet && tz == 3) {
     o[3] = 0.0;
   }
 }
@@ -941,6 +940,7 @@ int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream
   cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
   k_spread_dipoles<float, float4><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
       n, c->theta32, c->gbase, v, K, c->grid32, c->op_stop);
+  if (c->spread_event) cudaEventRecord(c->ev_spread, st);
   int r = exec_fft(c, true, true);
   if (!r) {
     k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32, c->op_stop);
