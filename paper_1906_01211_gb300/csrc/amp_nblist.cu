@@ -219,30 +219,47 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
   int* srow = kMode == 2 ? slab + (long long)i * P.slab : nullptr;
   // lane c < span^2 fetches the atom ranges of (x, y) column c up front, so
   // the scan below waits on no cell_start load
+  // With five or more cells per axis the periodic image of a candidate follows
+  // from its cell offset: the run's atoms are compared with atom i moved by
+  // minus that image shift (sx, sy per column, sz per z run), which is the
+  // minimum image of every candidate within the cutoff. With fewer cells the
+  // float minimum image is taken per candidate.
   const int ncol = span * span;
   int rs[2] = {0, 0}, re[2] = {0, 0};
+  float sxl = 0.f, syl = 0.f;
   if (lane < ncol) {
     const int ox = lane / span, oy = lane % span;
-    const int cx = all ? ox : (ci[0] + ox - 2 + nc) % nc;
-    const int cy = all ? oy : (ci[1] + oy - 2 + nc) % nc;
+    const int cxr = ci[0] + ox - 2, cyr = ci[1] + oy - 2;  // unwrapped (when !all)
+    const int cx = all ? ox : (cxr + nc) % nc;
+    const int cy = all ? oy : (cyr + nc) % nc;
+    if (!all) {
+      sxl = cxr < 0 ? -P.Lf : (cxr >= nc ? P.Lf : 0.f);
+      syl = cyr < 0 ? -P.Lf : (cyr >= nc ? P.Lf : 0.f);
+    }
     const int base = (cx * nc + cy) * nc;
     for (int r = 0; r < nr; ++r) {
       rs[r] = cell_start[base + zr[r][0]];
       re[r] = cell_start[base + zr[r][1] + 1];
     }
   }
+  // z shift of run r: the second run is the wrapped one
+  const float szr[2] = {0.f, all ? 0.f : (ci[2] - 2 < 0 ? -P.Lf : P.Lf)};
   for (int col = 0; col < ncol; ++col) {
+    const float sx = __shfl_sync(0xffffffffu, sxl, col), sy = __shfl_sync(0xffffffffu, syl, col);
     for (int r = 0; r < nr; ++r) {
       const int s = __shfl_sync(0xffffffffu, rs[r], col), e = __shfl_sync(0xffffffffu, re[r], col);
+      const float px = pi.x - sx, py = pi.y - sy, pz = pi.z - szr[r];
       for (int k0 = s; k0 < e; k0 += 32) {
         const int k = k0 + lane;
         bool in = false;
         if (k < e && k != i) {
           const float4 pj = pos32[k];
-          float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-          dx -= P.Lf * rintf(dx * P.invLf);
-          dy -= P.Lf * rintf(dy * P.invLf);
-          dz -= P.Lf * rintf(dz * P.invLf);
+          float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+          if (all) {
+            dx -= P.Lf * rintf(dx * P.invLf);
+            dy -= P.Lf * rintf(dy * P.invLf);
+            dz -= P.Lf * rintf(dz * P.invLf);
+          }
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
         }
