@@ -291,14 +291,36 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
   }
 }
 
+// Speculative fill (the lists were sized by an earlier call): the fill kernels
+// run before the host has read the new counts and do nothing when a slab row
+// overflowed (flag bit 4) or the lists do not fit their buffers (then they set
+// flag bit 8); the host checks both after its single synchronisation and
+// refills on the two-pass path.
+struct ListGuard {
+  const int* flags;  // null: counts known on the host, nothing to check
+  int n;
+  long long cap_full, cap_half;
+};
+
+__device__ __forceinline__ bool list_skip(const ListGuard& g, const int* full_start, const int* half_start,
+                                          int* flags) {
+  if (!g.flags) return false;
+  if (*g.flags & 4) return true;
+  if (full_start[g.n] > g.cap_full || half_start[g.n] > g.cap_half) {
+    atomicOr(flags, 8);
+    return true;
+  }
+  return false;
+}
+
 // Slab rows -> owned part of the full rows and the half list.
 __global__ void k_slab_copy(int n, int slab_cap, const int* __restrict__ slab, const int* __restrict__ half_cnt,
                             const int* __restrict__ full_start, const int* __restrict__ half_start,
                             int* __restrict__ full_j, int* __restrict__ full_ref, int* __restrict__ half_i,
-                            int* __restrict__ half_j) {
+                            int* __restrict__ half_j, ListGuard g, int* __restrict__ flags) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (i >= n) return;
+  if (i >= n || list_skip(g, full_start, half_start, flags)) return;
   const int m = half_cnt[i], fb = full_start[i], hb = half_start[i];
   const int* row = slab + (long long)i * slab_cap;
   for (int r = lane; r < m; r += 32) {
@@ -315,9 +337,11 @@ __global__ void k_slab_copy(int n, int slab_cap, const int* __restrict__ slab, c
 // by pair id, so the final order does not depend on the atomics.
 __global__ void k_transpose_scatter(long long nh, const int* __restrict__ half_j,
                                     const int* __restrict__ full_start, const int* __restrict__ half_cnt,
-                                    int* __restrict__ tcount, int* __restrict__ tmp) {
+                                    int* __restrict__ tcount, int* __restrict__ tmp, ListGuard g,
+                                    const int* __restrict__ half_start, int* __restrict__ flags) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pid >= nh) return;
+  if (g.flags) nh = half_start[g.n];  // speculative: the count is on the device only
+  if (pid >= nh || list_skip(g, full_start, half_start, flags)) return;
   const int j = half_j[pid];
   const int slot = full_start[j] + half_cnt[j] + atomicAdd(&tcount[j], 1);
   tmp[slot] = (int)pid;
@@ -329,11 +353,12 @@ __global__ void __launch_bounds__(256) k_transpose_sort(int n, const int* __rest
                                                         const int* __restrict__ half_cnt,
                                                         const int* __restrict__ tmp, const int* __restrict__ half_i,
                                                         int* __restrict__ full_j, int* __restrict__ full_ref,
-                                                        int* __restrict__ pos_tr) {
+                                                        int* __restrict__ pos_tr, ListGuard g,
+                                                        const int* __restrict__ half_start, int* __restrict__ flags) {
   __shared__ int stage[256 / 32][kSortCap];
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (i >= n) return;  // whole warps leave together
+  if (i >= n || list_skip(g, full_start, half_start, flags)) return;  // whole warps leave together
   const int lo = full_start[i] + half_cnt[i], hi = full_start[i + 1], m = hi - lo;
   const bool staged = m <= kSortCap;
   if (staged)
@@ -419,6 +444,22 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->slab, c->flags);
   k_scan_exclusive<<<2, 1024, 0, st>>>(c->full_cnt, c->full_start, n, c->half_cnt, c->half_start);
   if ((r = cuda_check(c, cudaGetLastError(), "list count launch"))) return r;
+  // Lists sized by an earlier call: fill them before reading the counts (one
+  // host round trip instead of two); the kernels skip the fill if it would not
+  // fit or a slab row overflowed, and the two-pass path below redoes it.
+  const bool speculative = c->cap_full > 0 && c->cap_half > 0;
+  const ListGuard none{nullptr, n, 0, 0};
+  if (speculative) {
+    const ListGuard g{c->flags, n, c->cap_full, c->cap_half};
+    k_slab_copy<<<lb, 256, 0, st>>>(n, slab, c->slab, c->half_cnt, c->full_start, c->half_start, c->full_j,
+                                    c->full_ref, c->half_i, c->half_j, g, c->flags);
+    cudaMemsetAsync(c->full_cnt, 0, sizeof(int) * n, st);  // reused as the per-row slot counter
+    k_transpose_scatter<<<amp_blocks(c->cap_half, 256), 256, 0, st>>>(c->cap_half, c->half_j, c->full_start,
+                                                                      c->half_cnt, c->full_cnt, c->tr_tmp, g,
+                                                                      c->half_start, c->flags);
+    k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref,
+                                        c->pos_tr, g, c->half_start, c->flags);
+  }
   cudaMemcpyAsync(&c->hibuf[0], c->full_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&c->hibuf[1], c->half_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -428,6 +469,7 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   c->n_half = c->hibuf[1];
   if (c->n_full != 2 * c->n_half) return fail(c, AMP_ERR_GEOMETRY, "inconsistent neighbour counts");
   if (c->n_full > (1LL << 30)) return fail(c, AMP_ERR_GEOMETRY, "too many pairs");
+  if (speculative && !(c->hibuf[2] & (4 | 8))) return AMP_OK;  // filled in place
   if (c->n_full > c->cap_full || c->n_half > c->cap_half) {
     void** bufs[] = {(void**)&c->full_j, (void**)&c->full_ref, (void**)&c->tr_tmp, (void**)&c->half_i, (void**)&c->half_j,
                      (void**)&c->T64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32,
@@ -457,16 +499,14 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
                                         nullptr, nullptr);
   else
     k_slab_copy<<<lb, 256, 0, st>>>(n, slab, c->slab, c->half_cnt, c->full_start, c->half_start, c->full_j,
-                                    c->full_ref, c->half_i, c->half_j);
+                                    c->full_ref, c->half_i, c->half_j, none, c->flags);
   cudaMemsetAsync(c->full_cnt, 0, sizeof(int) * n, st);  // reused as the per-row slot counter
   k_transpose_scatter<<<amp_blocks(c->n_half, 256), 256, 0, st>>>(c->n_half, c->half_j, c->full_start, c->half_cnt,
-                                                                  c->full_cnt, c->tr_tmp);
+                                                                  c->full_cnt, c->tr_tmp, none, c->half_start,
+                                                                  c->flags);
   k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref,
-                                      c->pos_tr);
-  cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if ((r = cuda_check(c, cudaStreamSynchronize(st), "list fill"))) return r;
-  if (c->hibuf[2] & 1) return fail(c, AMP_ERR_GEOMETRY, "neighbour list transpose failed");
-  return AMP_OK;
+                                      c->pos_tr, none, c->half_start, c->flags);
+  return cuda_check(c, cudaGetLastError(), "list fill launch");
 }
 
 }  // namespace amp

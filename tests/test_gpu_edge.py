@@ -96,3 +96,42 @@ def test_apply_T_is_bitwise_reproducible():
     a = s.apply_T(v).clone()
     b = s.apply_T(v).clone()
     assert torch.equal(a, b)
+
+
+def test_list_refill_paths_on_one_context():
+    """One context through every neighbour-list fill path: the first call
+    sizes the lists; later calls fill them before the counts reach the host
+    and refill on the two-pass path when the lists outgrow their buffers
+    (twice the waters in the same box) or an owned row overflows its slab
+    row (waters packed into one corner), alone or together. Pair count, E0 and T*v against the
+    oracle after each call."""
+    from paper_1906_01211_gb300 import amoebapol as ap
+    from paper_1906_01211_gb300.synth import System, density_box_edge, make_waters
+    L = density_box_edge(300)
+    rc, beta = 7.0, 0.5446
+    K = 32
+    s = ap.Polarization(ap.Config(box=L, cutoff=rc, ewald_beta=beta, pme_grid=K, tol_debye=1e-10))
+    sparse = make_waters(150, L, 71)
+    dense = make_waters(300, L, 72)
+    # two thirds of the dense waters squeezed into one corner (0.3 of the
+    # edge): up to 345 owned neighbours per row there, the slab holds 288
+    xyz = dense.xyz.copy()
+    n_c = 3 * 200
+    xyz[:n_c] = xyz[:n_c] * 0.3
+    packed = System(xyz=xyz, q=dense.q, dip=dense.dip, quad=dense.quad, alpha=dense.alpha, thole=dense.thole,
+                    mol=dense.mol, box=L)
+    rng = np.random.default_rng(73)
+    # sparse sizes the lists; dense outgrows them; packed outgrows them and
+    # overflows a slab row; sparse and dense then fit; packed again fits but
+    # overflows a slab row
+    for sysm in (sparse, dense, packed, sparse, dense, packed):
+        op = Operator(sysm, Setup(box=L, cutoff=rc, beta=beta, grid=K, order=5))
+        s.set_synthetic(sysm)
+        assert s.pair_count() == op.n_pairs
+        E0 = s.permanent_field().cpu().numpy()
+        assert np.linalg.norm(E0 - op.permanent_field()) < 1e-12 * np.linalg.norm(op.permanent_field())
+        v = rng.normal(size=(sysm.n, 3)) * 0.1
+        t = s.apply_T(torch.tensor(v)).cpu().numpy()
+        ref = op.apply_T(v)
+        assert np.linalg.norm(t - ref) < 1e-12 * np.linalg.norm(ref)
+    s.close()
