@@ -229,7 +229,6 @@ int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += r
 // reciprocal field of dipoles on stream st: out += field (set: out = field)
 int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* out,
                      cudaStream_t st, bool set);
-int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream_t st, bool set);
 
 // solver (amp_pcg.cu)
 void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst);

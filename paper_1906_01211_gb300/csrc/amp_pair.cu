@@ -640,11 +640,11 @@ void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, doub
                                         out, c->op_stop);
 }
 
-// v's split goes through p32/plo (free during the check: k_cg_init rewrites them).
+// v's split must be in p32/plo (free during the check: k_cg_init rewrites
+// them); the caller splits it before the reciprocal part forks.
 void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out) {
   const PairGeom g = geom(c);
   const int blocks = amp_blocks((long long)c->n * kRowGroup, 256);
-  launch_split(c, v, c->p32, c->plo);
   c->n_launch += c->n_half > 0 ? 2 : 1;
   if (c->n_half > 0)
     k_pair_tv_df<<<amp_blocks(c->n_half, 256), 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd,

@@ -439,25 +439,33 @@ void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo) {
   k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, hi, lo, lo ? c->vhl : nullptr, c->vmax_part);
 }
 
+// Real-space kernel of an operator application.
+enum RealMode { kRealDf, kRealF32, kRealDirectDf };
+
 // T v = t (+ t2). With t2 == nullptr the whole product lands in t. With t2
 // given (periodic systems) the reciprocal part runs on the side stream into t2
 // while the real-space kernel runs on the main stream into t: the two parts
-// are independent. In the float64 path the real-space kernel starts once the
-// dipoles are spread: the spreading keeps every SM busy by itself, while the
-// three FFT passes that follow are latency bound and leave most of the GPU to
-// the real-space kernel. The main stream waits for the side stream before
-// returning.
-static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const float4* v32, const float4* vlo,
-                       double4_32a* t, double4_32a* t2, bool fp64_real_cached, bool fp64_real_direct) {
+// are independent. The real-space kernel starts once the dipoles are spread:
+// the spreading keeps every SM busy by itself, while the three FFT passes
+// that follow are latency bound and leave most of the GPU to the real-space
+// kernel. The main stream waits for the side stream before returning. The
+// reciprocal part is the double-float chain in both precisions; the float64
+// check (kRealDirectDf) first splits v into (p32, plo) for both parts.
+static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* t,
+                       double4_32a* t2, RealMode mode) {
   int r;
+  if (mode == kRealDirectDf) {
+    launch_split(c, v, c->p32, c->plo);
+    v32 = c->p32;
+    vlo = c->plo;
+  }
   if (t2) {
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     {
       PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
-      c->spread_event = fp64_pme == fp64_real_cached && !fp64_real_direct;
-      r = fp64_pme ? pme_dipole_field(c, v, v32, vlo, t2, c->side, true)
-                   : pme_dipole_field32(c, v32, t2, c->side, true);
+      c->spread_event = mode != kRealDirectDf;
+      r = pme_dipole_field(c, v, v32, vlo, t2, c->side, true);
       if (c->spread_event) cudaStreamWaitEvent(c->stream, c->ev_spread, 0);
       c->spread_event = false;
     }
@@ -469,9 +477,9 @@ static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const fl
   }
   {
     PhaseScope ps(c, AMP_PHASE_T_REAL);
-    if (fp64_real_direct)
+    if (mode == kRealDirectDf)
       launch_t_real_fp64_direct(c, v, t);
-    else if (fp64_real_cached)
+    else if (mode == kRealDf)
       launch_t_real(c, v, v32, vlo, t);
     else
       launch_t_real32(c, v32, v, t);
@@ -481,8 +489,7 @@ static int fork_join_T(amp_ctx* c, bool fp64_pme, const double4_32a* v, const fl
     return AMP_OK;
   }
   PhaseScope ps(c, AMP_PHASE_T_RECIP);
-  return fp64_pme ? pme_dipole_field(c, v, v32, vlo, t, c->stream, false)
-                  : pme_dipole_field32(c, v32, t, c->stream, false);
+  return pme_dipole_field(c, v, v32, vlo, t, c->stream, false);
 }
 
 // t (+ t2) = T v in the solver's working precision. v32 (+ vlo) must mirror
@@ -496,7 +503,7 @@ int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, const fl
     if (t2) cudaMemsetAsync(t2, 0, sizeof(double4_32a) * c->n, c->stream);
     return AMP_OK;
   }
-  return fork_join_T(c, fp64, v, v32, vlo, t, t2, fp64, false);
+  return fork_join_T(c, v, v32, vlo, t, t2, fp64 ? kRealDf : kRealF32);
 }
 
 // Mixed path: t (+ t2) = T v with every term in float64 (pair tensors recomputed).
@@ -507,7 +514,7 @@ static int apply_T_sorted_fp64_check(amp_ctx* c, const double4_32a* v, double4_3
     if (t2) cudaMemsetAsync(t2, 0, sizeof(double4_32a) * c->n, c->stream);
     return AMP_OK;
   }
-  return fork_join_T(c, true, v, nullptr, nullptr, t, t2, false, true);
+  return fork_join_T(c, v, nullptr, nullptr, t, t2, kRealDirectDf);
 }
 
 static int read_flags(amp_ctx* c) {

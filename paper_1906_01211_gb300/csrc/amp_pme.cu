@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, con
   const int s = (int)(item / (kOrder * kOrder)), tyz = (int)(item - (long long)s * (kOrder * kOrder));
   const int ty = tyz / kOrder, tz = tyz - ty * kOrder;
   const float2* th = th_df + (long long)kThDf * s;
-  const float4 h = v32[s], l = vlo[s];
+  const float4 h = v32[s], l = vlo ? vlo[s] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float2 y0 = th[(1 * 2 + 0) * kOrder + ty], y1 = th[(1 * 2 + 1) * kOrder + ty];
   const float2 z0 = th[(2 * 2 + 0) * kOrder + tz], z1 = th[(2 * 2 + 1) * kOrder + tz];
   // P = mu_y w'_y w_z + mu_z w_y w'_z, Q = mu_x w_y w_z: the point's value is P w_x + Q w'_x
@@ -734,8 +734,8 @@ int pme_influence(amp_ctx* c) {
                                       "G upload")))
     return r;
   if ((r = cuda_check(c, cudaStreamSynchronize(c->stream), "G upload"))) return r;
-  // the float64 path transforms power-of-two grids with its own double-float FFT
-  if (c->cfg.precision == AMP_FP64 && fft_df_supported(K)) return fft_df_setup(c, G.data());
+  // power-of-two grids are transformed by our own double-float FFT
+  if (fft_df_supported(K)) return fft_df_setup(c, G.data());
   return AMP_OK;
 }
 
@@ -747,15 +747,15 @@ int pme_setup(amp_ctx* c) {
   if ((r = dev_alloc(c, &c->grid64, ng)) || (r = dev_alloc(c, &c->cgrid64, nh)) ||
       (r = dev_alloc(c, &c->G64, nh)))
     return r;
-  if (c->cfg.precision == AMP_FP64) {
-    if ((r = dev_alloc(c, &c->phi_df, ng)) || (r = dev_alloc(c, &c->gridfx, ng)) ||
-        (r = dev_alloc(c, &c->kcount, ng)) || (r = dev_alloc(c, &c->fx_info, 4)))
-      return r;
-    // the fixed-point grid starts at zero; the kernel that reads it zeroes it again
-    if ((r = cuda_check(c, cudaMemsetAsync(c->gridfx, 0, sizeof(unsigned long long) * ng, c->stream),
-                        "grid memset")))
-      return r;
-  }
+  // the reciprocal part of both precisions: fixed-point grid, double-float
+  // transform and gather (the mixed path's float32 grids serve its forces)
+  if ((r = dev_alloc(c, &c->phi_df, ng)) || (r = dev_alloc(c, &c->gridfx, ng)) ||
+      (r = dev_alloc(c, &c->kcount, ng)) || (r = dev_alloc(c, &c->fx_info, 4)))
+    return r;
+  // the fixed-point grid starts at zero; the kernel that reads it zeroes it again
+  if ((r = cuda_check(c, cudaMemsetAsync(c->gridfx, 0, sizeof(unsigned long long) * ng, c->stream),
+                      "grid memset")))
+    return r;
   if (c->cfg.precision == AMP_MIXED) {
     if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
         (r = dev_alloc(c, &c->G32, nh)))
@@ -782,62 +782,47 @@ int pme_alloc_atoms(amp_ctx* c, int n_cap) {
   int r;
   if ((r = dev_alloc(c, &c->theta, (long long)kTh * n_cap)) || (r = dev_alloc(c, &c->gbase, n_cap))) return r;
   if (c->cfg.precision == AMP_MIXED && (r = dev_alloc(c, &c->theta32, (long long)kTh * n_cap))) return r;
-  if (c->cfg.precision == AMP_FP64 && ((r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap)) ||
-                                        (r = dev_alloc(c, &c->theta_df2, 3LL * kOrder * n_cap))))
+  if ((r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap)) ||
+      (r = dev_alloc(c, &c->theta_df2, 3LL * kOrder * n_cap)))
     return r;
   return AMP_OK;
 }
 
-// B-spline weights of the current system. Float64 path: double-float weights
-// (k_theta_df); the float64 copy, which only the force kernels read, is built
-// on demand by pme_theta64. Mixed path: float64 and float32 weights.
+// B-spline weights of the current system in double-float (k_theta_df), for
+// the reciprocal parts of both precisions; the float64 copy (and the mixed
+// path's float32 one), which only the force kernels read, are built on demand
+// by pme_theta64.
 void launch_pme_theta(amp_ctx* c) {
   c->n_launch += 1;
-  if (c->theta_df) {
-    cudaMemsetAsync(c->kcount, 0, sizeof(int) * (long long)c->K * c->K * c->K, c->stream);
-    cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 4, c->stream);
-    const double sc = (double)c->K / c->cfg.box;
-    const float sh = (float)sc;
-    k_theta_df<<<amp_blocks(4LL * c->n, 128), 128, 0, c->stream>>>(
-        c->n, c->atomA, c->atomB, c->atomC, c->atomD, c->cfg.box, c->K, make_float2(sh, (float)(sc - (double)sh)),
-        c->theta_df, c->theta_df2, c->gbase, c->kcount, c->fx_info);
-    c->theta64_valid = false;
-    return;
-  }
-  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
-                                                       nullptr, c->gbase, nullptr, nullptr);
-  c->theta64_valid = true;
+  cudaMemsetAsync(c->kcount, 0, sizeof(int) * (long long)c->K * c->K * c->K, c->stream);
+  cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 4, c->stream);
+  const double sc = (double)c->K / c->cfg.box;
+  const float sh = (float)sc;
+  k_theta_df<<<amp_blocks(4LL * c->n, 128), 128, 0, c->stream>>>(
+      c->n, c->atomA, c->atomB, c->atomC, c->atomD, c->cfg.box, c->K, make_float2(sh, (float)(sc - (double)sh)),
+      c->theta_df, c->theta_df2, c->gbase, c->kcount, c->fx_info);
+  c->theta64_valid = false;
 }
 
 void pme_theta64(amp_ctx* c) {
   if (c->theta64_valid) return;
   c->n_launch += 1;
-  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, nullptr,
+  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
                                                        nullptr, c->gbase, nullptr, nullptr);
   c->theta64_valid = true;
 }
 
 int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
   const int K = c->K, n = c->n;
-  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
   cudaStream_t st = c->stream;
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  int r;
-  if (c->cfg.precision == AMP_FP64) {  // double-float, fixed-point grid (zero on entry), as for the dipoles
-    k_spread_multipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
-        n, c->theta_df, c->theta_df2, c->gbase, c->mp_df, c->fx_info, K, c->gridfx);
-    bool split = true;
-    if ((r = conv_to_phi(c, st, &split, true))) return r;
-    gather_df<false>(c, st, out_add, split);
-  } else {
-    cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
-    k_spread_multipoles<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->atomA, c->atomB,
-                                                                   c->atomC, c->atomD, K, c->grid32);
-    if ((r = exec_fft(c, true, true))) return r;
-    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32);
-    if ((r = exec_fft(c, true, false))) return r;
-    k_gather_field<float><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(n, c->theta32, c->gbase, c->grid32, K, out_add);
-  }
+  // double-float, fixed-point grid (zero on entry), as for the dipoles
+  k_spread_multipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
+      n, c->theta_df, c->theta_df2, c->gbase, c->mp_df, c->fx_info, K, c->gridfx);
+  bool split = true;
+  const int r = conv_to_phi(c, st, &split, true);
+  if (r) return r;
+  gather_df<false>(c, st, out_add, split);
   return AMP_OK;
 }
 
@@ -883,80 +868,28 @@ int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, 
 
 // Reciprocal field of the dipoles v on stream st: out (+)= -grad phi. With
 // set = true the result overwrites out (used when it runs beside the real-space
-// kernel on a second stream and is summed later). In a float64 context v must
-// come with its double-float split (v32, vlo) and the per-block maxima that the
-// splitting kernel left in vmax_part.
+// kernel on a second stream and is summed later). The dipoles come as their
+// float split, v32 + vlo (vlo null: v32 alone, the mixed path's operator
+// input), with the per-block maxima that the splitting kernel left in
+// vmax_part.
 int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* out,
                      cudaStream_t st, bool set) {
+  (void)v;
   const int K = c->K, n = c->n;
-  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  if (c->theta_df) {  // float64 context: fixed-point spread, own FFT (or cuFFT + split), double-float gather
-    if (!v32 || !vlo) return fail(c, AMP_ERR_STATE, "float64 reciprocal field needs the split vector");
-    launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
-               dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
-               (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
-    if (c->spread_event) cudaEventRecord(c->ev_spread, st);
-    bool split = true;
-    const int r = conv_to_phi(c, st, &split, true);
-    if (r) return r;
-    if (set)
-      gather_df<true>(c, st, out, split);
-    else
-      gather_df<false>(c, st, out, split);
-    return AMP_OK;
-  }
-  // float64 check of the mixed path: float64 spread, cuFFT float64 and a float64 gather
-  cudaMemsetAsync(c->grid64, 0, sizeof(double) * ng, st);
-  k_spread_dipoles<double, double4_32a><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-      n, c->theta, c->gbase, v, K, c->grid64);
-  cufftSetStream(c->plan_d2z, st);
-  cufftSetStream(c->plan_z2d, st);
-  int r = exec_fft(c, false, true);
-  if (!r) {
-    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid64, c->G64);
-    r = exec_fft(c, false, false);
-  }
-  if (!r) {
-    if (set) {
-      k_gather_field<double, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-          n, c->theta, c->gbase, c->grid64, K, out);
-    } else {
-      k_gather_field<double, false><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-          n, c->theta, c->gbase, c->grid64, K, out);
-    }
-  }
-  cufftSetStream(c->plan_d2z, c->stream);
-  cufftSetStream(c->plan_z2d, c->stream);
-  return r;
-}
-
-int pme_dipole_field32(amp_ctx* c, const float4* v, double4_32a* out, cudaStream_t st, bool set) {
-  const int K = c->K, n = c->n;
-  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
-  c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  cufftSetStream(c->plan_r2c, st);
-  cufftSetStream(c->plan_c2r, st);
-  cudaMemsetAsync(c->grid32, 0, sizeof(float) * ng, st);
-  k_spread_dipoles<float, float4><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-      n, c->theta32, c->gbase, v, K, c->grid32, c->op_stop);
+  if (!v32) return fail(c, AMP_ERR_STATE, "reciprocal field needs the float split of the vector");
+  launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
+             dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
+             (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
   if (c->spread_event) cudaEventRecord(c->ev_spread, st);
-  int r = exec_fft(c, true, true);
-  if (!r) {
-    k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32, c->op_stop);
-    r = exec_fft(c, true, false);
-  }
-  if (!r) {
-    if (set)
-      k_gather_field<float, true><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-          n, c->theta32, c->gbase, c->grid32, K, out, c->op_stop);
-    else
-      k_gather_field<float, false><<<amp_blocks((long long)n * kPmeGroup, 128), 128, 0, st>>>(
-          n, c->theta32, c->gbase, c->grid32, K, out, c->op_stop);
-  }
-  cufftSetStream(c->plan_r2c, c->stream);
-  cufftSetStream(c->plan_c2r, c->stream);
-  return r;
+  bool split = true;
+  const int r = conv_to_phi(c, st, &split, true);
+  if (r) return r;
+  if (set)
+    gather_df<true>(c, st, out, split);
+  else
+    gather_df<false>(c, st, out, split);
+  return AMP_OK;
 }
 
 }  // namespace amp
