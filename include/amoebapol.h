@@ -49,6 +49,7 @@ extern "C" {
 #define AMP_ERR_NOT_CONVERGED (-4) /* PCG reached max_iter above tolerance */
 #define AMP_ERR_GEOMETRY (-5)      /* cutoff >= box/2, list overflow, bad cell */
 #define AMP_ERR_STATE (-6)         /* call order: no system set */
+#define AMP_ERR_STALE (-8)         /* amp_update_positions: an atom moved more than skin/2 */
 
 #define AMP_FP64 0   /* all pair math, grids and FFTs in float64 */
 #define AMP_MIXED 1  /* float32 pair geometry/damping and PME, float64
@@ -98,6 +99,24 @@ const char* amp_last_error(const amp_ctx* ctx);
 int amp_set_system(amp_ctx* ctx, int n_atoms, const double* xyz, const double* q,
                    const double* dip, const double* quad, const double* alpha,
                    const double* thole, const int* mol);
+
+/* Neighbour-list skin (Angstrom, >= 0; periodic contexts; cutoff + skin <
+ * box/2), used from the next amp_set_system on: that call then also keeps the
+ * candidate pairs within cutoff + skin and the positions it saw, so that
+ * amp_update_positions can rebuild the lists from them (Verlet-style list
+ * reuse; the paper, Section "Hotspots", names the cell list builder among the
+ * hotspots). 0, the default, keeps no candidates. */
+int amp_set_list_skin(amp_ctx* ctx, double skin);
+
+/* New positions xyz [N][3] (device, caller order) for the atoms of the last
+ * amp_set_system, whose other inputs are kept. If a skin was set for that
+ * call and no atom has moved more than skin/2 (minimum image) since it, the
+ * neighbour lists are filtered out of its candidates (the same pairs, by the
+ * same float64 decision, as a new cell search), the pair terms and PME
+ * weights are rebuilt, and *reused = 1. Otherwise nothing changes and the call
+ * returns AMP_ERR_STALE: call amp_set_system. Synchronises the stream once
+ * (twice when the lists are rebuilt). */
+int amp_update_positions(amp_ctx* ctx, const double* xyz, int* reused);
 
 /* Permanent-multipole field at every site, E0 [N][3] (real space with the
  * intramolecular exclusion + PME + self). The right-hand side of the

@@ -25,6 +25,7 @@ AMP_ERR_OOM = -3
 AMP_ERR_NOT_CONVERGED = -4
 AMP_ERR_GEOMETRY = -5
 AMP_ERR_STATE = -6
+AMP_ERR_STALE = -8
 AMP_FP64 = 0
 AMP_MIXED = 1
 PHASES = ("list", "pair", "e0_real", "e0_recip", "t_real", "t_recip", "pcg", "fp64_check", "energy", "forces")
@@ -75,6 +76,8 @@ def _load() -> ctypes.CDLL:
         "amp_last_solve_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "amp_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
         "amp_polarization_energy_noalloc": (I, [I, P, P, P, P]),
+        "amp_set_list_skin": (I, [P, D]),
+        "amp_update_positions": (I, [P, P, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -123,6 +126,21 @@ def amp_last_error(ctx) -> str:
 
 def amp_set_system(ctx, n, xyz, q, dip, quad, alpha, thole, mol):
     _check(ctx, _lib.amp_set_system(ctx, int(n), xyz, q, dip, quad, alpha, thole, mol))
+
+
+def amp_set_list_skin(ctx, skin: float):
+    _check(ctx, _lib.amp_set_list_skin(ctx, float(skin)))
+
+
+def amp_update_positions(ctx, xyz) -> bool:
+    """True if the lists were rebuilt from the stored candidates; False if an
+    atom moved more than skin/2 (then nothing changed: set the system again)."""
+    reused = ctypes.c_int(0)
+    code = _lib.amp_update_positions(ctx, xyz, ctypes.byref(reused))
+    if code == AMP_ERR_STALE:
+        return False
+    _check(ctx, code)
+    return bool(reused.value)
 
 
 def amp_permanent_field(ctx, E0):
@@ -260,6 +278,21 @@ class Polarization:
         amp_set_system(self.ctx, self.n, *[a.data_ptr() for a in arrs])
         self._keep = arrs  # inputs stay alive while the stream may read them
         self.generation += 1
+
+    def set_list_skin(self, skin: float):
+        """Neighbour-list skin (Angstrom) used from the next set_system on."""
+        amp_set_list_skin(self.ctx, skin)
+
+    def update_positions(self, xyz) -> bool:
+        """New positions for the current atoms; True if the lists were reused
+        (rebuilt from the candidates of the last set_system), False if an atom
+        moved more than skin/2 (nothing changed: call set_system)."""
+        x = self._dev(xyz, self.torch.float64)
+        ok = amp_update_positions(self.ctx, x.data_ptr())
+        if ok:
+            self._keep = (x,) + tuple(self._keep[1:])
+            self.generation += 1
+        return ok
 
     def set_synthetic(self, system):
         """Upload a ``synth.System`` (numpy arrays)."""

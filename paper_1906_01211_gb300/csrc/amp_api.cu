@@ -179,6 +179,8 @@ int amp_reconfigure(amp_ctx* c, const amp_config* cfg) {
   const bool box_changed = cfg->box != c->cfg.box || cfg->ewald_beta != c->cfg.ewald_beta;
   c->cfg = *cfg;
   c->have_system = false;
+  c->skin_built = 0.0;
+  if (2.0 * (c->cfg.cutoff + c->skin) >= c->cfg.box) c->skin = 0.0;
   if (!cluster && box_changed) return pme_influence(c);
   return AMP_OK;
 }
@@ -235,6 +237,41 @@ int amp_set_system(amp_ctx* c, int n, const double* xyz, const double* q, const 
   }
   if ((r = cuda_check(c, cudaGetLastError(), "set_system launch"))) return r;
   c->have_system = true;
+  return AMP_OK;
+}
+
+int amp_set_list_skin(amp_ctx* c, double skin) {
+  if (!c) return AMP_ERR_ARG;
+  if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_set_list_skin: periodic contexts only");
+  if (!(skin >= 0.0) || !(2.0 * (c->cfg.cutoff + skin) < c->cfg.box))
+    return fail(c, AMP_ERR_ARG, "amp_set_list_skin: skin >= 0 with cutoff + skin < box/2");
+  c->skin = skin;
+  return AMP_OK;
+}
+
+int amp_update_positions(amp_ctx* c, const double* xyz, int* reused) {
+  if (!c) return AMP_ERR_ARG;
+  if (reused) *reused = 0;
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!xyz) return fail(c, AMP_ERR_ARG, "xyz is null");
+  if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_update_positions: periodic contexts only");
+  bool ok = false;
+  int r;
+  {
+    PhaseScope ps(c, AMP_PHASE_LIST);
+    if ((r = reuse_lists(c, xyz, &ok))) return r;
+  }
+  if (!ok) return fail(c, AMP_ERR_STALE, "an atom moved more than skin/2 since amp_set_system (or no skin)");
+  {
+    PhaseScope ps(c, AMP_PHASE_PAIR);
+    launch_pair_build(c);
+  }
+  {
+    PhaseScope ps(c, AMP_PHASE_E0_RECIP);
+    launch_pme_theta(c);
+  }
+  if ((r = cuda_check(c, cudaGetLastError(), "update_positions launch"))) return r;
+  if (reused) *reused = 1;
   return AMP_OK;
 }
 

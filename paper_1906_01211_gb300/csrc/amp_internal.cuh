@@ -74,6 +74,12 @@ struct amp_ctx {
   int *full_cnt = nullptr, *half_cnt = nullptr, *full_start = nullptr, *half_start = nullptr;
   int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr, *tr_tmp = nullptr;
   int* pos_tr = nullptr;  // full-list position of each pair's entry in its non-owner's row
+  // list reuse: skin for the next build; the candidates (pairs within cutoff
+  // + skin_built at the last cell search, CSR) and the sorted positions then
+  double skin = 0.0, skin_built = 0.0;
+  int *cand_start = nullptr, *cand_j = nullptr;
+  long long cand_cap = 0, cand_start_cap = 0;
+  double4_32a* xref = nullptr;
   long long n_full = 0, n_half = 0, cap_full = 0, cap_half = 0;
   int* flags = nullptr;  // [0] bit 1 list transpose failure, bit 2 bad alpha, bit 4 slab overflow
   int* slab = nullptr;   // single-pass list: owned neighbours per atom, fixed row capacity
@@ -203,6 +209,8 @@ struct PhaseScope {
 int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const double* dip,
                           const double* quad, const double* alpha, const double* thole,
                           const int* mol);
+int filter_lists(amp_ctx* c);  // exact lists from the stored candidates
+int reuse_lists(amp_ctx* c, const double* xyz, bool* reused);  // new positions if within skin/2
 
 // pair terms and real-space sums (amp_pair.cu)
 void launch_pair_build(amp_ctx* c);

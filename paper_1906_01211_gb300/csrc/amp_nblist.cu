@@ -24,6 +24,7 @@
 //   6. each pair id is scattered to its non-owner's row, which sorts that part
 //      of the row by pair id (deterministic order).
 #include <cmath>
+#include <cstring>
 #include <cstdarg>
 #include <cstdio>
 
@@ -178,6 +179,34 @@ __device__ __forceinline__ bool exact_in_range(const double4_32a& a, const doubl
   return r2 < rc2;
 }
 
+// One round of 32 candidates of row i (lane: candidate k, in range or not):
+// owned pairs (rule (i < k) != (i + k odd)) open the row, the full slot and
+// the pair id sharing the rank. kMode 0 counts; 1 writes at the row offsets;
+// 2 writes the owned neighbours into the slab row srow (capacity slab_cap).
+template <int kMode>
+__device__ __forceinline__ void emit_round(bool in, int i, int k, unsigned lt, int& nfull, int& nhalf, int fbase,
+                                           int hbase, int* srow, int slab_cap, int* __restrict__ full_j,
+                                           int* __restrict__ full_ref, int* __restrict__ half_i,
+                                           int* __restrict__ half_j) {
+  const bool own = in && ((i < k) != (((i + k) & 1) != 0));
+  const unsigned mf = __ballot_sync(0xffffffffu, in);
+  const unsigned mh = __ballot_sync(0xffffffffu, own);
+  if (own) {
+    const int rank = nhalf + __popc(mh & lt);
+    if (kMode == 1) {
+      const int pid = hbase + rank;
+      full_j[fbase + rank] = k;
+      full_ref[fbase + rank] = pid << 1;
+      half_i[pid] = i;
+      half_j[pid] = k;
+    } else if (kMode == 2 && rank < slab_cap) {
+      srow[rank] = k;
+    }
+  }
+  nfull += __popc(mf);
+  nhalf += __popc(mh);
+}
+
 // Candidates of atom i: cells within two cells per axis (cell edge >= rc/2;
 // every cell when there are fewer than five per axis). For each (x, y) cell
 // column the z cells form one or two runs of consecutive cells, hence of
@@ -263,24 +292,7 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
         }
-        const bool own = in && ((i < k) != (((i + k) & 1) != 0));
-        const unsigned mf = __ballot_sync(0xffffffffu, in);
-        const unsigned mh = __ballot_sync(0xffffffffu, own);
-        if (own) {
-          // owned pairs open the row: full slot and pair id share the rank
-          const int rank = nhalf + __popc(mh & lt);
-          if (kMode == 1) {
-            const int pid = hbase + rank;
-            full_j[fbase + rank] = k;
-            full_ref[fbase + rank] = pid << 1;
-            half_i[pid] = i;
-            half_j[pid] = k;
-          } else if (kMode == 2 && rank < P.slab) {
-            srow[rank] = k;
-          }
-        }
-        nfull += __popc(mf);
-        nhalf += __popc(mh);
+        emit_round<kMode>(in, i, k, lt, nfull, nhalf, fbase, hbase, srow, P.slab, full_j, full_ref, half_i, half_j);
       }
     }
   }
@@ -289,6 +301,91 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
     half_cnt[i] = nhalf;
     if (kMode == 2 && nhalf > P.slab) atomicOr(flags, 4);
   }
+}
+
+// The same list from stored candidates: row i of (cand_start, cand_j) holds
+// the pairs that were within cutoff + skin at the last cell search; the
+// in-range decision (float prefilter, float64 operations near the cutoff) and
+// the emission are those of k_neighbours, with the float minimum image per
+// candidate (the atoms have moved since the candidates were found).
+template <int kMode>
+__global__ void k_filter(ListParams P, const float4* __restrict__ pos32, const double4_32a* __restrict__ A,
+                         const int* __restrict__ cand_start, const int* __restrict__ cand_j,
+                         int* __restrict__ full_cnt, int* __restrict__ half_cnt,
+                         const int* __restrict__ full_start, const int* __restrict__ half_start,
+                         int* __restrict__ full_j, int* __restrict__ full_ref, int* __restrict__ half_i,
+                         int* __restrict__ half_j, int* __restrict__ slab, int* __restrict__ flags) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= P.n) return;
+  const unsigned lt = (1u << lane) - 1u;
+  const float4 pi = pos32[i];
+  const double4_32a ai = A[i];
+  int nfull = 0, nhalf = 0;
+  const int fbase = kMode == 1 ? full_start[i] : 0;
+  const int hbase = kMode == 1 ? half_start[i] : 0;
+  int* srow = kMode == 2 ? slab + (long long)i * P.slab : nullptr;
+  const int s = cand_start[i], e = cand_start[i + 1];
+  for (int k0 = s; k0 < e; k0 += 32) {
+    const int kk = k0 + lane;
+    int k = 0;
+    bool in = false;
+    if (kk < e) {
+      k = cand_j[kk];
+      const float4 pj = pos32[k];
+      float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+      dx -= P.Lf * rintf(dx * P.invLf);
+      dy -= P.Lf * rintf(dy * P.invLf);
+      dz -= P.Lf * rintf(dz * P.invLf);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
+    }
+    emit_round<kMode>(in, i, k, lt, nfull, nhalf, fbase, hbase, srow, P.slab, full_j, full_ref, half_i, half_j);
+  }
+  if (kMode != 1 && lane == 0) {
+    full_cnt[i] = nfull;
+    half_cnt[i] = nhalf;
+    if (kMode == 2 && nhalf > P.slab) atomicOr(flags, 4);
+  }
+}
+
+// Largest squared minimum-image displacement of the caller's new positions
+// xyz [N][3] from the sorted reference positions ref, as float bits (non-
+// negative floats order like their bits) in *dmax (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_displacement(int n, const int* __restrict__ perm,
+                                                      const double* __restrict__ xyz,
+                                                      const double4_32a* __restrict__ ref, double L,
+                                                      int* __restrict__ dmax) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  float d2 = 0.f;
+  if (s < n) {
+    const int i = perm[s];
+    const double4_32a r = ref[s];
+    double dx = xyz[3 * i] - r.x, dy = xyz[3 * i + 1] - r.y, dz = xyz[3 * i + 2] - r.z;
+    dx -= L * rint(dx / L);
+    dy -= L * rint(dy / L);
+    dz -= L * rint(dz / L);
+    d2 = (float)(dx * dx + dy * dy + dz * dz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dmax, __float_as_int(d2));
+}
+
+// New positions into the sorted per-atom records (A.xyz, float copies), the
+// other inputs unchanged.
+__global__ void k_apply_positions(int n, const int* __restrict__ perm, const double* __restrict__ xyz, double L,
+                                  double4_32a* __restrict__ A, float4* __restrict__ pos32) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  double4_32a a = A[s];
+  a.x = x;
+  a.y = y;
+  a.z = z;
+  A[s] = a;
+  pos32[s] = make_float4((float)wrap_box(x, L), (float)wrap_box(y, L), (float)wrap_box(z, L), 0.f);
 }
 
 // Speculative fill (the lists were sized by an earlier call): the fill kernels
@@ -379,45 +476,14 @@ __global__ void __launch_bounds__(256) k_transpose_sort(int n, const int* __rest
 
 }  // namespace
 
-int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const double* dip,
-                          const double* quad, const double* alpha, const double* thole, const int* mol) {
+namespace {
+
+// Slab rows for the single-pass list: four times the mean number of owned
+// neighbours (half of 4/3 pi rc^3 n / L^3) within rc, at least 64; a row that
+// would overflow sends the build through the two-pass count / fill path.
+int list_params(amp_ctx* c, double rc, ListParams* P) {
   const int n = c->n;
-  const double L = c->cfg.box, rc = c->cfg.cutoff;
-  cudaStream_t st = c->stream;
-  // cells of edge >= rc / 2 (the neighbour search spans two cells per axis)
-  int nc = (int)floor(2.0 * L / (rc + 1e-6));
-  if (nc < 1) nc = 1;
-  if (nc > 1024) nc = 1024;
-  const int ncell = nc * nc * nc;
-  if (ncell > c->ncell_cap) {
-    dev_free(c, c->cell_count);
-    dev_free(c, c->cell_start);
-    dev_free(c, c->cell_fill);
-    c->cell_count = c->cell_start = c->cell_fill = nullptr;
-    int r;
-    if ((r = dev_alloc(c, &c->cell_count, ncell)) || (r = dev_alloc(c, &c->cell_start, ncell + 1)) ||
-        (r = dev_alloc(c, &c->cell_fill, ncell)))
-      return r;
-    c->ncell_cap = ncell;
-  }
-  c->nc = nc;
-  c->ncell = ncell;
-  int r;
-  if ((r = cuda_check(c, cudaMemsetAsync(c->cell_count, 0, sizeof(int) * ncell, st), "memset")) ||
-      (r = cuda_check(c, cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * ncell, st), "memset")) ||
-      (r = cuda_check(c, cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, st), "memset")))
-    return r;
-  c->n_launch += 10;  // cell_assign .. transpose_sort below
-  k_cell_assign<<<amp_blocks(n, 256), 256, 0, st>>>(n, xyz, L, nc, c->cell_of, c->cell_count);
-  k_scan_exclusive<<<1, 1024, 0, st>>>(c->cell_count, c->cell_start, ncell);
-  k_cell_scatter<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->cell_of, c->cell_start, c->cell_fill, c->slot_tmp);
-  k_cell_sort<<<amp_blocks((long long)ncell * 32, 256), 256, 0, st>>>(ncell, c->cell_start, c->slot_tmp, c->perm);
-  k_gather_atoms<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, q, dip, quad, alpha, thole, mol, L,
-                                                     c->inv_perm, c->atomA, c->atomB, c->atomC, c->atomD,
-                                                     c->pos32, c->cell_of, c->slot_tmp, c->alph, c->flags);
-  // slab rows for the single-pass list: four times the mean number of owned
-  // neighbours (half of 4/3 pi rc^3 n / L^3), at least 64; a row that would
-  // overflow sends the build through the two-pass count / fill path instead
+  const double L = c->cfg.box;
   const double mean_full = 4.0 / 3.0 * M_PI * rc * rc * rc * (double)n / (L * L * L);
   int slab = (int)std::ceil(2.0 * mean_full / 32.0) * 32;
   if (slab < 64) slab = 64;
@@ -426,27 +492,34 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
     dev_free(c, c->slab);
     c->slab = nullptr;
     c->slab_cap = 0;
+    int r;
     if ((r = dev_alloc(c, &c->slab, (long long)n * slab))) return r;
     c->slab_cap = (long long)n * slab;
   }
-  ListParams P;
-  P.n = n;
-  P.nc = nc;
-  P.slab = slab;
-  P.L = L;
-  P.rc2 = rc * rc;
-  P.Lf = (float)L;
-  P.invLf = (float)(1.0 / L);
-  P.lo2 = (float)(rc * rc - 0.01);
-  P.hi2 = (float)(rc * rc + 0.01);
+  P->n = n;
+  P->nc = c->nc;
+  P->slab = slab;
+  P->L = L;
+  P->rc2 = rc * rc;
+  P->Lf = (float)L;
+  P->invLf = (float)(1.0 / L);
+  P->lo2 = (float)(rc * rc - 0.01);
+  P->hi2 = (float)(rc * rc + 0.01);
+  return AMP_OK;
+}
+
+// After the counting (and slab) pass of the cell search or of the candidate
+// filter: row offsets, the fill, one host round trip. Lists sized by an
+// earlier call are filled before the counts reach the host; the fill kernels
+// skip themselves if the lists outgrew the buffers or a slab row overflowed,
+// and the two-pass path below redoes the fill (second pass of the same source).
+int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
+  const int n = c->n, slab = P.slab;
+  cudaStream_t st = c->stream;
   const int lb = amp_blocks((long long)n * 32, 256);
-  k_neighbours<2><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, c->full_cnt, c->half_cnt,
-                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->slab, c->flags);
+  int r;
   k_scan_exclusive<<<2, 1024, 0, st>>>(c->full_cnt, c->full_start, n, c->half_cnt, c->half_start);
   if ((r = cuda_check(c, cudaGetLastError(), "list count launch"))) return r;
-  // Lists sized by an earlier call: fill them before reading the counts (one
-  // host round trip instead of two); the kernels skip the fill if it would not
-  // fit or a slab row overflowed, and the two-pass path below redoes it.
   const bool speculative = c->cap_full > 0 && c->cap_half > 0;
   const ListGuard none{nullptr, n, 0, 0};
   if (speculative) {
@@ -493,13 +566,19 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
     c->cap_half = caph;
     c->cap_full = capf;
   }
-  if (c->hibuf[2] & 4)  // a slab row overflowed: second scan of the candidates
-    k_neighbours<1><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, nullptr, nullptr,
-                                        c->full_start, c->half_start, c->full_j, c->full_ref, c->half_i, c->half_j,
-                                        nullptr, nullptr);
-  else
+  if (c->hibuf[2] & 4) {  // a slab row overflowed: second pass over the same candidates
+    if (from_candidates)
+      k_filter<1><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->cand_start, c->cand_j, nullptr, nullptr,
+                                      c->full_start, c->half_start, c->full_j, c->full_ref, c->half_i, c->half_j,
+                                      nullptr, nullptr);
+    else
+      k_neighbours<1><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, nullptr, nullptr,
+                                          c->full_start, c->half_start, c->full_j, c->full_ref, c->half_i,
+                                          c->half_j, nullptr, nullptr);
+  } else {
     k_slab_copy<<<lb, 256, 0, st>>>(n, slab, c->slab, c->half_cnt, c->full_start, c->half_start, c->full_j,
                                     c->full_ref, c->half_i, c->half_j, none, c->flags);
+  }
   cudaMemsetAsync(c->full_cnt, 0, sizeof(int) * n, st);  // reused as the per-row slot counter
   k_transpose_scatter<<<amp_blocks(c->n_half, 256), 256, 0, st>>>(c->n_half, c->half_j, c->full_start, c->half_cnt,
                                                                   c->full_cnt, c->tr_tmp, none, c->half_start,
@@ -507,6 +586,126 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref,
                                       c->pos_tr, none, c->half_start, c->flags);
   return cuda_check(c, cudaGetLastError(), "list fill launch");
+}
+
+}  // namespace
+
+// Exact lists (cutoff) from the stored candidates (cutoff + skin).
+int filter_lists(amp_ctx* c) {
+  ListParams P;
+  int r;
+  if ((r = list_params(c, c->cfg.cutoff, &P))) return r;
+  c->n_launch += 6;
+  cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->stream);
+  k_filter<2><<<amp_blocks((long long)c->n * 32, 256), 256, 0, c->stream>>>(
+      P, c->pos32, c->atomA, c->cand_start, c->cand_j, c->full_cnt, c->half_cnt, nullptr, nullptr, nullptr, nullptr,
+      nullptr, nullptr, c->slab, c->flags);
+  return finish_lists(c, P, true);
+}
+
+int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const double* dip,
+                          const double* quad, const double* alpha, const double* thole, const int* mol) {
+  const int n = c->n;
+  const double L = c->cfg.box, rc = c->cfg.cutoff;
+  // with a skin the cell search collects the candidates within rc + skin
+  const double skin = c->skin, rlist = rc + skin;
+  cudaStream_t st = c->stream;
+  // cells of edge >= rlist / 2 (the neighbour search spans two cells per axis)
+  int nc = (int)floor(2.0 * L / (rlist + 1e-6));
+  if (nc < 1) nc = 1;
+  if (nc > 1024) nc = 1024;
+  const int ncell = nc * nc * nc;
+  if (ncell > c->ncell_cap) {
+    dev_free(c, c->cell_count);
+    dev_free(c, c->cell_start);
+    dev_free(c, c->cell_fill);
+    c->cell_count = c->cell_start = c->cell_fill = nullptr;
+    int r;
+    if ((r = dev_alloc(c, &c->cell_count, ncell)) || (r = dev_alloc(c, &c->cell_start, ncell + 1)) ||
+        (r = dev_alloc(c, &c->cell_fill, ncell)))
+      return r;
+    c->ncell_cap = ncell;
+  }
+  c->nc = nc;
+  c->ncell = ncell;
+  c->skin_built = 0.0;
+  int r;
+  if ((r = cuda_check(c, cudaMemsetAsync(c->cell_count, 0, sizeof(int) * ncell, st), "memset")) ||
+      (r = cuda_check(c, cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * ncell, st), "memset")) ||
+      (r = cuda_check(c, cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, st), "memset")))
+    return r;
+  c->n_launch += 6;  // cell_assign .. k_neighbours below
+  k_cell_assign<<<amp_blocks(n, 256), 256, 0, st>>>(n, xyz, L, nc, c->cell_of, c->cell_count);
+  k_scan_exclusive<<<1, 1024, 0, st>>>(c->cell_count, c->cell_start, ncell);
+  k_cell_scatter<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->cell_of, c->cell_start, c->cell_fill, c->slot_tmp);
+  k_cell_sort<<<amp_blocks((long long)ncell * 32, 256), 256, 0, st>>>(ncell, c->cell_start, c->slot_tmp, c->perm);
+  k_gather_atoms<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, q, dip, quad, alpha, thole, mol, L,
+                                                     c->inv_perm, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                     c->pos32, c->cell_of, c->slot_tmp, c->alph, c->flags);
+  ListParams P;
+  if ((r = list_params(c, rlist, &P))) return r;
+  const int lb = amp_blocks((long long)n * 32, 256);
+  k_neighbours<2><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, c->full_cnt, c->half_cnt,
+                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->slab, c->flags);
+  c->n_launch += 4;  // scan .. transpose_sort
+  if ((r = finish_lists(c, P, false))) return r;
+  if (skin <= 0.0) return AMP_OK;
+  // keep the candidates (rows of the list within rc + skin) and the positions
+  // they were found at, then filter the exact lists out of them
+  if (n + 1 > c->cand_start_cap) {
+    dev_free(c, c->cand_start);
+    dev_free(c, c->xref);
+    c->cand_start = nullptr;
+    c->xref = nullptr;
+    c->cand_start_cap = 0;
+    if ((r = dev_alloc(c, &c->cand_start, (long long)n + 1)) || (r = dev_alloc(c, &c->xref, (long long)n)))
+      return r;
+    c->cand_start_cap = n + 1;
+  }
+  if (c->n_full > c->cand_cap) {
+    dev_free(c, c->cand_j);
+    c->cand_j = nullptr;
+    c->cand_cap = 0;
+    const long long cap = c->n_full + c->n_full / 4 + 1024;
+    if ((r = dev_alloc(c, &c->cand_j, cap))) return r;
+    c->cand_cap = cap;
+  }
+  cudaMemcpyAsync(c->cand_start, c->full_start, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->cand_j, c->full_j, sizeof(int) * c->n_full, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->xref, c->atomA, sizeof(double4_32a) * n, cudaMemcpyDeviceToDevice, st);
+  if ((r = filter_lists(c))) return r;
+  c->skin_built = skin;
+  return AMP_OK;
+}
+
+// New positions for the current atoms: true in *reused if no atom moved more
+// than skin/2 (minimum image) since the candidates were found; then the exact
+// lists are filtered out of them (the pair terms and PME weights are the
+// caller's next steps). Otherwise nothing changes and *reused is false.
+int reuse_lists(amp_ctx* c, const double* xyz, bool* reused) {
+  *reused = false;
+  if (c->skin_built <= 0.0) return AMP_OK;
+  const int n = c->n;
+  cudaStream_t st = c->stream;
+  int r;
+  if ((r = cuda_check(c, cudaMemsetAsync(c->flags + 3, 0, sizeof(int), st), "memset"))) return r;
+  c->n_launch += 1;
+  k_displacement<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, c->xref, c->cfg.box, c->flags + 3);
+  cudaMemcpyAsync(&c->hibuf[3], c->flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if ((r = cuda_check(c, cudaStreamSynchronize(st), "displacement"))) return r;
+  const float d2 = [&] {
+    float f;
+    std::memcpy(&f, &c->hibuf[3], sizeof f);
+    return f;
+  }();
+  const double half = 0.5 * c->skin_built;
+  // the float maximum is rounded: keep a relative margin below (skin/2)^2
+  if (!((double)d2 <= half * half * (1.0 - 1e-5))) return AMP_OK;
+  c->n_launch += 1;
+  k_apply_positions<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, c->cfg.box, c->atomA, c->pos32);
+  if ((r = filter_lists(c))) return r;
+  *reused = true;
+  return AMP_OK;
 }
 
 }  // namespace amp
