@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-md", action="store_true", help="skip the list-reuse trajectory measurement")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement (request stream, rates) as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
@@ -53,6 +54,52 @@ def parse():
 
 
 # ------------------------------------------------------------------ serving
+
+def run_md_reuse(solver, sysm, dev, dev_in, stream, flush, frames: int = 24, skin: float = 1.0,
+                 step_sigma: float = 0.02, seed: int = 9):
+    """A random-walk trajectory (every atom moves N(0, step_sigma) Angstrom per
+    axis per frame; frames generated on the device before timing). Each frame:
+    new positions, permanent field, solve, energy. Timed twice on the same
+    frames: with a list skin (amp_update_positions, amp_set_system when an atom
+    has moved more than skin/2) and with amp_set_system on every frame."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(seed)
+    x0 = dev_in[0]
+    steps = torch.randn((frames,) + tuple(x0.shape), generator=g, device=dev, dtype=torch.float64) * step_sigma
+    traj = x0.unsqueeze(0) + torch.cumsum(steps, dim=0)
+    rest = dev_in[1:]
+    E0 = torch.empty_like(x0)
+
+    def run(p, reuse):
+        p.set_system(x0, *rest)
+        rebuilds, ms = 0, []
+        for f in range(frames):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if not (reuse and p.update_positions(traj[f])):
+                p.set_system(traj[f], *rest)
+                rebuilds += 1
+            p.permanent_field(out=E0)
+            mu, it, rms = p.solve(E0)
+            p.energy(mu, E0)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, rebuilds, mu
+
+    p = solver("fp64")
+    ms_full, _, mu_full = run(p, False)
+    p.set_list_skin(skin)
+    run(p, True)  # warm the reuse path (candidate buffers)
+    ms_reuse, rebuilds, mu_reuse = run(p, True)
+    p.close()
+    d = (mu_reuse - mu_full).double()
+    return {"frames": frames, "skin_angstrom": skin, "step_sigma_angstrom": step_sigma,
+            "ms_per_step_rebuild_every_frame": statistics.mean(ms_full),
+            "ms_per_step_reuse": statistics.mean(ms_reuse), "list_rebuilds_reuse": rebuilds,
+            "last_frame_mu_rms_diff_debye": float(4.8032047 * torch.sqrt((d * d).sum() / d.shape[0]))}
+
 
 def run_serving(n_requests: int, slots: int, rate_factors, warm: int = 40):
     """Poisson stream of solve requests (sizes log-uniform 64..4096 waters, half
@@ -442,6 +489,13 @@ def main():
     if not args.no_serving:
         serving = run_serving(args.requests, args.slots, [float(x) for x in args.rates.split(",")])
 
+    # ---- list reuse along a trajectory (not the headline step: every frame is
+    # new positions, so each step does its full work except the cell search,
+    # which the reuse path replaces by filtering the stored candidates)
+    md = None
+    if not args.no_md:
+        md = run_md_reuse(solver, sysm, dev, dev_in, stream, flush)
+
     cpu = None
     if not args.no_cpu_baseline:
         pairs_o, times, t_build = oracle_sample(w, 2, 0)
@@ -464,6 +518,7 @@ def main():
         "phase_ms_per_step": phase_ms,
         "mixed": mixed,
         "serving": serving,
+        "md_list_reuse": md,
         "roofline": roofline,
         "roofline_other": [r for r in rooflines if r is not roofline],
         "cpu_baseline": cpu,
