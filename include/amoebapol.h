@@ -115,7 +115,7 @@ int amp_set_list_skin(amp_ctx* ctx, double skin);
  * same float64 decision, as a new cell search), the pair terms and PME
  * weights are rebuilt, and *reused = 1. Otherwise nothing changes and the call
  * returns AMP_ERR_STALE: call amp_set_system. Synchronises the stream once
- * (twice when the lists are rebuilt). */
+ * (twice when it returns AMP_ERR_STALE). */
 int amp_update_positions(amp_ctx* ctx, const double* xyz, int* reused);
 
 /* Permanent-multipole field at every site, E0 [N][3] (real space with the

@@ -80,6 +80,8 @@ struct amp_ctx {
   int *cand_start = nullptr, *cand_j = nullptr;
   long long cand_cap = 0, cand_start_cap = 0;
   double4_32a* xref = nullptr;
+  double4_32a* abak = nullptr;  // positions before an update (put back if it is refused)
+  float4* pbak = nullptr;
   long long n_full = 0, n_half = 0, cap_full = 0, cap_half = 0;
   int* flags = nullptr;  // [0] bit 1 list transpose failure, bit 2 bad alpha, bit 4 slab overflow
   int* slab = nullptr;   // single-pass list: owned neighbours per atom, fixed row capacity

@@ -535,7 +535,7 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
   }
   cudaMemcpyAsync(&c->hibuf[0], c->full_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&c->hibuf[1], c->half_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, st);  // flags[0..3] -> hibuf[2..5]
   if ((r = cuda_check(c, cudaStreamSynchronize(st), "list count"))) return r;
   if (c->hibuf[2] & 2) return fail(c, AMP_ERR_ARG, "alpha must be > 0 for every site");
   c->n_full = c->hibuf[0];
@@ -596,7 +596,7 @@ int filter_lists(amp_ctx* c) {
   int r;
   if ((r = list_params(c, c->cfg.cutoff, &P))) return r;
   c->n_launch += 6;
-  cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->stream);
+  cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream);  // flags[3] (a displacement) is kept
   k_filter<2><<<amp_blocks((long long)c->n * 32, 256), 256, 0, c->stream>>>(
       P, c->pos32, c->atomA, c->cand_start, c->cand_j, c->full_cnt, c->half_cnt, nullptr, nullptr, nullptr, nullptr,
       nullptr, nullptr, c->slab, c->flags);
@@ -655,10 +655,14 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   if (n + 1 > c->cand_start_cap) {
     dev_free(c, c->cand_start);
     dev_free(c, c->xref);
+    dev_free(c, c->abak);
+    dev_free(c, c->pbak);
     c->cand_start = nullptr;
-    c->xref = nullptr;
+    c->xref = c->abak = nullptr;
+    c->pbak = nullptr;
     c->cand_start_cap = 0;
-    if ((r = dev_alloc(c, &c->cand_start, (long long)n + 1)) || (r = dev_alloc(c, &c->xref, (long long)n)))
+    if ((r = dev_alloc(c, &c->cand_start, (long long)n + 1)) || (r = dev_alloc(c, &c->xref, (long long)n)) ||
+        (r = dev_alloc(c, &c->abak, (long long)n)) || (r = dev_alloc(c, &c->pbak, (long long)n)))
       return r;
     c->cand_start_cap = n + 1;
   }
@@ -681,7 +685,10 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
 // New positions for the current atoms: true in *reused if no atom moved more
 // than skin/2 (minimum image) since the candidates were found; then the exact
 // lists are filtered out of them (the pair terms and PME weights are the
-// caller's next steps). Otherwise nothing changes and *reused is false.
+// caller's next steps). The positions are applied and filtered at once, the
+// largest displacement read with the list counts (one host round trip); if it
+// is too large, the previous positions and their lists are put back and
+// *reused is false (a second round trip, the rare case).
 int reuse_lists(amp_ctx* c, const double* xyz, bool* reused) {
   *reused = false;
   if (c->skin_built <= 0.0) return AMP_OK;
@@ -689,23 +696,23 @@ int reuse_lists(amp_ctx* c, const double* xyz, bool* reused) {
   cudaStream_t st = c->stream;
   int r;
   if ((r = cuda_check(c, cudaMemsetAsync(c->flags + 3, 0, sizeof(int), st), "memset"))) return r;
-  c->n_launch += 1;
+  c->n_launch += 2;
   k_displacement<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, c->xref, c->cfg.box, c->flags + 3);
-  cudaMemcpyAsync(&c->hibuf[3], c->flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if ((r = cuda_check(c, cudaStreamSynchronize(st), "displacement"))) return r;
-  const float d2 = [&] {
-    float f;
-    std::memcpy(&f, &c->hibuf[3], sizeof f);
-    return f;
-  }();
-  const double half = 0.5 * c->skin_built;
-  // the float maximum is rounded: keep a relative margin below (skin/2)^2
-  if (!((double)d2 <= half * half * (1.0 - 1e-5))) return AMP_OK;
-  c->n_launch += 1;
+  cudaMemcpyAsync(c->abak, c->atomA, sizeof(double4_32a) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->pbak, c->pos32, sizeof(float4) * n, cudaMemcpyDeviceToDevice, st);
   k_apply_positions<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, c->cfg.box, c->atomA, c->pos32);
   if ((r = filter_lists(c))) return r;
-  *reused = true;
-  return AMP_OK;
+  float d2;
+  std::memcpy(&d2, &c->hibuf[5], sizeof d2);  // flags[3], read with the counts
+  const double half = 0.5 * c->skin_built;
+  // the float maximum is rounded: keep a relative margin below (skin/2)^2
+  if ((double)d2 <= half * half * (1.0 - 1e-5)) {
+    *reused = true;
+    return AMP_OK;
+  }
+  cudaMemcpyAsync(c->atomA, c->abak, sizeof(double4_32a) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->pos32, c->pbak, sizeof(float4) * n, cudaMemcpyDeviceToDevice, st);
+  return filter_lists(c);
 }
 
 }  // namespace amp
