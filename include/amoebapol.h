@@ -118,6 +118,15 @@ int amp_set_list_skin(amp_ctx* ctx, double skin);
  * (twice when it returns AMP_ERR_STALE). */
 int amp_update_positions(amp_ctx* ctx, const double* xyz, int* reused);
 
+/* Warm start along a trajectory: order k (0 .. 6) keeps the last k + 2
+ * converged solutions of amp_solve_induced (cleared by amp_set_system, kept
+ * by amp_update_positions), and use_guess = 2 starts the next solve from
+ * their always-stable predictor-corrector extrapolation (Kolafa, J. Comput.
+ * Chem. 25, 335 (2004): mu_0 = sum_j B_j mu_{-j}, B_j = (-1)^(j+1) j
+ * C(2k+4, k+2-j) / C(2k+2, k+1)); the solve then converges to the same
+ * tolerance from there. -1 (the default) keeps no history. */
+int amp_set_predictor(amp_ctx* ctx, int order);
+
 /* Permanent-multipole field at every site, E0 [N][3] (real space with the
  * intramolecular exclusion + PME + self). The right-hand side of the
  * polarization equation (routine efld0_direct2). */
@@ -129,7 +138,10 @@ int amp_apply_T(amp_ctx* ctx, const double* mu, double* Tmu);
 
 /* Solve (1/alpha - T) mu = E0 by diagonal-preconditioned CG.
  * use_guess = 0: start from mu = alpha*E0 (mu is output only);
- * use_guess = 1: start from the mu passed in.
+ * use_guess = 1: start from the mu passed in;
+ * use_guess = 2: start from the predictor of amp_set_predictor over the
+ *   solutions this context has converged to since its last amp_set_system
+ *   (alpha*E0 while there are fewer than order + 2 of them).
  * On return mu holds the solution; *iters the number of iterations and
  * *rms_debye the final preconditioned-residual RMS (Debye). In AMP_MIXED the
  * final check is a float64 residual; if it is above tol, iterations continue.

@@ -78,6 +78,7 @@ def _load() -> ctypes.CDLL:
         "amp_polarization_energy_noalloc": (I, [I, P, P, P, P]),
         "amp_set_list_skin": (I, [P, D]),
         "amp_update_positions": (I, [P, P, ctypes.POINTER(I)]),
+        "amp_set_predictor": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -151,11 +152,16 @@ def amp_apply_T(ctx, mu, Tmu):
     _check(ctx, _lib.amp_apply_T(ctx, mu, Tmu))
 
 
-def amp_solve_induced(ctx, E0, mu, use_guess: bool):
+def amp_solve_induced(ctx, E0, mu, use_guess: int):
+    """use_guess: 0 start from alpha*E0, 1 from mu, 2 from the predictor."""
     it = ctypes.c_int(0)
     rms = ctypes.c_double(0.0)
-    code = _lib.amp_solve_induced(ctx, E0, mu, int(bool(use_guess)), ctypes.byref(it), ctypes.byref(rms))
+    code = _lib.amp_solve_induced(ctx, E0, mu, int(use_guess), ctypes.byref(it), ctypes.byref(rms))
     return code, it.value, rms.value
+
+
+def amp_set_predictor(ctx, order: int):
+    _check(ctx, _lib.amp_set_predictor(ctx, int(order)))
 
 
 def amp_polarization_energy(ctx, mu, E0) -> float:
@@ -279,6 +285,10 @@ class Polarization:
         self._keep = arrs  # inputs stay alive while the stream may read them
         self.generation += 1
 
+    def set_predictor(self, order: int):
+        """ASPC warm start of order k (-1: off) for solve(..., predict=True)."""
+        amp_set_predictor(self.ctx, order)
+
     def set_list_skin(self, skin: float):
         """Neighbour-list skin (Angstrom) used from the next set_system on."""
         amp_set_list_skin(self.ctx, skin)
@@ -311,12 +321,13 @@ class Polarization:
         amp_apply_T(self.ctx, mu.data_ptr(), out.data_ptr())
         return out
 
-    def solve(self, E0, mu=None, check=True):
-        """Returns (mu, iterations, final RMS in Debye)."""
+    def solve(self, E0, mu=None, check=True, predict=False):
+        """Returns (mu, iterations, final RMS in Debye). mu: initial guess;
+        predict: start from the predictor of set_predictor instead."""
         torch = self.torch
         E0 = self._dev(E0, torch.float64)
-        guess = mu is not None
-        mu = self._dev(mu, torch.float64).clone() if guess else torch.empty_like(E0)
+        guess = 2 if predict else (1 if mu is not None else 0)
+        mu = self._dev(mu, torch.float64).clone() if guess == 1 else torch.empty_like(E0)
         code, it, rms = amp_solve_induced(self.ctx, E0.data_ptr(), mu.data_ptr(), guess)
         if check:
             _check(self.ctx, code)

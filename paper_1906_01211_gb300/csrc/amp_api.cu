@@ -213,6 +213,7 @@ int amp_set_system(amp_ctx* c, int n, const double* xyz, const double* q, const 
                    const double* alpha, const double* thole, const int* mol) {
   if (!c) return AMP_ERR_ARG;
   c->have_system = false;
+  c->hist_len = c->hist_head = 0;  // a new system: no solution history
   if (n < 2 || !xyz || !q || !dip || !quad || !alpha || !thole || !mol)
     return fail(c, AMP_ERR_ARG, "amp_set_system: n >= 2 and all arrays are required");
   int r;
@@ -275,6 +276,14 @@ int amp_update_positions(amp_ctx* c, const double* xyz, int* reused) {
   return AMP_OK;
 }
 
+int amp_set_predictor(amp_ctx* c, int order) {
+  if (!c) return AMP_ERR_ARG;
+  if (order < -1 || order > 6) return fail(c, AMP_ERR_ARG, "amp_set_predictor: order in -1 .. 6");
+  c->pred_order = order;
+  c->hist_len = c->hist_head = 0;
+  return AMP_OK;
+}
+
 int amp_permanent_field(amp_ctx* c, double* E0) {
   if (!c) return AMP_ERR_ARG;
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
@@ -315,10 +324,17 @@ int amp_solve_induced(amp_ctx* c, const double* E0, double* mu, int use_guess, i
   if (!c) return AMP_ERR_ARG;
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!E0 || !mu) return fail(c, AMP_ERR_ARG, "null vector");
+  if (use_guess < 0 || use_guess > 2) return fail(c, AMP_ERR_ARG, "use_guess must be 0, 1 or 2");
   launch_to_sorted(c, E0, c->E0s);
-  if (use_guess) launch_to_sorted(c, mu, c->mu);
-  int r = solve(c, use_guess != 0);
+  bool guess = use_guess == 1;
+  if (use_guess == 1) launch_to_sorted(c, mu, c->mu);
+  if (use_guess == 2) guess = predict_guess(c);
+  int r = solve(c, guess);
   if (r != AMP_OK && r != AMP_ERR_NOT_CONVERGED) return r;
+  if (r == AMP_OK) {
+    const int e = push_history(c);
+    if (e) return e;
+  }
   launch_from_sorted(c, c->mu, mu);
   if (iters) *iters = c->stats.iters;
   if (rms) *rms = c->stats.rms;

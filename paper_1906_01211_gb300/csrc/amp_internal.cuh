@@ -177,6 +177,11 @@ struct amp_ctx {
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
   amp::Stats stats;
   int last_iters = 0;  // iterations of the last solve (first chunk of the next one)
+  // ASPC warm start: order (-1 off), ring of the last order + 2 converged
+  // dipole vectors (cell order), cleared by set_system
+  int pred_order = -1, hist_len = 0, hist_head = 0;
+  double4_32a* hist = nullptr;
+  long long hist_cap = 0;  // vectors x atoms allocated
   bool have_system = false;
 };
 
@@ -244,6 +249,8 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
 void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst);
 void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst);
 int solve(amp_ctx* c, bool use_guess);
+bool predict_guess(amp_ctx* c);  // c->mu from the solution history; false if too short
+int push_history(amp_ctx* c);     // c->mu into the solution history
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o);
 void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo);  // v = hi + lo
 

@@ -564,6 +564,76 @@ static int restart(amp_ctx* c, bool fp64_operator) {
   return AMP_OK;
 }
 
+// ASPC predictor (Kolafa, J. Comput. Chem. 25, 335 (2004)): the initial
+// dipoles of a solve along a trajectory from the last k + 2 converged ones,
+//   mu_0 = sum_{j=1}^{k+2} B_j mu_{-j},
+//   B_j = (-1)^{j+1} j C(2k+4, k+2-j) / C(2k+2, k+1)
+// (k = 0: 2 mu_{-1} - mu_{-2}; k = 1: 2.5 mu_{-1} - 2 mu_{-2} + 0.5 mu_{-3}).
+constexpr int kMaxHistory = 8;
+struct Predictor {
+  int nh;
+  const double4_32a* v[kMaxHistory];
+  double b[kMaxHistory];
+};
+
+__global__ void k_predict(int n, Predictor P, double4_32a* __restrict__ mu) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double x = 0.0, y = 0.0, z = 0.0;
+  for (int t = 0; t < P.nh; ++t) {
+    const double4_32a h = P.v[t][s];
+    x += P.b[t] * h.x;
+    y += P.b[t] * h.y;
+    z += P.b[t] * h.z;
+  }
+  mu[s] = make_double4_32a(x, y, z, 0.0);
+}
+
+static double binom(int a, int b) {
+  if (b < 0 || b > a) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= b; ++i) r = r * (double)(a - b + i) / (double)i;
+  return r;
+}
+
+bool predict_guess(amp_ctx* c) {
+  const int k = c->pred_order, m = k + 2;
+  if (k < 0 || c->hist_len < m) return false;
+  Predictor P{};
+  P.nh = m;
+  const int cap = (int)(c->hist_cap / (c->n > 0 ? c->n : 1));
+  for (int j = 1; j <= m; ++j) {  // j-th most recent
+    const int slot = ((c->hist_head - j) % cap + cap) % cap;
+    P.v[j - 1] = c->hist + (long long)slot * c->n;
+    P.b[j - 1] = ((j + 1) % 2 == 0 ? 1.0 : -1.0) * j * binom(2 * k + 4, k + 2 - j) / binom(2 * k + 2, k + 1);
+  }
+  c->n_launch += 1;
+  k_predict<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, P, c->mu);
+  return true;
+}
+
+int push_history(amp_ctx* c) {
+  const int k = c->pred_order;
+  if (k < 0) return AMP_OK;
+  const int m = k + 2;
+  if ((long long)m * c->n > c->hist_cap) {
+    dev_free(c, c->hist);
+    c->hist = nullptr;
+    c->hist_cap = 0;
+    int r;
+    if ((r = dev_alloc(c, &c->hist, (long long)m * c->n))) return r;
+    c->hist_cap = (long long)m * c->n;
+    c->hist_len = c->hist_head = 0;
+  }
+  const int cap = (int)(c->hist_cap / c->n);
+  c->hist_head %= cap;
+  cudaMemcpyAsync(c->hist + (long long)c->hist_head * c->n, c->mu, sizeof(double4_32a) * c->n,
+                  cudaMemcpyDeviceToDevice, c->stream);
+  c->hist_head = (c->hist_head + 1) % cap;
+  if (c->hist_len < m) ++c->hist_len;
+  return AMP_OK;
+}
+
 int solve(amp_ctx* c, bool use_guess) {
   const bool mixed = c->cfg.precision == AMP_MIXED;
   cudaStream_t st = c->stream;

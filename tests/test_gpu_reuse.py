@@ -132,3 +132,62 @@ def test_skin_arguments_are_checked():
     # no skin at set_system: every update is refused
     assert not s.update_positions(w.system().xyz)
     s.close()
+
+
+def test_predictor_of_a_repeated_solution_starts_converged():
+    """The ASPC coefficients sum to one: with the same system solved k + 2
+    times the predicted start is the solution, and the next solve takes no
+    iteration; before the history is full the start is alpha*E0."""
+    w = WATER_648
+    s = solver(w.L, w.cutoff, w.beta, w.grid, 1e-8)
+    sysm = w.system()
+    s.set_synthetic(sysm)
+    s.set_predictor(1)  # three solutions: 2.5 mu_-1 - 2 mu_-2 + 0.5 mu_-3
+    E0 = s.permanent_field()
+    mu_cold, it_cold, _ = s.solve(E0)
+    mu1, it1, _ = s.solve(E0, predict=True)  # history 1 < 3: cold start again
+    assert it1 == it_cold
+    s.solve(E0, predict=True)
+    mu3, it3, _ = s.solve(E0, predict=True)  # history 3: predicted = mu
+    assert it3 == 0
+    d = (mu3 - mu_cold).cpu().numpy()
+    assert DEBYE * np.sqrt((d * d).sum() / sysm.n) < 1e-8
+    # a new system clears the history
+    s.set_synthetic(sysm)
+    E0 = s.permanent_field()
+    _, it4, _ = s.solve(E0, predict=True)
+    assert it4 == it_cold
+    s.close()
+
+
+def test_predictor_along_a_trajectory_matches_the_oracle():
+    """Frames of a random walk through list reuse, each solved from the
+    predictor (order 0 = linear extrapolation once two solutions exist):
+    every frame converges to the oracle's dipoles, in fewer iterations than a
+    cold start once the history is full."""
+    from paper_1906_01211_gb300 import amoebapol as ap
+    w = WATER_648
+    setup = Setup(box=w.L, cutoff=w.cutoff, beta=w.beta, grid=w.grid, order=5)
+    rng = np.random.default_rng(91)
+    s = solver(w.L, w.cutoff, w.beta, w.grid, 1e-8)
+    s.set_list_skin(1.0)
+    s.set_predictor(0)
+    sysm = w.system()
+    s.set_synthetic(sysm)
+    xyz = sysm.xyz.copy()
+    iters = []
+    for f in range(5):
+        if f:
+            xyz = xyz + rng.normal(size=xyz.shape) * 0.01
+            assert s.update_positions(xyz)
+        E0 = s.permanent_field()
+        mu, it, _ = s.solve(E0, predict=True)
+        iters.append(it)
+        op = Operator(moved(sysm, xyz), setup)
+        mu_ref, it_ref, _ = solve(op, op.permanent_field(), 1e-8)
+        d = mu.cpu().numpy() - mu_ref
+        assert DEBYE * np.sqrt((d * d).sum() / sysm.n) < 1e-7
+    assert max(iters[2:]) < iters[0]
+    with pytest.raises(ap.AmpError):
+        s.set_predictor(7)
+    s.close()
