@@ -56,23 +56,26 @@ def parse():
 # ------------------------------------------------------------------ serving
 
 def run_md_reuse(solver, sysm, dev, dev_in, stream, flush, frames: int = 24, skin: float = 1.0,
-                 step_sigma: float = 0.02, seed: int = 9):
-    """A random-walk trajectory (every atom moves N(0, step_sigma) Angstrom per
-    axis per frame; frames generated on the device before timing). Each frame:
-    new positions, permanent field, solve, energy. Timed twice on the same
-    frames: with a list skin (amp_update_positions, amp_set_system when an atom
-    has moved more than skin/2) and with amp_set_system on every frame."""
+                 speed: float = 0.01, seed: int = 9, order: int = 2):
+    """An MD-like trajectory: every atom moves at a constant random velocity,
+    N(0, speed) Angstrom per axis per frame (frames generated on the device
+    before timing). Each frame: new positions, permanent field, solve, energy.
+    Timed three times on the same frames: amp_set_system on every frame with a
+    cold start; with a list skin (amp_update_positions, amp_set_system when an
+    atom has moved more than skin/2) and a cold start; the same with the ASPC
+    warm start of the given order."""
     import torch
     g = torch.Generator(device=dev).manual_seed(seed)
     x0 = dev_in[0]
-    steps = torch.randn((frames,) + tuple(x0.shape), generator=g, device=dev, dtype=torch.float64) * step_sigma
-    traj = x0.unsqueeze(0) + torch.cumsum(steps, dim=0)
+    vel = torch.randn(tuple(x0.shape), generator=g, device=dev, dtype=torch.float64) * speed
+    traj = x0.unsqueeze(0) + vel.unsqueeze(0) * torch.arange(1, frames + 1, device=dev,
+                                                              dtype=torch.float64).view(-1, 1, 1)
     rest = dev_in[1:]
     E0 = torch.empty_like(x0)
 
-    def run(p, reuse):
+    def run(p, reuse, predict):
         p.set_system(x0, *rest)
-        rebuilds, ms = 0, []
+        rebuilds, ms, its = 0, [], []
         for f in range(frames):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -81,23 +84,29 @@ def run_md_reuse(solver, sysm, dev, dev_in, stream, flush, frames: int = 24, ski
                 p.set_system(traj[f], *rest)
                 rebuilds += 1
             p.permanent_field(out=E0)
-            mu, it, rms = p.solve(E0)
+            mu, it, rms = p.solve(E0, predict=predict)
             p.energy(mu, E0)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        return ms, rebuilds, mu
+            its.append(it)
+        return ms, rebuilds, its, mu
 
     p = solver("fp64")
-    ms_full, _, mu_full = run(p, False)
+    ms_full, _, it_full, mu_full = run(p, False, False)
     p.set_list_skin(skin)
-    run(p, True)  # warm the reuse path (candidate buffers)
-    ms_reuse, rebuilds, mu_reuse = run(p, True)
+    run(p, True, False)  # warm the reuse path (candidate buffers)
+    ms_reuse, rebuilds, it_reuse, _ = run(p, True, False)
+    p.set_predictor(order)
+    ms_pred, rebuilds_p, it_pred, mu_pred = run(p, True, True)
     p.close()
-    d = (mu_reuse - mu_full).double()
-    return {"frames": frames, "skin_angstrom": skin, "step_sigma_angstrom": step_sigma,
+    d = (mu_pred - mu_full).double()
+    return {"frames": frames, "skin_angstrom": skin, "speed_angstrom_per_frame": speed,
             "ms_per_step_rebuild_every_frame": statistics.mean(ms_full),
-            "ms_per_step_reuse": statistics.mean(ms_reuse), "list_rebuilds_reuse": rebuilds,
+            "mean_iters_cold": statistics.mean(it_full),
+            "ms_per_step_list_reuse": statistics.mean(ms_reuse), "list_rebuilds": rebuilds,
+            "ms_per_step_list_reuse_aspc": statistics.mean(ms_pred), "aspc_order": order,
+            "mean_iters_aspc": statistics.mean(it_pred), "list_rebuilds_aspc": rebuilds_p,
             "last_frame_mu_rms_diff_debye": float(4.8032047 * torch.sqrt((d * d).sum() / d.shape[0]))}
 
 
