@@ -127,6 +127,10 @@ int amp_update_positions(amp_ctx* ctx, const double* xyz, int* reused);
  * tolerance from there. -1 (the default) keeps no history. */
 int amp_set_predictor(amp_ctx* ctx, int order);
 
+/* The predictor's coefficients B_1 .. B_{order+2} into b (host memory; no
+ * context, no GPU). AMP_ERR_ARG for an order outside 0 .. 6. */
+int amp_predictor_coefficients(int order, double* b);
+
 /* Permanent-multipole field at every site, E0 [N][3] (real space with the
  * intramolecular exclusion + PME + self). The right-hand side of the
  * polarization equation (routine efld0_direct2). */

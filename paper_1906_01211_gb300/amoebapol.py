@@ -79,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "amp_set_list_skin": (I, [P, D]),
         "amp_update_positions": (I, [P, P, ctypes.POINTER(I)]),
         "amp_set_predictor": (I, [P, I]),
+        "amp_predictor_coefficients": (I, [I, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +163,14 @@ def amp_solve_induced(ctx, E0, mu, use_guess: int):
 
 def amp_set_predictor(ctx, order: int):
     _check(ctx, _lib.amp_set_predictor(ctx, int(order)))
+
+
+def amp_predictor_coefficients(order: int) -> list[float]:
+    b = (ctypes.c_double * 8)()
+    code = _lib.amp_predictor_coefficients(int(order), b)
+    if code != AMP_OK:
+        raise AmpError(code, "order must be 0 .. 6")
+    return [b[j] for j in range(order + 2)]
 
 
 def amp_polarization_energy(ctx, mu, E0) -> float:

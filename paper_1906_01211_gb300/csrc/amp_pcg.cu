@@ -601,11 +601,11 @@ bool predict_guess(amp_ctx* c) {
   if (k < 0 || c->hist_len < m) return false;
   Predictor P{};
   P.nh = m;
+  amp_predictor_coefficients(k, P.b);
   const int cap = (int)(c->hist_cap / (c->n > 0 ? c->n : 1));
   for (int j = 1; j <= m; ++j) {  // j-th most recent
     const int slot = ((c->hist_head - j) % cap + cap) % cap;
     P.v[j - 1] = c->hist + (long long)slot * c->n;
-    P.b[j - 1] = ((j + 1) % 2 == 0 ? 1.0 : -1.0) * j * binom(2 * k + 4, k + 2 - j) / binom(2 * k + 2, k + 1);
   }
   c->n_launch += 1;
   k_predict<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, P, c->mu);
@@ -692,3 +692,11 @@ int energy(amp_ctx* c, const double* mu, const double* E0, double* U) {
 }
 
 }  // namespace amp
+
+extern "C" int amp_predictor_coefficients(int order, double* b) {
+  if (order < 0 || order > 6 || !b) return AMP_ERR_ARG;
+  const int k = order;
+  for (int j = 1; j <= k + 2; ++j)
+    b[j - 1] = ((j + 1) % 2 == 0 ? 1.0 : -1.0) * j * amp::binom(2 * k + 4, k + 2 - j) / amp::binom(2 * k + 2, k + 1);
+  return AMP_OK;
+}

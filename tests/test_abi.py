@@ -44,3 +44,23 @@ def test_null_context_calls_fail_cleanly(lib_path):
     from paper_1906_01211_gb300 import amoebapol as ap
     assert ap._lib.amp_set_system(None, 3, None, None, None, None, None, None, None) == ap.AMP_ERR_ARG
     assert ap.amp_last_error(None) == "null context"
+
+
+def test_predictor_coefficients(lib_path):
+    """ASPC coefficients (Kolafa, J. Comput. Chem. 25, 335 (2004)): the values
+    of orders 0..2 printed there, and for every order the two properties that
+    make the predictor consistent: the coefficients sum to one and the
+    predictor is exact on data linear in time (sum of -j B_j = 0)."""
+    from fractions import Fraction as F
+    from paper_1906_01211_gb300 import amoebapol as ap
+    published = {0: [2, -1], 1: [F(5, 2), -2, F(1, 2)], 2: [F(14, 5), F(-14, 5), F(6, 5), F(-1, 5)]}
+    for k, want in published.items():
+        got = ap.amp_predictor_coefficients(k)
+        assert len(got) == k + 2
+        assert all(abs(g - float(w)) < 1e-14 for g, w in zip(got, want))
+    for k in range(7):
+        b = ap.amp_predictor_coefficients(k)
+        assert abs(sum(b) - 1.0) < 1e-13
+        assert abs(sum(-(j + 1) * bj for j, bj in enumerate(b))) < 1e-12
+    with pytest.raises(ap.AmpError):
+        ap.amp_predictor_coefficients(7)
