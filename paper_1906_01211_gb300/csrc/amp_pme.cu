@@ -58,43 +58,30 @@ __device__ __forceinline__ void bspline5(double f, double s, double w[4][kOrder]
   }
 }
 
-// kcount (float64 path): atoms per base cell k0, and fx_info[1] = the largest count.
+// Float64 B-spline weights (derivatives 0..3, which the force kernels need),
+// with their float32 copy when theta32 is given (mixed path). The base
+// indices are the same as those of k_theta_df (same float64 operations).
 __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int K, double* __restrict__ theta,
-                        float* __restrict__ theta32, float2* __restrict__ theta_df, int4* __restrict__ gbase,
-                        int* __restrict__ kcount, int* __restrict__ fx_info) {
+                        float* __restrict__ theta32) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double4_32a a = A[s];
   const double xs[3] = {a.x, a.y, a.z};
   const double sc = (double)K / L;
-  int base[3];
   double* th = theta + (long long)kTh * s;
   for (int ax = 0; ax < 3; ++ax) {
     double u = xs[ax] * sc;
-    u = u - (double)K * floor(u / (double)K);
+    u = u - (double)K * floor(u * (1.0 / (double)K));
     if (u >= (double)K) u -= (double)K;
     if (u < 0.0) u += (double)K;
     const double k0 = floor(u);
-    base[ax] = (int)k0;
     double w[4][kOrder];
     bspline5(u - k0, sc, w);
     for (int d = 0; d < 4; ++d)
       for (int t = 0; t < kOrder; ++t) {
         th[(ax * 4 + d) * kOrder + t] = w[d][t];
         if (theta32) theta32[(long long)kTh * s + (ax * 4 + d) * kOrder + t] = (float)w[d][t];
-        if (theta_df && d < 2) {
-          const float h = __double2float_rn(w[d][t]);
-          theta_df[(long long)kThDf * s + (ax * 2 + d) * kOrder + t] =
-              make_float2(h, __double2float_rn(w[d][t] - (double)h));
-        }
       }
-  }
-  gbase[s] = make_int4(base[0], base[1], base[2], 0);
-  if (kcount) {
-    const int cnt = atomicAdd(kcount + ((long long)base[0] * K + base[1]) * K + base[2], 1) + 1;
-    const unsigned active = __activemask();
-    const int m = __reduce_max_sync(active, cnt);
-    if ((threadIdx.x & 31) == __ffs(active) - 1) atomicMax(fx_info + 1, m);
   }
 }
 
@@ -807,8 +794,7 @@ void launch_pme_theta(amp_ctx* c) {
 void pme_theta64(amp_ctx* c) {
   if (c->theta64_valid) return;
   c->n_launch += 1;
-  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32,
-                                                       nullptr, c->gbase, nullptr, nullptr);
+  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32);
   c->theta64_valid = true;
 }
 
