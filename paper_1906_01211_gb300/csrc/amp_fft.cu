@@ -11,7 +11,7 @@
 //     (rows y and y + K/2), forward z transforms, the two half spectra
 //     separated, then forward y transforms; the plane's half spectrum goes
 //     to H[x][mz][my] (my in bit-reversed order);
-//   B (lines along x, four neighbouring my per block): forward x transform,
+//   B (lines along x, two neighbouring my per block): forward x transform,
 //     times G, inverse x transform, in place;
 //   C (one cluster of CTAs per x plane): inverse y transforms, the two real z lines
 //     rebuilt from their half spectra as one complex line, inverse z
@@ -189,7 +189,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
 // Pass B: lines along x of H[x][mz][my], kLinesB neighbouring my per block;
 // forward, times G(mx, my, mz), inverse. Position t along x holds
 // mx = bitrev(t); position p along y holds my = bitrev(p).
-constexpr int kLinesB = 4;
+constexpr int kLinesB = 2;
 template <int K>
 __global__ void __launch_bounds__(32 * kLinesB) k_fft_x_conv(float4* __restrict__ H, const float4* __restrict__ tw_g,
                                                             const float2* __restrict__ Gh,
