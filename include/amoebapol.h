@@ -52,10 +52,11 @@ extern "C" {
 #define AMP_ERR_STALE (-8)         /* amp_update_positions: an atom moved more than skin/2 */
 
 #define AMP_FP64 0   /* all pair math, grids and FFTs in float64 */
-#define AMP_MIXED 1  /* float32 pair geometry/damping and PME, float64
+#define AMP_MIXED 1  /* float32 pair geometry/damping and a float32
+                        operator input (PME as in AMP_FP64), float64
                         accumulation, scalars, self terms and a final float64
-                        residual check ("decreasing precision", paper
-                        Section "Conclusion") */
+                        residual check (lower precision, paper Section
+                        "Conclusion") */
 
 typedef struct amp_ctx amp_ctx;
 

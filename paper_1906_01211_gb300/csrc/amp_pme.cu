@@ -10,11 +10,12 @@
 //   phi = unnormalised C2R( G . R2C(Q) ),
 //   G(m) = exp(-pi^2 m~^2/beta^2) / (pi V m~^2) |b1 b2 b3|^2, G(0) = 0;
 //   E_i = -sum_g grad W_i(g) phi(g).
-// The 3D FFTs are cuFFT (library call) or, for the float64 path on
-// power-of-two grids, the double-float FFT of amp_fft.cu. Spreading of the
-// permanent multipoles uses float64 (float32 in the mixed path) atomics; the
-// float64 path spreads dipoles in double-float into a 64-bit fixed-point grid.
-// Gathering runs one group of lanes per atom.
+// Both precisions spread (permanent multipoles once per geometry, dipoles at
+// every T*mu; the mixed path's dipoles are its float32 operator input) in
+// double-float into a 64-bit fixed-point grid, transform it with the
+// double-float FFT of amp_fft.cu on power-of-two grids (else cuFFT float64, a
+// library call, and a split), and gather in double-float. The force kernels'
+// potentials use float64 (float32 in the mixed path) atomics and cuFFT.
 // |b(m)|^2 = 1/|sum_{k=0}^{3} M5(k+1) e^{2 pi i m k/K}|^2; where that sum
 // vanishes (m = K/2, even K) the mean of the neighbours m-1, m+1 is used.
 #include <cmath>
