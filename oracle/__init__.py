@@ -18,7 +18,9 @@ standard Ewald / smooth-PME literature):
   and Section "Sequential performance": the solver calls the product about
   nine times per step), here preconditioned conjugate gradients;
 * the polarization energy and its gradients (paper, Section "Hotspots":
-  ``epolar1``).
+  ``epolar1``);
+* the permanent-multipole energy and its gradients (paper, Section
+  "Hotspots": ``empole1``).
 
 Modules:
   ewald      screened Coulomb kernels B_n and Thole damping
@@ -29,6 +31,7 @@ Modules:
   solver     operator assembly, PCG, dense Cholesky solve
   energy     polarization energy
   forces     gradients of the polarization energy (positions, multipoles)
+  multipole  permanent-multipole energy and gradients (derivative tensors)
 
 Every function works in float64 numpy. Pins that tie it to the physics
 (closed forms, brute force, invariants) live in ``tests/test_oracle_*.py``.

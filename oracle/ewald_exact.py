@@ -112,3 +112,42 @@ class ExactEwald:
         def rho(k):
             return -1j * (mu @ k.T)
         return real + self._recip_field(rho) + self.selfc * mu
+
+
+def multipole_energy_exact(sys, beta, rmax=None, nimg=None) -> float:
+    """Ewald energy of the permanent multipoles by direct sums (kcal/mol).
+
+    real: 1/2 sum over ordered (i, j, n) of U_ij(x_i - x_j - n L), r < rmax,
+    skipping (j = i, n = 0), same-molecule pairs excluded at n = 0 only, with
+    U_ij the pair energy of ``multipole`` on the screened kernels;
+    reciprocal: (1/(2 pi V)) sum_{m != 0} exp(-pi^2 m~^2/beta^2)/m~^2 |S(m)|^2
+    with S(m) = sum_j rho_j(k) exp(-i k.x_j) (rho as above);
+    plus the self and neutralising-background terms of ``multipole``.
+    """
+    from .multipole import _contract, _full, _kernels, _moments, derivative_tensor, self_and_background
+    from .setup import COULOMB, Setup
+
+    L = sys.box
+    if rmax is None:
+        rmax = 7.5 / beta
+    if nimg is None:
+        nimg = int(np.ceil(rmax / L)) + 1
+    i, j, r, zero = _image_pairs(sys.xyz, L, rmax, nimg)
+    dist = np.sqrt((r * r).sum(1))
+    excl = (zero & (sys.mol[i] == sys.mol[j])).astype(np.float64)
+    b = _kernels(dist, excl, beta, 4)
+    T = [derivative_tensor(r, b, k) for k in range(5)]
+    Mi, Mj = _moments(sys, i), _moments(sys, j)
+    u_real = 0.0
+    for k in range(3):
+        for l in range(3):
+            u_real += (-1.0) ** l * float(_full(Mi[k], _contract(T[k + l], Mj[l])).sum())
+    u_real *= 0.5
+    mt, f = _kvectors(L, beta)
+    k = 2.0 * np.pi * mt
+    th = quad_matrix(sys.quad)
+    rho = sys.q[:, None] - 1j * (sys.dip @ k.T) - np.einsum("ma,nab,mb->nm", k, th, k) / 3.0
+    S = (rho * np.exp(-1j * sys.xyz @ k.T)).sum(0)
+    u_rec = float((f * np.abs(S) ** 2).sum()) / (2.0 * np.pi * L ** 3)
+    u_self = self_and_background(sys, Setup(box=L, beta=beta))[0]
+    return COULOMB * (u_real + u_rec + u_self)
