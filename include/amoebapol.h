@@ -169,6 +169,27 @@ int amp_polarization_energy(amp_ctx* ctx, const double* mu, const double* E0, do
  * geometry of the current system; allocates its buffers on the first call. */
 int amp_forces(amp_ctx* ctx, const double* mu, double* F, double* gq, double* gdip, double* gquad);
 
+/* Energy of the permanent multipoles with each other and its gradients (paper,
+ * Section "Hotspots": routine empole1 computes this energy and its forces).
+ * Ewald sum with tin-foil boundary:
+ *   U = C [ sum over unique pairs within the cutoff of U_ij  (minimum image)
+ *         + 1/2 sum_g Q(g) phi(g)                            (smooth PME)
+ *         - beta/sqrt(pi) sum_i (q_i^2 + 2 beta^2/3 |d_i|^2 + 8 beta^4/45 Theta_i:Theta_i)
+ *         - pi Q_tot^2 / (2 V beta^2) ],
+ * U_ij = (q_i + d_i.grad + Theta_i:grad grad/3)(q_j - d_j.grad + Theta_j:grad grad/3) B_0
+ * at r = x_i - x_j with the Ewald-screened kernels, minus the bare ones for two
+ * sites of one molecule (excluded pair); no Thole damping.
+ *   U     kcal/mol into *U (host); may be NULL;
+ *   F     [N][3] -dU/dr (kcal/mol/Angstrom); gq [N] dU/dq; gdip [N][3] dU/dd;
+ *   gquad [N][6] dU/dTheta for the six stored components, each off-diagonal
+ *         standing for two entries, with the mean of the three diagonal ones
+ *         removed (quadrupoles are traceless, so only traceless changes
+ *         exist); each may be NULL to skip it (at least one output).
+ * Caller order, device pointers except U. Float64 arithmetic in both precision
+ * modes. Periodic contexts only (AMP_ERR_ARG for a cluster). Uses the geometry
+ * and lists of the current system; allocates its buffers on the first call. */
+int amp_multipole_energy(amp_ctx* ctx, double* U, double* F, double* gq, double* gdip, double* gquad);
+
 /* Number of unique atom pairs within the cutoff of the current system. */
 int amp_pair_count(const amp_ctx* ctx, long long* n_pairs);
 
@@ -183,7 +204,7 @@ int amp_pair_count(const amp_ctx* ctx, long long* n_pairs);
 #define AMP_PHASE_PCG 6         /* fused PCG vector updates and reductions */
 #define AMP_PHASE_FP64_CHECK 7  /* mixed path: float64 residual check */
 #define AMP_PHASE_ENERGY 8      /* energy reduction */
-#define AMP_PHASE_FORCES 9      /* adjoint backward: forces and moment gradients */
+#define AMP_PHASE_FORCES 9      /* forces and moment gradients (polarization, multipoles) */
 #define AMP_NPHASE 10
 
 /* enable != 0: start recording (clears totals); 0: stop. */

@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "amp_polarization_energy": (I, [P, P, P, ctypes.POINTER(D)]),
         "amp_pair_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
         "amp_forces": (I, [P, P, P, P, P, P]),
+        "amp_multipole_energy": (I, [P, ctypes.POINTER(D), P, P, P, P]),
         "amp_profile": (I, [P, I]),
         "amp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]),
         "amp_last_solve_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -181,6 +182,13 @@ def amp_polarization_energy(ctx, mu, E0) -> float:
 
 def amp_forces(ctx, mu, F, gq=None, gdip=None, gquad=None):
     _check(ctx, _lib.amp_forces(ctx, mu, F, gq, gdip, gquad))
+
+
+def amp_multipole_energy(ctx, F=None, gq=None, gdip=None, gquad=None) -> float:
+    """Permanent-multipole energy (kcal/mol); gradients into the non-null device pointers."""
+    u = ctypes.c_double(0.0)
+    _check(ctx, _lib.amp_multipole_energy(ctx, ctypes.byref(u), F, gq, gdip, gquad))
+    return u.value
 
 
 def amp_pair_count(ctx) -> int:
@@ -359,6 +367,21 @@ class Polarization:
         gt = torch.empty((n, 6), dtype=torch.float64, device="cuda")
         amp_forces(self.ctx, mu.data_ptr(), F.data_ptr(), gq.data_ptr(), gd.data_ptr(), gt.data_ptr())
         return F, gq, gd, gt
+
+    def multipole_energy(self, gradients: bool = True):
+        """Permanent-multipole energy U (kcal/mol) and, if asked, (F, dU/dq, dU/dd,
+        dU/dTheta6) of the current system; quadrupole gradients projected onto
+        traceless changes."""
+        if not gradients:
+            return amp_multipole_energy(self.ctx)
+        torch = self.torch
+        n = self.n
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gq = torch.empty((n,), dtype=torch.float64, device="cuda")
+        gd = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gt = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        U = amp_multipole_energy(self.ctx, F.data_ptr(), gq.data_ptr(), gd.data_ptr(), gt.data_ptr())
+        return U, F, gq, gd, gt
 
     def pair_count(self) -> int:
         return amp_pair_count(self.ctx)

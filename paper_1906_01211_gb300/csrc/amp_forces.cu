@@ -26,8 +26,8 @@
 namespace amp {
 namespace {
 
-constexpr int kPairStride = 24;  // force(3), pad, side0 grads(10), side1 grads(10)
-constexpr int kRecipStride = 16;  // force(3), gq, gd(3), gquad(6), pad(3)
+constexpr int kPairStride = kForcePairStride;   // force(3), pad, side0 grads(10), side1 grads(10)
+constexpr int kRecipStride = kForceAtomStride;  // force(3), gq, gd(3), gquad(6), pad(3)
 constexpr int kTh = 3 * 4 * kOrder;
 constexpr int kGroup = 8;
 
@@ -346,13 +346,10 @@ __global__ void __launch_bounds__(256) k_force_rows(int n, const int* __restrict
 
 }  // namespace
 
-int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out);
-
-int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt) {
-  const bool fp32 = c->cfg.precision == AMP_MIXED;
+// Per-pair (24 doubles) and per-atom (16 doubles) backward buffers, sized
+// with the lists, and the second float64 grid.
+int force_buffers(amp_ctx* c) {
   int r;
-  pme_theta64(c);  // the float64 B-spline weights (float64 path: built on first use)
-  // per-pair and per-atom buffers, sized with the lists
   if (c->force_pair_cap < c->cap_half) {
     dev_free(c, c->force_pair);
     c->force_pair = nullptr;
@@ -367,6 +364,15 @@ int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, doub
   }
   const long long ng = (long long)c->K * c->K * c->K;
   if (!c->grid64b && (r = dev_alloc(c, &c->grid64b, ng))) return r;
+  return AMP_OK;
+}
+
+int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt) {
+  const bool fp32 = c->cfg.precision == AMP_MIXED;
+  int r;
+  pme_theta64(c);  // the float64 B-spline weights (float64 path: built on first use)
+  if ((r = force_buffers(c))) return r;
+  const long long ng = (long long)c->K * c->K * c->K;
   if (fp32 && !c->grid32b && (r = dev_alloc(c, &c->grid32b, ng))) return r;
   FGeom g;
   const double b = c->cfg.ewald_beta;

@@ -41,6 +41,8 @@ constexpr double kDebye = 4.8032047;
 constexpr double kCoulomb = 332.0637133;
 constexpr double kSqrtPi = 1.7724538509055160273;
 constexpr int kRowGroup = 16;       // lanes that share one neighbour row
+constexpr int kForcePairStride = 24;  // backward per-pair record (doubles)
+constexpr int kForceAtomStride = 16;  // backward per-atom reciprocal record (doubles)
 constexpr int kReduceBlocks = 296;  // 2 x 152 SMs: blocks of the PCG kernels
 constexpr int kReduceThreads = 256;
 
@@ -165,6 +167,8 @@ struct amp_ctx {
   int force_atom_cap = 0;
   double* grid64b = nullptr;
   float* grid32b = nullptr;
+  double* mpole_e = nullptr;  // per-atom permanent-multipole energy (sorted order)
+  int mpole_e_cap = 0;
 
   // isolated cluster (box == 0): all-pairs kernels, column-slice partial sums
   bool cluster = false;
@@ -256,6 +260,11 @@ void launch_split(amp_ctx* c, const double4_32a* v, float4* hi, float4* lo);  //
 
 // backward (amp_forces.cu)
 int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt);
+int force_buffers(amp_ctx* c);
+// float64 (or float32) grid potential of the dipoles v, or of the permanent
+// multipoles (multipoles = true), through cuFFT: the backward kernels' grids
+int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out);
+int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, double* gt);
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
 
 // isolated clusters (amp_cluster.cu)
