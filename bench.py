@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-md", action="store_true", help="skip the list-reuse trajectory measurement")
+    ap.add_argument("--no-multipole", action="store_true", help="skip the permanent-multipole energy measurement")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement (request stream, rates) as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
@@ -108,6 +109,35 @@ def run_md_reuse(solver, sysm, dev, dev_in, stream, flush, frames: int = 24, ski
             "ms_per_step_list_reuse_aspc": statistics.mean(ms_pred), "aspc_order": order,
             "mean_iters_aspc": statistics.mean(it_pred), "list_rebuilds_aspc": rebuilds_p,
             "last_frame_mu_rms_diff_debye": float(4.8032047 * torch.sqrt((d * d).sum() / d.shape[0]))}
+
+
+def run_multipole(solver, dev_in, stream, flush, reps: int = 10):
+    """Permanent-multipole energy with forces and moment gradients
+    (amp_multipole_energy) on the bench system: list build by amp_set_system
+    once, then `reps` calls, each timed with CUDA events on the context's
+    stream and including the energy's readback to the host."""
+    import torch
+    from paper_1906_01211_gb300.amoebapol import amp_multipole_energy
+    p = solver("fp64")
+    p.set_system(*dev_in)
+    n = dev_in[0].shape[0]
+    outs = [torch.empty(sh, dtype=torch.float64, device=dev_in[0].device) for sh in ((n, 3), (n,), (n, 3), (n, 6))]
+    ptrs = [t.data_ptr() for t in outs]
+    for _ in range(3):
+        U = amp_multipole_energy(p.ctx, *ptrs)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U = amp_multipole_energy(p.ctx, *ptrs)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    pairs = p.pair_count()
+    p.close()
+    return {"ms_per_call": statistics.mean(ms), "ms_min": min(ms), "U_kcal_mol": U, "unique_pairs": pairs,
+            "outputs": "U, F, dU/dq, dU/dd, dU/dTheta (float64)"}
 
 
 def run_serving(n_requests: int, slots: int, rate_factors, warm: int = 40):
@@ -505,6 +535,10 @@ def main():
     if not args.no_md:
         md = run_md_reuse(solver, sysm, dev, dev_in, stream, flush)
 
+    mpole = None
+    if not args.no_multipole:
+        mpole = run_multipole(solver, dev_in, stream, flush)
+
     cpu = None
     if not args.no_cpu_baseline:
         pairs_o, times, t_build = oracle_sample(w, 2, 0)
@@ -528,6 +562,7 @@ def main():
         "mixed": mixed,
         "serving": serving,
         "md_list_reuse": md,
+        "multipole_energy": mpole,
         "roofline": roofline,
         "roofline_other": [r for r in rooflines if r is not roofline],
         "cpu_baseline": cpu,

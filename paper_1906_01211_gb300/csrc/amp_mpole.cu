@@ -2,7 +2,9 @@
 // permanent multipoles with each other, the paper's "empole1" (Section
 // "Hotspots": the second electrostatic routine of an AMOEBA step beside the
 // polarization ones). Charges, dipoles and traceless quadrupoles in the global
-// frame, so there are no torques. Everything here runs in float64.
+// frame, so there are no torques. The pair terms run in double-float on the
+// float32 units (no float64 instruction: GB300's float64 rate is 1/64 of its
+// float32 rate), the reciprocal gather and the per-atom epilogue in float64.
 //
 // Real space, unique pair (i, j), r = x_i - x_j (minimum image), kernels
 // b_n = B_n (Ewald-screened) or B_n - bare_n for two sites of one molecule
@@ -39,22 +41,47 @@ namespace {
 constexpr int kGroup = 8;  // lanes per atom in the reciprocal gather (one per x plane)
 constexpr int kTh = 3 * 4 * kOrder;
 
-struct MGeom {
-  double L, beta, twob2, gpre;
+// ---- double-float arithmetic with operators (the pair kernel issues no
+// float64 instruction: inputs come pre-split, outputs stay split)
+struct D2 {
+  dflt v;
+};
+__device__ __forceinline__ D2 operator+(D2 a, D2 b) { return {df_add(a.v, b.v)}; }
+__device__ __forceinline__ D2 operator-(D2 a, D2 b) { return {df_sub(a.v, b.v)}; }
+__device__ __forceinline__ D2 operator*(D2 a, D2 b) { return {df_mul(a.v, b.v)}; }
+__device__ __forceinline__ D2 operator-(D2 a) { return {df_neg(a.v)}; }
+__device__ __forceinline__ D2 num(float x) { return {{x, 0.f}}; }  // exactly representable
+__device__ __forceinline__ D2 twice(D2 a) { return {{2.f * a.v.hi, 2.f * a.v.lo}}; }
+
+// 1/3, 2/3, 1/9, 2/9, 4/9 as hi + lo (rounded at compile time)
+constexpr float kC3h = (float)(1.0 / 3.0), kC3l = (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0));
+constexpr float kC23h = (float)(2.0 / 3.0), kC23l = (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
+constexpr float kC9h = (float)(1.0 / 9.0), kC9l = (float)(1.0 / 9.0 - (double)(float)(1.0 / 9.0));
+constexpr float kC29h = (float)(2.0 / 9.0), kC29l = (float)(2.0 / 9.0 - (double)(float)(2.0 / 9.0));
+constexpr float kC49h = (float)(4.0 / 9.0), kC49l = (float)(4.0 / 9.0 - (double)(float)(4.0 / 9.0));
+
+struct MGeomDf {
+  dflt L, beta, twob2, gpre;
+  float invL;
 };
 
-__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
+// minimum-image component: the pair lies within rc < L/2, so rounding d/L
+// from the hi part picks the same image as exact arithmetic would
+__device__ __forceinline__ D2 min_image(D2 d, const MGeomDf& g) {
+  const float sh = rintf(d.v.hi * g.invL);
+  return sh == 0.f ? d : d - num(sh) * D2{g.L};
+}
 
 // Theta (xx, yy, zz, xy, xz, yz) times v
-__device__ __forceinline__ void th_mul(const double* t, const double* v, double* o) {
+__device__ __forceinline__ void th_mul(const D2* t, const D2* v, D2* o) {
   o[0] = t[0] * v[0] + t[3] * v[1] + t[4] * v[2];
   o[1] = t[3] * v[0] + t[1] * v[1] + t[5] * v[2];
   o[2] = t[4] * v[0] + t[5] * v[1] + t[2] * v[2];
 }
 
-__device__ __forceinline__ double dot3(const double* a, const double* b) {
-  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
-}
+__device__ __forceinline__ D2 dot3(const D2* a, const D2* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+__device__ __forceinline__ void put(float2* o, D2 v) { *o = make_float2(v.v.hi, v.v.lo); }
 
 // Derivatives of the pair energy in the moments of the field-point site, for
 // a source (q, d, Theta) at displacement r (field point minus source):
@@ -63,90 +90,111 @@ __device__ __forceinline__ double dot3(const double* a, const double* b) {
 //   o[4..9] = E_ab for ab = xx, yy, zz, xy, xz, yz (off-diagonals doubled),
 //     E_ab = b2 [q r_a r_b/3 - (d_a r_b + d_b r_a)/3 + 2/9 Th_ab]
 //          + b3 [(d.r) r_a r_b/3 - 2/9 (r_a (Th r)_b + (Th r)_a r_b)] + b4 (r.Th.r) r_a r_b/9
-__device__ __forceinline__ void moment_jet(const double* r, double q, const double* d, const double* th,
-                                           const double* b, double* o) {
-  double t[3];
+__device__ __forceinline__ void moment_jet(const D2* r, D2 q, const D2* d, const D2* th, const D2* b, float2* o) {
+  const D2 third = {{kC3h, kC3l}}, two3 = {{kC23h, kC23l}}, ninth = {{kC9h, kC9l}}, two9 = {{kC29h, kC29l}};
+  D2 t[3];
   th_mul(th, r, t);
-  const double dr = dot3(d, r), trr = dot3(t, r);
-  o[0] = q * b[0] + dr * b[1] + trr * b[2] * (1.0 / 3.0);
-  const double rad = -q * b[1] - dr * b[2] - trr * b[3] * (1.0 / 3.0);
-  for (int a = 0; a < 3; ++a) o[1 + a] = rad * r[a] + b[1] * d[a] + (2.0 / 3.0) * b[2] * t[a];
+  const D2 dr = dot3(d, r), trr = dot3(t, r);
+  put(o, q * b[0] + dr * b[1] + trr * b[2] * third);
+  const D2 rad = -(q * b[1] + dr * b[2] + trr * b[3] * third);
+  const D2 b2t = b[2] * two3;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) put(o + 1 + a, rad * r[a] + b[1] * d[a] + b2t * t[a]);
   const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
-  const double c0 = b[2] * q * (1.0 / 3.0) + b[3] * dr * (1.0 / 3.0) + b[4] * trr * (1.0 / 9.0);
+  const D2 c0 = (b[2] * q + b[3] * dr) * third + b[4] * trr * ninth;
+  const D2 c1 = b[2] * third, c2 = b[2] * two9, c3 = b[3] * two9;
+#pragma unroll
   for (int k = 0; k < 6; ++k) {
     const int a = ia[k], bb = ib[k];
-    const double e = c0 * r[a] * r[bb] - b[2] * (1.0 / 3.0) * (d[a] * r[bb] + d[bb] * r[a]) +
-                     b[2] * (2.0 / 9.0) * th[k] - b[3] * (2.0 / 9.0) * (r[a] * t[bb] + t[a] * r[bb]);
-    o[4 + k] = k < 3 ? e : 2.0 * e;
+    const D2 e = c0 * r[a] * r[bb] - c1 * (d[a] * r[bb] + d[bb] * r[a]) + c2 * th[k] -
+                 c3 * (r[a] * t[bb] + t[a] * r[bb]);
+    put(o + 4 + k, k < 3 ? e : twice(e));
   }
 }
 
-// One thread per unique pair: the force on i (F_j = -F_i) and the moment
-// derivatives of both ends, in the backward per-pair record
-// [force(3), unused, i's derivatives(10), j's derivatives(10)], units of C.
-__global__ void __launch_bounds__(256) k_mpole_pairs(long long nh, const int* __restrict__ half_i,
-                                                     const int* __restrict__ half_j,
-                                                     const double4_32a* __restrict__ A,
-                                                     const double4_32a* __restrict__ B,
-                                                     const double4_32a* __restrict__ C,
-                                                     const double4_32a* __restrict__ D, MGeom g,
-                                                     double* __restrict__ out) {
+// One thread per unique pair, in double-float: the force on i (F_j = -F_i)
+// and the moment derivatives of both ends, as the per-pair record of 24
+// (hi, lo) pairs [force(3), unused, i's derivatives(10), j's derivatives(10)],
+// units of C. Inputs: pd = split positions (and molecule), mp = split
+// moments, tab = the double-float function table.
+__global__ void __launch_bounds__(128) k_mpole_pairs_df(long long nh, const int* __restrict__ half_i,
+                                                        const int* __restrict__ half_j,
+                                                        const float4* __restrict__ pd,
+                                                        const float4* __restrict__ mp, MGeomDf g,
+                                                        const float2* __restrict__ tab, float2* __restrict__ out) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
-  const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], ci = C[i], cj = C[j], di = D[i], dj = D[j];
-  const double r[3] = {min_image(ai.x - aj.x, g.L), min_image(ai.y - aj.y, g.L), min_image(ai.z - aj.z, g.L)};
-  const double nr[3] = {-r[0], -r[1], -r[2]};
-  const double r2 = dot3(r, r), rr = sqrt(r2), ir = 1.0 / rr, ir2 = ir * ir;
-  const double br = g.beta * rr;
-  double b[6];
-  double fac = exp(-br * br) * g.gpre;
-  b[0] = erfc(br) * ir;
+  const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
+  const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
+  const D2 r[3] = {min_image(D2{{hi_i.x, lo_i.x}} - D2{{hi_j.x, lo_j.x}}, g),
+                   min_image(D2{{hi_i.y, lo_i.y}} - D2{{hi_j.y, lo_j.y}}, g),
+                   min_image(D2{{hi_i.z, lo_i.z}} - D2{{hi_j.z, lo_j.z}}, g)};
+  const D2 nr[3] = {-r[0], -r[1], -r[2]};
+  const D2 r2 = dot3(r, r);
+  const D2 ir = {df_rsqrt(r2.v)};
+  const D2 br = D2{g.beta} * (r2 * ir);
+  const D2 e2 = {df_exp_neg((br * br).v, tab)};  // exp(-beta^2 r^2)
+  const D2 ir2 = ir * ir;
+  D2 b[6];
+  b[0] = D2{df_erfcx(br.v, tab)} * e2 * ir;  // erfc(beta r)/r
+  D2 fac = e2 * D2{g.gpre};
+#pragma unroll
   for (int n = 1; n < 6; ++n) {
-    b[n] = ((2 * n - 1) * b[n - 1] + fac) * ir2;
-    fac *= g.twob2;
+    b[n] = (num((float)(2 * n - 1)) * b[n - 1] + fac) * ir2;
+    fac = fac * D2{g.twob2};
   }
-  if (di.w == dj.w) {  // same molecule: remove the bare kernels
-    double e = ir;
-    b[0] -= e;
+  if (__float_as_int(th_i.z) == __float_as_int(th_j.z)) {  // same molecule: remove the bare kernels
+    D2 e = ir;
+    b[0] = b[0] - e;
+#pragma unroll
     for (int n = 1; n < 6; ++n) {
-      e *= (2 * n - 1) * ir2;
-      b[n] -= e;
+      e = e * num((float)(2 * n - 1)) * ir2;
+      b[n] = b[n] - e;
     }
   }
-  const double qi = ai.w, qj = aj.w;
-  const double dpi[3] = {bi.x, bi.y, bi.z}, dpj[3] = {bj.x, bj.y, bj.z};
-  const double thi[6] = {ci.x, ci.y, ci.z, ci.w, di.x, di.y};
-  const double thj[6] = {cj.x, cj.y, cj.z, cj.w, dj.x, dj.y};
-  double ti[3], tj[3];
-  th_mul(thi, r, ti);
-  th_mul(thj, r, tj);
-  const double dir = dot3(dpi, r), djr = dot3(dpj, r), tir = dot3(ti, r), tjr = dot3(tj, r);
-  const double thth = thi[0] * thj[0] + thi[1] * thj[1] + thi[2] * thj[2] +
-                      2.0 * (thi[3] * thj[3] + thi[4] * thj[4] + thi[5] * thj[5]);
-  const double G0 = qi * qj;
-  const double G1 = qi * djr - qj * dir + dot3(dpi, dpj);
-  const double G2 = -dir * djr + (qi * tjr + qj * tir) * (1.0 / 3.0) + (2.0 / 3.0) * (dot3(dpi, tj) - dot3(dpj, ti)) +
-                    (2.0 / 9.0) * thth;
-  const double G3 = (djr * tir - dir * tjr) * (1.0 / 3.0) - (4.0 / 9.0) * dot3(ti, tj);
-  const double G4 = tir * tjr * (1.0 / 9.0);
-  const double rad = G0 * b[1] + G1 * b[2] + G2 * b[3] + G3 * b[4] + G4 * b[5];
-  double tjdi[3], tidj[3], titj[3], tjti[3];
-  th_mul(thj, dpi, tjdi);
-  th_mul(thi, dpj, tidj);
-  th_mul(thi, tj, titj);
-  th_mul(thj, ti, tjti);
-  double* o = out + (long long)kForcePairStride * pid;
-  for (int a = 0; a < 3; ++a) {
-    const double g1 = qi * dpj[a] - qj * dpi[a];
-    const double g2 = -(dpi[a] * djr + dpj[a] * dir) + (2.0 / 3.0) * (qi * tj[a] + qj * ti[a]) +
-                      (2.0 / 3.0) * (tjdi[a] - tidj[a]);
-    const double g3 = -(2.0 * tj[a] * dir + tjr * dpi[a]) * (1.0 / 3.0) + (dpj[a] * tir + 2.0 * djr * ti[a]) * (1.0 / 3.0) -
-                      (4.0 / 9.0) * (titj[a] + tjti[a]);
-    const double g4 = (2.0 / 9.0) * (ti[a] * tjr + tj[a] * tir);
-    o[a] = rad * r[a] - (b[1] * g1 + b[2] * g2 + b[3] * g3 + b[4] * g4);
+  // split moments: (q, dx), (dy, dz), (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz) as hi/lo
+  const float4* mi = mp + 5 * (long long)i;
+  const float4* mj = mp + 5 * (long long)j;
+  const float4 i0 = mi[0], i1 = mi[1], i2 = mi[2], i3 = mi[3], i4 = mi[4];
+  const float4 j0 = mj[0], j1 = mj[1], j2 = mj[2], j3 = mj[3], j4 = mj[4];
+  const D2 qi = {{i0.x, i0.y}}, qj = {{j0.x, j0.y}};
+  const D2 dpi[3] = {{{i0.z, i0.w}}, {{i1.x, i1.y}}, {{i1.z, i1.w}}};
+  const D2 dpj[3] = {{{j0.z, j0.w}}, {{j1.x, j1.y}}, {{j1.z, j1.w}}};
+  const D2 thi[6] = {{{i2.x, i2.y}}, {{i2.z, i2.w}}, {{i3.x, i3.y}}, {{i3.z, i3.w}}, {{i4.x, i4.y}}, {{i4.z, i4.w}}};
+  const D2 thj[6] = {{{j2.x, j2.y}}, {{j2.z, j2.w}}, {{j3.x, j3.y}}, {{j3.z, j3.w}}, {{j4.x, j4.y}}, {{j4.z, j4.w}}};
+  const D2 third = {{kC3h, kC3l}}, two3 = {{kC23h, kC23l}}, ninth = {{kC9h, kC9l}}, two9 = {{kC29h, kC29l}},
+           four9 = {{kC49h, kC49l}};
+  float2* o = out + (long long)kForcePairStride * pid;
+  {
+    D2 ti[3], tj[3];
+    th_mul(thi, r, ti);
+    th_mul(thj, r, tj);
+    const D2 dir = dot3(dpi, r), djr = dot3(dpj, r), tir = dot3(ti, r), tjr = dot3(tj, r);
+    const D2 thth = thi[0] * thj[0] + thi[1] * thj[1] + thi[2] * thj[2] +
+                    twice(thi[3] * thj[3] + thi[4] * thj[4] + thi[5] * thj[5]);
+    const D2 G0 = qi * qj;
+    const D2 G1 = qi * djr - qj * dir + dot3(dpi, dpj);
+    const D2 G2 = (qi * tjr + qj * tir) * third - dir * djr + (dot3(dpi, tj) - dot3(dpj, ti)) * two3 + thth * two9;
+    const D2 G3 = (djr * tir - dir * tjr) * third - dot3(ti, tj) * four9;
+    const D2 G4 = tir * tjr * ninth;
+    const D2 rad = G0 * b[1] + G1 * b[2] + G2 * b[3] + G3 * b[4] + G4 * b[5];
+    D2 tjdi[3], tidj[3], titj[3], tjti[3];
+    th_mul(thj, dpi, tjdi);
+    th_mul(thi, dpj, tidj);
+    th_mul(thi, tj, titj);
+    th_mul(thj, ti, tjti);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const D2 g1 = qi * dpj[a] - qj * dpi[a];
+      const D2 g2 = (qi * tj[a] + qj * ti[a] + tjdi[a] - tidj[a]) * two3 - (dpi[a] * djr + dpj[a] * dir);
+      const D2 g3 = (dpj[a] * tir + twice(djr * ti[a]) - twice(tj[a] * dir) - tjr * dpi[a]) * third -
+                    (titj[a] + tjti[a]) * four9;
+      const D2 g4 = (ti[a] * tjr + tj[a] * tir) * two9;
+      put(o + a, rad * r[a] - (b[1] * g1 + b[2] * g2 + b[3] * g3 + b[4] * g4));
+    }
+    o[3] = make_float2(0.f, 0.f);
   }
-  o[3] = 0.0;
   moment_jet(r, qj, dpj, thj, b, o + 4);    // at i, of j
   moment_jet(nr, qi, dpi, thi, b, o + 14);  // at j, of i
 }
@@ -291,22 +339,16 @@ __global__ void __launch_bounds__(1024) k_block_sum(int n, const double* __restr
   }
 }
 
-__device__ __forceinline__ double gsum(double v) {
-  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
-#pragma unroll
-  for (int o = kRowGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kRowGroup);
-  return v;
-}
-
 struct SelfTerms {
   double q, d, th, bg;  // dU/dq = q*q_i + bg*Q_tot, dU/dd = d*d_i, dU/dTheta_ab = th*Theta_ab
 };
 
-// Row sums of the per-pair records + reciprocal + self + background, times C,
-// quadrupole diagonal projected; outputs in caller order; per-atom energy
+// Row sums of the per-pair records (double-float, fixed order within each
+// lane group) + reciprocal + self + background, times C, quadrupole diagonal
+// projected; outputs in caller order; per-atom energy
 // 1/2 (q dU/dq + d.dU/dd + Theta.dU/dTheta) in sorted order.
 __global__ void __launch_bounds__(256) k_mpole_rows(int n, const int* __restrict__ full_start,
-                                                    const int* __restrict__ full_ref, const double* __restrict__ pair,
+                                                    const int* __restrict__ full_ref, const float2* __restrict__ pair,
                                                     const double* __restrict__ recip,
                                                     const double4_32a* __restrict__ A,
                                                     const double4_32a* __restrict__ B,
@@ -318,52 +360,71 @@ __global__ void __launch_bounds__(256) k_mpole_rows(int n, const int* __restrict
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gid / kRowGroup, l = gid % kRowGroup;
   if (i >= n) return;
-  double acc[13];
-  for (int k = 0; k < 13; ++k) acc[k] = 0.0;
+  dflt acc[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) acc[k] = {0.f, 0.f};
   const int e = full_start[i + 1];
   for (int k = full_start[i] + l; k < e; k += kRowGroup) {
     const int ref = full_ref[k];
-    const double* p = pair + (long long)kForcePairStride * (ref >> 1);
-    const double sgn = (ref & 1) ? -1.0 : 1.0;
-    acc[0] += sgn * p[0];
-    acc[1] += sgn * p[1];
-    acc[2] += sgn * p[2];
-    const double* g = p + 4 + 10 * (ref & 1);
-    for (int m = 0; m < 10; ++m) acc[3 + m] += g[m];
+    const float2* p = pair + (long long)kForcePairStride * (ref >> 1);
+    const float sgn = (ref & 1) ? -1.f : 1.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 f = p[a];
+      acc[a] = df_add(acc[a], {sgn * f.x, sgn * f.y});
+    }
+    const float2* g = p + 4 + 10 * (ref & 1);
+#pragma unroll
+    for (int m = 0; m < 10; ++m) {
+      const float2 v = g[m];
+      acc[3 + m] = df_add(acc[3 + m], {v.x, v.y});
+    }
   }
-  for (int k = 0; k < 13; ++k) acc[k] = gsum(acc[k]);
+#pragma unroll
+  for (int k = 0; k < 13; ++k) acc[k] = df_group_sum(acc[k]);
   if (l != 0) return;
   const double* rc = recip + (long long)kForceAtomStride * i;
-  for (int k = 0; k < 13; ++k) acc[k] += rc[k];
+  double v[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) v[k] = df_to_double(acc[k]) + rc[k];
   const double4_32a a = A[i], b = B[i], c = C[i], d = D[i];
   const double th[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
-  acc[3] += st.q * a.w + st.bg * (*qtot);
-  acc[4] += st.d * b.x;
-  acc[5] += st.d * b.y;
-  acc[6] += st.d * b.z;
-  for (int k = 0; k < 6; ++k) acc[7 + k] += (k < 3 ? 1.0 : 2.0) * st.th * th[k];
-  for (int k = 0; k < 13; ++k) acc[k] *= kCoulomb;
-  const double mean = (acc[7] + acc[8] + acc[9]) * (1.0 / 3.0);
-  acc[7] -= mean;
-  acc[8] -= mean;
-  acc[9] -= mean;
-  double u = a.w * acc[3] + b.x * acc[4] + b.y * acc[5] + b.z * acc[6];
-  for (int k = 0; k < 6; ++k) u += th[k] * acc[7 + k];
+  v[3] += st.q * a.w + st.bg * (*qtot);
+  v[4] += st.d * b.x;
+  v[5] += st.d * b.y;
+  v[6] += st.d * b.z;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v[7 + k] += (k < 3 ? 1.0 : 2.0) * st.th * th[k];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) v[k] *= kCoulomb;
+  const double mean = (v[7] + v[8] + v[9]) * (1.0 / 3.0);
+  v[7] -= mean;
+  v[8] -= mean;
+  v[9] -= mean;
+  double u = a.w * v[3] + b.x * v[4] + b.y * v[5] + b.z * v[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) u += th[k] * v[7 + k];
   e_atom[i] = 0.5 * u;
   const int o = perm[i];
   if (F) {
-    F[3 * o] = acc[0];
-    F[3 * o + 1] = acc[1];
-    F[3 * o + 2] = acc[2];
+    F[3 * o] = v[0];
+    F[3 * o + 1] = v[1];
+    F[3 * o + 2] = v[2];
   }
-  if (gq) gq[o] = acc[3];
+  if (gq) gq[o] = v[3];
   if (gd) {
-    gd[3 * o] = acc[4];
-    gd[3 * o + 1] = acc[5];
-    gd[3 * o + 2] = acc[6];
+    gd[3 * o] = v[4];
+    gd[3 * o + 1] = v[5];
+    gd[3 * o + 2] = v[6];
   }
   if (gt)
-    for (int k = 0; k < 6; ++k) gt[6 * o + k] = acc[7 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) gt[6 * o + k] = v[7 + k];
+}
+
+dflt split_host(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
 }
 
 }  // namespace
@@ -379,11 +440,12 @@ int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, d
     c->mpole_e_cap = c->n_cap;
   }
   const double b = c->cfg.ewald_beta, L = c->cfg.box;
-  MGeom g;
-  g.L = L;
-  g.beta = b;
-  g.twob2 = 2.0 * b * b;
-  g.gpre = 2.0 * b / kSqrtPi;
+  MGeomDf g;
+  g.L = split_host(L);
+  g.beta = split_host(b);
+  g.twob2 = split_host(2.0 * b * b);
+  g.gpre = split_host(2.0 * b / kSqrtPi);
+  g.invL = (float)(1.0 / L);
   const double c0 = 2.0 * b / kSqrtPi;
   SelfTerms st;
   st.q = -c0;
@@ -391,6 +453,8 @@ int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, d
   st.th = -c0 * (8.0 * b * b * b * b / 45.0);
   st.bg = -3.14159265358979323846 / (L * L * L * b * b);
   cudaStream_t s = c->stream;
+  // the per-pair records are (hi, lo) float pairs in the backward pair buffer
+  float2* pair = reinterpret_cast<float2*>(c->force_pair);
   {
     PhaseScope ps(c, AMP_PHASE_FORCES);
     if ((r = pme_potential(c, false, true, nullptr, nullptr, c->grid64b))) return r;
@@ -400,12 +464,12 @@ int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, d
     k_block_sum<<<1, 1024, 0, s>>>(c->n, reinterpret_cast<const double*>(c->atomA) + 3, 4, c->scal + 4);
     if (c->n_half > 0) {
       c->n_launch += 1;
-      k_mpole_pairs<<<amp_blocks(c->n_half, 256), 256, 0, s>>>(c->n_half, c->half_i, c->half_j, c->atomA, c->atomB,
-                                                               c->atomC, c->atomD, g, c->force_pair);
+      k_mpole_pairs_df<<<amp_blocks(c->n_half, 128), 128, 0, s>>>(c->n_half, c->half_i, c->half_j, c->pd,
+                                                                   c->mp_df, g, c->dfm, pair);
     }
     c->n_launch += 2;
     k_mpole_rows<<<amp_blocks((long long)c->n * kRowGroup, 256), 256, 0, s>>>(
-        c->n, c->full_start, c->full_ref, c->force_pair, c->force_recip, c->atomA, c->atomB, c->atomC, c->atomD,
+        c->n, c->full_start, c->full_ref, pair, c->force_recip, c->atomA, c->atomB, c->atomC, c->atomD,
         c->scal + 4, st, c->perm, F, gq, gd, gt, c->mpole_e);
     k_block_sum<<<1, 1024, 0, s>>>(c->n, c->mpole_e, 1, c->scal + 5);
   }
