@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-md", action="store_true", help="skip the list-reuse trajectory measurement")
     ap.add_argument("--no-multipole", action="store_true", help="skip the permanent-multipole energy measurement")
+    ap.add_argument("--multipole-only", action="store_true",
+                    help="time only the permanent-multipole energy call on the workload and print it")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement (request stream, rates) as its own JSON line")
     ap.add_argument("--requests", type=int, default=300)
@@ -403,6 +405,12 @@ def main():
     E0 = torch.empty((n, 3), dtype=torch.float64, device=dev)
     mu_host = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    if args.multipole_only:
+        if rank == 0:
+            print(json.dumps({"config": {"workload": w.name, "n_atoms": n},
+                              "multipole_energy": run_multipole(solver, dev_in, stream, flush)}), flush=True)
+        return
 
     p = solver("fp64")
     n_pairs = None

@@ -81,6 +81,12 @@ __device__ __forceinline__ void th_mul(const D2* t, const D2* v, D2* o) {
 
 __device__ __forceinline__ D2 dot3(const D2* a, const D2* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
+// row a of Theta times v
+__device__ __forceinline__ D2 th_row(const D2* t, int a, const D2* v) {
+  const int k0 = a == 0 ? 0 : (a == 1 ? 3 : 4), k1 = a == 0 ? 3 : (a == 1 ? 1 : 5), k2 = a == 0 ? 4 : (a == 1 ? 5 : 2);
+  return t[k0] * v[0] + t[k1] * v[1] + t[k2] * v[2];
+}
+
 __device__ __forceinline__ void put(float2* o, D2 v) { *o = make_float2(v.v.hi, v.v.lo); }
 
 // Derivatives of the pair energy in the moments of the field-point site, for
@@ -179,17 +185,13 @@ __global__ void __launch_bounds__(128) k_mpole_pairs_df(long long nh, const int*
     const D2 G3 = (djr * tir - dir * tjr) * third - dot3(ti, tj) * four9;
     const D2 G4 = tir * tjr * ninth;
     const D2 rad = G0 * b[1] + G1 * b[2] + G2 * b[3] + G3 * b[4] + G4 * b[5];
-    D2 tjdi[3], tidj[3], titj[3], tjti[3];
-    th_mul(thj, dpi, tjdi);
-    th_mul(thi, dpj, tidj);
-    th_mul(thi, tj, titj);
-    th_mul(thj, ti, tjti);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const D2 g1 = qi * dpj[a] - qj * dpi[a];
-      const D2 g2 = (qi * tj[a] + qj * ti[a] + tjdi[a] - tidj[a]) * two3 - (dpi[a] * djr + dpj[a] * dir);
+      const D2 g2 = (qi * tj[a] + qj * ti[a] + th_row(thj, a, dpi) - th_row(thi, a, dpj)) * two3 -
+                    (dpi[a] * djr + dpj[a] * dir);
       const D2 g3 = (dpj[a] * tir + twice(djr * ti[a]) - twice(tj[a] * dir) - tjr * dpi[a]) * third -
-                    (titj[a] + tjti[a]) * four9;
+                    (th_row(thi, a, tj) + th_row(thj, a, ti)) * four9;
       const D2 g4 = (ti[a] * tjr + tj[a] * tir) * two9;
       put(o + a, rad * r[a] - (b[1] * g1 + b[2] * g2 + b[3] * g3 + b[4] * g4));
     }
@@ -366,18 +368,31 @@ __global__ void __launch_bounds__(256) k_mpole_rows(int n, const int* __restrict
   const int e = full_start[i + 1];
   for (int k = full_start[i] + l; k < e; k += kRowGroup) {
     const int ref = full_ref[k];
-    const float2* p = pair + (long long)kForcePairStride * (ref >> 1);
-    const float sgn = (ref & 1) ? -1.f : 1.f;
+    const int side = ref & 1;
+    // the record is 192 bytes (32-byte aligned): four 32-byte loads take the
+    // force (entries 0..2) and this side's derivatives (entries 4..13 or 14..23)
+    const float4* p = reinterpret_cast<const float4*>(pair + (long long)kForcePairStride * (ref >> 1));
+    float4 w[8];
+    ld8_ro(p, w[0], w[1]);
+    ld8_ro(p + (side ? 6 : 2), w[2], w[3]);
+    ld8_ro(p + (side ? 8 : 4), w[4], w[5]);
+    ld8_ro(p + (side ? 10 : 6), w[6], w[7]);
+    const float sgn = side ? -1.f : 1.f;
+    acc[0] = df_add(acc[0], {sgn * w[0].x, sgn * w[0].y});
+    acc[1] = df_add(acc[1], {sgn * w[0].z, sgn * w[0].w});
+    acc[2] = df_add(acc[2], {sgn * w[1].x, sgn * w[1].y});
+    // w[2..7] hold entries base..base+11 (base = 4 or 12) as (hi, lo) pairs;
+    // this side's ten start at entry 4 (side 0) or 14 (side 1)
+    float2 v[12];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float2 f = p[a];
-      acc[a] = df_add(acc[a], {sgn * f.x, sgn * f.y});
+    for (int m = 0; m < 6; ++m) {
+      v[2 * m] = make_float2(w[2 + m].x, w[2 + m].y);
+      v[2 * m + 1] = make_float2(w[2 + m].z, w[2 + m].w);
     }
-    const float2* g = p + 4 + 10 * (ref & 1);
 #pragma unroll
     for (int m = 0; m < 10; ++m) {
-      const float2 v = g[m];
-      acc[3 + m] = df_add(acc[3 + m], {v.x, v.y});
+      const float2 x = side ? v[m + 2] : v[m];
+      acc[3 + m] = df_add(acc[3 + m], {x.x, x.y});
     }
   }
 #pragma unroll
