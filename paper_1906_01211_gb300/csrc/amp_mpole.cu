@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(1024) k_block_sum(int n, const double* __restr
                                                     double* __restrict__ out) {
   __shared__ double part[32];
   double s = 0.0;
+#pragma unroll 8
   for (int k = threadIdx.x; k < n; k += blockDim.x) s += src[(long long)k * stride];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -397,44 +398,50 @@ __global__ void __launch_bounds__(256) k_mpole_rows(int n, const int* __restrict
   }
 #pragma unroll
   for (int k = 0; k < 13; ++k) acc[k] = df_group_sum(acc[k]);
-  if (l != 0) return;
-  const double* rc = recip + (long long)kForceAtomStride * i;
-  double v[13];
-#pragma unroll
-  for (int k = 0; k < 13; ++k) v[k] = df_to_double(acc[k]) + rc[k];
+  // epilogue spread over the row's lanes: lane l < 13 finishes component l
+  // (force x, y, z, q, d x, y, z, Theta xx, yy, zz, xy, xz, yz) in float64
   const double4_32a a = A[i], b = B[i], c = C[i], d = D[i];
-  const double th[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
-  v[3] += st.q * a.w + st.bg * (*qtot);
-  v[4] += st.d * b.x;
-  v[5] += st.d * b.y;
-  v[6] += st.d * b.z;
+  dflt mine = acc[0];
+  double m = 0.0, self = 0.0;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) v[7 + k] += (k < 3 ? 1.0 : 2.0) * st.th * th[k];
+  for (int k = 1; k < 13; ++k)
+    if (l == k) mine = acc[k];
+  switch (l) {
+    case 3: m = a.w; self = st.q * a.w + st.bg * (*qtot); break;
+    case 4: m = b.x; self = st.d * b.x; break;
+    case 5: m = b.y; self = st.d * b.y; break;
+    case 6: m = b.z; self = st.d * b.z; break;
+    case 7: m = c.x; self = st.th * c.x; break;
+    case 8: m = c.y; self = st.th * c.y; break;
+    case 9: m = c.z; self = st.th * c.z; break;
+    case 10: m = c.w; self = 2.0 * st.th * c.w; break;
+    case 11: m = d.x; self = 2.0 * st.th * d.x; break;
+    case 12: m = d.y; self = 2.0 * st.th * d.y; break;
+    default: break;
+  }
+  const double* rc = recip + (long long)kForceAtomStride * i;
+  double v = l < 13 ? (df_to_double(mine) + rc[l] + self) * kCoulomb : 0.0;
+  // project the quadrupole diagonal (lanes 7, 8, 9) onto traceless changes
+  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
+  const int g0 = (threadIdx.x & 31) & ~(kRowGroup - 1);
+  const double mean = (__shfl_sync(mask, v, g0 + 7) + __shfl_sync(mask, v, g0 + 8) + __shfl_sync(mask, v, g0 + 9)) *
+                      (1.0 / 3.0);
+  if (l >= 7 && l <= 9) v -= mean;
+  // per-atom energy 1/2 sum_k moment_k dU/dmoment_k (fixed order over the lanes)
+  double u = m * v;
 #pragma unroll
-  for (int k = 0; k < 13; ++k) v[k] *= kCoulomb;
-  const double mean = (v[7] + v[8] + v[9]) * (1.0 / 3.0);
-  v[7] -= mean;
-  v[8] -= mean;
-  v[9] -= mean;
-  double u = a.w * v[3] + b.x * v[4] + b.y * v[5] + b.z * v[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) u += th[k] * v[7 + k];
-  e_atom[i] = 0.5 * u;
+  for (int o = kRowGroup / 2; o > 0; o >>= 1) u += __shfl_xor_sync(mask, u, o, kRowGroup);
+  if (l == 0) e_atom[i] = 0.5 * u;
   const int o = perm[i];
-  if (F) {
-    F[3 * o] = v[0];
-    F[3 * o + 1] = v[1];
-    F[3 * o + 2] = v[2];
+  if (l < 3) {
+    if (F) F[3 * o + l] = v;
+  } else if (l == 3) {
+    if (gq) gq[o] = v;
+  } else if (l < 7) {
+    if (gd) gd[3 * o + l - 4] = v;
+  } else if (l < 13) {
+    if (gt) gt[6 * o + l - 7] = v;
   }
-  if (gq) gq[o] = v[3];
-  if (gd) {
-    gd[3 * o] = v[4];
-    gd[3 * o + 1] = v[5];
-    gd[3 * o + 2] = v[6];
-  }
-  if (gt)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) gt[6 * o + k] = v[7 + k];
 }
 
 dflt split_host(double v) {
