@@ -185,9 +185,10 @@ int amp_forces(amp_ctx* ctx, const double* mu, double* F, double* gq, double* gd
  *         standing for two entries, with the mean of the three diagonal ones
  *         removed (quadrupoles are traceless, so only traceless changes
  *         exist); each may be NULL to skip it (at least one output).
- * Caller order, device pointers except U. Float64 arithmetic in both precision
- * modes. Periodic contexts only (AMP_ERR_ARG for a cluster). Uses the geometry
- * and lists of the current system; allocates its buffers on the first call. */
+ * An isolated cluster (box = 0) has only the pair sum, over all pairs, with the
+ * bare kernels. Caller order, device pointers except U. Float64 results in
+ * both precision modes. Uses the geometry and lists of the current system;
+ * allocates its buffers on the first call. */
 int amp_multipole_energy(amp_ctx* ctx, double* U, double* F, double* gq, double* gdip, double* gquad);
 
 /* Number of unique atom pairs within the cutoff of the current system. */

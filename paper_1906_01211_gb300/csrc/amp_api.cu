@@ -354,7 +354,6 @@ int amp_forces(amp_ctx* c, const double* mu, double* F, double* gq, double* gdip
 int amp_multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gdip, double* gquad) {
   if (!c) return AMP_ERR_ARG;
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
-  if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_multipole_energy: not available for isolated clusters");
   if (!U && !F && !gq && !gdip && !gquad) return fail(c, AMP_ERR_ARG, "amp_multipole_energy: no output requested");
   return multipole_energy(c, U, F, gq, gdip, gquad);
 }

@@ -265,6 +265,7 @@ int force_buffers(amp_ctx* c);
 // multipoles (multipoles = true), through cuFFT: the backward kernels' grids
 int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out);
 int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, double* gt);
+void launch_split_multipoles(amp_ctx* c);  // pd and mp_df from the atom records
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
 
 // isolated clusters (amp_cluster.cu)

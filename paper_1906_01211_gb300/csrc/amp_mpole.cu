@@ -96,16 +96,16 @@ __device__ __forceinline__ void put(float2* o, D2 v) { *o = make_float2(v.v.hi, 
 //   o[4..9] = E_ab for ab = xx, yy, zz, xy, xz, yz (off-diagonals doubled),
 //     E_ab = b2 [q r_a r_b/3 - (d_a r_b + d_b r_a)/3 + 2/9 Th_ab]
 //          + b3 [(d.r) r_a r_b/3 - 2/9 (r_a (Th r)_b + (Th r)_a r_b)] + b4 (r.Th.r) r_a r_b/9
-__device__ __forceinline__ void moment_jet(const D2* r, D2 q, const D2* d, const D2* th, const D2* b, float2* o) {
+__device__ __forceinline__ void moment_jet(const D2* r, D2 q, const D2* d, const D2* th, const D2* b, D2* o) {
   const D2 third = {{kC3h, kC3l}}, two3 = {{kC23h, kC23l}}, ninth = {{kC9h, kC9l}}, two9 = {{kC29h, kC29l}};
   D2 t[3];
   th_mul(th, r, t);
   const D2 dr = dot3(d, r), trr = dot3(t, r);
-  put(o, q * b[0] + dr * b[1] + trr * b[2] * third);
+  o[0] = q * b[0] + dr * b[1] + trr * b[2] * third;
   const D2 rad = -(q * b[1] + dr * b[2] + trr * b[3] * third);
   const D2 b2t = b[2] * two3;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) put(o + 1 + a, rad * r[a] + b[1] * d[a] + b2t * t[a]);
+  for (int a = 0; a < 3; ++a) o[1 + a] = rad * r[a] + b[1] * d[a] + b2t * t[a];
   const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
   const D2 c0 = (b[2] * q + b[3] * dr) * third + b[4] * trr * ninth;
   const D2 c1 = b[2] * third, c2 = b[2] * two9, c3 = b[3] * two9;
@@ -114,8 +114,59 @@ __device__ __forceinline__ void moment_jet(const D2* r, D2 q, const D2* d, const
     const int a = ia[k], bb = ib[k];
     const D2 e = c0 * r[a] * r[bb] - c1 * (d[a] * r[bb] + d[bb] * r[a]) + c2 * th[k] -
                  c3 * (r[a] * t[bb] + t[a] * r[bb]);
-    put(o + 4 + k, k < 3 ? e : twice(e));
+    o[4 + k] = k < 3 ? e : twice(e);
   }
+}
+
+// -dU_ij/dr (the force on i) = r sum_n G_n b_{n+1} - sum_n b_n grad G_n
+__device__ __forceinline__ void pair_force(const D2* r, const D2* b, D2 qi, const D2* dpi, const D2* thi, D2 qj,
+                                           const D2* dpj, const D2* thj, D2* f) {
+  const D2 third = {{kC3h, kC3l}}, two3 = {{kC23h, kC23l}}, ninth = {{kC9h, kC9l}}, two9 = {{kC29h, kC29l}},
+           four9 = {{kC49h, kC49l}};
+  D2 ti[3], tj[3];
+  th_mul(thi, r, ti);
+  th_mul(thj, r, tj);
+  const D2 dir = dot3(dpi, r), djr = dot3(dpj, r), tir = dot3(ti, r), tjr = dot3(tj, r);
+  const D2 thth = thi[0] * thj[0] + thi[1] * thj[1] + thi[2] * thj[2] +
+                  twice(thi[3] * thj[3] + thi[4] * thj[4] + thi[5] * thj[5]);
+  const D2 G0 = qi * qj;
+  const D2 G1 = qi * djr - qj * dir + dot3(dpi, dpj);
+  const D2 G2 = (qi * tjr + qj * tir) * third - dir * djr + (dot3(dpi, tj) - dot3(dpj, ti)) * two3 + thth * two9;
+  const D2 G3 = (djr * tir - dir * tjr) * third - dot3(ti, tj) * four9;
+  const D2 G4 = tir * tjr * ninth;
+  const D2 rad = G0 * b[1] + G1 * b[2] + G2 * b[3] + G3 * b[4] + G4 * b[5];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const D2 g1 = qi * dpj[a] - qj * dpi[a];
+    const D2 g2 = (qi * tj[a] + qj * ti[a] + th_row(thj, a, dpi) - th_row(thi, a, dpj)) * two3 -
+                  (dpi[a] * djr + dpj[a] * dir);
+    const D2 g3 = (dpj[a] * tir + twice(djr * ti[a]) - twice(tj[a] * dir) - tjr * dpi[a]) * third -
+                  (th_row(thi, a, tj) + th_row(thj, a, ti)) * four9;
+    const D2 g4 = (ti[a] * tjr + tj[a] * tir) * two9;
+    f[a] = rad * r[a] - (b[1] * g1 + b[2] * g2 + b[3] * g3 + b[4] * g4);
+  }
+}
+
+// Split moments of atom s: (q, dx), (dy, dz), (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz) as hi/lo
+struct Moments {
+  D2 q, d[3], th[6];
+};
+
+__device__ __forceinline__ Moments load_moments(const float4* __restrict__ mp, int s) {
+  const float4* m = mp + 5 * (long long)s;
+  const float4 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3], m4 = m[4];
+  Moments o;
+  o.q = {{m0.x, m0.y}};
+  o.d[0] = {{m0.z, m0.w}};
+  o.d[1] = {{m1.x, m1.y}};
+  o.d[2] = {{m1.z, m1.w}};
+  o.th[0] = {{m2.x, m2.y}};
+  o.th[1] = {{m2.z, m2.w}};
+  o.th[2] = {{m3.x, m3.y}};
+  o.th[3] = {{m3.z, m3.w}};
+  o.th[4] = {{m4.x, m4.y}};
+  o.th[5] = {{m4.z, m4.w}};
+  return o;
 }
 
 // One thread per unique pair, in double-float: the force on i (F_j = -F_i)
@@ -159,46 +210,91 @@ __global__ void __launch_bounds__(128) k_mpole_pairs_df(long long nh, const int*
       b[n] = b[n] - e;
     }
   }
-  // split moments: (q, dx), (dy, dz), (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz) as hi/lo
-  const float4* mi = mp + 5 * (long long)i;
-  const float4* mj = mp + 5 * (long long)j;
-  const float4 i0 = mi[0], i1 = mi[1], i2 = mi[2], i3 = mi[3], i4 = mi[4];
-  const float4 j0 = mj[0], j1 = mj[1], j2 = mj[2], j3 = mj[3], j4 = mj[4];
-  const D2 qi = {{i0.x, i0.y}}, qj = {{j0.x, j0.y}};
-  const D2 dpi[3] = {{{i0.z, i0.w}}, {{i1.x, i1.y}}, {{i1.z, i1.w}}};
-  const D2 dpj[3] = {{{j0.z, j0.w}}, {{j1.x, j1.y}}, {{j1.z, j1.w}}};
-  const D2 thi[6] = {{{i2.x, i2.y}}, {{i2.z, i2.w}}, {{i3.x, i3.y}}, {{i3.z, i3.w}}, {{i4.x, i4.y}}, {{i4.z, i4.w}}};
-  const D2 thj[6] = {{{j2.x, j2.y}}, {{j2.z, j2.w}}, {{j3.x, j3.y}}, {{j3.z, j3.w}}, {{j4.x, j4.y}}, {{j4.z, j4.w}}};
-  const D2 third = {{kC3h, kC3l}}, two3 = {{kC23h, kC23l}}, ninth = {{kC9h, kC9l}}, two9 = {{kC29h, kC29l}},
-           four9 = {{kC49h, kC49l}};
+  const Moments mi = load_moments(mp, i), mj = load_moments(mp, j);
   float2* o = out + (long long)kForcePairStride * pid;
-  {
-    D2 ti[3], tj[3];
-    th_mul(thi, r, ti);
-    th_mul(thj, r, tj);
-    const D2 dir = dot3(dpi, r), djr = dot3(dpj, r), tir = dot3(ti, r), tjr = dot3(tj, r);
-    const D2 thth = thi[0] * thj[0] + thi[1] * thj[1] + thi[2] * thj[2] +
-                    twice(thi[3] * thj[3] + thi[4] * thj[4] + thi[5] * thj[5]);
-    const D2 G0 = qi * qj;
-    const D2 G1 = qi * djr - qj * dir + dot3(dpi, dpj);
-    const D2 G2 = (qi * tjr + qj * tir) * third - dir * djr + (dot3(dpi, tj) - dot3(dpj, ti)) * two3 + thth * two9;
-    const D2 G3 = (djr * tir - dir * tjr) * third - dot3(ti, tj) * four9;
-    const D2 G4 = tir * tjr * ninth;
-    const D2 rad = G0 * b[1] + G1 * b[2] + G2 * b[3] + G3 * b[4] + G4 * b[5];
+  D2 v[10];
+  pair_force(r, b, mi.q, mi.d, mi.th, mj.q, mj.d, mj.th, v);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const D2 g1 = qi * dpj[a] - qj * dpi[a];
-      const D2 g2 = (qi * tj[a] + qj * ti[a] + th_row(thj, a, dpi) - th_row(thi, a, dpj)) * two3 -
-                    (dpi[a] * djr + dpj[a] * dir);
-      const D2 g3 = (dpj[a] * tir + twice(djr * ti[a]) - twice(tj[a] * dir) - tjr * dpi[a]) * third -
-                    (th_row(thi, a, tj) + th_row(thj, a, ti)) * four9;
-      const D2 g4 = (ti[a] * tjr + tj[a] * tir) * two9;
-      put(o + a, rad * r[a] - (b[1] * g1 + b[2] * g2 + b[3] * g3 + b[4] * g4));
-    }
-    o[3] = make_float2(0.f, 0.f);
+  for (int a = 0; a < 3; ++a) put(o + a, v[a]);
+  o[3] = make_float2(0.f, 0.f);
+  moment_jet(r, mj.q, mj.d, mj.th, b, v);  // at i, of j
+#pragma unroll
+  for (int k = 0; k < 10; ++k) put(o + 4 + k, v[k]);
+  moment_jet(nr, mi.q, mi.d, mi.th, b, v);  // at j, of i
+#pragma unroll
+  for (int k = 0; k < 10; ++k) put(o + 14 + k, v[k]);
+}
+
+// Float64 epilogue of one atom's 13 sums (force, q, d, Theta): times C, the
+// quadrupole diagonal projected onto traceless changes, outputs in caller
+// order, per-atom energy 1/2 (q dU/dq + d.dU/dd + Theta.dU/dTheta).
+__device__ __forceinline__ void finish_atom(double* v, const double4_32a& a, const double4_32a& b,
+                                            const double4_32a& c, const double4_32a& d, int o, double* F, double* gq,
+                                            double* gd, double* gt, double* e_atom, int i) {
+  const double th[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
+  const double mean = (v[7] + v[8] + v[9]) * (1.0 / 3.0);
+  v[7] -= mean;
+  v[8] -= mean;
+  v[9] -= mean;
+  double u = a.w * v[3] + b.x * v[4] + b.y * v[5] + b.z * v[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) u += th[k] * v[7 + k];
+  e_atom[i] = 0.5 * u;
+  if (F)
+    for (int k = 0; k < 3; ++k) F[3 * o + k] = v[k];
+  if (gq) gq[o] = v[3];
+  if (gd)
+    for (int k = 0; k < 3; ++k) gd[3 * o + k] = v[4 + k];
+  if (gt)
+    for (int k = 0; k < 6; ++k) gt[6 * o + k] = v[7 + k];
+}
+
+// Isolated clusters (no box): every pair with the bare kernels b_n = bare_n;
+// pairs inside one molecule are skipped (B_n - bare_n vanishes at beta = 0).
+// One thread per atom i visits every j (warp-uniform loads) and sums the force
+// on i and i's moment derivatives in double-float; no reciprocal, self or
+// background terms.
+__global__ void __launch_bounds__(128) k_mpole_cluster_df(int n, const float4* __restrict__ pd,
+                                                          const float4* __restrict__ mp,
+                                                          const double4_32a* __restrict__ A,
+                                                          const double4_32a* __restrict__ B,
+                                                          const double4_32a* __restrict__ C,
+                                                          const double4_32a* __restrict__ D,
+                                                          const int* __restrict__ perm, double* __restrict__ F,
+                                                          double* __restrict__ gq, double* __restrict__ gd,
+                                                          double* __restrict__ gt, double* __restrict__ e_atom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
+  const Moments mi = load_moments(mp, i);
+  D2 acc[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) acc[k] = num(0.f);
+  for (int j = 0; j < n; ++j) {
+    const float4 th_j = pd[3 * (long long)j + 2];
+    if (__float_as_int(th_i.z) == __float_as_int(th_j.z)) continue;  // same molecule (and j == i)
+    const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1];
+    const D2 r[3] = {D2{{hi_i.x, lo_i.x}} - D2{{hi_j.x, lo_j.x}}, D2{{hi_i.y, lo_i.y}} - D2{{hi_j.y, lo_j.y}},
+                     D2{{hi_i.z, lo_i.z}} - D2{{hi_j.z, lo_j.z}}};
+    const D2 ir = {df_rsqrt(dot3(r, r).v)};
+    const D2 ir2 = ir * ir;
+    D2 b[6];
+    b[0] = ir;
+#pragma unroll
+    for (int k = 1; k < 6; ++k) b[k] = b[k - 1] * num((float)(2 * k - 1)) * ir2;
+    const Moments mj = load_moments(mp, j);
+    D2 v[10];
+    pair_force(r, b, mi.q, mi.d, mi.th, mj.q, mj.d, mj.th, v);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[a] = acc[a] + v[a];
+    moment_jet(r, mj.q, mj.d, mj.th, b, v);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[3 + k] = acc[3 + k] + v[k];
   }
-  moment_jet(r, qj, dpj, thj, b, o + 4);    // at i, of j
-  moment_jet(nr, qi, dpi, thi, b, o + 14);  // at j, of i
+  double v[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) v[k] = df_to_double(acc[k].v) * kCoulomb;
+  finish_atom(v, A[i], B[i], C[i], D[i], perm[i], F, gq, gd, gt, e_atom, i);
 }
 
 __device__ __forceinline__ unsigned group_mask() {
@@ -453,31 +549,38 @@ dflt split_host(double v) {
 
 int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, double* gt) {
   int r;
-  pme_theta64(c);
-  if ((r = force_buffers(c))) return r;
   if (c->mpole_e_cap < c->n_cap) {
     dev_free(c, c->mpole_e);
     c->mpole_e = nullptr;
     if ((r = dev_alloc(c, &c->mpole_e, c->n_cap))) return r;
     c->mpole_e_cap = c->n_cap;
   }
-  const double b = c->cfg.ewald_beta, L = c->cfg.box;
-  MGeomDf g;
-  g.L = split_host(L);
-  g.beta = split_host(b);
-  g.twob2 = split_host(2.0 * b * b);
-  g.gpre = split_host(2.0 * b / kSqrtPi);
-  g.invL = (float)(1.0 / L);
-  const double c0 = 2.0 * b / kSqrtPi;
-  SelfTerms st;
-  st.q = -c0;
-  st.d = -c0 * (2.0 * b * b / 3.0);
-  st.th = -c0 * (8.0 * b * b * b * b / 45.0);
-  st.bg = -3.14159265358979323846 / (L * L * L * b * b);
   cudaStream_t s = c->stream;
-  // the per-pair records are (hi, lo) float pairs in the backward pair buffer
-  float2* pair = reinterpret_cast<float2*>(c->force_pair);
-  {
+  if (c->cluster) {
+    PhaseScope ps(c, AMP_PHASE_FORCES);
+    launch_split_multipoles(c);
+    c->n_launch += 2;
+    k_mpole_cluster_df<<<amp_blocks(c->n, 128), 128, 0, s>>>(c->n, c->pd, c->mp_df, c->atomA, c->atomB, c->atomC,
+                                                            c->atomD, c->perm, F, gq, gd, gt, c->mpole_e);
+    k_block_sum<<<1, 1024, 0, s>>>(c->n, c->mpole_e, 1, c->scal + 5);
+  } else {
+    pme_theta64(c);
+    if ((r = force_buffers(c))) return r;
+    const double b = c->cfg.ewald_beta, L = c->cfg.box;
+    MGeomDf g;
+    g.L = split_host(L);
+    g.beta = split_host(b);
+    g.twob2 = split_host(2.0 * b * b);
+    g.gpre = split_host(2.0 * b / kSqrtPi);
+    g.invL = (float)(1.0 / L);
+    const double c0 = 2.0 * b / kSqrtPi;
+    SelfTerms st;
+    st.q = -c0;
+    st.d = -c0 * (2.0 * b * b / 3.0);
+    st.th = -c0 * (8.0 * b * b * b * b / 45.0);
+    st.bg = -3.14159265358979323846 / (L * L * L * b * b);
+    // the per-pair records are (hi, lo) float pairs in the backward pair buffer
+    float2* pair = reinterpret_cast<float2*>(c->force_pair);
     PhaseScope ps(c, AMP_PHASE_FORCES);
     if ((r = pme_potential(c, false, true, nullptr, nullptr, c->grid64b))) return r;
     c->n_launch += 2;

@@ -601,6 +601,13 @@ void launch_pair_build(amp_ctx* c) {
                                                 c->T32, c->Ep32);
 }
 
+// The split positions and moments alone (clusters, which build no pair terms).
+void launch_split_multipoles(amp_ctx* c) {
+  c->n_launch += 1;
+  k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
+                                                                  c->mp_df, c->pd);
+}
+
 // Self term of the permanent field: +4 beta^3/(3 sqrt(pi)) d_i, d_i from atomB.
 void launch_e0_real(amp_ctx* c, double4_32a* out) {
   const PairGeom g = geom(c);

@@ -1,8 +1,8 @@
 """Permanent-multipole energy and gradients on the GPU against the oracle.
 
-Element by element on the 648-atom box and on small boxes (a ragged 8-water
-box, a charged variant that exercises the neutralising background), in both
-precision modes (the multipole path is float64 in both); on the 23,556-atom
+Element by element on the 648-atom box, on small boxes (a ragged 8-water
+box, a charged variant that exercises the neutralising background) and on a
+40-water cluster, in both precision modes (float64 results in both); on the 23,556-atom
 box the energy and eight sampled atoms against stored oracle values. Also
 after a position update that reuses the skin lists, and the argument checks.
 Tolerances: energy 1e-10 relative, gradients 1e-10 (2-norm relative).
@@ -111,10 +111,17 @@ def test_energy_only_and_argument_checks():
     U, _ = gpu_mpole(p)
     # the float64 grid is spread with atomic adds: equal up to summation order
     assert U_only == pytest.approx(U, rel=1e-13)
-    c = ap.Polarization(ap.Config(box=0.0, tol_debye=1e-8))
-    c.set_synthetic(make_waters(3, 6.0, 3, periodic=False))
-    with pytest.raises(ap.AmpError):
-        c.multipole_energy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cluster_matches_oracle(precision):
+    """Isolated cluster: every pair with the bare kernels, nothing else."""
+    from paper_1906_01211_gb300 import amoebapol as ap
+    s = make_waters(40, 12.0, 4, periodic=False)
+    ref = multipole_energy(s, Setup.cluster())
+    p = ap.Polarization(ap.Config(box=0.0, tol_debye=1e-8, precision=precision))
+    p.set_synthetic(s)
+    check(*gpu_mpole(p), ref)
 
 
 def test_autograd_matches_the_call_and_finite_differences():
