@@ -145,6 +145,38 @@ def test_exact_ewald_energy_independent_of_beta(charged):
     assert max(us) - min(us) < 1e-10 * abs(us[0])
 
 
+def _lattice(m, a, q, dip):
+    pts = np.array(list(itertools.product(range(m), repeat=3)), float)
+    n = len(pts)
+    return pts, System(xyz=pts * a + 0.1, q=q(pts), dip=np.tile(dip, (n, 1)), quad=np.zeros((n, 6)),
+                       alpha=np.ones(n), thole=np.full(n, 0.39), mol=np.arange(n, dtype=np.int32), box=m * a)
+
+
+def test_rock_salt_madelung_constant():
+    """Charges +-1 on a rock-salt lattice (nearest-neighbour distance a): the
+    energy per ion pair is -C M / a with the Madelung constant of NaCl,
+    M = 1.747564594633182 (standard tables)."""
+    a = 2.8
+    pts, s = _lattice(4, a, lambda p: np.where(p.sum(1) % 2 == 0, 1.0, -1.0), np.zeros(3))
+    for beta in (0.7, 0.9):
+        U = multipole_energy_exact(s, beta)
+        assert -U / (s.n / 2) * a / COULOMB == pytest.approx(1.747564594633182, rel=1e-12)
+    L = s.box
+    st = Setup(box=L, cutoff=L / 2 - 1e-6, beta=3.8122 / (L / 2 - 1e-6), grid=32, order=8)
+    assert -energy(s, st) / (s.n / 2) * a / COULOMB == pytest.approx(1.747564594633182, rel=1e-6)
+
+
+def test_cubic_lattice_of_parallel_dipoles():
+    """Identical dipoles d on a simple cubic lattice (edge a): the lattice sum
+    vanishes by cubic symmetry, so with tin-foil boundary the energy per dipole
+    is the surface-term difference, -(2 pi / 3) C |d|^2 / a^3."""
+    a, d = 3.0, np.array([0.02, -0.05, 0.03])
+    _, s = _lattice(2, a, lambda p: np.zeros(len(p)), d)
+    for beta in (0.6, 0.9):
+        assert multipole_energy_exact(s, beta) / s.n == pytest.approx(-2 * np.pi / 3 * (d @ d) / a ** 3 * COULOMB,
+                                                                      rel=1e-12)
+
+
 def test_pme_converges_to_exact_ewald():
     """Minimum-image real space + PME approach the lattice sum truncated at the
     same cutoff as the grid is refined, and meet it at order 8."""
