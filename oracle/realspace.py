@@ -44,7 +44,7 @@ def quad_matrix(quad6: np.ndarray) -> np.ndarray:
 
 def scatter_add(n: int, idx: np.ndarray, vals: np.ndarray) -> np.ndarray:
     """out[k] = sum of vals[p] over p with idx[p] == k; vals (P, ...)."""
-    flat = vals.reshape(vals.shape[0], -1)
+    flat = vals.reshape(vals.shape[0], int(np.prod(vals.shape[1:])))
     out = np.empty((n, flat.shape[1]))
     for c in range(flat.shape[1]):
         out[:, c] = np.bincount(idx, weights=flat[:, c], minlength=n)

@@ -239,6 +239,53 @@ def test_pme_converges_to_kspace_sum(box64):
     assert rel(permanent_field_recip(s, st, g), perm_ex) < 1e-7
 
 
+def _cubic_lattice(m, a, d, alpha):
+    pts = np.array([[i, j, k] for i in range(m) for j in range(m) for k in range(m)], float)
+    n = len(pts)
+    return System(xyz=pts * a + 0.1, q=np.zeros(n), dip=np.tile(d, (n, 1)), quad=np.zeros((n, 6)),
+                  alpha=np.full(n, alpha), thole=np.full(n, 0.39), mol=np.arange(n, dtype=np.int32), box=m * a)
+
+
+def test_cubic_lattice_lorentz_field_and_induced_dipoles():
+    """Identical sites with identical permanent dipoles d on a simple cubic
+    lattice (edge a). The dipole tensor summed over complete cubic shells
+    vanishes, so under tin-foil Ewald the field at every site is the Lorentz
+    field k d, k = 4 pi / (3 a^3); the induced dipoles are then uniform with
+    mu = alpha k (d + mu), i.e. mu = alpha k d / (1 - alpha k). (Thole damping
+    changes the shell sums by x e^-x / r^3 per neighbour, ~1e-14 here.)"""
+    a, d, alpha = 3.0, np.array([0.02, -0.05, 0.03]), 0.3
+    k = 4 * np.pi / (3 * a ** 3)
+    e_ref, mu_ref = k * d, alpha * k * d / (1 - alpha * k)
+    s = _cubic_lattice(2, a, d, alpha)
+    for beta in (0.8, 1.1):
+        ex = ExactEwald(s, beta)
+        e0 = ex.permanent_field()
+        mu, _, _ = pcg(lambda v: (1 / s.alpha)[:, None] * v - ex.apply_T(v), s.alpha, e0, 1e-13, 100)
+        assert np.abs(e0 - e_ref).max() < 1e-12 * np.abs(e_ref).max()
+        assert np.abs(mu - mu_ref).max() < 1e-12 * np.abs(mu_ref).max()
+    # production oracle (minimum image + PME) on a 3 x 3 x 3 box: complete shells inside the cutoff
+    s = _cubic_lattice(3, a, d, alpha)
+    rc, beta, K = small_box_settings(s.box)
+    errs = []
+    for grid, order in ((K, 5), (32, 5), (32, 8)):
+        op = Operator(s, Setup(box=s.box, cutoff=rc, beta=beta, grid=grid, order=order))
+        e0 = op.permanent_field()
+        mu, _, _ = solve(op, e0, 1e-13, 100)
+        errs.append((np.abs(e0 - e_ref).max() / np.abs(e_ref).max(), np.abs(mu - mu_ref).max() / np.abs(mu_ref).max()))
+    assert errs[0][0] > errs[1][0] > errs[2][0] and errs[2][0] < 1e-5 and errs[2][1] < 1e-5
+    # 2 x 2 x 2 box: the neighbours sit at a = L/2, beyond the cutoff, so no
+    # pair is listed and reciprocal + self carry the field (the screened
+    # nearest-neighbour terms left out are ~3e-5 of it)
+    s = _cubic_lattice(2, a, d, alpha)
+    rc, beta, K = small_box_settings(s.box)
+    op = Operator(s, Setup(box=s.box, cutoff=rc, beta=beta, grid=32, order=8))
+    assert op.n_pairs == 0
+    e0 = op.permanent_field()
+    mu, _, _ = solve(op, e0, 1e-13, 100)
+    assert np.abs(e0 - e_ref).max() < 1e-4 * np.abs(e_ref).max()
+    assert np.abs(mu - mu_ref).max() < 1e-4 * np.abs(mu_ref).max()
+
+
 def test_energy_independent_of_ewald_beta():
     """Exact Ewald polarization energy does not depend on the splitting."""
     s = make_waters(8, 7.0, 7)
