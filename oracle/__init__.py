@@ -20,7 +20,9 @@ standard Ewald / smooth-PME literature):
 * the polarization energy and its gradients (paper, Section "Hotspots":
   ``epolar1``);
 * the permanent-multipole energy and its gradients (paper, Section
-  "Hotspots": ``empole1``).
+  "Hotspots": ``empole1``);
+* the TCG-1 energy (one truncated conjugate-gradient step) and its exact
+  gradients (paper, Section "Perspectives on Tinker-HP 1.2 performance").
 
 Modules:
   ewald      screened Coulomb kernels B_n and Thole damping
@@ -32,6 +34,7 @@ Modules:
   energy     polarization energy
   forces     gradients of the polarization energy (positions, multipoles)
   multipole  permanent-multipole energy and gradients (derivative tensors)
+  tcg        TCG-1 energy and gradients; d(c.E)/dx and d(a.T b)/dx
 
 Every function works in float64 numpy. Pins that tie it to the physics
 (closed forms, brute force, invariants) live in ``tests/test_oracle_*.py``.
