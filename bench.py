@@ -228,6 +228,31 @@ def oracle_sample(workload, steps: int, warmup: int):
     return op.n_pairs, times, t_build
 
 
+def oracle_multipole_sample(workload, pairs_sample: int = 200_000):
+    """The CPU oracle's permanent-multipole energy and gradients on the
+    workload, timed on a bounded sample: the real-space pair terms of the
+    first `pairs_sample` unique pairs (scaled to all pairs) plus one full
+    reciprocal evaluation."""
+    from oracle import Setup
+    from oracle.multipole import real_space, reciprocal
+    from oracle.pairs import periodic_pairs
+    w = workload
+    sysm = w.system()
+    st = Setup(box=w.L, cutoff=w.cutoff, beta=w.beta, grid=w.grid, order=w.order)
+    i, j, r = periodic_pairs(sysm.xyz, st.box, st.cutoff)
+    p = min(pairs_sample, len(i))
+    t0 = time.perf_counter()
+    real_space(sysm, st, (i[:p], j[:p], r[:p]))
+    t_real = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    reciprocal(sysm, st)
+    t_rec = time.perf_counter() - t0
+    est = t_real * len(i) / p + t_rec
+    return {"ms_per_call": 1e3 * est, "cores": 1, "kind": "oracle",
+            "sample": f"real-space pair terms of {p} of {len(i)} unique pairs ({t_real:.1f} s, scaled to all "
+                      f"pairs) + one reciprocal evaluation ({t_rec:.1f} s) of the float64 numpy oracle on {w.name}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -546,6 +571,8 @@ def main():
     mpole = None
     if not args.no_multipole:
         mpole = run_multipole(solver, dev_in, stream, flush)
+        if not args.no_cpu_baseline and rank == 0:
+            mpole["cpu_baseline"] = oracle_multipole_sample(w)
 
     cpu = None
     if not args.no_cpu_baseline:
