@@ -22,7 +22,9 @@ standard Ewald / smooth-PME literature):
 * the permanent-multipole energy and its gradients (paper, Section
   "Hotspots": ``empole1``);
 * the TCG-1 energy (one truncated conjugate-gradient step) and its exact
-  gradients (paper, Section "Perspectives on Tinker-HP 1.2 performance").
+  gradients (paper, Section "Perspectives on Tinker-HP 1.2 performance");
+* local-frame multipoles and the forces their frames add (paper, Section
+  "Polarizable AMOEBA force field").
 
 Modules:
   ewald      screened Coulomb kernels B_n and Thole damping
@@ -35,6 +37,7 @@ Modules:
   forces     gradients of the polarization energy (positions, multipoles)
   multipole  permanent-multipole energy and gradients (derivative tensors)
   tcg        TCG-1 energy and gradients; d(c.E)/dx and d(a.T b)/dx
+  frames     local frames (Z-then-X, bisector), global moments, frame forces
 
 Every function works in float64 numpy. Pins that tie it to the physics
 (closed forms, brute force, invariants) live in ``tests/test_oracle_*.py``.

@@ -134,6 +134,20 @@ def make_waters(n_waters: int, L: float, seed: int, periodic: bool = True) -> Sy
                   meta={"n_waters": n_waters, "seed": seed, "L": float(L)})
 
 
+def water_frames(n_waters: int):
+    """Local-frame topology of the waters of ``make_waters`` (O, H, H order):
+    (kind, z atom, x atom) per site, AMOEBA's water convention. Oxygen:
+    bisector (kind 1) of its two hydrogens; each hydrogen: Z-then-X (kind 0)
+    with z toward its oxygen and x toward the other hydrogen. With these
+    frames the drawn dipoles and quadrupoles are read as local-frame values.
+    Topology only: the frames themselves are computed by the method."""
+    base = 3 * np.arange(n_waters, dtype=np.int32)
+    kind = np.tile(np.array([1, 0, 0], dtype=np.int32), n_waters)
+    zatom = np.stack([base + 1, base, base], axis=1).reshape(-1)
+    xatom = np.stack([base + 2, base + 2, base + 1], axis=1).reshape(-1)
+    return kind, zatom.astype(np.int32), xatom.astype(np.int32)
+
+
 def density_box_edge(n_waters: int) -> float:
     """Edge of a cube holding ``n_waters`` at 0.0334 waters per Angstrom^3."""
     return (n_waters / WATER_DENSITY) ** (1.0 / 3.0)
