@@ -23,8 +23,9 @@ standard Ewald / smooth-PME literature):
   "Hotspots": ``empole1``);
 * the TCG-1 energy (one truncated conjugate-gradient step) and its exact
   gradients (paper, Section "Perspectives on Tinker-HP 1.2 performance");
-* local-frame multipoles and the forces their frames add (paper, Section
-  "Polarizable AMOEBA force field").
+* local-frame multipoles and the forces their frames add, and the
+  two-field (direct / polarization scaled) solve with its energy and
+  gradients (paper, Section "Polarizable AMOEBA force field").
 
 Modules:
   ewald      screened Coulomb kernels B_n and Thole damping
@@ -38,6 +39,7 @@ Modules:
   multipole  permanent-multipole energy and gradients (derivative tensors)
   tcg        TCG-1 energy and gradients; d(c.E)/dx and d(a.T b)/dx
   frames     local frames (Z-then-X, bisector), global moments, frame forces
+  two_rhs    direct- and polarization-scaled fields, two solves, energy, gradients
 
 Every function works in float64 numpy. Pins that tie it to the physics
 (closed forms, brute force, invariants) live in ``tests/test_oracle_*.py``.

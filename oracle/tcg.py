@@ -60,15 +60,18 @@ def _hessians(g, phi, n):
     return h
 
 
-def field_gradients(op, c):
-    """(d(c.E)/dx (N,3), d/dq (N,), d/dd (N,3), d/dTheta6 (N,6)) at fixed c."""
+def field_gradients(op, c, scale=None):
+    """(d(c.E)/dx (N,3), d/dq (N,), d/dd (N,3), d/dTheta6 (N,6)) at fixed c.
+
+    scale: per-pair scale of the permanent field (default: 0 inside a
+    molecule, 1 otherwise)."""
     sys, setup, t = op.sys, op.setup, op.terms
     n = sys.n
     i, j, r, dist = t.i, t.j, t.r, t.dist
     rhat = r / dist[:, None]
     l3, l5, l7, _ = t.lam
     l3p, l5p, l7p = _lambda_derivs(t.x, dist)
-    s = t.inter
+    s = t.inter if scale is None else scale
     b1, db1 = _damped(t, 1, s, l3, l3p)
     b2, db2 = _damped(t, 2, s, l5, l5p)
     b3, db3 = _damped(t, 3, s, l7, l7p)
