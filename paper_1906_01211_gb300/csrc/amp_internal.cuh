@@ -228,7 +228,7 @@ void launch_pair_build(amp_ctx* c);
 int dfm_setup(amp_ctx* c);  // builds c->dfm
 void launch_e0_real(amp_ctx* c, double4_32a* out);  // out = real-space E0 + self
 // out = T_real v + self v (float64 path, double-float arithmetic; vhi + vlo = v)
-void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const float4* vlo, double4_32a* out);
+void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out);
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out);
 void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* out);
 

@@ -398,20 +398,6 @@ __global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __res
   }
 }
 
-__device__ __forceinline__ void t_entry(dflt& sx, dflt& sy, dflt& sz, float4 a, float4 b, float4 c, float4 h,
-                                        float4 w) {
-  // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
-  df_fma(sx, a.x, b.z, h.x, w.x);
-  df_fma(sx, a.w, c.y, h.y, w.y);
-  df_fma(sx, b.x, c.z, h.z, w.z);
-  df_fma(sy, a.w, c.y, h.x, w.x);
-  df_fma(sy, a.y, b.w, h.y, w.y);
-  df_fma(sy, b.y, c.w, h.z, w.z);
-  df_fma(sz, b.x, c.z, h.x, w.x);
-  df_fma(sz, b.y, c.w, h.y, w.y);
-  df_fma(sz, a.z, c.x, h.z, w.z);
-}
-
 constexpr int kTRealBlocksPerSm = 4;  // of the 5 (float64) or 6 (mixed) that the registers would allow
 
 // out_i = sum_j T_ij v_j + selfc v_i for the float64 path, in double-float:
@@ -622,9 +608,9 @@ void launch_e0_real(amp_ctx* c, double4_32a* out) {
                                                             c->atomB, out);
 }
 
-// v must be mirrored in its float-pair split (vhi, vlo) = (p32, plo); the
-// kernel reads the same split from vhl, which every split kernel writes beside.
-void launch_t_real(amp_ctx* c, const double4_32a* v, const float4* vhi, const float4* vlo, double4_32a* out) {
+// v must be mirrored in its float-pair split, which the kernel reads from vhl
+// (every split kernel writes it beside p32 / plo).
+void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out) {
   const PairGeom g = geom(c);
   c->n_launch += 1;
   // At most kTRealBlocksPerSm blocks per SM (the rows are grid-strided): the

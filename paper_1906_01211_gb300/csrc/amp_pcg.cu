@@ -480,7 +480,7 @@ static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, cons
     if (mode == kRealDirectDf)
       launch_t_real_fp64_direct(c, v, t);
     else if (mode == kRealDf)
-      launch_t_real(c, v, v32, vlo, t);
+      launch_t_real(c, v, t);
     else
       launch_t_real32(c, v32, v, t);
   }

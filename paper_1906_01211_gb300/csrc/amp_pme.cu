@@ -223,10 +223,6 @@ __device__ __forceinline__ int wrapk(int g, int K) { return g < 0 ? g + K : g; }
 // thread per atom, which the float64 pipe needs to stay busy.
 constexpr int kPmeGroup = 8;
 
-__device__ __forceinline__ unsigned pme_group_mask() {
-  return ((1u << kPmeGroup) - 1u) << ((threadIdx.x & 31) & ~(kPmeGroup - 1));
-}
-
 template <typename R>
 __global__ void __launch_bounds__(128) k_spread_multipoles(int n, const R* __restrict__ theta,
                                                            const int4* __restrict__ gbase,
@@ -452,67 +448,6 @@ __global__ void k_convolve(long long m, C* __restrict__ cg, const R* __restrict_
   v.x *= g;
   v.y *= g;
   cg[k] = v;
-}
-
-// out_i += -sum_g grad W_i(g) phi(g) (kSet: out_i = ...); lane t of the atom's
-// group sums plane k0x - t, the group adds the five planes.
-template <typename R, bool kSet = false>
-__global__ void __launch_bounds__(128) k_gather_field(int n, const R* __restrict__ theta,
-                                                      const int4* __restrict__ gbase, const R* __restrict__ phi,
-                                                      int K, double4_32a* __restrict__ out,
-                                                      const int* __restrict__ stop = nullptr) {
-  if (stop && *stop) return;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = gid / kPmeGroup, tx = gid % kPmeGroup;
-  if (s >= n) return;  // whole groups leave together
-  double ex = 0.0, ey = 0.0, ez = 0.0;
-  const int4 b = gbase[s];
-  if (tx < kOrder) {
-    const R* th = theta + (long long)kTh * s;
-    const R wx0 = th[(0 * 4 + 0) * kOrder + tx], wx1 = th[(0 * 4 + 1) * kOrder + tx];
-    R wz0[kOrder], wz1[kOrder];
-    for (int t = 0; t < kOrder; ++t) {
-      wz0[t] = th[(2 * 4 + 0) * kOrder + t];
-      wz1[t] = th[(2 * 4 + 1) * kOrder + t];
-    }
-    const int gx = wrapk(b.x - tx, K);
-    R px = 0, py = 0, pz = 0;
-    for (int ty = 0; ty < kOrder; ++ty) {
-      const R wy0 = th[(1 * 4 + 0) * kOrder + ty], wy1 = th[(1 * 4 + 1) * kOrder + ty];
-      const int gy = wrapk(b.y - ty, K);
-      const R* row = phi + ((long long)gx * K + gy) * K;
-      R s0 = 0, s1 = 0;
-      for (int tz = 0; tz < kOrder; ++tz) {
-        const R p = row[wrapk(b.z - tz, K)];
-        s0 += wz0[tz] * p;
-        s1 += wz1[tz] * p;
-      }
-      px += wy0 * s0;
-      py += wy1 * s0;
-      pz += wy0 * s1;
-    }
-    ex = (double)(wx1 * px);
-    ey = (double)(wx0 * py);
-    ez = (double)(wx0 * pz);
-  }
-  const unsigned mask = pme_group_mask();
-#pragma unroll
-  for (int o = kPmeGroup / 2; o > 0; o >>= 1) {
-    ex += __shfl_xor_sync(mask, ex, o, kPmeGroup);
-    ey += __shfl_xor_sync(mask, ey, o, kPmeGroup);
-    ez += __shfl_xor_sync(mask, ez, o, kPmeGroup);
-  }
-  if (tx == 0) {
-    if (kSet) {
-      out[s] = make_double4_32a(-ex, -ey, -ez, 0.0);
-    } else {
-      double4_32a o = out[s];
-      o.x -= ex;
-      o.y -= ey;
-      o.z -= ez;
-      out[s] = o;
-    }
-  }
 }
 
 // phi = hi + lo for every grid point (float64 path, once per gather)
