@@ -22,7 +22,8 @@ standard Ewald / smooth-PME literature):
 * the permanent-multipole energy and its gradients (paper, Section
   "Hotspots": ``empole1``);
 * the TCG-1 energy (one truncated conjugate-gradient step) and its exact
-  gradients (paper, Section "Perspectives on Tinker-HP 1.2 performance");
+  gradients, and divide-and-conquer Jacobi iterations (paper, Section
+  "Perspectives on Tinker-HP 1.2 performance");
 * local-frame multipoles and the forces their frames add, and the
   two-field (direct / polarization scaled) solve with its energy and
   gradients (paper, Section "Polarizable AMOEBA force field").
@@ -38,6 +39,7 @@ Modules:
   forces     gradients of the polarization energy (positions, multipoles)
   multipole  permanent-multipole energy and gradients (derivative tensors)
   tcg        TCG-1 energy and gradients; d(c.E)/dx and d(a.T b)/dx
+  dcji       divide-and-conquer (block) Jacobi iterations on the dense operator
   frames     local frames (Z-then-X, bisector), global moments, frame forces
   two_rhs    direct- and polarization-scaled fields, two solves, energy, gradients
 
