@@ -43,7 +43,20 @@ def test_create_rejects_bad_config(lib_path):
 def test_null_context_calls_fail_cleanly(lib_path):
     from paper_1906_01211_gb300 import amoebapol as ap
     assert ap._lib.amp_set_system(None, 3, None, None, None, None, None, None, None) == ap.AMP_ERR_ARG
+    assert ap._lib.amp_multipole_energy(None, None, None, None, None, None) == ap.AMP_ERR_ARG
     assert ap.amp_last_error(None) == "null context"
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: loading the binding against a missing library raises."""
+    import subprocess
+    import sys
+    code = ("import paper_1906_01211_gb300.amoebapol as ap, ctypes\n"
+            "ap.LIB_PATH = %r\n"
+            "try:\n    ap._load()\nexcept ImportError as e:\n    print('raised')\n") % str(tmp_path / "missing.so")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert "raised" in out.stdout, out.stderr
 
 
 def test_predictor_coefficients(lib_path):
