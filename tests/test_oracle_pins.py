@@ -215,6 +215,22 @@ def test_bspline_matches_scipy_basis_element():
         assert np.allclose(cardinal_bspline_deriv(5, u, d), expect, atol=1e-13)
 
 
+def test_bspline_moduli_properties():
+    """|b(m)|^2 = 1/|sum_k M_n(k+1) exp(2 pi i m k/K)|^2: 1 at m = 0 (the
+    B-spline weights sum to one), even in m, and for odd order and even K the
+    denominator vanishes at m = K/2, where the neighbour mean is used."""
+    from oracle.pme import bspline_moduli, cardinal_bspline
+    for K in (16, 24):
+        b2 = bspline_moduli(K, 5)
+        assert b2[0] == pytest.approx(1.0, abs=1e-14)
+        assert np.allclose(b2[1:], b2[1:][::-1], rtol=1e-13)
+        kk = np.arange(4)
+        den = abs((cardinal_bspline(5, kk + 1.0) * np.exp(2j * np.pi * (K // 2) * kk / K)).sum()) ** 2
+        assert den < 1e-12
+        assert b2[K // 2] == pytest.approx(0.5 * (b2[K // 2 - 1] + b2[K // 2 + 1]), rel=1e-14)
+        assert np.all(np.isfinite(b2)) and np.all(b2 >= 1.0 - 1e-14)
+
+
 def test_pme_converges_to_kspace_sum(box64):
     s, L, rc, beta, K = box64
     ex = ExactEwald(s, beta)
