@@ -198,6 +198,23 @@ def run_serving(n_requests: int, slots: int, rate_factors, warm: int = 40):
     return out
 
 
+def max_over_ranks(t_ms: float, world: int, device) -> float:
+    """The largest of every rank's time (t_ms itself on one rank): the job
+    takes as long as its slowest replica."""
+    if world <= 1:
+        return t_ms
+    import torch
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_ms: float) -> float:
+    """Units per second of the whole job: every rank processes the same
+    units (weak scaling, independent replicas) in at most t_ms."""
+    return world * units_per_rank / (t_ms / 1e3)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -470,13 +487,9 @@ def main():
     torch.cuda.synchronize()
     launches = p.launch_count() - launches0
     clk = clocks.stop() if clocks else None
-    t_total = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(sum(step_ms), world, dev)
     apps = sum(applications)
-    value = world * n_pairs * apps / (t_total / 1e3)
+    value = whole_job_rate(n_pairs * apps, world, t_total)
 
     # ---- end to end through the public API with host buffers
     e2e_ms = []
@@ -490,12 +503,8 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        tt = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(tt.item())
-    e2e_value = world * n_pairs * apps / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(sum(e2e_ms), world, dev)
+    e2e_value = whole_job_rate(n_pairs * apps, world, e2e_total)
     d2h_bytes = mu_host.numel() * 8 + 8
 
     if rank != 0:
