@@ -7,7 +7,11 @@ per-pair tensors, permanent field (real + PME + self), the PCG solve (each
 iteration one T*mu = real + PME + self) and the polarization energy.
 
 value = unique pairs x T*mu applications in the step / step time  (pairs/s)
-ms_per_step = solve time from positions to energy.
+ms_per_step = step_ms = time of the whole step, positions to energy;
+solve_ms = amp_solve_induced alone, from the permanent field to the converged
+dipoles. The mixed-precision step on the same box and the 96,000-atom box
+(float64 and mixed) are reported beside it with their errors against the
+oracle's stored solutions (tests/golden).
 
 Multi-GPU: independent replicas (one per rank, same workload, no data-path
 collective), weak scaling; a barrier and a max over ranks bracket the timing.
@@ -32,6 +36,13 @@ if ROOT not in sys.path:
 
 METRIC = "T·μ pairs/s & solve ms, FP64 vs mixed @1e-5 D RMS; serving p50/p99"
 UNIT = "pairs/s"
+# The headline path's arithmetic: per-pair terms, T*mu and its PME chain in
+# double-float (a value is the unevaluated sum of two floats), the permanent
+# field and the PCG vectors, dot products and scalars in float64.
+DTYPE = "f32x2+f64"
+DTYPE_NOTE = ("double-float (hi + lo float32 pairs, ~48-bit significand) for the pair terms, T*mu and its PME "
+              "spreading, FFTs and gather; float64 for the permanent field E0 and the PCG vectors, dot products "
+              "and scalars")
 
 
 def parse():
@@ -45,14 +56,17 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-md", action="store_true", help="skip the list-reuse trajectory measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 96,000-atom box (float64 and mixed)")
     ap.add_argument("--no-multipole", action="store_true", help="skip the permanent-multipole energy measurement")
     ap.add_argument("--multipole-only", action="store_true",
                     help="time only the permanent-multipole energy call on the workload and print it")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement (request stream, rates) as its own JSON line")
-    ap.add_argument("--requests", type=int, default=300)
-    ap.add_argument("--slots", type=int, default=8)
-    ap.add_argument("--rates", default="2.0", help="arrival rates as multiples of the float64 capacity")
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--workers", type=int, default=6, help="serving: context workers beside the batched engine")
+    ap.add_argument("--rates", default="1,2", help="serving: arrival rates as multiples of the float64 capacity")
+    ap.add_argument("--rates-capacity", default="0.5,0.8",
+                    help="serving: arrival rates as multiples of the server's measured capacity")
     return ap.parse_args()
 
 
@@ -142,59 +156,97 @@ def run_multipole(solver, dev_in, stream, flush, reps: int = 10):
             "outputs": "U, F, dU/dq, dU/dd, dU/dTheta (float64)"}
 
 
-def run_serving(n_requests: int, slots: int, rate_factors, warm: int = 40):
-    """Poisson stream of solve requests (sizes log-uniform 64..4096 waters, half
-    clusters, half periodic boxes; mixed precision, 1e-5 D) through the
-    continuous-batching server, against one-at-a-time float64 solves."""
+def run_serving(n_requests: int, workers: int, rates_vs_fp64, rates_vs_capacity, baseline_requests: int = 2000,
+                warm: int = 60):
+    """The native server (amp_server_*) on a seeded Poisson stream of solve
+    requests (sizes log-uniform 64..4096 waters, half clusters, half periodic
+    boxes; mixed precision, 1e-5 D), against one-at-a-time float64 solves.
+
+    1. one-at-a-time float64 (one worker, no batched engine, each request
+       submitted after the previous one finished) on the first
+       baseline_requests of the stream: its throughput is the float64
+       capacity, its latency the service time alone;
+    2. the server saturated (all requests submitted at once): its capacity;
+    3. Poisson arrivals at multiples of the server's capacity and of the
+       float64 capacity: throughput, p50 and p99 latency (submission to
+       result), mean iterations, and which path served the requests.
+    Warm-up requests (one per PME grid size the stream needs, the largest
+    box of each, and a few clusters) run first on every server, so that the
+    context pool is built before the timed stream."""
     import numpy as np
     from paper_1906_01211_gb300.serve import Server, percentile, request_stream
     reqs = request_stream(n_requests + warm, seed=4)
     warm_reqs, reqs = reqs[:warm], reqs[warm:]
-    # one-at-a-time float64: one slot, each request alone, back to back
-    base = Server(n_slots=1, precision="fp64", tol_debye=1e-5)
-    for s in warm_reqs:
-        base.result(base.submit(s))
+    # the largest periodic box per grid size, so that every pooled context is sized once
+    by_grid = {}
+    for r in reqs:
+        if r.box is not None:
+            from paper_1906_01211_gb300.synth import small_box_settings
+            K = small_box_settings(r.box)[2]
+            if K not in by_grid or r.n > by_grid[K].n:
+                by_grid[K] = r
+    warm_set = list(by_grid.values()) + warm_reqs
+
+    def warm_up(srv):
+        ids = [srv.submit(s) for s in warm_set]
+        for i in ids:
+            r = srv.result(i)
+            if not r.ok:
+                raise RuntimeError(r.error)
+
+    base = Server(n_workers=1, precision="fp64", tol_debye=1e-5, batch_max_atoms=0)
+    warm_up(base)
+    sample = reqs[:baseline_requests]
     service = []
     t0 = time.perf_counter()
-    for s in reqs:
+    for s in sample:
         r = base.result(base.submit(s))
         if not r.ok:
             raise RuntimeError(r.error)
-        service.append(r.t_done - r.t_start)
-    t_base = time.perf_counter() - t0
+        service.append(r.t_done - r.t_submit)
+    cap64 = len(sample) / (time.perf_counter() - t0)
     base.close()
-    cap = len(reqs) / t_base
-    out = {"requests": len(reqs), "slots": slots, "precision": "mixed", "tol_debye": 1e-5,
-           "one_at_a_time_fp64": {"throughput_per_s": cap, "p50_ms": 1e3 * percentile(service, 50),
-                                  "p99_ms": 1e3 * percentile(service, 99)},
+    out = {"requests": len(reqs), "workers": workers, "precision": "mixed", "tol_debye": 1e-5,
+           "one_at_a_time_fp64": {"requests": len(sample), "throughput_per_s": cap64,
+                                  "p50_ms": 1e3 * percentile(service, 50), "p99_ms": 1e3 * percentile(service, 99)},
            "rates": []}
-    rng = np.random.Generator(np.random.PCG64(44))
-    for f in rate_factors:
-        srv = Server(n_slots=slots, precision="mixed", tol_debye=1e-5)
-        for s in warm_reqs:
-            srv.result(srv.submit(s))
-        lam = f * cap
-        gaps = rng.exponential(1.0 / lam, len(reqs))
+
+    def stream(srv, lam, gaps):
         t_start = time.perf_counter()
         t_next = t_start
         ids = []
         for s, g in zip(reqs, gaps):
-            t_next += g
-            dt = t_next - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
+            if lam is not None:
+                t_next += g
+                dt = t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
             ids.append(srv.submit(s))
         res = [srv.result(i) for i in ids]
-        t_end = max(r.t_done for r in res)
-        srv.close()
+        wall = time.perf_counter() - t_start
         bad = [r.error for r in res if not r.ok]
         if bad:
             raise RuntimeError(bad[0])
         lat = [r.latency for r in res]
-        out["rates"].append({"arrival_per_s": lam, "rate_vs_fp64_capacity": f,
-                             "throughput_per_s": len(res) / (t_end - t_start),
-                             "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
-                             "mean_iters": float(np.mean([r.iters for r in res]))})
+        paths = {p: sum(1 for r in res if r.path == p) for p in ("batched", "worker")}
+        return {"throughput_per_s": len(res) / wall, "p50_ms": 1e3 * percentile(lat, 50),
+                "p99_ms": 1e3 * percentile(lat, 99), "mean_iters": float(np.mean([r.iters for r in res])),
+                "served_by": paths}
+
+    srv = Server(n_workers=workers, precision="mixed", tol_debye=1e-5)
+    warm_up(srv)
+    sat = stream(srv, None, [0.0] * len(reqs))
+    cap = sat["throughput_per_s"]
+    out["saturated"] = sat
+    out["batch_launches"] = srv.stats()["batch_launches"]
+    rng = np.random.Generator(np.random.PCG64(44))
+    for label, f, ref in [("capacity", f, cap) for f in rates_vs_capacity] + \
+                         [("fp64_capacity", f, cap64) for f in rates_vs_fp64]:
+        lam = f * ref
+        res = stream(srv, lam, rng.exponential(1.0 / lam, len(reqs)))
+        res.update({"arrival_per_s": lam, "rate_vs": label, "factor": f})
+        out["rates"].append(res)
+    srv.close()
     return out
 
 
@@ -222,27 +274,139 @@ def dist_env():
 
 # ------------------------------------------------------------------ oracle side
 
-def oracle_sample(workload, steps: int, warmup: int):
-    """Time T*mu applications of the CPU oracle on the workload (one per step)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(conn, workload_name: str, part: int, parts: int):
+    """One process of the oracle pool. With one part it computes the whole
+    T*mu. With several, part 0 computes the reciprocal and self terms and part
+    k >= 1 the real-space terms of every (parts-1)-th unique pair from k-1 on
+    (the oracle's own PairTerms and dipole_field_real on that subset of the
+    pair list). Receives mu, sends its partial T*mu."""
     import numpy as np
     from oracle import Setup
-    from oracle.solver import Operator
-    w = workload
+    from oracle.pairs import pairs_for
+    from oracle.pme import PmeGrid, dipole_field_recip, self_field
+    from oracle.realspace import PairTerms, dipole_field_real
+    from paper_1906_01211_gb300.synth import WORKLOADS
+    w = WORKLOADS[workload_name]
     sysm = w.system()
     st = Setup(box=w.L, cutoff=w.cutoff, beta=w.beta, grid=w.grid, order=w.order)
+    i, j, r = pairs_for(sysm.xyz, st)
+    terms = None
+    if parts == 1 or part > 0:
+        sel = slice(0, None, 1) if parts == 1 else slice(part - 1, None, parts - 1)
+        terms = PairTerms(sysm, st, i[sel], j[sel], r[sel])
+    grid = PmeGrid(sysm.xyz, st.box, st.grid, st.order, st.beta) if part == 0 else None
+    conn.send(len(i))
+    while True:
+        mu = conn.recv()
+        if mu is None:
+            break
+        t = np.zeros_like(mu)
+        if terms is not None:
+            t = t + dipole_field_real(sysm, st, mu, terms)
+        if grid is not None:
+            t = t + dipole_field_recip(sysm, st, mu, grid) + self_field(st, mu)
+        conn.send(t)
+    conn.close()
+
+
+class OraclePool:
+    """The float64 numpy oracle's T*mu split over `procs` processes, each
+    single-threaded (started with spawn, so it is safe beside CUDA): the
+    harness divides the pair list and sums the partial fields; every term is
+    the oracle's own code."""
+
+    def __init__(self, workload_name: str, procs: int):
+        import multiprocessing as mp
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for k in range(procs):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, workload_name, k, procs), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        self.n_pairs = [c.recv() for c in self.conns][0]
+
+    def apply_T(self, mu):
+        for c in self.conns:
+            c.send(mu)
+        out = None
+        for c in self.conns:
+            t = c.recv()
+            out = t if out is None else out + t
+        return out
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except Exception:
+                pass
+        for pr in self.procs:
+            pr.join(timeout=10)
+
+
+def oracle_sample(workload, steps: int, warmup: int, procs: int = 1):
+    """Time T*mu applications (real + PME + self, float64 numpy oracle) on the
+    workload, one per step, on `procs` single-threaded host processes."""
+    import numpy as np
     t0 = time.perf_counter()
-    op = Operator(sysm, st)
+    pool = OraclePool(workload.name, procs)
     t_build = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    mu = rng.normal(size=(sysm.n, 3)) * 0.1
-    for _ in range(warmup):
-        op.apply_T(mu)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        op.apply_T(mu)
-        times.append(time.perf_counter() - t0)
-    return op.n_pairs, times, t_build
+    try:
+        mu = np.random.default_rng(0).normal(size=(3 * workload.n_waters, 3)) * 0.1
+        for _ in range(warmup):
+            pool.apply_T(mu)
+        times = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            pool.apply_T(mu)
+            times.append(time.perf_counter() - t0)
+    finally:
+        pool.close()
+    return pool.n_pairs, times, t_build
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baselines(workload, steps_one: int = 2, steps_all: int = 8):
+    """The oracle's T*mu pairs/s on one host core and on every host core."""
+    cores = host_cores()
+    model = cpu_model()
+    pairs, t1, b1 = oracle_sample(workload, steps_one, 0, 1)
+    out = {"value": pairs * len(t1) / sum(t1), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_model": model, "host_cores": cores,
+           "sample": f"{len(t1)} T*mu applications (real+PME+self) of the float64 numpy oracle on "
+                     f"{workload.name}, one single-threaded process; geometry terms built once "
+                     f"({b1:.1f} s, untimed)"}
+    if cores > 1:
+        pairs, ta, ba = oracle_sample(workload, steps_all, 1, cores)
+        out["all_cores"] = {"value": pairs * len(ta) / sum(ta), "unit": UNIT, "cores": cores,
+                            "sample": f"{len(ta)} T*mu applications after one warm-up on {cores} "
+                                      f"single-threaded processes: the reciprocal and self terms in one, the "
+                                      f"real-space pair list split over the others, partial fields summed by "
+                                      f"the harness"}
+    return out
 
 
 def oracle_multipole_sample(workload, pairs_sample: int = 200_000):
@@ -276,7 +440,8 @@ def run_reference(args):
         return
     from paper_1906_01211_gb300.synth import WORKLOADS
     w = WORKLOADS[args.workload]
-    pairs, times, t_build = oracle_sample(w, args.steps, args.warmup)
+    cores = host_cores()
+    pairs, times, t_build = oracle_sample(w, args.steps, args.warmup, cores)
     total = sum(times)
     value = pairs * len(times) / total
     line = {
@@ -285,9 +450,11 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w.name, "n_atoms": 3 * w.n_waters, "box": w.L,
                                         "pme_grid": w.grid, "cutoff": w.cutoff, "beta": w.beta},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{len(times)} T*mu applications (real+PME+self) on {w.name}, "
-                                   f"operator geometry built once ({t_build:.1f} s, untimed)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"{len(times)} T*mu applications (real+PME+self) on {w.name} on {cores} "
+                                   f"single-threaded processes (reciprocal and self terms in one, the "
+                                   f"real-space pair list split over the others); operator geometry built "
+                                   f"once ({t_build:.1f} s, untimed)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -305,35 +472,57 @@ PAIR_BUILD_FLOPS = 130
 # (the df_* helpers: a double-float multiply-add is one multiply, three fused
 # multiply-adds and about nine adds).
 DF_FP32_PER_FP64 = 13
-# DRAM traffic (read + write) per launch of k_t_real_df, from one ncu capture of
-# the current kernel on this workload (profiles/k_t_real_df_water23556.md).
+# DRAM traffic (read + write) per launch of k_t_real_df on water-23556, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernel.
 T_REAL_TRAFFIC = {"water-23556": 182.5e6}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
 
 
 def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
     """Roofline entries from the live phase timers (one kernel per phase).
 
+    real-space T*v (k_t_real_df): bound "hbm". achieved = the algorithmic
+    bytes of one T*mu, 80 B per atom (float64 position, dipole, damping
+    factor and output field) + 4 B per unique pair (a half-list index),
+    divided by the kernel's average launch time; peak = MEASURED_PEAKS.json
+    hbm_gbs. This kernel does not recompute the pair terms: it streams the
+    damped tensor stored per directed entry (48 B) with its neighbour index
+    (4 B) plus 92 B per atom, 21x the algorithmic bytes at water-23556; those
+    bytes are reported as stored_tensor_bytes with their own fraction, and
+    the DRAM traffic measured by ncu as traffic.
     pair build (k_pair_build_df): bound "alu" on the float32 pipe, which runs
     it in double-float; achieved = PAIR_BUILD_FLOPS float64 operations per
     unique pair / launch time, peak = the float32 pipe's rate divided by
     DF_FP32_PER_FP64 (152 SMs x 128 lanes x 2 flop x max SM clock / 13), the
     float64-equivalent rate of double-float arithmetic on this GPU.
-    real-space T*v (k_t_real_df): HBM, algorithmic bytes per launch = 48 B
-    tensor + 4 B neighbour index per directed entry (the tensor is stored
-    once per entry, in row order) + 92 B per atom (row start, v as float
-    hi/lo, float64 v for the self term, the float64 output), peak =
-    MEASURED_PEAKS.json hbm_gbs.
     """
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     df_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 / DF_FP32_PER_FP64
     hbm = peaks.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
     steps_seen = max(1, phases["pair"][1])
     out = []
+    ms, cnt = phases["t_real"]
+    if cnt:
+        per = ms / cnt
+        nbytes = 80 * n_atoms + 4 * n_pairs
+        stored = (48 + 4) * 2 * n_pairs + 92 * n_atoms
+        ach = nbytes / (per / 1e3) / 1e9
+        ach_stored = stored / (per / 1e3) / 1e9
+        out.append({"kernel": "k_t_real_df (real-space T*v, double-float)", "bound": "hbm", "achieved": ach,
+                    "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": T_REAL_TRAFFIC.get(workload), "algorithmic_bytes": nbytes,
+                    "stored_tensor_bytes": stored, "achieved_stored": ach_stored, "frac_stored": ach_stored / peak,
+                    "launch_ms": per, "ms_per_step": ms / steps_seen,
+                    "peak_source": "measured" if hbm else "fallback"})
     ms, cnt = phases["pair"]
     if cnt:
         per = ms / cnt
@@ -342,16 +531,6 @@ def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
                     "bound": "alu", "achieved": ach, "peak": df_peak, "unit": "TFLOP/s", "frac": ach / df_peak,
                     "traffic": None, "launch_ms": per, "ms_per_step": ms / steps_seen,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock / 13 (double-float cost)"})
-    ms, cnt = phases["t_real"]
-    if cnt:
-        per = ms / cnt
-        nbytes = (48 + 4) * 2 * n_pairs + 92 * n_atoms
-        ach = nbytes / (per / 1e3) / 1e9
-        peak = hbm if hbm else 6800.0
-        out.append({"kernel": "k_t_real_df (real-space T*v, double-float)", "bound": "hbm", "achieved": ach,
-                    "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": T_REAL_TRAFFIC.get(workload), "algorithmic_bytes": nbytes, "launch_ms": per,
-                    "ms_per_step": ms / steps_seen, "peak_source": "measured" if hbm else "fallback"})
     return out
 
 
@@ -402,6 +581,104 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ precision runs
+
+def load_oracle_solution(name: str):
+    """The oracle's stored solutions of a box (tests/golden, written by
+    make_oracle_solutions.py), or None."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", name.replace("-", "") + "_oracle.npz")
+    if not os.path.exists(path):
+        return None
+    return np.load(path)
+
+
+def oracle_errors(mu, U, gold):
+    """Errors of a GPU solution (mu on the device, U) against the oracle's
+    solutions of the box: the run to the box's tolerance and the converged one."""
+    import numpy as np
+    m = mu.double().cpu().numpy()
+    out = {}
+    for key, mkey, ukey in (("vs_oracle_at_tol", "mu_tol", "U_tol"), ("vs_oracle_converged", "mu", "U")):
+        d = m - gold[mkey]
+        out[key] = {"rms_debye": float(4.8032047 * np.sqrt((d * d).sum() / d.shape[0])),
+                    "max_atom_debye": float(4.8032047 * np.linalg.norm(d, axis=1).max()),
+                    "energy_rel": abs(U / float(gold[ukey]) - 1.0)}
+    out["oracle_iters"] = {"at_tol": int(gold["iters_tol"]), "converged": int(gold["iters"]),
+                           "converged_tol_debye": float(gold["tol_debye"])}
+    return out
+
+
+def precision_run(ap, w, precision, dev_in, stream, flush, warmup, steps, mu_ref=None, U_ref=None, gold=None):
+    """Whole steps (set_system, permanent field, solve, energy) of workload w
+    in one precision, timed with CUDA events on the context's stream: step_ms
+    per step and solve_ms from the permanent field to the converged dipoles
+    (amp_solve_induced); phase times on three more steps with the library's
+    timers. Errors against a reference solution and the oracle's stored ones."""
+    import torch
+    p = ap.Polarization(ap.Config(box=w.L, cutoff=w.cutoff, ewald_beta=w.beta, pme_grid=w.grid,
+                                  tol_debye=w.tol_debye, precision=precision), stream)
+    step_ms, solve_ms = [], []
+    for k in range(warmup + steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        p.set_system(*dev_in)
+        E0 = p.permanent_field()
+        ev[1].record(stream)
+        mu, it, rms = p.solve(E0)
+        ev[2].record(stream)
+        U = p.energy(mu, E0)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        if k >= warmup:
+            step_ms.append(ev[0].elapsed_time(ev[3]))
+            solve_ms.append(ev[1].elapsed_time(ev[2]))
+    torch.cuda.synchronize()
+    p.profile(True)
+    for _ in range(3):
+        flush.zero_()
+        p.set_system(*dev_in)
+        E0p = p.permanent_field()
+        mup, _, _ = p.solve(E0p)
+        p.energy(mup, E0p)
+    torch.cuda.synchronize()
+    phases = p.profile_read()
+    p.profile(False)
+    n_pairs = p.pair_count()
+    out = {"precision": precision, "step_ms": statistics.mean(step_ms), "solve_ms": statistics.mean(solve_ms),
+           "iters": it, "fp64_checks": p.last_solve_stats()[1], "unique_pairs": n_pairs,
+           "tmu_pairs_per_s_in_solve": n_pairs * (it + (1 if precision == "mixed" else 0)) /
+           (statistics.mean(solve_ms) / 1e3),
+           "phase_ms_per_step": {k: round(v[0] / 3, 4) for k, v in phases.items()}}
+    if mu_ref is not None:
+        d = (mu - mu_ref).double()
+        out["rms_vs_fp64_gpu_debye"] = float(4.8032047 * torch.sqrt((d * d).sum() / d.shape[0]))
+        out["energy_rel_vs_fp64_gpu"] = abs(U / U_ref - 1.0)
+    if gold is not None:
+        out.update(oracle_errors(mu, U, gold))
+    p.close()
+    return out, mu, U
+
+
+def run_large_box(ap, dev, stream, flush):
+    """The 96,000-atom box at its own tolerance (1e-5 D): float64 and mixed
+    whole steps, each against the oracle's stored solutions."""
+    import numpy as np
+    import torch
+    from paper_1906_01211_gb300.synth import WATER_96000
+    w = WATER_96000
+    sysm = w.system()
+    host = [np.ascontiguousarray(a) for a in
+            (sysm.xyz, sysm.q, sysm.dip, sysm.quad, sysm.alpha, sysm.thole, sysm.mol.astype(np.int32))]
+    dev_in = [torch.from_numpy(a).to(dev) for a in host]
+    gold = load_oracle_solution(w.name)
+    f64, mu64, U64 = precision_run(ap, w, "fp64", dev_in, stream, flush, 2, 3, gold=gold)
+    mix, _, _ = precision_run(ap, w, "mixed", dev_in, stream, flush, 2, 3, mu_ref=mu64, U_ref=U64, gold=gold)
+    return {"workload": w.name, "n_atoms": sysm.n, "box": w.L, "pme_grid": w.grid, "tol_debye": w.tol_debye,
+            "fp64": f64, "mixed": mix, "mixed_solve_speedup_vs_fp64": f64["solve_ms"] / mix["solve_ms"]}
+
+
 # ------------------------------------------------------------------ GPU side
 
 def main():
@@ -415,10 +692,10 @@ def main():
     torch.cuda.set_device(local)
     if args.serving:
         if rank == 0:
-            rates = [float(x) for x in args.rates.split(",")]
-            sv = run_serving(args.requests, args.slots, rates)
+            sv = run_serving(args.requests, args.workers, [float(x) for x in args.rates.split(",")],
+                             [float(x) for x in args.rates_capacity.split(",")])
             print(json.dumps({"metric": "serving solves/s and p50/p99 latency", "unit": "solves/s",
-                              "value": sv["rates"][-1]["throughput_per_s"], "higher_is_better": True,
+                              "value": sv["saturated"]["throughput_per_s"], "higher_is_better": True,
                               "dtype": "f32+f64", "data": "synthetic",
                               "config": {"workload": "water request stream (64..4096 waters, half clusters)"},
                               "serving": sv}), flush=True)
@@ -457,10 +734,14 @@ def main():
     p = solver("fp64")
     n_pairs = None
 
-    def step(inputs):
+    def step(inputs, marks=None):
         p.set_system(*inputs)
         p.permanent_field(out=E0)
+        if marks:
+            marks[0].record(stream)
         mu, it, rms = p.solve(E0)
+        if marks:
+            marks[1].record(stream)
         U = p.energy(mu, E0)
         return mu, it, rms, U
 
@@ -474,15 +755,17 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     launches0 = p.launch_count()
-    step_ms, applications = [], []
+    step_ms, solve_ms, applications = [], [], []
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
         e0.record(stream)
-        mu, it, rms, U = step(dev_in)
+        mu, it, rms, U = step(dev_in, marks)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        solve_ms.append(marks[0].elapsed_time(marks[1]))
         applications.append(1 + it)
     torch.cuda.synchronize()
     launches = p.launch_count() - launches0
@@ -531,44 +814,25 @@ def main():
     phase_ms = {k: round(v[0] / prof_steps, 4) for k, v in phases.items()}
 
     # ---- mixed precision on the same workload, against the float64 result
+    # and against the oracle's solutions of this box
     mixed = None
+    gold = load_oracle_solution(w.name)
+    if gold is not None:
+        fp64_err = oracle_errors(mu, U, gold)
+    else:
+        fp64_err = None
     if not args.no_mixed:
-        mu64 = mu.clone()
-        pm = solver("mixed")
-        ms_m = []
-        for k in range(args.warmup + 3):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pm.set_system(*dev_in)
-            E0m = pm.permanent_field()
-            mum, itm, rmsm = pm.solve(E0m)
-            Um = pm.energy(mum, E0m)
-            e1.record(stream)
-            e1.synchronize()
-            if k >= args.warmup:
-                ms_m.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-        pm.profile(True)
-        for _ in range(3):
-            flush.zero_()
-            pm.set_system(*dev_in)
-            E0p = pm.permanent_field()
-            mup, _, _ = pm.solve(E0p)
-            pm.energy(mup, E0p)
-        torch.cuda.synchronize()
-        phases_m = pm.profile_read()
-        pm.profile(False)
-        d = (mum - mu64).double()
-        mixed = {"solve_ms": statistics.mean(ms_m), "iters": itm, "fp64_checks": pm.last_solve_stats()[1],
-                 "phase_ms_per_step": {k: round(v[0] / 3, 4) for k, v in phases_m.items()},
-                 "rms_vs_fp64_gpu_debye": float(4.8032047 * torch.sqrt((d * d).sum() / n)),
-                 "energy_rel_vs_fp64_gpu": abs(Um / U - 1.0)}
-        pm.close()
+        mixed, _, _ = precision_run(ap, w, "mixed", dev_in, stream, flush, args.warmup, 3, mu_ref=mu, U_ref=U,
+                                    gold=gold)
 
+    # ---- the 96,000-atom box (Puddle-sized), float64 and mixed
+    large = None
+    if not args.no_large and w.name != "water-96000":
+        large = run_large_box(ap, dev, stream, flush)
     serving = None
     if not args.no_serving:
-        serving = run_serving(args.requests, args.slots, [float(x) for x in args.rates.split(",")])
+        serving = run_serving(args.requests, args.workers, [float(x) for x in args.rates.split(",")],
+                              [float(x) for x in args.rates_capacity.split(",")])
 
     # ---- list reuse along a trajectory (not the headline step: every frame is
     # new positions, so each step does its full work except the cell search,
@@ -585,25 +849,27 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
-        pairs_o, times, t_build = oracle_sample(w, 2, 0)
-        cpu = {"value": pairs_o * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} T*mu applications (real+PME+self) of the float64 numpy oracle "
-                         f"on {w.name}; geometry terms built once ({t_build:.1f} s, untimed)"}
+        cpu = cpu_baselines(w)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "dtype_note": DTYPE_NOTE, "data": "synthetic",
         "config": {"workload": w.name, "n_atoms": n, "box": w.L, "cutoff": w.cutoff, "beta": w.beta,
                    "pme_grid": w.grid, "tol_debye": w.tol_debye, "unique_pairs": n_pairs,
                    "tmu_applications_per_step": apps / args.steps,
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "solve_ms": t_total / args.steps,
+        "step_ms": t_total / args.steps,
+        "solve_ms": statistics.mean(solve_ms),
+        "iters": it,
+        "fp64_vs_oracle": fp64_err,
         "tmu_pairs_per_s_operator": n_pairs / ((phases["t_real"][0] + phases["t_recip"][0])
                                                / max(phases["t_real"][1], 1) / 1e3),
         "phase_ms_per_step": phase_ms,
         "mixed": mixed,
+        "mixed_solve_speedup_vs_fp64": (statistics.mean(solve_ms) / mixed["solve_ms"]) if mixed else None,
+        "water_96000": large,
         "serving": serving,
         "md_list_reuse": md,
         "multipole_energy": mpole,

@@ -51,7 +51,15 @@ extern "C" {
 #define AMP_ERR_STATE (-6)         /* call order: no system set */
 #define AMP_ERR_STALE (-8)         /* amp_update_positions: an atom moved more than skin/2 */
 
-#define AMP_FP64 0   /* all pair math, grids and FFTs in float64 */
+#define AMP_FP64 0   /* float64-accurate results. The permanent field E0
+                        is float64 arithmetic (its reciprocal part, and the
+                        excluded intramolecular real-space terms that cancel
+                        against it); the per-pair terms, T*mu and its PME
+                        spreading, FFTs and gather run in double-float (a
+                        value is the unevaluated sum of two floats, ~48
+                        significant bits, on the float32 units, because
+                        float64 is 1/64 of the float32 rate on GB300); the
+                        PCG vectors, dot products and scalars are float64 */
 #define AMP_MIXED 1  /* float32 pair geometry/damping and a float32
                         operator input (PME as in AMP_FP64), float64
                         accumulation, scalars, self terms and a final float64
@@ -81,8 +89,8 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream);
 /* Change box, cutoff, beta, tolerance and iteration cap of a context while
  * keeping its buffers and cuFFT plans: the PME grid size, B-spline order,
  * precision and cluster/periodic mode must stay those given to amp_create
- * (else AMP_ERR_ARG). Recomputes the influence function when box or beta
- * change (synchronises the stream); the next call must be amp_set_system. */
+ * (else AMP_ERR_ARG). Recomputes the influence function on the device when
+ * box or beta change; the next call must be amp_set_system. */
 int amp_reconfigure(amp_ctx* ctx, const amp_config* cfg);
 
 /* Free every device buffer and plan of the context. NULL is ignored. */
@@ -224,6 +232,104 @@ int amp_launch_count(const amp_ctx* ctx, long long* n);
  * either may be NULL). */
 int amp_last_solve_stats(const amp_ctx* ctx, int* iters, int* fp64_checks);
 
+/* ---- Serving: continuous batching of many independent solves.
+ *
+ * The paper has no serving counterpart (its throughput runs are many MPI
+ * ranks on one system, Section "Parallel performance"); the solves
+ * themselves are the calls above. A server owns one GPU (the device given to
+ * amp_server_create) and accepts requests at any time from any thread: an
+ * isolated cluster (box = 0: every pair, no Ewald) or a periodic cubic box,
+ * each with its own atoms. Requests run as soon as memory and a place free
+ * up, beside those already running:
+ *   - clusters of at most batch_max_atoms atoms (without a key) join the
+ *     batched engine: one device arena, one PCG state per request, and every
+ *     iteration of all of them is one pair of launches of persistent kernels
+ *     that take (request, 64-row tile) work items from a device queue;
+ *   - the other requests go to n_workers workers, each with its own CUDA
+ *     stream, running the single-system calls above on contexts taken from
+ *     a pool keyed by PME grid size (created on first need, kept for later
+ *     requests of that size, destroyed to make room for another size when the
+ *     memory budget is reached).
+ * Admission: a request starts when its memory (an upper estimate for a new
+ * context, the exact bytes of a pooled one; arena space in the batched
+ * engine) fits in mem_budget_bytes beside what is in use. Dipoles of keyed
+ * requests stay on the device (LRU, resident_bytes) and start the next solve
+ * of the same key. Every request's inputs are copied at submission (host
+ * arrays, caller's order, layouts as above); results are host copies. Each
+ * request's arithmetic is that of a solve alone: the result does not depend
+ * on what else runs. Failures are per request (invalid input, a request
+ * larger than the whole budget); the server and the other requests go on. */
+#define AMP_PENDING 1  /* amp_server_poll: the request has not finished */
+
+typedef struct amp_server amp_server;
+
+typedef struct {
+  int n_workers;               /* context workers (>= 1) */
+  long long mem_budget_bytes;  /* device memory for contexts, arena and resident dipoles */
+  int precision;               /* AMP_MIXED or AMP_FP64, for every request */
+  double tol_debye;            /* PCG stop, every request */
+  int max_iter;                /* PCG iteration cap, every request */
+  int batch_max_atoms;         /* clusters up to this size use the batched engine (0: no engine) */
+  int batch_arena_atoms;       /* atoms the batched engine holds at once (>= batch_max_atoms) */
+  int batch_max_requests;      /* requests the batched engine holds at once */
+  long long resident_bytes;    /* budget of the resident dipoles of keyed requests */
+} amp_server_config;
+
+typedef struct {
+  int status;        /* AMP_OK, or the request's error code */
+  int iters;         /* PCG iterations */
+  double rms_debye;  /* final preconditioned residual RMS (Debye) */
+  double energy;     /* polarization energy U = -1/2 C mu.E0 (kcal/mol) */
+  double t_submit, t_start, t_done;  /* seconds on the server's steady clock */
+  int path;          /* 0 batched engine, 1 context worker */
+  int warm_start;    /* 1 if started from a keyed request's resident dipoles */
+  char error[160];   /* message when status != AMP_OK */
+} amp_server_result;
+
+typedef struct {
+  long long submitted, done, failed;
+  int queued, running_batch, running_workers, contexts;
+  long long bytes_in_use, budget;
+  long long batch_launches;  /* pair + vector launches of the batched engine */
+} amp_server_counters;
+
+/* Start a server on CUDA device `device` (threads and streams of its own).
+ * AMP_ERR_ARG for a bad configuration, AMP_ERR_CUDA / AMP_ERR_OOM when the
+ * device or the arena cannot be had. */
+int amp_server_create(amp_server** out, const amp_server_config* cfg, int device);
+
+/* Queue one request; *ticket identifies it. Host arrays in the layouts of
+ * amp_set_system (copied before the call returns). box = 0: isolated
+ * cluster; box > 0: periodic cubic box whose cutoff, Ewald beta and PME grid
+ * are taken from cutoff, beta, grid when given (> 0), else cutoff =
+ * min(7, box/2 - 1e-6), beta = 3.8122/cutoff (erfc(beta cutoff) = 7e-8) and
+ * grid = the smallest 2,3,5-smooth size >= box beta/0.5446 (at least 8). key
+ * (may be NULL) names a request whose dipoles stay resident for the next one
+ * of the same key. AMP_ERR_ARG for null arrays or n_atoms < 2, AMP_ERR_STATE
+ * after amp_server_destroy began. A request larger than the whole memory
+ * budget is accepted and fails alone (its result has AMP_ERR_OOM). */
+int amp_server_submit(amp_server* s, int n_atoms, double box, double cutoff, double beta, int grid,
+                      const double* xyz, const double* q, const double* dip, const double* quad,
+                      const double* alpha, const double* thole, const int* mol, const char* key,
+                      long long* ticket);
+
+/* AMP_PENDING while the request runs or waits. Once it has finished:
+ * AMP_OK, its dipoles into mu [N][3] (host; may be NULL) and its record into
+ * *res (may be NULL); the ticket is then released (a later poll returns
+ * AMP_ERR_ARG). AMP_ERR_ARG for an unknown ticket. */
+int amp_server_poll(amp_server* s, long long ticket, double* mu, amp_server_result* res);
+
+/* amp_server_poll that waits up to timeout_s seconds (< 0: without limit);
+ * AMP_PENDING if the time ran out first. */
+int amp_server_wait(amp_server* s, long long ticket, double timeout_s, double* mu, amp_server_result* res);
+
+/* Counters at the time of the call. */
+int amp_server_stats(amp_server* s, amp_server_counters* out);
+
+/* Finish the requests already queued, stop the threads, free the device
+ * memory. NULL is ignored. */
+void amp_server_destroy(amp_server* s);
+
 /* Polarization energy without any allocation. The paper has no counterpart to
  * this entry point: it exists for callers that cannot allocate device memory
  * when they need the energy (a host framework that owns all device memory in
@@ -243,7 +349,10 @@ int amp_last_solve_stats(const amp_ctx* ctx, int* iters, int* fp64_checks);
  * kernels overlap on the GPU race and give wrong results. Each call writes
  * every partial it reads, so no clearing between calls is needed.
  * Returns AMP_OK, AMP_ERR_ARG (null pointer, n_atoms < 1), AMP_ERR_TOO_LARGE
- * or AMP_ERR_CUDA. */
+ * or AMP_ERR_CUDA. A CUDA error already pending on the calling thread (from an
+ * earlier call) is left pending and the call returns AMP_ERR_CUDA without
+ * launching; a launch error of this call is cleared and returned as
+ * AMP_ERR_CUDA. */
 #define AMP_ERR_TOO_LARGE (-7)
 #define AMP_NOALLOC_MAX_ATOMS 1048576
 int amp_polarization_energy_noalloc(int n_atoms, const double* mu, const double* E0, double* U,

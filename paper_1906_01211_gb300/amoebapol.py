@@ -44,6 +44,50 @@ class amp_config(ctypes.Structure):
     ]
 
 
+class amp_server_config(ctypes.Structure):
+    _fields_ = [
+        ("n_workers", ctypes.c_int),
+        ("mem_budget_bytes", ctypes.c_longlong),
+        ("precision", ctypes.c_int),
+        ("tol_debye", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("batch_max_atoms", ctypes.c_int),
+        ("batch_arena_atoms", ctypes.c_int),
+        ("batch_max_requests", ctypes.c_int),
+        ("resident_bytes", ctypes.c_longlong),
+    ]
+
+
+class amp_server_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("rms_debye", ctypes.c_double),
+        ("energy", ctypes.c_double),
+        ("t_submit", ctypes.c_double),
+        ("t_start", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+        ("path", ctypes.c_int),
+        ("warm_start", ctypes.c_int),
+        ("error", ctypes.c_char * 160),
+    ]
+
+
+class amp_server_counters(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong),
+        ("done", ctypes.c_longlong),
+        ("failed", ctypes.c_longlong),
+        ("queued", ctypes.c_int),
+        ("running_batch", ctypes.c_int),
+        ("running_workers", ctypes.c_int),
+        ("contexts", ctypes.c_int),
+        ("bytes_in_use", ctypes.c_longlong),
+        ("budget", ctypes.c_longlong),
+        ("batch_launches", ctypes.c_longlong),
+    ]
+
+
 class AmpError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libamoebapol error {code}: {msg}")
@@ -81,6 +125,13 @@ def _load() -> ctypes.CDLL:
         "amp_update_positions": (I, [P, P, ctypes.POINTER(I)]),
         "amp_set_predictor": (I, [P, I]),
         "amp_predictor_coefficients": (I, [I, ctypes.POINTER(D)]),
+        "amp_server_create": (I, [ctypes.POINTER(P), ctypes.POINTER(amp_server_config), I]),
+        "amp_server_submit": (I, [P, I, D, D, D, I, P, P, P, P, P, P, P, ctypes.c_char_p,
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+        "amp_server_poll": (I, [P, ctypes.c_longlong, P, ctypes.POINTER(amp_server_result)]),
+        "amp_server_wait": (I, [P, ctypes.c_longlong, D, P, ctypes.POINTER(amp_server_result)]),
+        "amp_server_stats": (I, [P, ctypes.POINTER(amp_server_counters)]),
+        "amp_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -208,6 +259,49 @@ def amp_profile_read(ctx) -> dict:
     cnt = (ctypes.c_longlong * n)()
     _check(ctx, _lib.amp_profile_read(ctx, ms, cnt))
     return {name: (ms[k], cnt[k]) for k, name in enumerate(PHASES)}
+
+
+AMP_PENDING = 1
+
+
+def amp_server_create(cfg: amp_server_config, device: int = 0):
+    h = ctypes.c_void_p()
+    code = _lib.amp_server_create(ctypes.byref(h), ctypes.byref(cfg), int(device))
+    if code != AMP_OK:
+        raise AmpError(code, "amp_server_create: invalid configuration or device error")
+    return h
+
+
+def amp_server_submit(srv, n, box, cutoff, beta, grid, xyz, q, dip, quad, alpha, thole, mol, key=None) -> int:
+    """Host arrays (numpy, contiguous float64 / int32) in; the ticket out."""
+    t = ctypes.c_longlong(-1)
+    code = _lib.amp_server_submit(srv, int(n), float(box), float(cutoff), float(beta), int(grid),
+                                  xyz.ctypes.data, q.ctypes.data, dip.ctypes.data, quad.ctypes.data,
+                                  alpha.ctypes.data, thole.ctypes.data, mol.ctypes.data,
+                                  key.encode() if key is not None else None, ctypes.byref(t))
+    if code != AMP_OK:
+        raise AmpError(code, "amp_server_submit")
+    return t.value
+
+
+def amp_server_poll(srv, ticket: int, mu_ptr, res: amp_server_result) -> int:
+    return _lib.amp_server_poll(srv, ctypes.c_longlong(ticket), mu_ptr, ctypes.byref(res))
+
+
+def amp_server_wait(srv, ticket: int, timeout_s: float, mu_ptr, res: amp_server_result) -> int:
+    return _lib.amp_server_wait(srv, ctypes.c_longlong(ticket), float(timeout_s), mu_ptr, ctypes.byref(res))
+
+
+def amp_server_stats(srv) -> amp_server_counters:
+    c = amp_server_counters()
+    code = _lib.amp_server_stats(srv, ctypes.byref(c))
+    if code != AMP_OK:
+        raise AmpError(code, "amp_server_stats")
+    return c
+
+
+def amp_server_destroy(srv):
+    _lib.amp_server_destroy(srv)
 
 
 AMP_ERR_TOO_LARGE = -7

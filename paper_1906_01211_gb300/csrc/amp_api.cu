@@ -20,14 +20,33 @@ int dev_alloc_bytes(amp_ctx* c, void** p, size_t bytes) {
     return fail(c, AMP_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
   }
   c->allocs.push_back(*p);
+  c->alloc_sizes.push_back(bytes);
+  c->bytes += (long long)bytes;
   return AMP_OK;
 }
 
 void dev_free(amp_ctx* c, void* p) {
   if (!p) return;
-  for (auto& a : c->allocs)
-    if (a == p) a = nullptr;
+  for (size_t k = 0; k < c->allocs.size(); ++k)
+    if (c->allocs[k] == p) {
+      c->allocs[k] = nullptr;
+      c->bytes -= (long long)c->alloc_sizes[k];
+      c->alloc_sizes[k] = 0;
+    }
   cudaFree(p);
+}
+
+// Work of the context goes to stream st from now on (the serving layer moves
+// pooled contexts between its workers' streams).
+void ctx_bind_stream(amp_ctx* c, cudaStream_t st) {
+  join_geometry(c);
+  c->stream = st;
+  if (c->plans) {
+    cufftSetStream(c->plan_d2z, st);
+    cufftSetStream(c->plan_z2d, st);
+    if (c->plan_r2c) cufftSetStream(c->plan_r2c, st);
+    if (c->plan_c2r) cufftSetStream(c->plan_c2r, st);
+  }
 }
 
 constexpr int kEvPool = 8192;
@@ -82,7 +101,7 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
                    (void**)&c->trec, (void**)&c->plo, (void**)&c->vhl, (void**)&c->mp_df, (void**)&c->wv,
-                   (void**)&c->theta_df, (void**)&c->theta_df2, (void**)&c->pd};
+                   (void**)&c->theta_df, (void**)&c->pd, (void**)&c->e0rec, (void**)&c->e0intra};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -101,10 +120,19 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = dev_alloc(c, &c->qv, cap)) || (r = dev_alloc(c, &c->tv, cap)) || (r = dev_alloc(c, &c->tmp, cap)) ||
       (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)) ||
       (r = dev_alloc(c, &c->wv, cap)) || (r = dev_alloc(c, &c->vhl, 2LL * cap)) ||
-      (r = dev_alloc(c, &c->mp_df, 5LL * cap)) || (r = dev_alloc(c, &c->pd, 3LL * cap)))
+      (r = dev_alloc(c, &c->mp_df, 5LL * cap)) || (r = dev_alloc(c, &c->pd, 3LL * cap)) ||
+      (r = dev_alloc(c, &c->e0rec, cap)) || (r = dev_alloc(c, &c->e0intra, cap)))
     return r;
   c->n_cap = cap;
   return AMP_OK;
+}
+
+// The context stream waits for the geometry work that pme_geometry put on
+// the side stream (once per new geometry).
+void join_geometry(amp_ctx* c) {
+  if (!c->geom_pending) return;
+  cudaStreamWaitEvent(c->stream, c->ev_geom, 0);
+  c->geom_pending = false;
 }
 
 }  // namespace amp
@@ -154,6 +182,7 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_geom, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_spread, cudaEventDisableTiming) != cudaSuccess) {
     amp_destroy(c);
     return AMP_ERR_CUDA;
@@ -168,6 +197,7 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
 
 int amp_reconfigure(amp_ctx* c, const amp_config* cfg) {
   if (!c || !cfg) return AMP_ERR_ARG;
+  join_geometry(c);
   const bool cluster = cfg->box == 0.0;
   if (cluster != c->cluster || cfg->precision != c->cfg.precision)
     return fail(c, AMP_ERR_ARG, "amp_reconfigure: precision and cluster/periodic mode are fixed at creation");
@@ -195,6 +225,7 @@ void amp_destroy(amp_ctx* c) {
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_geom) cudaEventDestroy(c->ev_geom);
   if (c->ev_spread) cudaEventDestroy(c->ev_spread);
   if (c->plan_d2z) cufftDestroy(c->plan_d2z);
   if (c->plan_z2d) cufftDestroy(c->plan_z2d);
@@ -212,6 +243,7 @@ const char* amp_last_error(const amp_ctx* c) { return c ? c->err : "null context
 int amp_set_system(amp_ctx* c, int n, const double* xyz, const double* q, const double* dip, const double* quad,
                    const double* alpha, const double* thole, const int* mol) {
   if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
   c->have_system = false;
   c->hist_len = c->hist_head = 0;  // a new system: no solution history
   if (n < 2 || !xyz || !q || !dip || !quad || !alpha || !thole || !mol)
@@ -231,10 +263,6 @@ int amp_set_system(amp_ctx* c, int n, const double* xyz, const double* q, const 
   {
     PhaseScope ps(c, AMP_PHASE_PAIR);
     launch_pair_build(c);
-  }
-  {
-    PhaseScope ps(c, AMP_PHASE_E0_RECIP);
-    launch_pme_theta(c);
   }
   if ((r = cuda_check(c, cudaGetLastError(), "set_system launch"))) return r;
   c->have_system = true;
@@ -256,6 +284,7 @@ int amp_update_positions(amp_ctx* c, const double* xyz, int* reused) {
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!xyz) return fail(c, AMP_ERR_ARG, "xyz is null");
   if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_update_positions: periodic contexts only");
+  join_geometry(c);
   bool ok = false;
   int r;
   {
@@ -263,13 +292,10 @@ int amp_update_positions(amp_ctx* c, const double* xyz, int* reused) {
     if ((r = reuse_lists(c, xyz, &ok))) return r;
   }
   if (!ok) return fail(c, AMP_ERR_STALE, "an atom moved more than skin/2 since amp_set_system (or no skin)");
+  if ((r = pme_geometry(c))) return r;
   {
     PhaseScope ps(c, AMP_PHASE_PAIR);
     launch_pair_build(c);
-  }
-  {
-    PhaseScope ps(c, AMP_PHASE_E0_RECIP);
-    launch_pme_theta(c);
   }
   if ((r = cuda_check(c, cudaGetLastError(), "update_positions launch"))) return r;
   if (reused) *reused = 1;
@@ -289,26 +315,25 @@ int amp_permanent_field(amp_ctx* c, double* E0) {
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!E0) return fail(c, AMP_ERR_ARG, "E0 is null");
   if (c->cluster) {
-    PhaseScope ps(c, AMP_PHASE_E0_REAL);
-    cluster_permanent_field(c, c->E0s);
+    {
+      PhaseScope ps(c, AMP_PHASE_E0_REAL);
+      cluster_permanent_field(c, c->E0s);
+    }
+    launch_from_sorted(c, c->E0s, E0);
   } else {
     {
       PhaseScope ps(c, AMP_PHASE_E0_REAL);
       launch_e0_real(c, c->E0s);
     }
-    int r;
-    {
-      PhaseScope ps(c, AMP_PHASE_E0_RECIP);
-      r = pme_permanent_field(c, c->E0s);
-    }
-    if (r) return r;
+    join_geometry(c);  // the reciprocal part, computed beside the pair build
+    launch_add_from_sorted(c, c->E0s, c->e0rec, E0);
   }
-  launch_from_sorted(c, c->E0s, E0);
   return cuda_check(c, cudaGetLastError(), "permanent_field launch");
 }
 
 int amp_apply_T(amp_ctx* c, const double* mu, double* Tmu) {
   if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!mu || !Tmu) return fail(c, AMP_ERR_ARG, "null vector");
   launch_to_sorted(c, mu, c->tmp);
@@ -322,6 +347,7 @@ int amp_apply_T(amp_ctx* c, const double* mu, double* Tmu) {
 
 int amp_solve_induced(amp_ctx* c, const double* E0, double* mu, int use_guess, int* iters, double* rms) {
   if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!E0 || !mu) return fail(c, AMP_ERR_ARG, "null vector");
   if (use_guess < 0 || use_guess > 2) return fail(c, AMP_ERR_ARG, "use_guess must be 0, 1 or 2");
@@ -344,6 +370,7 @@ int amp_solve_induced(amp_ctx* c, const double* E0, double* mu, int use_guess, i
 
 int amp_forces(amp_ctx* c, const double* mu, double* F, double* gq, double* gdip, double* gquad) {
   if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!mu || !F) return fail(c, AMP_ERR_ARG, "mu and F are required");
   if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_forces: not available for isolated clusters");
@@ -353,6 +380,7 @@ int amp_forces(amp_ctx* c, const double* mu, double* F, double* gq, double* gdip
 
 int amp_multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gdip, double* gquad) {
   if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!U && !F && !gq && !gdip && !gquad) return fail(c, AMP_ERR_ARG, "amp_multipole_energy: no output requested");
   return multipole_energy(c, U, F, gq, gdip, gquad);
@@ -360,6 +388,7 @@ int amp_multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* g
 
 int amp_polarization_energy(amp_ctx* c, const double* mu, const double* E0, double* U) {
   if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
   if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
   if (!mu || !E0 || !U) return fail(c, AMP_ERR_ARG, "null pointer");
   return energy(c, mu, E0, U);

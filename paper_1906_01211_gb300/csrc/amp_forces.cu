@@ -370,7 +370,7 @@ int force_buffers(amp_ctx* c) {
 int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, double* gd, double* gt) {
   const bool fp32 = c->cfg.precision == AMP_MIXED;
   int r;
-  pme_theta64(c);  // the float64 B-spline weights (float64 path: built on first use)
+  pme_theta64(c, c->stream);  // the float64 B-spline weights (float64 path: built on first use)
   if ((r = force_buffers(c))) return r;
   const long long ng = (long long)c->K * c->K * c->K;
   if (fp32 && !c->grid32b && (r = dev_alloc(c, &c->grid32b, ng))) return r;
@@ -387,15 +387,15 @@ int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, doub
     // reciprocal: phi_mu into the primary grid, phi_M into the second grid
     if (fp32) {
       launch_to32(c, mu_sorted, c->p32);
-      if ((r = pme_potential(c, true, false, mu_sorted, c->p32, c->grid32))) return r;
-      if ((r = pme_potential(c, true, true, nullptr, nullptr, c->grid32b))) return r;
+      if ((r = pme_potential(c, true, false, mu_sorted, c->p32, c->grid32, c->stream))) return r;
+      if ((r = pme_potential(c, true, true, nullptr, nullptr, c->grid32b, c->stream))) return r;
       c->n_launch += 1;
       k_recip_gradients<float><<<amp_blocks((long long)c->n * kGroup, 128), 128, 0, st>>>(
           c->n, c->theta32, c->gbase, c->grid32, c->grid32b, c->K, mu_sorted, c->atomA, c->atomB, c->atomC,
           c->atomD, c->force_recip);
     } else {
-      if ((r = pme_potential(c, false, false, mu_sorted, nullptr, c->grid64))) return r;
-      if ((r = pme_potential(c, false, true, nullptr, nullptr, c->grid64b))) return r;
+      if ((r = pme_potential(c, false, false, mu_sorted, nullptr, c->grid64, c->stream))) return r;
+      if ((r = pme_potential(c, false, true, nullptr, nullptr, c->grid64b, c->stream))) return r;
       c->n_launch += 1;
       k_recip_gradients<double><<<amp_blocks((long long)c->n * kGroup, 128), 128, 0, st>>>(
           c->n, c->theta, c->gbase, c->grid64, c->grid64b, c->K, mu_sorted, c->atomA, c->atomB, c->atomC,

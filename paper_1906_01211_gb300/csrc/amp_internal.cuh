@@ -18,7 +18,9 @@
 //              row for which (i < j) != ((i + j) odd) — each pair exactly once,
 //              about half of each row's neighbours.
 // Pair data indexed by pid (computed once per geometry):
-//   T32[pid*6 + {xx,yy,zz,xy,xz,yz}]  damped dipole-field tensor (mixed path)
+//   T32: the mixed path's float32 tensor once per full-list entry, in entry
+//     order: (xx, yy, zz, xy) as float4 from the start, (xz, yz) as float2
+//     after cap_full entries
 //   T64: the float64 path's tensor once per full-list entry, in entry order:
 //     32 bytes per entry (hi xx yy zz xy xz yz, lo xx yy) from the start,
 //     then 16 bytes per entry (lo zz xy xz yz) after cap_full entries
@@ -76,6 +78,7 @@ struct amp_ctx {
   int *full_cnt = nullptr, *half_cnt = nullptr, *full_start = nullptr, *half_start = nullptr;
   int *full_j = nullptr, *full_ref = nullptr, *half_i = nullptr, *half_j = nullptr, *tr_tmp = nullptr;
   int* pos_tr = nullptr;  // full-list position of each pair's entry in its non-owner's row
+  int* intra = nullptr;   // float64 path: [0] count, then the pair ids of two sites of one molecule
   // list reuse: skin for the next build; the candidates (pairs within cutoff
   // + skin_built at the last cell search, CSR) and the sorted positions then
   double skin = 0.0, skin_built = 0.0;
@@ -99,27 +102,39 @@ struct amp_ctx {
   int K = 0;
   double* theta = nullptr;  // [n][3 axes][4 derivatives][5 points]
   float* theta32 = nullptr;
-  float2* theta_df = nullptr;  // float64 path: weights and first derivatives as hi/lo [n][3][2][5]
-  float2* theta_df2 = nullptr;  // float64 path: second derivatives as hi/lo [n][3][5]
-  bool theta64_valid = false;   // theta (float64) matches the current system (float64 path: built on demand)
+  float2* theta_df = nullptr;  // weights and first derivatives as hi/lo [n][3][2][5] (dipole products)
+  bool theta64_valid = false;   // theta (float64) matches the current system (built on first use)
   float2* phi_df = nullptr;    // float64 path: grid potential as hi/lo pairs for the gather
   // float64 path's dipole spreading: 64-bit fixed-point grid (integer
   // atomics, exact and order-independent), scaled by 2^fx_info[0]; fx_info[1]
   // bounds the atoms that reach one grid point; kcount = atoms per base cell.
   unsigned long long* gridfx = nullptr;
-  int* fx_info = nullptr;  // [0] scale exponent of the last spread, [1] atoms per base cell (max),
-                           // [2] float bits of the largest per-atom multipole bound
+  int* fx_info = nullptr;  // [0] scale exponent of the last spread, [1] atoms per base cell (max)
   int* kcount = nullptr;
   // max |hi component| of the last split vector: [0, kReduceBlocks) per block,
   // [kReduceBlocks] the whole vector, [kReduceBlocks + 1] arrival counter
   float* vmax_part = nullptr;
-  float4* fft_grid = nullptr;  // double-float complex grid of the float64 path's own FFT
-  float2* fft_G = nullptr;     // full-spectrum influence function, hi/lo
+  float4* fft_grid = nullptr;  // double-float complex half spectrum of the own FFT (power-of-two K)
+  float2* fft_G = nullptr;     // influence function on that half spectrum, hi/lo
   float4* fft_tw = nullptr;    // twiddles (cos hi, lo, sin hi, lo)
+  // mixed path's float32 reciprocal chain: spreading grid (kept at zero
+  // between applications), grid potential, and the own FFT's float32 half
+  // spectrum and twiddles (G: G32)
+  float* spread32 = nullptr;
+  float* phi32 = nullptr;
+  float2* fft_grid32 = nullptr;
+  float2* fft_tw32 = nullptr;
+  // the own FFT's float64 variant (the permanent field): half spectrum,
+  // twiddles; phi64 its output grid potential (G: G64)
+  double2* fft_grid64 = nullptr;
+  double2* fft_tw64 = nullptr;
+  double* spread64 = nullptr;  // the permanent multipoles' float64 grid (kept zero between uses)
+  double* phi64 = nullptr;
   int4* gbase = nullptr;    // [n] base grid index per axis
   double* grid64 = nullptr;
   double2* cgrid64 = nullptr;
   double* G64 = nullptr;
+  double* bmod = nullptr;  // B-spline moduli |b(m)|^2, m = 0 .. K-1
   float* grid32 = nullptr;
   float2* cgrid32 = nullptr;
   float* G32 = nullptr;
@@ -137,6 +152,13 @@ struct amp_ctx {
   cudaStream_t side = nullptr;  // second stream: PME beside the real-space kernel
   int n_sm = 1;                 // streaming multiprocessors of the device
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // recorded on the side stream after the geometry's reciprocal-space work
+  // (weights, permanent field's reciprocal part into e0rec); every call that
+  // follows amp_set_system / amp_update_positions waits for it once
+  cudaEvent_t ev_geom = nullptr;
+  bool geom_pending = false;
+  double4_32a* e0rec = nullptr;  // reciprocal part of the permanent field (float64, cell order)
+  double4_32a* e0intra = nullptr;  // float64 path: the intramolecular (excluded) permanent-field terms
   // recorded after the dipole spreading when spread_event is set: the
   // real-space kernel waits for it, so it runs beside the FFTs only
   cudaEvent_t ev_spread = nullptr;
@@ -179,6 +201,8 @@ struct amp_ctx {
 
   long long n_launch = 0;      // kernels this library has launched (own kernels only)
   std::vector<void*> allocs;   // every device allocation, freed by amp_destroy
+  std::vector<size_t> alloc_sizes;
+  long long bytes = 0;         // device bytes the context holds
   amp::Stats stats;
   int last_iters = 0;  // iterations of the last solve (first chunk of the next one)
   // ASPC warm start: order (-1 off), ring of the last order + 2 converged
@@ -202,6 +226,7 @@ inline int dev_alloc(amp_ctx* c, T** p, long long count) {
   return r;
 }
 int cuda_check(amp_ctx* c, cudaError_t e, const char* what);
+void ctx_bind_stream(amp_ctx* c, cudaStream_t st);
 
 // Phase timers: record an event pair around a phase on the context stream.
 int prof_begin(amp_ctx* c, int phase, cudaStream_t st);
@@ -226,6 +251,7 @@ int reuse_lists(amp_ctx* c, const double* xyz, bool* reused);  // new positions 
 // pair terms and real-space sums (amp_pair.cu)
 void launch_pair_build(amp_ctx* c);
 int dfm_setup(amp_ctx* c);  // builds c->dfm
+void dfm_host_table(std::vector<float2>& tab);  // the table of c->dfm, on the host
 void launch_e0_real(amp_ctx* c, double4_32a* out);  // out = real-space E0 + self
 // out = T_real v + self v (float64 path, double-float arithmetic; vhi + vlo = v)
 void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out);
@@ -237,21 +263,28 @@ int pme_setup(amp_ctx* c);
 int pme_alloc_atoms(amp_ctx* c, int n_cap);
 int pme_influence(amp_ctx* c);
 
-// double-float 3D FFT convolution (amp_fft.cu), power-of-two grids
-bool fft_df_supported(int K);
-int fft_df_setup(amp_ctx* c, const double* G_half);
-// grid64 (fixed = false) or gridfx (fixed = true, zeroed on the way) -> phi_df
-void fft_df_convolve(amp_ctx* c, cudaStream_t st, bool fixed);
-void launch_pme_theta(amp_ctx* c);
-void pme_theta64(amp_ctx* c);  // float64 B-spline weights for the force kernels (float64 path: on demand)
-int pme_permanent_field(amp_ctx* c, double4_32a* out_add);           // out += recip field
-// reciprocal field of dipoles on stream st: out += field (set: out = field)
+// own 3D FFT convolution (amp_fft.cu), power-of-two grids up to 64
+bool fft_own_supported(int K);
+int fft_own_setup(amp_ctx* c);  // buffers and twiddles (K only); G comes from pme_influence
+void fft_df_convolve(amp_ctx* c, cudaStream_t st);   // gridfx (zeroed on the way) -> phi_df, double-float
+void fft_f32_convolve(amp_ctx* c, cudaStream_t st);  // spread32 (zeroed on the way) -> phi32, float32
+void fft_f64_convolve(amp_ctx* c, cudaStream_t st, double* grid, double* phi);  // grid (zeroed on the way) -> phi
+void launch_pme_theta(amp_ctx* c, cudaStream_t st);
+void pme_theta64(amp_ctx* c, cudaStream_t st);  // float64 B-spline weights (permanent field, force kernels)
+int pme_geometry(amp_ctx* c);  // weights and e0rec on the side stream (ev_geom)
+void join_geometry(amp_ctx* c);  // the context stream waits for pme_geometry's work
+// reciprocal field of dipoles on stream st: out += field (set: out = field);
+// double-float chain from the split v32 + vlo (vlo null: v32 alone)
 int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* out,
                      cudaStream_t st, bool set);
+// the mixed path's operator: the float32 chain from v32
+int pme_dipole_field32(amp_ctx* c, const float4* v32, double4_32a* out, cudaStream_t st, bool set);
 
 // solver (amp_pcg.cu)
 void launch_to_sorted(amp_ctx* c, const double* src, double4_32a* dst);
 void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst);
+// a += b (cell order), and dst (caller order) = the sum
+void launch_add_from_sorted(amp_ctx* c, double4_32a* a, const double4_32a* b, double* dst);
 int solve(amp_ctx* c, bool use_guess);
 bool predict_guess(amp_ctx* c);  // c->mu from the solution history; false if too short
 int push_history(amp_ctx* c);     // c->mu into the solution history
@@ -263,7 +296,8 @@ int forces(amp_ctx* c, const double4_32a* mu_sorted, double* F, double* gq, doub
 int force_buffers(amp_ctx* c);
 // float64 (or float32) grid potential of the dipoles v, or of the permanent
 // multipoles (multipoles = true), through cuFFT: the backward kernels' grids
-int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out);
+int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out,
+                  cudaStream_t st);
 int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, double* gt);
 void launch_split_multipoles(amp_ctx* c);  // pd and mp_df from the atom records
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);

@@ -564,7 +564,7 @@ int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, d
                                                             c->atomD, c->perm, F, gq, gd, gt, c->mpole_e);
     k_block_sum<<<1, 1024, 0, s>>>(c->n, c->mpole_e, 1, c->scal + 5);
   } else {
-    pme_theta64(c);
+    pme_theta64(c, c->stream);
     if ((r = force_buffers(c))) return r;
     const double b = c->cfg.ewald_beta, L = c->cfg.box;
     MGeomDf g;
@@ -582,7 +582,7 @@ int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, d
     // the per-pair records are (hi, lo) float pairs in the backward pair buffer
     float2* pair = reinterpret_cast<float2*>(c->force_pair);
     PhaseScope ps(c, AMP_PHASE_FORCES);
-    if ((r = pme_potential(c, false, true, nullptr, nullptr, c->grid64b))) return r;
+    if ((r = pme_potential(c, false, true, nullptr, nullptr, c->grid64b, c->stream))) return r;
     c->n_launch += 2;
     k_recip_mpole<<<amp_blocks((long long)c->n * kGroup, 128), 128, 0, s>>>(
         c->n, c->theta, c->gbase, c->grid64b, c->K, c->atomA, c->atomB, c->atomC, c->atomD, c->force_recip);

@@ -546,7 +546,7 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
   if (c->n_full > c->cap_full || c->n_half > c->cap_half) {
     void** bufs[] = {(void**)&c->full_j, (void**)&c->full_ref, (void**)&c->tr_tmp, (void**)&c->half_i, (void**)&c->half_j,
                      (void**)&c->T64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32,
-                     (void**)&c->pos_tr};
+                     (void**)&c->pos_tr, (void**)&c->intra};
     for (void** b : bufs) {
       dev_free(c, *b);
       *b = nullptr;
@@ -559,9 +559,9 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
         (r = dev_alloc(c, &c->pos_tr, caph)) || (r = dev_alloc(c, &c->Ep64, 6 * caph)))
       return r;
     if (c->cfg.precision == AMP_FP64) {
-      if ((r = dev_alloc(c, &c->T64, 6 * capf))) return r;
+      if ((r = dev_alloc(c, &c->T64, 6 * capf)) || (r = dev_alloc(c, &c->intra, caph + 1))) return r;
     } else {
-      if ((r = dev_alloc(c, &c->T32, 6 * caph)) || (r = dev_alloc(c, &c->Ep32, 6 * caph))) return r;
+      if ((r = dev_alloc(c, &c->T32, 6 * capf)) || (r = dev_alloc(c, &c->Ep32, 6 * caph))) return r;
     }
     c->cap_half = caph;
     c->cap_full = capf;
@@ -642,6 +642,9 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   k_gather_atoms<<<amp_blocks(n, 256), 256, 0, st>>>(n, c->perm, xyz, q, dip, quad, alpha, thole, mol, L,
                                                      c->inv_perm, c->atomA, c->atomB, c->atomC, c->atomD,
                                                      c->pos32, c->cell_of, c->slot_tmp, c->alph, c->flags);
+  // the atom records in cell order are complete: the reciprocal-space work of
+  // the geometry starts on the side stream, beside the neighbour search
+  if ((r = pme_geometry(c))) return r;
   ListParams P;
   if ((r = list_params(c, rlist, &P))) return r;
   const int lb = amp_blocks((long long)n * 32, 256);

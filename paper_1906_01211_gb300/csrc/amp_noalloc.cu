@@ -113,10 +113,16 @@ extern "C" int amp_polarization_energy_noalloc(int n_atoms, const double* mu, co
   double* partials = nullptr;
   int r = partials_address(&partials);
   if (r != AMP_OK) return r;
+  // An error left by an earlier, unrelated call on this thread is not ours to
+  // consume: it stays pending for its owner, and nothing is launched.
+  if (cudaPeekAtLastError() != cudaSuccess) return AMP_ERR_CUDA;
   const int nblocks = (n_atoms + kNoallocThreads - 1) / kNoallocThreads;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   k_energy_partials_noalloc<<<nblocks, kNoallocThreads, 0, st>>>(n_atoms, mu, E0, partials);
   k_energy_finish_noalloc<<<1, kNoallocThreads, 0, st>>>(nblocks, partials, U);
-  if (cudaGetLastError() != cudaSuccess) return AMP_ERR_CUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();  // this call's own launch error, reported through the return code
+    return AMP_ERR_CUDA;
+  }
   return AMP_OK;
 }

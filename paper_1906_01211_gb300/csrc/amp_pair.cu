@@ -120,12 +120,17 @@ __device__ __forceinline__ dflt min_image_df(dflt d, const PairGeomDf& g) {
 // Mixed path pair build: the displacement from the split positions (minimum
 // image in double-float, then rounded to float), every other quantity in
 // float32 from the float parts of the per-atom records (pd, mp_df), so that
-// no float64 instruction is issued. Writes the tensor and both permanent
-// fields in float32, 6 + 6 per pair.
+// no float64 instruction is issued. Writes the tensor to both full-list
+// entries of the pair (the owner's and the transposed one, as the float64
+// path does), so that the product kernel reads each row's tensors
+// contiguously, and both permanent fields, in float32.
 __global__ void __launch_bounds__(256) k_pair_build32(long long nh, const int* __restrict__ half_i,
                                                       const int* __restrict__ half_j, const float4* __restrict__ pd,
                                                       const float4* __restrict__ mp_df, PairGeomDf gd, PairGeom32 g,
-                                                      float* __restrict__ T, float* __restrict__ Ep) {
+                                                      const int* __restrict__ full_start,
+                                                      const int* __restrict__ half_start,
+                                                      const int* __restrict__ pos_tr, float4* __restrict__ T4,
+                                                      float2* __restrict__ T2, float* __restrict__ Ep) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
@@ -138,13 +143,16 @@ __global__ void __launch_bounds__(256) k_pair_build32(long long nh, const int* _
   const float r2 = rx * rx + ry * ry + rz * rz;
   const Kern<float> k = pair_kernels32(r2, hi_i.w, hi_j.w, th_i.x, th_j.x,
                                        __float_as_int(th_i.z) == __float_as_int(th_j.z), g);
-  float* t = T + 6 * pid;
-  t[0] = k.b2u * rx * rx - k.b1u;
-  t[1] = k.b2u * ry * ry - k.b1u;
-  t[2] = k.b2u * rz * rz - k.b1u;
-  t[3] = k.b2u * rx * ry;
-  t[4] = k.b2u * rx * rz;
-  t[5] = k.b2u * ry * rz;
+  {
+    const float4 ta = make_float4(k.b2u * rx * rx - k.b1u, k.b2u * ry * ry - k.b1u, k.b2u * rz * rz - k.b1u,
+                                  k.b2u * rx * ry);
+    const float2 tb = make_float2(k.b2u * rx * rz, k.b2u * ry * rz);
+    const long long k1 = full_start[i] + (pid - half_start[i]), k2 = pos_tr[pid];
+    T4[k1] = ta;
+    T2[k1] = tb;
+    T4[k2] = ta;
+    T2[k2] = tb;
+  }
   // float parts of q, d, Theta (mp_df: (q, dx), (dy, dz), (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz) as hi/lo)
   const float4* mi = mp_df + 5 * (long long)i;
   const float4* mj = mp_df + 5 * (long long)j;
@@ -211,12 +219,25 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
                                                        const int* __restrict__ full_start,
                                                        const int* __restrict__ half_start,
                                                        const int* __restrict__ pos_tr, float4* __restrict__ T8,
-                                                       float4* __restrict__ T4, float* __restrict__ Ep) {
+                                                       float4* __restrict__ T4, float* __restrict__ Ep,
+                                                       int* __restrict__ intra) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
   const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
   const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
+  {  // pairs of two sites of one molecule join the list of k_intra_fields64 (one atomic per warp)
+    const bool same = __float_as_int(th_i.z) == __float_as_int(th_j.z);
+    const unsigned live = __activemask();
+    const unsigned m = __ballot_sync(live, same);
+    if (m) {
+      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(intra, __popc(m));
+      base = __shfl_sync(live, base, leader);
+      if (same) intra[1 + base + __popc(m & ((1u << lane) - 1u))] = (int)pid;
+    }
+  }
   const PairTermsDf p = pair_terms_df(hi_i, lo_i, th_i, hi_j, lo_j, th_j, g, tab);
   const dflt(&R)[3] = p.R;
   const dflt NR[3] = {df_neg(R[0]), df_neg(R[1]), df_neg(R[2])};
@@ -274,6 +295,8 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
   dflt fi[3], fj[3];
   mp_field_df(R, mpj, b1e, b2e, b3e, fi);
   mp_field_df(NR, mpi, b1e, b2e, b3e, fj);
+  if (__float_as_int(th_i.z) == __float_as_int(th_j.z))  // same molecule: float64, by k_intra_fields64
+    for (int a = 0; a < 3; ++a) fi[a] = fj[a] = dflt{0.f, 0.f};
   float4* e = reinterpret_cast<float4*>(Ep + 12 * pid);
   e[0] = make_float4(fi[0].hi, fi[0].lo, fi[1].hi, fi[1].lo);
   e[1] = make_float4(fi[2].hi, fi[2].lo, fj[0].hi, fj[0].lo);
@@ -301,11 +324,14 @@ __global__ void k_split_multipoles(int n, const double4_32a* __restrict__ A, con
   }
 }
 
-// E0_i = sum over row entries of the split permanent fields + selfc d_i
+// out_i = sum over row entries of the split per-pair fields + add_i (if
+// given) + selfc selfv_i. E0: the permanent fields of the pair build (zero
+// for two sites of one molecule), add = their float64 intramolecular terms.
 __global__ void __launch_bounds__(256) k_row_sum_fields_df(int n, const int* __restrict__ full_start,
                                                            const int* __restrict__ full_ref,
                                                            const float* __restrict__ Ep, double selfc,
                                                            const double4_32a* __restrict__ selfv,
+                                                           const double4_32a* __restrict__ add,
                                                            double4_32a* __restrict__ out) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gid / kRowGroup, l = gid % kRowGroup;
@@ -325,8 +351,66 @@ __global__ void __launch_bounds__(256) k_row_sum_fields_df(int n, const int* __r
   sz = df_group_sum(sz);
   if (l == 0) {
     const double4_32a s = selfv[i];
-    out[i] = make_double4_32a(df_to_double(sx) + selfc * s.x, df_to_double(sy) + selfc * s.y,
-                              df_to_double(sz) + selfc * s.z, 0.0);
+    const double4_32a a = add ? add[i] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    out[i] = make_double4_32a(df_to_double(sx) + a.x + selfc * s.x, df_to_double(sy) + a.y + selfc * s.y,
+                              df_to_double(sz) + a.z + selfc * s.z, 0.0);
+  }
+}
+
+__device__ __forceinline__ double group_sum(double v) {
+  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
+#pragma unroll
+  for (int o = kRowGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kRowGroup);
+  return v;
+}
+
+// Permanent field of the intramolecular pairs (scale 0: the screened kernels
+// minus the bare ones, no Thole damping) in float64, one pair per thread over
+// the list that the pair build appended (a float64 instruction holds the
+// float64 pipe as long for one active lane as for 32, so these pairs are not
+// evaluated inside the rows, where they are two in ~70). r = x_i - x_j
+// minimum image, B_n by the recurrence above; the fields at i (from j) and
+// at j (from i) are added to the per-atom sums out (float64 atomics; a site
+// with two partners, as in water, gets the same sum in either order).
+__global__ void __launch_bounds__(128) k_intra_fields64(const int* __restrict__ intra,
+                                                        const int* __restrict__ half_i,
+                                                        const int* __restrict__ half_j, PairGeom g,
+                                                        const double4_32a* __restrict__ A,
+                                                        const double4_32a* __restrict__ B,
+                                                        const double4_32a* __restrict__ C,
+                                                        const double4_32a* __restrict__ D,
+                                                        double4_32a* __restrict__ out) {
+  const int cnt = intra[0];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    const int pid = intra[1 + k];
+    const int i = half_i[pid], j = half_j[pid];
+    const double4_32a ai = A[i], aj = A[j];
+    double r3[3] = {ai.x - aj.x, ai.y - aj.y, ai.z - aj.z};
+    for (int a = 0; a < 3; ++a) r3[a] -= g.L * rint(r3[a] * g.invL);
+    const double r2 = r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2];
+    const double r = sqrt(r2), ir = 1.0 / r, ir2 = ir * ir;
+    const double br = g.beta * r;
+    double fac = exp(-br * br) * g.gpre;
+    const double b0 = erfc(br) * ir;
+    const double B1 = (b0 + fac) * ir2;
+    fac *= g.twob2;
+    const double B2 = (3.0 * B1 + fac) * ir2;
+    fac *= g.twob2;
+    const double B3 = (5.0 * B2 + fac) * ir2;
+    const double bare1 = ir * ir2, bare2 = 3.0 * bare1 * ir2, bare3 = 5.0 * bare2 * ir2;
+    const double b1 = B1 - bare1, b2 = B2 - bare2, b3 = B3 - bare3;
+    const double4_32a bi = B[i], bj = B[j], ci = C[i], cj = C[j], di = D[i], dj = D[j];
+    double f[6];
+    multipole_field<double>(r3[0], r3[1], r3[2], aj.w, bj.x, bj.y, bj.z, cj.x, cj.y, cj.z, cj.w, dj.x, dj.y, b1,
+                            b2, b3, f[0], f[1], f[2]);
+    multipole_field<double>(-r3[0], -r3[1], -r3[2], ai.w, bi.x, bi.y, bi.z, ci.x, ci.y, ci.z, ci.w, di.x, di.y,
+                            b1, b2, b3, f[3], f[4], f[5]);
+    double* oi = reinterpret_cast<double*>(out + i);
+    double* oj = reinterpret_cast<double*>(out + j);
+    for (int a = 0; a < 3; ++a) {
+      atomicAdd(oi + a, f[a]);
+      atomicAdd(oj + a, f[3 + a]);
+    }
   }
 }
 
@@ -359,13 +443,6 @@ __global__ void __launch_bounds__(256) k_pair_tv_df(long long nh, const int* __r
   e[0] = make_float4(f[0][0].hi, f[0][0].lo, f[0][1].hi, f[0][1].lo);
   e[1] = make_float4(f[0][2].hi, f[0][2].lo, f[1][0].hi, f[1][0].lo);
   e[2] = make_float4(f[1][1].hi, f[1][1].lo, f[1][2].hi, f[1][2].lo);
-}
-
-__device__ __forceinline__ double group_sum(double v) {
-  const unsigned mask = ((1u << kRowGroup) - 1u) << ((threadIdx.x & 31) & ~(kRowGroup - 1));
-#pragma unroll
-  for (int o = kRowGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kRowGroup);
-  return v;
 }
 
 // out_i = sum over row entries of the stored per-pair vectors (side-selected)
@@ -456,41 +533,51 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
   }
 }
 
-// Mixed precision: float32 tensors and float32 copy of v, products summed in
-// float32 per lane over its share of the row; the row total in double-float
-// across the lanes, then lanes 0..2 finish one component each in float64 (a
-// float64 instruction holds the float64 pipe as long for one active lane as
-// for 32). Rows are grid-strided.
+// acc += x, error-free: the rounding error of the float sum goes to acc.lo
+// (cascaded summation; acc.hi + acc.lo carries the sum to ~float64 level)
+__device__ __forceinline__ void acc_add(dflt& acc, float x) {
+  const dflt s = df_two_sum(acc.hi, x);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, s.lo);
+}
+
+// Mixed precision: float32 tensors (stored per full-list entry, in row order:
+// one 16-byte and one 8-byte load per entry, contiguous across the lanes of a
+// row) and the float32 copy of v (a 16-byte gather per entry); each entry's
+// field T_ij v_j in float32, summed over the lane's entries with error-free
+// two-sums (acc_add), the row total in double-float across the lanes, then
+// lanes 0..2 finish one component each in float64 (a float64 instruction
+// holds the float64 pipe as long for one active lane as for 32). Rows are
+// grid-strided.
 __global__ void __launch_bounds__(256) k_t_real32(int n, const int* __restrict__ full_start,
-                                                  const int* __restrict__ full_j, const int* __restrict__ full_ref,
-                                                  const float* __restrict__ T, double selfc,
+                                                  const int* __restrict__ full_j, const float4* __restrict__ T4,
+                                                  const float2* __restrict__ T2, double selfc,
                                                   const float4* __restrict__ v32, const double4_32a* __restrict__ v64,
                                                   double4_32a* __restrict__ out, const int* __restrict__ stop) {
   if (stop && *stop) return;
   const int l = threadIdx.x % kRowGroup;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup; i < n; i += gridDim.x * (blockDim.x / kRowGroup)) {
-    float sx = 0.f, sy = 0.f, sz = 0.f;
+    dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
     const int e = full_start[i + 1];
-    for (int k = full_start[i] + l; k < e; k += kRowGroup) {
-      const int j = full_j[k];
-      const float2* t = reinterpret_cast<const float2*>(T + 6 * (long long)(full_ref[k] >> 1));
-      const float2 t0 = t[0], t1 = t[1], t2 = t[2];
+    int k = full_start[i] + l;
+    int jn = k < e ? __ldcs(full_j + k) : 0;
+    for (; k < e; k += kRowGroup) {
+      const int j = jn;
+      if (k + kRowGroup < e) jn = __ldcs(full_j + k + kRowGroup);
+      const float4 a = __ldcs(T4 + k);  // xx yy zz xy
+      const float2 b = __ldcs(T2 + k);  // xz yz
       const float4 vj = v32[j];
-      sx = fmaf(t0.x, vj.x, sx);
-      sx = fmaf(t1.y, vj.y, sx);
-      sx = fmaf(t2.x, vj.z, sx);
-      sy = fmaf(t1.y, vj.x, sy);
-      sy = fmaf(t0.y, vj.y, sy);
-      sy = fmaf(t2.y, vj.z, sy);
-      sz = fmaf(t2.x, vj.x, sz);
-      sz = fmaf(t2.y, vj.y, sz);
-      sz = fmaf(t1.x, vj.z, sz);
+      acc_add(sx, fmaf(b.x, vj.z, fmaf(a.w, vj.y, a.x * vj.x)));
+      acc_add(sy, fmaf(b.y, vj.z, fmaf(a.y, vj.y, a.w * vj.x)));
+      acc_add(sz, fmaf(a.z, vj.z, fmaf(b.y, vj.y, b.x * vj.x)));
     }
-    const dflt dx = df_group_sum({sx, 0.f}), dy = df_group_sum({sy, 0.f}), dz = df_group_sum({sz, 0.f});
+    sx = df_group_sum(sx);
+    sy = df_group_sum(sy);
+    sz = df_group_sum(sz);
     if (l < 4) {
       double* o = reinterpret_cast<double*>(out + i);
       if (l < 3) {
-        const dflt d = l == 0 ? dx : (l == 1 ? dy : dz);
+        const dflt d = l == 0 ? sx : (l == 1 ? sy : sz);
         o[l] = df_to_double(d) + selfc * reinterpret_cast<const double*>(v64 + i)[l];
       } else {
         o[3] = 0.0;
@@ -534,8 +621,8 @@ PairGeomDf geom_df(const PairGeom& g) {
 //   a_0 = erfc(x0) exp(x0^2), a_1 = 2 x0 a_0 - 2/sqrt(pi),
 //   (n + 1) a_{n+1} = 2 x0 a_n + 2 a_{n-1}  (n >= 1);
 // with |t| <= 1/16 the series is cut after t^11 (remainder below 1e-17).
-int dfm_setup(amp_ctx* c) {
-  std::vector<float2> tab(kDfmTableSize);
+void dfm_host_table(std::vector<float2>& tab) {
+  tab.assign(kDfmTableSize, make_float2(0.f, 0.f));
   auto put = [&](int k, long double v) {
     const float h = (float)v;
     tab[k] = make_float2(h, (float)(v - (long double)h));
@@ -550,6 +637,11 @@ int dfm_setup(amp_ctx* c) {
     for (int n = 0; n < kErfcxTerms; ++n) put(i * kErfcxTerms + n, a[n]);
   }
   for (int j = -11; j <= 11; ++j) put(kExpTable + 11 + j, std::exp((long double)j / 32.0L));
+}
+
+int dfm_setup(amp_ctx* c) {
+  std::vector<float2> tab;
+  dfm_host_table(tab);
   int r;
   if (!c->dfm && (r = dev_alloc(c, &c->dfm, kDfmTableSize))) return r;
   if ((r = cuda_check(c, cudaMemcpyAsync(c->dfm, tab.data(), sizeof(float2) * kDfmTableSize, cudaMemcpyHostToDevice,
@@ -565,17 +657,22 @@ void launch_pair_build(amp_ctx* c) {
   c->n_launch += 1;
   k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
                                                                   c->mp_df, c->pd);
+  if (c->cfg.precision == AMP_FP64) cudaMemsetAsync(c->e0intra, 0, sizeof(double4_32a) * c->n, c->stream);
   if (c->n_half == 0) return;
   const PairGeom g = geom(c);
   const int blocks = amp_blocks(c->n_half, 256);
   c->n_launch += 1;
   if (c->cfg.precision == AMP_FP64) {
     const PairGeomDf gd = geom_df(g);
+    cudaMemsetAsync(c->intra, 0, sizeof(int), c->stream);
     k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, gd, c->dfm,
                                                    c->full_start, c->half_start, c->pos_tr,
                                                    reinterpret_cast<float4*>(c->T64),
                                                    reinterpret_cast<float4*>(c->T64) + 2 * c->cap_full,
-                                                   reinterpret_cast<float*>(c->Ep64));
+                                                   reinterpret_cast<float*>(c->Ep64), c->intra);
+    c->n_launch += 1;
+    k_intra_fields64<<<4 * c->n_sm, 128, 0, c->stream>>>(c->intra, c->half_i, c->half_j, g, c->atomA, c->atomB,
+                                                         c->atomC, c->atomD, c->e0intra);
     return;
   }
   // mixed path: float32 pair terms from the split records, which also serve its float64 check
@@ -584,7 +681,9 @@ void launch_pair_build(amp_ctx* c) {
   g32.twob2 = (float)g.twob2;
   g32.gpre = (float)g.gpre;
   k_pair_build32<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, geom_df(g), g32,
-                                                c->T32, c->Ep32);
+                                                c->full_start, c->half_start, c->pos_tr,
+                                                reinterpret_cast<float4*>(c->T32),
+                                                reinterpret_cast<float2*>(c->T32 + 4 * c->cap_full), c->Ep32);
 }
 
 // The split positions and moments alone (clusters, which build no pair terms).
@@ -594,7 +693,7 @@ void launch_split_multipoles(amp_ctx* c) {
                                                                   c->mp_df, c->pd);
 }
 
-// Self term of the permanent field: +4 beta^3/(3 sqrt(pi)) d_i, d_i from atomB.
+// Real-space permanent field with the self term +4 beta^3/(3 sqrt(pi)) d_i (d_i from atomB).
 void launch_e0_real(amp_ctx* c, double4_32a* out) {
   const PairGeom g = geom(c);
   const int blocks = amp_blocks((long long)c->n * kRowGroup, 256);
@@ -602,7 +701,7 @@ void launch_e0_real(amp_ctx* c, double4_32a* out) {
   if (c->cfg.precision == AMP_FP64)
     k_row_sum_fields_df<<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref,
                                                        reinterpret_cast<const float*>(c->Ep64), g.selfc, c->atomB,
-                                                       out);
+                                                       c->e0intra, out);
   else
     k_row_sum_pairvec<float><<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref, c->Ep32, g.selfc,
                                                             c->atomB, out);
@@ -629,7 +728,8 @@ void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, doub
   c->n_launch += 1;
   const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256),
                                           (long long)kTRealBlocksPerSm * c->n_sm);
-  k_t_real32<<<tb, 256, 0, c->stream>>>(c->n, c->full_start, c->full_j, c->full_ref, c->T32, g.selfc, v32, v64,
+  k_t_real32<<<tb, 256, 0, c->stream>>>(c->n, c->full_start, c->full_j, reinterpret_cast<const float4*>(c->T32),
+                                        reinterpret_cast<const float2*>(c->T32 + 4 * c->cap_full), g.selfc, v32, v64,
                                         out, c->op_stop);
 }
 
@@ -644,7 +744,8 @@ void launch_t_real_fp64_direct(amp_ctx* c, const double4_32a* v, double4_32a* ou
                                                                     geom_df(g), c->dfm, c->p32, c->plo,
                                                                     reinterpret_cast<float*>(c->Ep64));
   k_row_sum_fields_df<<<blocks, 256, 0, c->stream>>>(c->n, c->full_start, c->full_ref,
-                                                     reinterpret_cast<const float*>(c->Ep64), g.selfc, v, out);
+                                                     reinterpret_cast<const float*>(c->Ep64), g.selfc, v, nullptr,
+                                                     out);
 }
 
 }  // namespace amp

@@ -393,6 +393,20 @@ __global__ void k_from_sorted(int n, const int* __restrict__ perm, const double4
   dst[3 * i + 2] = v.z;
 }
 
+// a += b in cell order, and dst (caller order) = the sum
+__global__ void k_add_from_sorted(int n, const int* __restrict__ perm, double4_32a* __restrict__ a,
+                                  const double4_32a* __restrict__ b, double* __restrict__ dst) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  const double4_32a u = a[s], w = b[s];
+  const double4_32a v = make_double4_32a(u.x + w.x, u.y + w.y, u.z + w.z, 0.0);
+  a[s] = v;
+  dst[3 * i] = v.x;
+  dst[3 * i + 1] = v.y;
+  dst[3 * i + 2] = v.z;
+}
+
 __global__ void __launch_bounds__(NT) k_split(int n, const double4_32a* __restrict__ v, float4* __restrict__ hi,
                                              float4* __restrict__ lo, float4* __restrict__ hl,
                                              float* __restrict__ vmax) {
@@ -429,6 +443,11 @@ void launch_from_sorted(amp_ctx* c, const double4_32a* src, double* dst) {
   k_from_sorted<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->perm, src, dst);
 }
 
+void launch_add_from_sorted(amp_ctx* c, double4_32a* a, const double4_32a* b, double* dst) {
+  c->n_launch += 1;
+  k_add_from_sorted<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->perm, a, b, dst);
+}
+
 void launch_to32(amp_ctx* c, const double4_32a* v, float4* o) {
   c->n_launch += 1;
   k_split<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, v, o, nullptr, nullptr, c->vmax_part);
@@ -449,8 +468,9 @@ enum RealMode { kRealDf, kRealF32, kRealDirectDf };
 // the spreading keeps every SM busy by itself, while the three FFT passes
 // that follow are latency bound and leave most of the GPU to the real-space
 // kernel. The main stream waits for the side stream before returning. The
-// reciprocal part is the double-float chain in both precisions; the float64
-// check (kRealDirectDf) first splits v into (p32, plo) for both parts.
+// reciprocal part is the double-float chain for the float64 path and the
+// mixed path's float64 check (kRealDirectDf, which first splits v into
+// (p32, plo) for both parts), the float32 chain for the mixed operator.
 static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* t,
                        double4_32a* t2, RealMode mode) {
   int r;
@@ -465,7 +485,8 @@ static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, cons
     {
       PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
       c->spread_event = mode != kRealDirectDf;
-      r = pme_dipole_field(c, v, v32, vlo, t2, c->side, true);
+      r = mode == kRealF32 ? pme_dipole_field32(c, v32, t2, c->side, true)
+                           : pme_dipole_field(c, v, v32, vlo, t2, c->side, true);
       if (c->spread_event) cudaStreamWaitEvent(c->stream, c->ev_spread, 0);
       c->spread_event = false;
     }
@@ -489,6 +510,7 @@ static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, cons
     return AMP_OK;
   }
   PhaseScope ps(c, AMP_PHASE_T_RECIP);
+  if (mode == kRealF32) return pme_dipole_field32(c, v32, t, c->stream, false);
   return pme_dipole_field(c, v, v32, vlo, t, c->stream, false);
 }
 

@@ -10,11 +10,12 @@
 //   phi = unnormalised C2R( G . R2C(Q) ),
 //   G(m) = exp(-pi^2 m~^2/beta^2) / (pi V m~^2) |b1 b2 b3|^2, G(0) = 0;
 //   E_i = -sum_g grad W_i(g) phi(g).
-// Both precisions spread (permanent multipoles once per geometry, dipoles at
-// every T*mu; the mixed path's dipoles are its float32 operator input) in
-// double-float into a 64-bit fixed-point grid, transform it with the
+// The permanent multipoles (once per geometry) are spread, transformed and
+// gathered in float64 (float64 atomics, cuFFT float64). The dipoles of every
+// T*mu (the mixed path's are its float32 operator input) are spread in
+// double-float into a 64-bit fixed-point grid, transformed by the
 // double-float FFT of amp_fft.cu on power-of-two grids (else cuFFT float64, a
-// library call, and a split), and gather in double-float. The force kernels'
+// library call, and a split) and gathered in double-float. The force kernels'
 // potentials use float64 (float32 in the mixed path) atomics and cuFFT.
 // |b(m)|^2 = 1/|sum_{k=0}^{3} M5(k+1) e^{2 pi i m k/K}|^2; where that sum
 // vanishes (m = K/2, even K) the mean of the neighbours m-1, m+1 is used.
@@ -60,38 +61,37 @@ __device__ __forceinline__ void bspline5(double f, double s, double w[4][kOrder]
 }
 
 // Float64 B-spline weights (derivatives 0..3, which the force kernels need),
-// with their float32 copy when theta32 is given (mixed path). The base
-// indices are the same as those of k_theta_df (same float64 operations).
+// with their float32 copy when theta32 is given (mixed path); one thread per
+// (atom, axis). The base indices are the same as those of k_theta_df (same
+// float64 operations).
 __global__ void k_theta(int n, const double4_32a* __restrict__ A, double L, int K, double* __restrict__ theta,
                         float* __restrict__ theta32) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3LL * n) return;
+  const int s = (int)(t / 3), ax = (int)(t - 3LL * s);
   const double4_32a a = A[s];
-  const double xs[3] = {a.x, a.y, a.z};
   const double sc = (double)K / L;
+  double u = (ax == 0 ? a.x : (ax == 1 ? a.y : a.z)) * sc;
+  u = u - (double)K * floor(u * (1.0 / (double)K));
+  if (u >= (double)K) u -= (double)K;
+  if (u < 0.0) u += (double)K;
+  const double k0 = floor(u);
+  double w[4][kOrder];
+  bspline5(u - k0, sc, w);
   double* th = theta + (long long)kTh * s;
-  for (int ax = 0; ax < 3; ++ax) {
-    double u = xs[ax] * sc;
-    u = u - (double)K * floor(u * (1.0 / (double)K));
-    if (u >= (double)K) u -= (double)K;
-    if (u < 0.0) u += (double)K;
-    const double k0 = floor(u);
-    double w[4][kOrder];
-    bspline5(u - k0, sc, w);
-    for (int d = 0; d < 4; ++d)
-      for (int t = 0; t < kOrder; ++t) {
-        th[(ax * 4 + d) * kOrder + t] = w[d][t];
-        if (theta32) theta32[(long long)kTh * s + (ax * 4 + d) * kOrder + t] = (float)w[d][t];
-      }
-  }
+  for (int d = 0; d < 4; ++d)
+    for (int k = 0; k < kOrder; ++k) {
+      th[(ax * 4 + d) * kOrder + k] = w[d][k];
+      if (theta32) theta32[(long long)kTh * s + (ax * 4 + d) * kOrder + k] = (float)w[d][k];
+    }
 }
 
-// The weights of bspline5 (derivatives 0..2) in double-float, from f as hi/lo
-// floats and s = K/L: the same recursion (Essmann et al. 1995, Eq. 4.1-4.4),
-// about 48 significant bits, on the float units.
+// The weights of bspline5 (derivatives 0 and 1) in double-float, from f as
+// hi/lo floats and s = K/L: the same recursion (Essmann et al. 1995, Eq.
+// 4.1-4.4), about 48 significant bits, on the float units.
 __device__ __forceinline__ dflt df_scale(dflt a, float c) { return {a.hi * c, a.lo * c}; }  // c a power of two
 
-__device__ __forceinline__ void bspline5_df(dflt f, dflt s, dflt w[3][kOrder]) {
+__device__ __forceinline__ void bspline5_df(dflt f, dflt s, dflt w[2][kOrder]) {
   const dflt one = {1.f, 0.f}, third = {0.333333343f, -9.93410776e-09f};  // 1/3 = hi + lo
   dflt m2[2] = {f, df_sub(one, f)};
   dflt m3[3], m4[4], m5[5];
@@ -116,38 +116,25 @@ __device__ __forceinline__ void bspline5_df(dflt f, dflt s, dflt w[3][kOrder]) {
     if (t >= 1) v = df_madd(gt, m4[t - 1], v);
     m5[t] = df_scale(v, 0.25f);
   }
-  const dflt s2 = df_mul(s, s);
   for (int t = 0; t < 5; ++t) {
     const dflt a4 = t < 4 ? m4[t] : dflt{0.f, 0.f}, b4 = t >= 1 ? m4[t - 1] : dflt{0.f, 0.f};
-    const dflt a3 = t < 3 ? m3[t] : dflt{0.f, 0.f}, b3 = (t >= 1 && t - 1 < 3) ? m3[t - 1] : dflt{0.f, 0.f},
-               c3 = (t >= 2 && t - 2 < 3) ? m3[t - 2] : dflt{0.f, 0.f};
     w[0][t] = m5[t];
     w[1][t] = df_mul(df_sub(a4, b4), s);
-    w[2][t] = df_mul(df_add(df_sub(a3, df_scale(b3, 2.f)), c3), s2);
   }
 }
 
-// Float64 path, one group of four lanes per atom: lane ax < 3 builds axis
-// ax's weights in double-float (theta_df: derivatives 0 and 1, theta_df2:
-// derivative 2) and its base index; lane 3 bounds the atom's multipole
-// contribution to one grid point for the fixed-point spreading,
-//   |q| + s (|dx| + |dy| + |dz|) + s^2 (|Qxx| + |Qyy| + |Qzz| + |Qxy| + |Qxz| + |Qyz|),
-// which covers |w| <= 1, |w'| <= s and |w''| <= 1.5 s^2 with the 1/3 and
-// 2/3 factors of the quadrupole terms. Lane 0 stores the base indices and
-// counts the atom in kcount; fx_info[1] = the largest count, fx_info[2] =
-// the largest bound (float bits, non-negative).
-__global__ void __launch_bounds__(128) k_theta_df(int n, const double4_32a* __restrict__ A,
-                                                   const double4_32a* __restrict__ B,
-                                                   const double4_32a* __restrict__ C,
-                                                   const double4_32a* __restrict__ D, double L, int K, float2 s_df,
-                                                   float2* __restrict__ theta_df, float2* __restrict__ theta_df2,
+// One group of four lanes per atom: lane ax < 3 builds axis ax's weights and
+// first derivatives in double-float (theta_df) and its base index, which lane
+// 0 stores, counting the atom in kcount; fx_info[1] = the largest count (the
+// atoms that reach one grid point, for the fixed-point dipole spreading).
+__global__ void __launch_bounds__(128) k_theta_df(int n, const double4_32a* __restrict__ A, double L, int K,
+                                                   float2 s_df, float2* __restrict__ theta_df,
                                                    int4* __restrict__ gbase, int* __restrict__ kcount,
                                                    int* __restrict__ fx_info) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = gid >> 2, lane4 = gid & 3;
   const bool valid = s < n;
   int base = 0;
-  float bound = 0.f;
   if (valid && lane4 < 3) {
     const double4_32a a = A[s];
     const double x = lane4 == 0 ? a.x : (lane4 == 1 ? a.y : a.z);
@@ -158,45 +145,32 @@ __global__ void __launch_bounds__(128) k_theta_df(int n, const double4_32a* __re
     if (u < 0.0) u += (double)K;
     const double k0 = floor(u);
     base = (int)k0;
-    dflt w[3][kOrder];
+    dflt w[2][kOrder];
     bspline5_df(df_split(u - k0), {s_df.x, s_df.y}, w);
     float2* o = theta_df + (long long)kThDf * s + lane4 * 2 * kOrder;
-    float2* o2 = theta_df2 + 3LL * kOrder * s + lane4 * kOrder;
     for (int t = 0; t < kOrder; ++t) {
       o[t] = make_float2(w[0][t].hi, w[0][t].lo);
       o[kOrder + t] = make_float2(w[1][t].hi, w[1][t].lo);
-      o2[t] = make_float2(w[2][t].hi, w[2][t].lo);
     }
-  } else if (valid) {
-    const double4_32a a = A[s], b = B[s], c = C[s], d = D[s];
-    const float sc = (float)((double)K / L);
-    const float dip = fabsf((float)b.x) + fabsf((float)b.y) + fabsf((float)b.z);
-    const float quad = fabsf((float)c.x) + fabsf((float)c.y) + fabsf((float)c.z) + fabsf((float)c.w) +
-                       fabsf((float)d.x) + fabsf((float)d.y);
-    bound = 1.01f * (fabsf((float)a.w) + sc * dip + sc * sc * quad);
   }
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int by = __shfl_sync(full, base, lane + 1), bz = __shfl_sync(full, base, lane + 2);
-  const int b4 = __shfl_sync(full, __float_as_int(bound), lane + 3);
   int cnt = 0;
   if (valid && lane4 == 0) {
     gbase[s] = make_int4(base, by, bz, 0);
     cnt = atomicAdd(kcount + ((long long)base * K + by) * K + bz, 1) + 1;
   }
-  // block maxima first: two atomics per block, skipped when the stored value
-  // is already as large (it only grows)
-  __shared__ int wmax[2][128 / 32];
-  const int mc = __reduce_max_sync(full, cnt), mb = __reduce_max_sync(full, lane4 == 0 ? b4 : 0);
-  if (lane == 0) {
-    wmax[0][threadIdx.x >> 5] = mc;
-    wmax[1][threadIdx.x >> 5] = mb;
-  }
+  // the block's maximum first: one atomic per block, skipped when the stored
+  // value is already as large (it only grows)
+  __shared__ int wmax[128 / 32];
+  const int mc = __reduce_max_sync(full, cnt);
+  if (lane == 0) wmax[threadIdx.x >> 5] = mc;
   __syncthreads();
-  if (threadIdx.x < 2) {
+  if (threadIdx.x == 0) {
     int m = 0;
-    for (int w = 0; w < 128 / 32; ++w) m = max(m, wmax[threadIdx.x][w]);
-    int* dst = fx_info + 1 + threadIdx.x;
+    for (int w = 0; w < 128 / 32; ++w) m = max(m, wmax[w]);
+    int* dst = fx_info + 1;
     if (m > __ldcg(dst)) atomicMax(dst, m);
   }
 }
@@ -261,6 +235,45 @@ __global__ void __launch_bounds__(128) k_spread_multipoles(int n, const R* __res
       const int gz = wrapk(b.z - tz, K);
       atomicAdd(row + gz, a0 * wz[0][tz] + a1 * wz[1][tz] + a2 * wz[2][tz]);
     }
+  }
+}
+
+// The permanent multipoles into the float64 grid (the right-hand side's
+// reciprocal part), one thread per (atom, y row, z point), which adds the
+// atom's values at the five x planes, P0 w_x + P1 w'_x + P2 w''_x with
+//   P0 = q w_y w_z + dy w'_y w_z + dz w_y w'_z + (Qyy w''_y w_z + Qzz w_y w''_z + 2 Qyz w'_y w'_z) / 3,
+//   P1 = dx w_y w_z + 2 (Qxy w'_y w_z + Qxz w_y w'_z) / 3,   P2 = Qxx w_y w_z / 3
+// (Sagui, Pedersen and Darden 2004, the quadrupole with the 1/3 of the
+// traceless form). Every lane works (a float64 instruction holds the float64
+// pipe as long for one active lane as for 32).
+__global__ void __launch_bounds__(256) k_spread_multipoles64(int n, const double* __restrict__ theta,
+                                                             const int4* __restrict__ gbase,
+                                                             const double4_32a* __restrict__ A,
+                                                             const double4_32a* __restrict__ B,
+                                                             const double4_32a* __restrict__ C,
+                                                             const double4_32a* __restrict__ D, int K,
+                                                             double* __restrict__ grid) {
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= (long long)n * (kOrder * kOrder)) return;
+  const int s = (int)(item / (kOrder * kOrder)), tyz = (int)(item - (long long)s * (kOrder * kOrder));
+  const int ty = tyz / kOrder, tz = tyz - ty * kOrder;
+  const double* th = theta + (long long)kTh * s;
+  const double y0 = th[(1 * 4 + 0) * kOrder + ty], y1 = th[(1 * 4 + 1) * kOrder + ty], y2 = th[(1 * 4 + 2) * kOrder + ty];
+  const double z0 = th[(2 * 4 + 0) * kOrder + tz], z1 = th[(2 * 4 + 1) * kOrder + tz], z2 = th[(2 * 4 + 2) * kOrder + tz];
+  const double4_32a a = A[s], b = B[s], c = C[s], d = D[s];
+  const double y0z0 = y0 * z0, y1z0 = y1 * z0, y0z1 = y0 * z1;
+  const double P0 = a.w * y0z0 + b.y * y1z0 + b.z * y0z1 +
+                    (1.0 / 3.0) * (c.y * y2 * z0 + c.z * y0 * z2 + 2.0 * d.y * y1 * z1);
+  const double P1 = b.x * y0z0 + (2.0 / 3.0) * (c.w * y1z0 + d.x * y0z1);
+  const double P2 = (1.0 / 3.0) * c.x * y0z0;
+  const int4 g = gbase[s];
+  double* col = grid + (long long)wrapk(g.y - ty, K) * K + wrapk(g.z - tz, K);
+  const long long plane = (long long)K * K;
+#pragma unroll
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const double x0 = th[(0 * 4 + 0) * kOrder + tx], x1 = th[(0 * 4 + 1) * kOrder + tx],
+                 x2 = th[(0 * 4 + 2) * kOrder + tx];
+    atomicAdd(col + wrapk(g.x - tx, K) * plane, fma(P2, x2, fma(P1, x1, P0 * x0)));
   }
 }
 
@@ -377,55 +390,6 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, con
   }
 }
 
-// Permanent multipoles into the fixed-point grid (float64 path): the charge,
-// dipole and quadrupole terms of Q(g) (Sagui, Pedersen and Darden 2004,
-// Eq. 11, quadrupoles with the 1/3 of the traceless form) in double-float
-// from the split multipoles (mp: q dx | dy dz | Qxx Qyy | Qzz Qxy | Qxz Qyz
-// as hi/lo pairs). One thread per (atom, y row, z point) adds the point
-// values of the five x planes, P0 w_x + P1 w'_x + P2 w''_x with
-//   P0 = q w_y w_z + dy w'_y w_z + dz w_y w'_z + (Qyy w''_y w_z + Qzz w_y w''_z + 2 Qyz w'_y w'_z) / 3,
-//   P1 = dx w_y w_z + 2 (Qxy w'_y w_z + Qxz w_y w'_z) / 3,   P2 = Qxx w_y w_z / 3.
-// The scale comes from the per-atom bound of k_theta_df (fx_info[2]) times the
-// atoms that reach one point; block 0 stores it in fx_info[0].
-__global__ void __launch_bounds__(kSpreadThreads) k_spread_multipoles_fx(
-    int n, const float2* __restrict__ th_df, const float2* __restrict__ th_df2, const int4* __restrict__ gbase,
-    const float4* __restrict__ mp, int* __restrict__ fx_info, int K, unsigned long long* __restrict__ grid) {
-  const int sfx = fixed_scale_bound(__int_as_float(fx_info[2]) * (float)(kOrder * kOrder * kOrder * fx_info[1]));
-  if (blockIdx.x == 0 && threadIdx.x == 0) fx_info[0] = sfx;
-  const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
-  if (item >= (long long)n * (kOrder * kOrder)) return;
-  const int s = (int)(item / (kOrder * kOrder)), tyz = (int)(item - (long long)s * (kOrder * kOrder));
-  const int ty = tyz / kOrder, tz = tyz - ty * kOrder;
-  const float2* th = th_df + (long long)kThDf * s;
-  const float2* th2 = th_df2 + 3LL * kOrder * s;
-  const float4* m = mp + 5LL * s;
-  const float4 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3], m4 = m[4];
-  const dflt q = {m0.x, m0.y}, dx = {m0.z, m0.w}, dy = {m1.x, m1.y}, dz = {m1.z, m1.w};
-  const dflt qxx = {m2.x, m2.y}, qyy = {m2.z, m2.w}, qzz = {m3.x, m3.y}, qxy = {m3.z, m3.w};
-  const dflt qxz = {m4.x, m4.y}, qyz = {m4.z, m4.w};
-  const float2 y0f = th[(1 * 2 + 0) * kOrder + ty], y1f = th[(1 * 2 + 1) * kOrder + ty], y2f = th2[1 * kOrder + ty];
-  const float2 z0f = th[(2 * 2 + 0) * kOrder + tz], z1f = th[(2 * 2 + 1) * kOrder + tz], z2f = th2[2 * kOrder + tz];
-  const dflt y0 = {y0f.x, y0f.y}, y1 = {y1f.x, y1f.y}, y2 = {y2f.x, y2f.y};
-  const dflt z0 = {z0f.x, z0f.y}, z1 = {z1f.x, z1f.y}, z2 = {z2f.x, z2f.y};
-  const dflt third = {0.333333343f, -9.93410776e-09f}, two3 = {0.666666687f, -1.98682155e-08f};
-  const dflt y0z0 = df_mul(y0, z0), y1z0 = df_mul(y1, z0), y0z1 = df_mul(y0, z1);
-  const dflt quad0 = df_madd(df_add(qyz, qyz), df_mul(y1, z1),
-                             df_madd(qzz, df_mul(y0, z2), df_mul(qyy, df_mul(y2, z0))));
-  const dflt P0 = df_madd(third, quad0, df_madd(dz, y0z1, df_madd(dy, y1z0, df_mul(q, y0z0))));
-  const dflt P1 = df_madd(two3, df_madd(qxz, y0z1, df_mul(qxy, y1z0)), df_mul(dx, y0z0));
-  const dflt P2 = df_mul(df_mul(third, qxx), y0z0);
-  const int4 b = gbase[s];
-  unsigned long long* col = grid + (long long)wrapk(b.y - ty, K) * K + wrapk(b.z - tz, K);
-  const long long plane = (long long)K * K;
-#pragma unroll
-  for (int tx = 0; tx < kOrder; ++tx) {
-    const float2 x0 = th[(0 * 2 + 0) * kOrder + tx], x1 = th[(0 * 2 + 1) * kOrder + tx], x2 = th2[tx];
-    const dflt val = df_madd(P2, {x2.x, x2.y}, df_madd(P1, {x1.x, x1.y}, df_mul(P0, {x0.x, x0.y})));
-    const long long qv = to_fixed(val.hi, sfx) + to_fixed(val.lo, sfx);
-    atomicAdd(col + wrapk(b.x - tx, K) * plane, (unsigned long long)qv);
-  }
-}
-
 // fixed-point grid -> float64 grid (for cuFFT), zeroing the fixed-point grid
 __global__ void k_fixed_to_double(long long ng, unsigned long long* __restrict__ qfx, const int* __restrict__ fx_info,
                                   double* __restrict__ out, const int* __restrict__ stop) {
@@ -538,6 +502,172 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_field_df(int n, const
   }
 }
 
+// The permanent field's reciprocal part in float64: float64 weights
+// (k_theta), float64 grid potential phi (cuFFT), float64 sums. Six atoms per
+// warp, five lanes each, as in k_gather_field_df; lane t of an atom sums z
+// plane k0z - t, then the five lanes add their sums in a fixed order.
+// out = -grad phi at each atom.
+__device__ __forceinline__ double sum_five64(double v, int base) {  // same order in all five lanes
+  double t = __shfl_sync(0xffffffffu, v, base);
+#pragma unroll
+  for (int k = 1; k < kOrder; ++k) t += __shfl_sync(0xffffffffu, v, base + k);
+  return t;
+}
+
+__global__ void __launch_bounds__(kGatherThreads) k_gather_field64(int n, const double* __restrict__ theta,
+                                                                    const int4* __restrict__ gbase,
+                                                                    const double* __restrict__ phi, int K,
+                                                                    double4_32a* __restrict__ out) {
+  const int lane = threadIdx.x & 31, seg = lane / kOrder, tz = lane - seg * kOrder;
+  const int warp = (blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
+  const int s = warp * kGatherAtomsPerWarp + seg;
+  if (warp * kGatherAtomsPerWarp >= n) return;
+  const bool active = seg < kGatherAtomsPerWarp && s < n;
+  double ex = 0.0, ey = 0.0, ez = 0.0;
+  if (active) {
+    const int4 b = gbase[s];
+    const double* th = theta + (long long)kTh * s;
+    const double wz0 = th[(2 * 4 + 0) * kOrder + tz], wz1 = th[(2 * 4 + 1) * kOrder + tz];
+    double wx0[kOrder], wx1[kOrder];
+    int gx[kOrder];
+    for (int t = 0; t < kOrder; ++t) {
+      wx0[t] = th[(0 * 4 + 0) * kOrder + t];
+      wx1[t] = th[(0 * 4 + 1) * kOrder + t];
+      gx[t] = wrapk(b.x - t, K) * K * K;
+    }
+    const double* pz = phi + wrapk(b.z - tz, K);
+    double px = 0.0, py = 0.0, pzz = 0.0;
+    for (int ty = 0; ty < kOrder; ++ty) {
+      const double wy0 = th[(1 * 4 + 0) * kOrder + ty], wy1 = th[(1 * 4 + 1) * kOrder + ty];
+      const double* col = pz + wrapk(b.y - ty, K) * K;
+      double s0 = 0.0, s1 = 0.0;
+      for (int tx = 0; tx < kOrder; ++tx) {
+        const double ph = col[gx[tx]];
+        s0 = fma(wx0[tx], ph, s0);
+        s1 = fma(wx1[tx], ph, s1);
+      }
+      px = fma(wy0, s1, px);
+      py = fma(wy1, s0, py);
+      pzz = fma(wy0, s0, pzz);
+    }
+    ex = wz0 * px;
+    ey = wz0 * py;
+    ez = wz1 * pzz;
+  }
+  const int base = min(seg, kGatherAtomsPerWarp - 1) * kOrder;
+  ex = sum_five64(ex, base);
+  ey = sum_five64(ey, base);
+  ez = sum_five64(ez, base);
+  if (!active || tz >= 4) return;
+  double* o = reinterpret_cast<double*>(out + s);
+  o[tz] = tz == 3 ? 0.0 : -(tz == 0 ? ex : (tz == 1 ? ey : ez));
+}
+
+// ---- the mixed path's operator: float32 reciprocal chain.
+// Spreading of the float32 dipoles v32 with float32 weights (the hi parts of
+// theta_df) into the float grid spread32 with float atomics, one thread per
+// (atom, y row, z point) over the five x planes, as in k_spread_dipoles_fx.
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles32(int n, const float2* __restrict__ th_df,
+                                                                     const int4* __restrict__ gbase,
+                                                                     const float4* __restrict__ v32, int K,
+                                                                     float* __restrict__ grid,
+                                                                     const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  pdl_wait();
+  pdl_trigger();
+  const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
+  if (item >= (long long)n * (kOrder * kOrder)) return;
+  const int s = (int)(item / (kOrder * kOrder)), tyz = (int)(item - (long long)s * (kOrder * kOrder));
+  const int ty = tyz / kOrder, tz = tyz - ty * kOrder;
+  const float2* th = th_df + (long long)kThDf * s;
+  const float4 h = v32[s];
+  const float y0 = th[(1 * 2 + 0) * kOrder + ty].x, y1 = th[(1 * 2 + 1) * kOrder + ty].x;
+  const float z0 = th[(2 * 2 + 0) * kOrder + tz].x, z1 = th[(2 * 2 + 1) * kOrder + tz].x;
+  // P = mu_y w'_y w_z + mu_z w_y w'_z, Q = mu_x w_y w_z: the point's value is P w_x + Q w'_x
+  const float P = fmaf(h.z * y0, z1, h.y * y1 * z0);
+  const float Q = h.x * y0 * z0;
+  const int4 b = gbase[s];
+  float* col = grid + (long long)wrapk(b.y - ty, K) * K + wrapk(b.z - tz, K);
+  const long long plane = (long long)K * K;
+#pragma unroll
+  for (int tx = 0; tx < kOrder; ++tx) {
+    const float x0 = th[(0 * 2 + 0) * kOrder + tx].x, x1 = th[(0 * 2 + 1) * kOrder + tx].x;
+    atomicAdd(col + wrapk(b.x - tx, K) * plane, fmaf(Q, x1, P * x0));
+  }
+}
+
+// Gather of the float32 field from the float potential phi with float32
+// weights, six atoms per warp and five lanes each as in k_gather_field_df;
+// the field lands in float64 (set: out = -grad phi, else out -= grad phi).
+__device__ __forceinline__ float sum_five32(float v, int base) {  // same order in all five lanes
+  float t = __shfl_sync(0xffffffffu, v, base);
+#pragma unroll
+  for (int k = 1; k < kOrder; ++k) t += __shfl_sync(0xffffffffu, v, base + k);
+  return t;
+}
+
+template <bool kSet>
+__global__ void __launch_bounds__(kGatherThreads) k_gather_field32(int n, const float2* __restrict__ th_df,
+                                                                    const int4* __restrict__ gbase,
+                                                                    const float* __restrict__ phi, int K,
+                                                                    double4_32a* __restrict__ out,
+                                                                    const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31, seg = lane / kOrder, tz = lane - seg * kOrder;
+  const int warp = (blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
+  const int s = warp * kGatherAtomsPerWarp + seg;
+  if (warp * kGatherAtomsPerWarp >= n) return;
+  const bool active = seg < kGatherAtomsPerWarp && s < n;
+  float ex = 0.f, ey = 0.f, ez = 0.f;
+  if (active) {
+    const int4 b = gbase[s];
+    const float2* th = th_df + (long long)kThDf * s;
+    const float wz0 = th[(2 * 2 + 0) * kOrder + tz].x, wz1 = th[(2 * 2 + 1) * kOrder + tz].x;
+    float wx0[kOrder], wx1[kOrder];
+    int gx[kOrder];
+    for (int t = 0; t < kOrder; ++t) {
+      wx0[t] = th[(0 * 2 + 0) * kOrder + t].x;
+      wx1[t] = th[(0 * 2 + 1) * kOrder + t].x;
+      gx[t] = wrapk(b.x - t, K) * K * K;
+    }
+    const float* pz = phi + wrapk(b.z - tz, K);
+    float px = 0.f, py = 0.f, pzz = 0.f;
+    for (int ty = 0; ty < kOrder; ++ty) {
+      const float wy0 = th[(1 * 2 + 0) * kOrder + ty].x, wy1 = th[(1 * 2 + 1) * kOrder + ty].x;
+      const float* col = pz + wrapk(b.y - ty, K) * K;
+      float s0 = 0.f, s1 = 0.f;
+      for (int tx = 0; tx < kOrder; ++tx) {
+        const float ph = col[gx[tx]];
+        s0 = fmaf(wx0[tx], ph, s0);
+        s1 = fmaf(wx1[tx], ph, s1);
+      }
+      px = fmaf(wy0, s1, px);
+      py = fmaf(wy1, s0, py);
+      pzz = fmaf(wy0, s0, pzz);
+    }
+    ex = wz0 * px;
+    ey = wz0 * py;
+    ez = wz1 * pzz;
+  }
+  const int base = min(seg, kGatherAtomsPerWarp - 1) * kOrder;
+  ex = sum_five32(ex, base);
+  ey = sum_five32(ey, base);
+  ez = sum_five32(ez, base);
+  if (!active) return;
+  double* o = reinterpret_cast<double*>(out + s);
+  if (tz < 3) {
+    const double f = (double)(tz == 0 ? ex : (tz == 1 ? ey : ez));
+    if (kSet)
+      o[tz] = -f;
+    else
+      o[tz] -= f;
+  } else if (kSet && tz == 3) {
+    o[3] = 0.0;
+  }
+}
+
 // gather the field in double-float from phi_hi/phi_lo (split = true: first
 // split the float64 grid potential in grid64 into them)
 template <bool kSet>
@@ -553,22 +683,19 @@ void gather_df(amp_ctx* c, cudaStream_t st, double4_32a* out, bool split) {
 
 int exec_fft(amp_ctx* c, bool fp32, bool forward);
 
-// Spread grid -> phi. The grid is grid64 (float64) or, with fixed = true,
-// gridfx (fixed point, zeroed on the way). The double-float FFT writes phi_df
-// directly when the grid size allows it, else cuFFT float64 leaves phi in
-// grid64 and *split_needed tells the gather to split it first.
-int conv_to_phi(amp_ctx* c, cudaStream_t st, bool* split_needed, bool fixed) {
+// Fixed-point grid gridfx (zeroed on the way) -> phi. The double-float FFT
+// writes phi_df directly when the grid size allows it, else cuFFT float64
+// leaves phi in grid64 and *split_needed tells the gather to split it first.
+int conv_to_phi(amp_ctx* c, cudaStream_t st, bool* split_needed) {
   if (c->fft_grid) {
-    fft_df_convolve(c, st, fixed);
+    fft_df_convolve(c, st);
     *split_needed = false;
     return AMP_OK;
   }
   const long long ng = (long long)c->K * c->K * c->K;
   const long long nh = (long long)c->K * c->K * (c->K / 2 + 1);
-  if (fixed) {
-    c->n_launch += 1;
-    k_fixed_to_double<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->gridfx, c->fx_info, c->grid64, c->op_stop);
-  }
+  c->n_launch += 2;
+  k_fixed_to_double<<<amp_blocks(ng, 256), 256, 0, st>>>(ng, c->gridfx, c->fx_info, c->grid64, c->op_stop);
   cufftSetStream(c->plan_d2z, st);
   cufftSetStream(c->plan_z2d, st);
   int r = exec_fft(c, false, true);
@@ -626,40 +753,42 @@ int exec_fft(amp_ctx* c, bool fp32, bool forward) {
   return AMP_OK;
 }
 
+// Influence function G(m) on the half spectrum for the current box and
+// beta, on the context stream (no host work, no synchronisation):
+//   G(m) = exp(-pi^2 m~^2/beta^2) / (pi V m~^2) |b(m1) b(m2) b(m3)|^2, G(0) = 0,
+// m~ = (m1, m2, m3)/L with m_a in (-K/2, K/2], index ((mx K + my)(K/2+1) + mz);
+// float64, its float copy (mixed path) and its hi/lo split (own FFT).
+__global__ void k_influence(int K, double L, double beta, const double* __restrict__ b2, double* __restrict__ G,
+                            float* __restrict__ G32, float2* __restrict__ Gdf) {
+  const long long nh = (long long)K * K * (K / 2 + 1);
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  const int mz = (int)(k % (K / 2 + 1));
+  const long long t = k / (K / 2 + 1);
+  const int my = (int)(t % K), mx = (int)(t / K);
+  const double fx = (mx <= K / 2 ? mx : mx - K) / L, fy = (my <= K / 2 ? my : my - K) / L, fz = mz / L;
+  const double m2 = fx * fx + fy * fy + fz * fz;
+  double g = 0.0;
+  if (m2 > 0.0)
+    g = exp(-M_PI * M_PI * m2 / (beta * beta)) / (M_PI * L * L * L * m2) * b2[mx] * b2[my] * b2[mz];
+  G[k] = g;
+  if (G32) G32[k] = (float)g;
+  if (Gdf) {
+    const float h = (float)g;
+    Gdf[k] = make_float2(h, (float)(g - (double)h));
+  }
+}
+
 }  // namespace
 
-// Influence function G(m) on the half spectrum for the current box and beta,
-// uploaded on the context stream.
 int pme_influence(amp_ctx* c) {
   const int K = c->K;
   const long long nh = (long long)K * K * (K / 2 + 1);
-  const std::vector<double> b2 = moduli(K);
-  const double L = c->cfg.box, beta = c->cfg.ewald_beta, V = L * L * L;
-  std::vector<double> G(nh);
-  std::vector<float> G32(c->cfg.precision == AMP_MIXED ? nh : 0);
-  for (int mx = 0; mx < K; ++mx)
-    for (int my = 0; my < K; ++my)
-      for (int mz = 0; mz <= K / 2; ++mz) {
-        const double fx = (mx <= K / 2 ? mx : mx - K) / L, fy = (my <= K / 2 ? my : my - K) / L, fz = mz / L;
-        const double m2 = fx * fx + fy * fy + fz * fz;
-        const long long k = ((long long)mx * K + my) * (K / 2 + 1) + mz;
-        double g = 0.0;
-        if (m2 > 0.0) g = std::exp(-M_PI * M_PI * m2 / (beta * beta)) / (M_PI * V * m2) * b2[mx] * b2[my] * b2[mz];
-        G[k] = g;
-        if (!G32.empty()) G32[k] = (float)g;
-      }
-  int r;
-  if ((r = cuda_check(c, cudaMemcpyAsync(c->G64, G.data(), sizeof(double) * nh, cudaMemcpyHostToDevice, c->stream),
-                      "G upload")))
-    return r;
-  if (!G32.empty() && (r = cuda_check(c, cudaMemcpyAsync(c->G32, G32.data(), sizeof(float) * nh,
-                                                         cudaMemcpyHostToDevice, c->stream),
-                                      "G upload")))
-    return r;
-  if ((r = cuda_check(c, cudaStreamSynchronize(c->stream), "G upload"))) return r;
-  // power-of-two grids are transformed by our own double-float FFT
-  if (fft_df_supported(K)) return fft_df_setup(c, G.data());
-  return AMP_OK;
+  c->n_launch += 1;
+  k_influence<<<amp_blocks(nh, 256), 256, 0, c->stream>>>(K, c->cfg.box, c->cfg.ewald_beta, c->bmod, c->G64,
+                                                         c->cfg.precision == AMP_MIXED ? c->G32 : nullptr,
+                                                         c->fft_grid ? c->fft_G : nullptr);
+  return cuda_check(c, cudaGetLastError(), "influence function");
 }
 
 int pme_setup(amp_ctx* c) {
@@ -681,9 +810,28 @@ int pme_setup(amp_ctx* c) {
     return r;
   if (c->cfg.precision == AMP_MIXED) {
     if ((r = dev_alloc(c, &c->grid32, ng)) || (r = dev_alloc(c, &c->cgrid32, nh)) ||
-        (r = dev_alloc(c, &c->G32, nh)))
+        (r = dev_alloc(c, &c->G32, nh)) || (r = dev_alloc(c, &c->spread32, ng)) || (r = dev_alloc(c, &c->phi32, ng)))
+      return r;
+    // the operator's float32 spreading grid starts at zero; the own FFT's
+    // first pass zeroes what it reads, the cuFFT path clears it before use
+    if ((r = cuda_check(c, cudaMemsetAsync(c->spread32, 0, sizeof(float) * ng, c->stream), "grid memset")))
       return r;
   }
+  if (fft_own_supported(K)) {
+    // the permanent field's float64 grids for the own FFT; its first pass
+    // zeroes the spreading grid as it reads it, so it stays zero between uses
+    if ((r = dev_alloc(c, &c->spread64, ng)) || (r = dev_alloc(c, &c->phi64, ng))) return r;
+    if ((r = cuda_check(c, cudaMemsetAsync(c->spread64, 0, sizeof(double) * ng, c->stream), "grid memset")))
+      return r;
+  }
+  {  // B-spline moduli |b(m)|^2 (they depend on K only)
+    const std::vector<double> b2 = moduli(K);
+    if ((r = dev_alloc(c, &c->bmod, K)) ||
+        (r = cuda_check(c, cudaMemcpyAsync(c->bmod, b2.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c->stream),
+                        "moduli upload")))
+      return r;
+  }
+  if (fft_own_supported(K) && (r = fft_own_setup(c))) return r;
   if ((r = pme_influence(c))) return r;
   if (cufftPlan3d(&c->plan_d2z, K, K, K, CUFFT_D2Z) != CUFFT_SUCCESS ||
       cufftPlan3d(&c->plan_z2d, K, K, K, CUFFT_Z2D) != CUFFT_SUCCESS)
@@ -705,64 +853,90 @@ int pme_alloc_atoms(amp_ctx* c, int n_cap) {
   int r;
   if ((r = dev_alloc(c, &c->theta, (long long)kTh * n_cap)) || (r = dev_alloc(c, &c->gbase, n_cap))) return r;
   if (c->cfg.precision == AMP_MIXED && (r = dev_alloc(c, &c->theta32, (long long)kTh * n_cap))) return r;
-  if ((r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap)) ||
-      (r = dev_alloc(c, &c->theta_df2, 3LL * kOrder * n_cap)))
-    return r;
+  if ((r = dev_alloc(c, &c->theta_df, (long long)kThDf * n_cap))) return r;
   return AMP_OK;
 }
 
 // B-spline weights of the current system in double-float (k_theta_df), for
-// the reciprocal parts of both precisions; the float64 copy (and the mixed
-// path's float32 one), which only the force kernels read, are built on demand
-// by pme_theta64.
-void launch_pme_theta(amp_ctx* c) {
+// the dipole products of both precisions, on stream st. The float64 copy
+// (and the mixed path's float32 one), which the permanent field and the
+// force kernels read, come from pme_theta64.
+void launch_pme_theta(amp_ctx* c, cudaStream_t st) {
   c->n_launch += 1;
-  cudaMemsetAsync(c->kcount, 0, sizeof(int) * (long long)c->K * c->K * c->K, c->stream);
-  cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 4, c->stream);
+  cudaMemsetAsync(c->kcount, 0, sizeof(int) * (long long)c->K * c->K * c->K, st);
+  cudaMemsetAsync(c->fx_info, 0, sizeof(int) * 4, st);
   const double sc = (double)c->K / c->cfg.box;
   const float sh = (float)sc;
-  k_theta_df<<<amp_blocks(4LL * c->n, 128), 128, 0, c->stream>>>(
-      c->n, c->atomA, c->atomB, c->atomC, c->atomD, c->cfg.box, c->K, make_float2(sh, (float)(sc - (double)sh)),
-      c->theta_df, c->theta_df2, c->gbase, c->kcount, c->fx_info);
+  k_theta_df<<<amp_blocks(4LL * c->n, 128), 128, 0, st>>>(c->n, c->atomA, c->cfg.box, c->K,
+                                                         make_float2(sh, (float)(sc - (double)sh)), c->theta_df,
+                                                         c->gbase, c->kcount, c->fx_info);
   c->theta64_valid = false;
 }
 
-void pme_theta64(amp_ctx* c) {
+void pme_theta64(amp_ctx* c, cudaStream_t st) {
   if (c->theta64_valid) return;
   c->n_launch += 1;
-  k_theta<<<amp_blocks(c->n, 128), 128, 0, c->stream>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32);
+  k_theta<<<amp_blocks(3LL * c->n, 128), 128, 0, st>>>(c->n, c->atomA, c->cfg.box, c->K, c->theta, c->theta32);
   c->theta64_valid = true;
 }
 
-int pme_permanent_field(amp_ctx* c, double4_32a* out_add) {
-  const int K = c->K, n = c->n;
-  cudaStream_t st = c->stream;
-  c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
-  // double-float, fixed-point grid (zero on entry), as for the dipoles
-  k_spread_multipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
-      n, c->theta_df, c->theta_df2, c->gbase, c->mp_df, c->fx_info, K, c->gridfx);
-  bool split = true;
-  const int r = conv_to_phi(c, st, &split, true);
-  if (r) return r;
-  gather_df<false>(c, st, out_add, split);
-  return AMP_OK;
+// The geometry-dependent reciprocal-space work of a new system, on the side
+// stream so that it runs beside the neighbour search, the pair build and the
+// real-space permanent field of the main stream (it keeps the float64 pipe
+// busy, they the float32 one): the B-spline weights (double-float, float64), then the permanent
+// field's reciprocal part into e0rec. That part is float64 throughout: in a
+// system whose molecules are far apart the excluded intramolecular
+// real-space terms and this part (each ~1e-1 e/A^2) cancel to a field ~1e-4,
+// so both are computed in float64 and meet in float64 (k_intra_fields64 for
+// the excluded terms). Float64 multipole spreading (atomics), cuFFT float64,
+// float64 gather. Every later call waits for it (join_geometry).
+int pme_geometry(amp_ctx* c) {
+  cudaEventRecord(c->ev_fork, c->stream);
+  cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  int r = AMP_OK;
+  {
+    PhaseScope ps(c, AMP_PHASE_E0_RECIP, c->side);
+    launch_pme_theta(c, c->side);
+    pme_theta64(c, c->side);
+    const double* phi = c->grid64;
+    if (c->fft_grid64) {  // power-of-two grid: the own float64 FFT, which zeroes spread64 as it reads it
+      c->n_launch += 1;
+      k_spread_multipoles64<<<amp_blocks((long long)c->n * kOrder * kOrder, 256), 256, 0, c->side>>>(
+          c->n, c->theta, c->gbase, c->atomA, c->atomB, c->atomC, c->atomD, c->K, c->spread64);
+      fft_f64_convolve(c, c->side, c->spread64, c->phi64);
+      phi = c->phi64;
+    } else {
+      r = pme_potential(c, false, true, nullptr, nullptr, c->grid64, c->side);
+    }
+    if (!r) {
+      const long long warps = (c->n + kGatherAtomsPerWarp - 1) / kGatherAtomsPerWarp;
+      c->n_launch += 1;
+      k_gather_field64<<<amp_blocks(warps * 32, kGatherThreads), kGatherThreads, 0, c->side>>>(
+          c->n, c->theta, c->gbase, phi, c->K, c->e0rec);
+    }
+  }
+  cudaEventRecord(c->ev_geom, c->side);
+  c->geom_pending = true;
+  return r;
 }
 
 // Grid potential phi = conv(Q) into grid_out (float64 or float32 grid), Q the
 // spread of the dipoles v (v32 in float32) or of the permanent multipoles.
-int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out) {
+int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out,
+                  cudaStream_t st) {
   const int K = c->K, n = c->n;
   const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
-  cudaStream_t st = c->stream;
   const int blocks = amp_blocks((long long)n * kPmeGroup, 128);
   c->n_launch += 2;
   cufftResult fr;
+  cufftSetStream(fp32 ? c->plan_r2c : c->plan_d2z, st);
+  cufftSetStream(fp32 ? c->plan_c2r : c->plan_z2d, st);
   if (!fp32) {
     double* g = static_cast<double*>(grid_out);
     cudaMemsetAsync(g, 0, sizeof(double) * ng, st);
     if (multipoles)
-      k_spread_multipoles<double><<<blocks, 128, 0, st>>>(n, c->theta, c->gbase, c->atomA, c->atomB, c->atomC,
-                                                          c->atomD, K, g);
+      k_spread_multipoles64<<<amp_blocks((long long)n * kOrder * kOrder, 256), 256, 0, st>>>(
+          n, c->theta, c->gbase, c->atomA, c->atomB, c->atomC, c->atomD, K, g);
     else
       k_spread_dipoles<double, double4_32a><<<blocks, 128, 0, st>>>(n, c->theta, c->gbase, v, K, g);
     fr = cufftExecD2Z(c->plan_d2z, g, reinterpret_cast<cufftDoubleComplex*>(c->cgrid64));
@@ -784,6 +958,8 @@ int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, 
       fr = cufftExecC2R(c->plan_c2r, reinterpret_cast<cufftComplex*>(c->cgrid32), g);
     }
   }
+  cufftSetStream(fp32 ? c->plan_r2c : c->plan_d2z, c->stream);
+  cufftSetStream(fp32 ? c->plan_c2r : c->plan_z2d, c->stream);
   if (fr != CUFFT_SUCCESS) return fail(c, AMP_ERR_CUDA, "cuFFT exec failed (%d)", (int)fr);
   return AMP_OK;
 }
@@ -805,12 +981,54 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
              (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
   if (c->spread_event) cudaEventRecord(c->ev_spread, st);
   bool split = true;
-  const int r = conv_to_phi(c, st, &split, true);
+  const int r = conv_to_phi(c, st, &split);
   if (r) return r;
   if (set)
     gather_df<true>(c, st, out, split);
   else
     gather_df<false>(c, st, out, split);
+  return AMP_OK;
+}
+
+// Reciprocal field of the float32 dipoles v32 in float32 (the mixed path's
+// operator; its float64 residual check takes the double-float chain): float
+// atomics into spread32, the own float32 FFT on power-of-two grids up to 64
+// (which zeroes spread32 as it reads it), else cuFFT R2C / C2R float32 with
+// spread32 cleared first, then the float32 gather; out (+)= -grad phi.
+int pme_dipole_field32(amp_ctx* c, const float4* v32, double4_32a* out, cudaStream_t st, bool set) {
+  const int K = c->K, n = c->n;
+  const long long ng = (long long)K * K * K, nh = (long long)K * K * (K / 2 + 1);
+  const bool own = c->fft_grid32 != nullptr;
+  int r = AMP_OK;
+  if (!own) cudaMemsetAsync(c->spread32, 0, sizeof(float) * ng, st);
+  c->n_launch += 2;
+  launch_pdl(k_spread_dipoles32, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
+             dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, K, c->spread32, c->op_stop);
+  if (c->spread_event) cudaEventRecord(c->ev_spread, st);
+  if (own) {
+    fft_f32_convolve(c, st);
+  } else {
+    c->n_launch += 1;
+    cufftSetStream(c->plan_r2c, st);
+    cufftSetStream(c->plan_c2r, st);
+    cufftResult fr = cufftExecR2C(c->plan_r2c, c->spread32, reinterpret_cast<cufftComplex*>(c->cgrid32));
+    if (fr == CUFFT_SUCCESS) {
+      k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32, c->op_stop);
+      fr = cufftExecC2R(c->plan_c2r, reinterpret_cast<cufftComplex*>(c->cgrid32), c->phi32);
+    }
+    cufftSetStream(c->plan_r2c, c->stream);
+    cufftSetStream(c->plan_c2r, c->stream);
+    if (fr != CUFFT_SUCCESS) r = fail(c, AMP_ERR_CUDA, "cuFFT exec failed (%d)", (int)fr);
+  }
+  if (r) return r;
+  const long long warps = (n + kGatherAtomsPerWarp - 1) / kGatherAtomsPerWarp;
+  const dim3 grid(amp_blocks(warps * 32, kGatherThreads));
+  if (set)
+    launch_pdl(k_gather_field32<true>, grid, dim3(kGatherThreads), 0, st, n, c->theta_df, c->gbase, c->phi32, K, out,
+               c->op_stop);
+  else
+    launch_pdl(k_gather_field32<false>, grid, dim3(kGatherThreads), 0, st, n, c->theta_df, c->gbase, c->phi32, K,
+               out, c->op_stop);
   return AMP_OK;
 }
 

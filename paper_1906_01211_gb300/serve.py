@@ -1,39 +1,33 @@
 """Continuous-batching server for polarization solves of uneven sizes.
 
+A thin binding of the native server in libamoebapol (amp_server_* in
+include/amoebapol.h): argument marshalling only. The scheduling, admission
+by memory, the context pool, the batched engine for small clusters
+(persistent kernels over a device work queue, per-request PCG state on the
+device) and the worker streams all run in the library.
+
 Requests (isolated clusters or small periodic boxes, any size) arrive at any
-time. The server keeps ``n_slots`` workers, each bound to its own CUDA stream
-and owning reusable solver contexts (one per PME grid size, plus one for
-clusters). A request is admitted as soon as a slot is free AND its estimated
-device memory fits into the budget next to the requests already running, so
-new requests join while others are still iterating and their kernels overlap
-on the device (one stream per running request). Per request the whole path
-runs in the CUDA library: neighbour lists (periodic) or all-pairs tiles
-(clusters), permanent field, PCG solve, energy.
+time; each is admitted as soon as memory and a place free up and runs beside
+the requests already in flight. Small clusters without a key share the
+batched engine; the other requests run on worker streams through the
+single-system calls, on contexts pooled by PME grid size. Dipoles of keyed
+requests stay on the device and warm-start the next solve of that key.
+Failures stay per request (invalid input, a request larger than the memory
+budget); the server and the other requests go on.
 
-State kept on the device between requests:
-  * every slot context keeps its buffers, neighbour lists and cuFFT plans, so
-    a request of the same grid size reuses them (no allocation);
-  * the last converged dipoles of each request ``key`` (byte budget, least
-    recently used evicted) warm-start the next solve of that key.
-
-Failures stay per request: an invalid input, a request larger than the whole
-memory budget or a cancelled request gets an error result; the other requests
-and the slots continue. A worker that dies is reported by ``health()``.
-
-Host-side scheduling only; the paper has no serving counterpart (its
-throughput runs are many MPI ranks on one system).
+The paper has no serving counterpart (its throughput runs are many MPI ranks
+on one system, Section "Parallel performance").
 """
 from __future__ import annotations
 
-import collections
 import math
-import threading
-import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
-from .synth import System, small_box_settings
+from .synth import System
+
+PATHS = ("batched", "worker")
 
 
 @dataclass
@@ -48,266 +42,92 @@ class Result:
     t_submit: float = 0.0
     t_start: float = 0.0
     t_done: float = 0.0
-    slot: int = -1
+    path: str = ""
     warm_start: bool = False
 
     @property
     def latency(self) -> float:
         return self.t_done - self.t_submit
 
-
-@dataclass
-class _Req:
-    rid: int
-    system: System
-    key: str | None
-    est_bytes: int
-    t_submit: float
-    done: threading.Event = field(default_factory=threading.Event)
-    result: Result | None = None
-
-
-def box_settings(L: float):
-    """Cutoff, beta and grid of a periodic request box (capped cutoff below L/2)."""
-    return small_box_settings(L)
-
-
-def estimate_bytes(system: System, precision: str) -> int:
-    """Device memory one request needs beyond the reusable context buffers."""
-    n = system.n
-    per_atom = 1200
-    if system.box is None:
-        return n * per_atom + 16 * 32 * n
-    rc, beta, K = box_settings(system.box)
-    density = n / system.box ** 3
-    half = int(n * 2.0 * math.pi / 3.0 * rc ** 3 * density) + 1024
-    per_pair = 16 + 48 + (48 if precision == "mixed" else 96) + 24
-    grid = K ** 3 * (8 + 8 + 4 + 4) + K * K * (K // 2 + 1) * (16 + 8 + 8 + 4)
-    return n * per_atom + half * per_pair + grid
-
-
-class _Slot:
-    def __init__(self, server: "Server", index: int):
-        self.server = server
-        self.index = index
-        self.stream = server._create_stream()
-        self.periodic = {}  # K -> Polarization
-        self.cluster = None
-        self.alive = True
-        self.thread = threading.Thread(target=self._run, name=f"amp-slot-{index}", daemon=True)
-
-    def solver_for(self, system: System):
-        from .amoebapol import Config, Polarization
-        srv = self.server
-        if system.box is None:
-            cfg = Config(box=0.0, tol_debye=srv.tol, max_iter=srv.max_iter, precision=srv.precision)
-            if self.cluster is None:
-                self.cluster = Polarization(cfg, self.stream)
-            return self.cluster
-        rc, beta, K = box_settings(system.box)
-        cfg = Config(box=system.box, cutoff=rc, ewald_beta=beta, pme_grid=K, tol_debye=srv.tol,
-                     max_iter=srv.max_iter, precision=srv.precision)
-        p = self.periodic.get(K)
-        if p is None:
-            p = Polarization(cfg, self.stream)
-            self.periodic[K] = p
-        else:
-            p.reconfigure(cfg)
-        return p
-
-    def _run(self):
-        srv = self.server
-        srv._bind_thread()
-        req = None
-        try:
-            while True:
-                req = srv._next(self)
-                if req is None:
-                    return
-                res = Result(rid=req.rid, ok=False, t_submit=req.t_submit, t_start=time.perf_counter(),
-                             slot=self.index)
-                try:
-                    srv._execute(self, req, res)
-                    res.ok = True
-                except Exception as exc:  # noqa: BLE001 - reported per request
-                    res.error = f"{type(exc).__name__}: {exc}"
-                res.t_done = time.perf_counter()
-                srv._finish(req, res)
-                req = None
-        except BaseException as exc:
-            # the worker is gone: fail its request, release its memory, let the
-            # other slots carry on; health() reports the dead slot
-            self.alive = False
-            if req is not None:
-                srv._finish(req, Result(req.rid, False, error=f"worker died: {type(exc).__name__}",
-                                        t_submit=req.t_submit, t_done=time.perf_counter(), slot=self.index))
+    @property
+    def service(self) -> float:
+        return self.t_done - self.t_start
 
 
 class Server:
-    """Continuous batching of polarization solves on one GPU (see module doc)."""
+    """The native server (see the module doc). precision "mixed" or "fp64";
+    clusters of at most batch_max_atoms atoms use the batched engine
+    (0 disables it); n_workers worker streams take the other requests."""
 
-    def __init__(self, n_slots: int = 4, mem_budget_bytes: int = 8 << 30, precision: str = "mixed",
-                 tol_debye: float = 1e-5, max_iter: int = 100, device: int = 0,
+    def __init__(self, n_workers: int = 4, mem_budget_bytes: int = 16 << 30, precision: str = "mixed",
+                 tol_debye: float = 1e-5, max_iter: int = 100, device: int = 0, batch_max_atoms: int = 3072,
+                 batch_arena_atoms: int = 1 << 19, batch_max_requests: int = 1024,
                  resident_budget_bytes: int = 256 << 20):
-        self.device = device
-        self._bind_thread()
-        self.precision = precision
-        self.tol = tol_debye
-        self.max_iter = max_iter
-        self.budget = int(mem_budget_bytes)
-        self.resident_budget = int(resident_budget_bytes)
-        self._cv = threading.Condition()
-        self._queue: collections.deque[_Req] = collections.deque()
-        self._reqs: dict[int, _Req] = {}
-        self._in_use = 0
-        self._running = 0
-        self._next_id = 0
-        self._closing = False
-        self._done = 0
-        self._failed = 0
-        self._resident: collections.OrderedDict[str, object] = collections.OrderedDict()
-        self._resident_bytes = 0
-        self._slots = [_Slot(self, k) for k in range(n_slots)]
-        for s in self._slots:
-            s.thread.start()
+        from . import amoebapol as ap
+        self._ap = ap
+        cfg = ap.amp_server_config(n_workers=int(n_workers), mem_budget_bytes=int(mem_budget_bytes),
+                                   precision=ap.AMP_MIXED if precision == "mixed" else ap.AMP_FP64,
+                                   tol_debye=float(tol_debye), max_iter=int(max_iter),
+                                   batch_max_atoms=int(batch_max_atoms),
+                                   batch_arena_atoms=int(max(batch_arena_atoms, batch_max_atoms)),
+                                   batch_max_requests=int(batch_max_requests),
+                                   resident_bytes=int(resident_budget_bytes))
+        self._h = ap.amp_server_create(cfg, device)
+        self._n = {}
 
-    # ---------------------------------------------------------------- client side
-    def submit(self, system: System, key: str | None = None) -> int:
-        est = estimate_bytes(system, self.precision)
-        with self._cv:
-            if self._closing:
-                raise RuntimeError("server is closed")
-            rid = self._next_id
-            self._next_id += 1
-            req = _Req(rid, system, key, est, time.perf_counter())
-            self._reqs[rid] = req
-            if est > self.budget:
-                self._finish_locked(req, Result(rid, False, error="request exceeds the memory budget",
-                                                t_submit=req.t_submit, t_done=req.t_submit))
-            else:
-                self._queue.append(req)
-                self._cv.notify_all()
+    def submit(self, system: System, key: str | None = None, cutoff: float = 0.0, beta: float = 0.0,
+               grid: int = 0) -> int:
+        """Queue one request; its host arrays are copied before this returns."""
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        box = 0.0 if system.box is None else float(system.box)
+        rid = self._ap.amp_server_submit(self._h, system.n, box, cutoff, beta, grid, f64(system.xyz), f64(system.q),
+                                         f64(system.dip), f64(system.quad), f64(system.alpha), f64(system.thole),
+                                         np.ascontiguousarray(system.mol, dtype=np.int32), key)
+        self._n[rid] = system.n
         return rid
 
+    def _result(self, rid: int, code: int, mu: np.ndarray, rec) -> Result:
+        ap = self._ap
+        self._n.pop(rid, None)
+        ok = code == ap.AMP_OK
+        return Result(rid=rid, ok=ok, error=None if ok else (rec.error.decode() or f"error {code}"),
+                      mu=mu if ok else None, energy=rec.energy, iters=rec.iters, rms_debye=rec.rms_debye,
+                      t_submit=rec.t_submit, t_start=rec.t_start, t_done=rec.t_done,
+                      path=PATHS[rec.path] if rec.path in (0, 1) else "", warm_start=bool(rec.warm_start))
+
     def result(self, rid: int, timeout: float | None = None) -> Result:
-        req = self._reqs[rid]
-        if not req.done.wait(timeout):
+        """Wait for a request (without limit, or up to timeout seconds)."""
+        ap = self._ap
+        mu = np.zeros((self._n[rid], 3))
+        rec = ap.amp_server_result()
+        code = ap.amp_server_wait(self._h, rid, -1.0 if timeout is None else float(timeout), mu.ctypes.data, rec)
+        if code == ap.AMP_PENDING:
             raise TimeoutError(f"request {rid} not finished")
-        return req.result
+        return self._result(rid, code, mu, rec)
 
     def poll(self, rid: int) -> Result | None:
-        req = self._reqs[rid]
-        return req.result if req.done.is_set() else None
-
-    def cancel(self, rid: int) -> bool:
-        """Cancel a request that has not started; returns False once it runs."""
-        with self._cv:
-            req = self._reqs[rid]
-            if req in self._queue:
-                self._queue.remove(req)
-                self._finish_locked(req, Result(rid, False, error="cancelled", t_submit=req.t_submit,
-                                                t_done=time.perf_counter()))
-                return True
-            return False
+        ap = self._ap
+        mu = np.zeros((self._n[rid], 3))
+        rec = ap.amp_server_result()
+        code = ap.amp_server_poll(self._h, rid, mu.ctypes.data, rec)
+        if code == ap.AMP_PENDING:
+            return None
+        return self._result(rid, code, mu, rec)
 
     def stats(self) -> dict:
-        with self._cv:
-            return {"queued": len(self._queue), "running": self._running, "done": self._done,
-                    "failed": self._failed, "bytes_in_use": self._in_use, "budget": self.budget,
-                    "resident_keys": len(self._resident), "resident_bytes": self._resident_bytes}
-
-    def health(self) -> dict:
-        return {f"slot{s.index}": s.alive and s.thread.is_alive() for s in self._slots}
+        c = self._ap.amp_server_stats(self._h)
+        return {name: getattr(c, name) for name, _ in c._fields_}
 
     def close(self):
-        with self._cv:
-            self._closing = True
-            self._cv.notify_all()
-        for s in self._slots:
-            s.thread.join()
-        for s in self._slots:
-            for p in list(s.periodic.values()) + ([s.cluster] if s.cluster else []):
-                p.close()
-        self._resident.clear()
+        if self._h is not None:
+            self._ap.amp_server_destroy(self._h)
+            self._h = None
 
-    # ---------------------------------------------------------------- device side
-    def _create_stream(self):
-        import torch
-        return torch.cuda.Stream(device=self.device)
+    def __enter__(self):
+        return self
 
-    def _bind_thread(self):
-        import torch
-        torch.cuda.set_device(self.device)
-
-    def _execute(self, slot: _Slot, req: _Req, res: Result):
-        """Run one request on the slot's stream: lists/tiles, E0, PCG, energy."""
-        import torch
-        with torch.cuda.stream(slot.stream):
-            p = slot.solver_for(req.system)
-            p.set_synthetic(req.system)
-            E0 = p.permanent_field()
-            guess = self._resident_get(req.key, req.system.n)
-            mu, it, rms = p.solve(E0, mu=guess)
-            U = p.energy(mu, E0)
-            self._resident_put(req.key, mu)
-            res.mu = mu.cpu().numpy()
-        res.energy, res.iters, res.rms_debye = U, it, rms
-        res.warm_start = guess is not None
-
-    # ---------------------------------------------------------------- slot side
-    def _next(self, slot: _Slot):
-        with self._cv:
-            while True:
-                if self._queue:
-                    head = self._queue[0]
-                    if self._in_use + head.est_bytes <= self.budget or self._running == 0:
-                        self._queue.popleft()
-                        self._in_use += head.est_bytes
-                        self._running += 1
-                        return head
-                elif self._closing:
-                    return None
-                self._cv.wait()
-
-    def _finish(self, req: _Req, res: Result):
-        with self._cv:
-            self._in_use -= req.est_bytes
-            self._running -= 1
-            self._finish_locked(req, res)
-            self._cv.notify_all()
-
-    def _finish_locked(self, req: _Req, res: Result):
-        req.result = res
-        if res.ok:
-            self._done += 1
-        else:
-            self._failed += 1
-        req.done.set()
-
-    def _resident_get(self, key, n):
-        if key is None:
-            return None
-        with self._cv:
-            mu = self._resident.get(key)
-            if mu is None or mu.shape[0] != n:
-                return None
-            self._resident.move_to_end(key)
-            return mu.clone()
-
-    def _resident_put(self, key, mu):
-        if key is None:
-            return
-        nbytes = mu.numel() * mu.element_size()
-        with self._cv:
-            old = self._resident.pop(key, None)
-            if old is not None:
-                self._resident_bytes -= old.numel() * old.element_size()
-            while self._resident and self._resident_bytes + nbytes > self.resident_budget:
-                _, ev = self._resident.popitem(last=False)
-                self._resident_bytes -= ev.numel() * ev.element_size()
-            if nbytes <= self.resident_budget:
-                self._resident[key] = mu.detach().clone()
-                self._resident_bytes += nbytes
+    def __exit__(self, *exc):
+        self.close()
 
 
 def request_stream(n_requests: int, seed: int = 4, min_waters: int = 64, max_waters: int = 4096):

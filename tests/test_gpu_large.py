@@ -1,13 +1,26 @@
 """The 96,000-atom periodic box (32,000 waters, L = 98.65 A, K = 100) at full
-size, float64 and mixed, against the oracle on what it can compute at this
-size: the exact pair count, the real-space parts at sampled sites by the
-oracle's direct scan, the reciprocal parts in full (oracle PME on the same
-grid), and for the solve, the float64 residual at sampled sites (a property
-that holds at any size) plus mixed vs float64 on the GPU.
+size, float64 and mixed, against the oracle:
 
-Tolerances as for the smaller boxes: float64 fields 1e-12 relative, mixed
-dipoles within 1e-5 D RMS of float64, energy 1e-6 relative.
+* the exact pair count (the oracle's brute-force periodic pair set);
+* E0 in full against the oracle's E0 stored by
+  tests/golden/make_water96000_golden.py (which calls only oracle/), and the
+  real-space parts at sampled sites by the oracle's direct scan;
+* T*v at sampled sites (real space by direct scan, reciprocal part in full);
+* the float64 solve run to 1e-8 D against the oracle's dipoles converged to
+  1e-8 D (stored);
+* the mixed solve run to the box's tolerance, 1e-5 D, against the oracle run
+  to the same tolerance (stored): both stop on a residual of that size, and
+  the energy -C mu.E0/2 carries a first-order error of the same order, so
+  holding a 1e-5 D solve to a 1e-8 D reference would measure the tolerance,
+  not the arithmetic; its error against the 1e-8 D oracle is printed.
+
+Tolerances as for the smaller boxes: float64 fields 1e-12 relative, float64
+dipoles 1e-8 D RMS, energy 1e-10; mixed dipoles within 1e-5 D RMS of the
+float64 oracle (5x that per atom), energy 1e-6 relative. Every norm check has
+a per-atom check beside it (tests/parity_metrics.py).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -15,16 +28,14 @@ from oracle import Setup
 from oracle.pairs import periodic_pairs
 from oracle.pme import PmeGrid, dipole_field_recip, permanent_field_recip, self_field
 from oracle.realspace import dipole_field_real_rows, permanent_field_real_rows
-from oracle.setup import DEBYE
 from paper_1906_01211_gb300.synth import WATER_96000
+from tests.parity_metrics import assert_dipoles, assert_fields, rms_debye
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "water96000_oracle.npz")
 
 
 @pytest.fixture(scope="module")
@@ -34,13 +45,15 @@ def big():
     setup = Setup(box=w.L, cutoff=w.cutoff, beta=w.beta, grid=w.grid, order=5)
     grid = PmeGrid(sysm.xyz, setup.box, setup.grid, setup.order, setup.beta)
     rows = np.random.default_rng(96).choice(sysm.n, 48, replace=False)
-    return w, sysm, setup, grid, rows
+    gold = np.load(GOLDEN)
+    assert str(gold["workload"]) == w.name
+    return w, sysm, setup, grid, rows, gold
 
 
-def solver(w, precision):
+def solver(w, precision, tol):
     from paper_1906_01211_gb300 import amoebapol as ap
     return ap.Polarization(ap.Config(box=w.L, cutoff=w.cutoff, ewald_beta=w.beta, pme_grid=w.grid,
-                                     tol_debye=w.tol_debye, precision=precision))
+                                     tol_debye=tol, precision=precision))
 
 
 def oracle_T_rows(sysm, setup, grid, v, rows):
@@ -49,39 +62,45 @@ def oracle_T_rows(sysm, setup, grid, v, rows):
 
 
 def test_96000_pair_count_and_fields(big):
-    w, sysm, setup, grid, rows = big
-    s = solver(w, "fp64")
+    w, sysm, setup, grid, rows, gold = big
+    s = solver(w, "fp64", w.tol_debye)
     s.set_synthetic(sysm)
     i, _, _ = periodic_pairs(sysm.xyz, w.L, w.cutoff)
-    assert s.pair_count() == len(i)
+    assert s.pair_count() == len(i) == int(gold["n_pairs"])
     E0 = s.permanent_field().cpu().numpy()
+    assert_fields(E0, gold["E0"], 1e-12)
     ref = (permanent_field_real_rows(sysm, setup, rows) + permanent_field_recip(sysm, setup, grid)[rows]
            + self_field(setup, sysm.dip)[rows])
-    assert rel(E0[rows], ref) < 1e-12
+    assert_fields(E0[rows], ref, 1e-12)
     v = np.random.default_rng(7).normal(size=(sysm.n, 3)) * 0.1
     t = s.apply_T(torch.tensor(v)).cpu().numpy()
-    assert rel(t[rows], oracle_T_rows(sysm, setup, grid, v, rows)) < 1e-12
+    assert_fields(t[rows], oracle_T_rows(sysm, setup, grid, v, rows), 1e-12)
 
 
-def test_96000_solve_residual_and_mixed(big):
-    w, sysm, setup, grid, rows = big
-    s = solver(w, "fp64")
+def test_96000_fp64_solve_matches_oracle(big):
+    w, sysm, setup, grid, rows, gold = big
+    s = solver(w, "fp64", float(gold["tol_debye"]))
     s.set_synthetic(sysm)
     E0 = s.permanent_field()
     mu, it, rms = s.solve(E0)
     U = s.energy(mu, E0)
-    assert rms < w.tol_debye
-    mu_np, E0_np = mu.cpu().numpy(), E0.cpu().numpy()
-    # z = alpha (E0 - mu/alpha + T mu) at sampled sites, T mu by the oracle
-    Tmu = oracle_T_rows(sysm, setup, grid, mu_np, rows)
-    alpha = sysm.alpha[rows, None]
-    z = alpha * (E0_np[rows] - mu_np[rows] / alpha + Tmu)
-    assert DEBYE * np.sqrt((z * z).sum() / len(rows)) < 3 * w.tol_debye
-    m = solver(w, "mixed")
+    assert rms < float(gold["tol_debye"])
+    assert it == int(gold["iters"])
+    assert_dipoles(mu.cpu().numpy(), gold["mu"], 1e-8)
+    assert abs(U / float(gold["U"]) - 1) < 1e-10
+
+
+def test_96000_mixed_matches_oracle(big):
+    w, sysm, setup, grid, rows, gold = big
+    m = solver(w, "mixed", w.tol_debye)
     m.set_synthetic(sysm)
-    E0m = m.permanent_field()
-    mum, _, rmsm = m.solve(E0m)
-    Um = m.energy(mum, E0m)
-    d = mum.cpu().numpy() - mu_np
-    assert DEBYE * np.sqrt((d * d).sum() / sysm.n) < 1e-5
-    assert abs(Um / U - 1) < 1e-6
+    E0 = m.permanent_field()
+    mu, it, rms = m.solve(E0)
+    U = m.energy(mu, E0)
+    assert rms < w.tol_debye
+    assert float(gold["tol_box"]) == w.tol_debye
+    err = rms_debye(mu.cpu().numpy(), gold["mu"])
+    print(f"water-96000 mixed: {it} iterations (oracle {int(gold['iters_tol'])}), mu - converged oracle mu "
+          f"{err:.3e} D RMS, U {U!r} (oracle at 1e-5 D {float(gold['U_tol'])!r}, at 1e-8 D {float(gold['U'])!r})")
+    assert_dipoles(mu.cpu().numpy(), gold["mu_tol"], 1e-5, 5.0)
+    assert abs(U / float(gold["U_tol"]) - 1) < 1e-6

@@ -4,6 +4,11 @@ Tolerances (float64 path): permanent field and T*mu to 1e-12 relative
 (2-norm of the difference over the 2-norm of the oracle vector), induced
 dipoles to 1e-8 Debye RMS, energy to 1e-10 relative. Mixed path: dipoles
 within 1e-5 Debye RMS of the float64 oracle, energy within 1e-6 relative.
+Beside every norm check, a per-atom one (tests/parity_metrics.py): the
+largest per-atom field error within the same tolerance relative to the
+largest per-atom field, the largest per-atom dipole error within the RMS
+tolerance (float64) or 5x it (mixed: its dipoles are converged to 1e-5 D
+RMS, so single atoms may sit a few times above that).
 """
 import numpy as np
 import pytest
@@ -11,23 +16,14 @@ import pytest
 from oracle import Setup
 from oracle.energy import polarization_energy
 from oracle.realspace import dipole_field_real_rows, permanent_field_real_rows
-from oracle.setup import DEBYE
 from oracle.solver import Operator, solve
 from paper_1906_01211_gb300.synth import (WATER_648, WATER_23556, density_box_edge, make_waters,
                                           small_box_settings)
+from tests.parity_metrics import assert_dipoles, assert_fields, rel
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
-
-
-def rms_debye(a, b):
-    d = np.asarray(a) - np.asarray(b)
-    return float(DEBYE * np.sqrt((d * d).sum() / d.shape[0]))
 
 
 def make_solver(L, rc, beta, K, tol, precision="fp64", max_iter=100):
@@ -77,7 +73,7 @@ def test_pair_count_matches_oracle(w648):
 
 def test_fp64_permanent_field_648(w648):
     s, E0, _, _, _, _ = run_gpu(w648)
-    assert rel(E0, w648.E0) < 1e-12
+    assert_fields(E0, w648.E0, 1e-12)
 
 
 def test_fp64_apply_T_648(w648):
@@ -87,14 +83,14 @@ def test_fp64_apply_T_648(w648):
     for _ in range(2):
         mu = rng.normal(size=(w648.sys.n, 3)) * 0.1
         t = s.apply_T(torch.tensor(mu)).cpu().numpy()
-        assert rel(t, w648.op.apply_T(mu)) < 1e-12
+        assert_fields(t, w648.op.apply_T(mu), 1e-12)
 
 
 def test_fp64_solve_and_energy_648(w648):
     s, E0, mu, it, rms, U = run_gpu(w648)
     assert rms < w648.tol
     assert it == w648.iters
-    assert rms_debye(mu, w648.mu) < 1e-8
+    assert_dipoles(mu, w648.mu, 1e-8)
     assert abs(U / w648.U - 1) < 1e-10
 
 
@@ -108,26 +104,26 @@ def test_fp64_reruns_agree(w648):
 def test_mixed_648_within_tolerance_of_fp64_oracle(w648):
     s, E0, mu, it, rms, U = run_gpu(w648, "mixed")
     assert rms < w648.tol
-    assert rms_debye(mu, w648.mu) < 1e-5
+    assert_dipoles(mu, w648.mu, 1e-5, 5.0)
     assert abs(U / w648.U - 1) < 1e-6
 
 
 def test_fp64_23556_full_vectors(w23556):
     s, E0, mu, it, rms, U = run_gpu(w23556)
     assert s.pair_count() == w23556.op.n_pairs
-    assert rel(E0, w23556.E0) < 1e-12
+    assert_fields(E0, w23556.E0, 1e-12)
     rng = np.random.default_rng(3)
     v = rng.normal(size=(w23556.sys.n, 3)) * 0.1
     t = s.apply_T(torch.tensor(v)).cpu().numpy()
-    assert rel(t, w23556.op.apply_T(v)) < 1e-12
+    assert_fields(t, w23556.op.apply_T(v), 1e-12)
     assert it == w23556.iters
-    assert rms_debye(mu, w23556.mu) < 1e-8
+    assert_dipoles(mu, w23556.mu, 1e-8)
     assert abs(U / w23556.U - 1) < 1e-10
 
 
 def test_mixed_23556(w23556):
     s, E0, mu, it, rms, U = run_gpu(w23556, "mixed")
-    assert rms_debye(mu, w23556.mu) < 1e-5
+    assert_dipoles(mu, w23556.mu, 1e-5, 5.0)
     assert abs(U / w23556.U - 1) < 1e-6
 
 
@@ -138,8 +134,8 @@ def test_small_boxes_ragged_sizes(nw, seed):
     rc, beta, K = small_box_settings(L)
     case = Case(make_waters(nw, L, seed), L, rc, beta, K, 1e-10)
     s, E0, mu, it, rms, U = run_gpu(case)
-    assert rel(E0, case.E0) < 1e-12
-    assert rms_debye(mu, case.mu) < 1e-8
+    assert_fields(E0, case.E0, 1e-12)
+    assert_dipoles(mu, case.mu, 1e-8)
     assert abs(U / case.U - 1) < 1e-10
 
 
@@ -151,10 +147,10 @@ def test_power_of_two_grids(nw, K):
     rc, beta, _ = small_box_settings(L)
     case = Case(make_waters(nw, L, 40 + K), L, rc, beta, K, 1e-10)
     s, E0, mu, it, rms, U = run_gpu(case)
-    assert rel(E0, case.E0) < 1e-12
+    assert_fields(E0, case.E0, 1e-12)
     v = np.random.default_rng(K).normal(size=(case.sys.n, 3)) * 0.1
-    assert rel(s.apply_T(torch.tensor(v)).cpu().numpy(), case.op.apply_T(v)) < 1e-12
-    assert rms_debye(mu, case.mu) < 1e-8
+    assert_fields(s.apply_T(torch.tensor(v)).cpu().numpy(), case.op.apply_T(v), 1e-12)
+    assert_dipoles(mu, case.mu, 1e-8)
 
 
 def test_isolated_atoms_have_empty_rows():
@@ -169,13 +165,11 @@ def test_isolated_atoms_have_empty_rows():
     case = Case(sysm, 40.0, 7.0, 0.5446, 40, 1e-10)
     s, E0, mu, it, rms, U = run_gpu(case)
     assert s.pair_count() == case.op.n_pairs == 6
-    # Here E0 (~1e-4) is what is left after the excluded intramolecular
-    # real-space terms and the reciprocal terms (~1e-1) cancel; the float64
-    # path's double-float kernels (~48 bits) are held to 1e-12 of those parts.
-    parts = case.op.permanent_field_parts()
-    scale = sum(np.linalg.norm(p) for p in parts)
-    assert np.linalg.norm(E0 - case.E0) < 1e-12 * scale
-    assert rms_debye(mu, case.mu) < 1e-8
+    # E0 (~1e-4) is what is left after the excluded intramolecular real-space
+    # terms and the reciprocal terms (~4e-2) cancel: both are float64 on the
+    # GPU, so E0 itself is held to 1e-12 relative.
+    assert_fields(E0, case.E0, 1e-12)
+    assert_dipoles(mu, case.mu, 1e-8)
 
 
 def test_sampled_rows_match_direct_scan(w23556):
@@ -188,9 +182,9 @@ def test_sampled_rows_match_direct_scan(w23556):
     rec_self = w23556.op.permanent_field_parts()
     real_gpu = E0 - rec_self[1] - rec_self[2]
     ref = permanent_field_real_rows(w23556.sys, w23556.setup, rows)
-    assert rel(real_gpu[rows], ref) < 1e-12
+    assert_fields(real_gpu[rows], ref, 1e-12)
     v = rng.normal(size=(w23556.sys.n, 3)) * 0.1
     t = s.apply_T(torch.tensor(v)).cpu().numpy()
     parts = w23556.op.apply_T_parts(v)
     ref_t = dipole_field_real_rows(w23556.sys, w23556.setup, v, rows)
-    assert rel((t - parts[1] - parts[2])[rows], ref_t) < 1e-12
+    assert_fields((t - parts[1] - parts[2])[rows], ref_t, 1e-12)

@@ -1,119 +1,77 @@
-"""Host-side scheduling of the serving layer, without a GPU.
-
-The device hooks of Server are replaced by fakes that sleep and record how
-many requests run at once; failures are injected on the host (a request that
-raises, a worker that dies), never on a GPU.
-"""
-import threading
-import time
+"""Serving layer on the host, without a GPU: the binding's structures against
+the header, the server's argument checks (which run before any CUDA call),
+and the seeded request stream. The server itself runs on the GPU
+(tests/test_gpu_serving.py); failures there are made on the host (invalid
+requests, a request larger than the budget), never on a GPU."""
+import ctypes
+import re
 
 import numpy as np
 import pytest
 
-from paper_1906_01211_gb300.serve import Server, estimate_bytes, percentile, request_stream
-from paper_1906_01211_gb300.synth import make_waters
+from paper_1906_01211_gb300.serve import percentile, request_stream
 
 
-class FakeServer(Server):
-    def __init__(self, *a, work_s=0.02, **kw):
-        self.work_s = work_s
-        self.lock = threading.Lock()
-        self.now_running = 0
-        self.max_running = 0
-        self.order = []
-        super().__init__(*a, **kw)
-
-    def _create_stream(self):
-        return None
-
-    def _bind_thread(self):
-        pass
-
-    def _execute(self, slot, req, res):
-        if req.system.alpha.min() <= 0:
-            raise ValueError("alpha must be > 0 for every site")
-        if req.key == "kill-worker":
-            raise SystemExit("injected worker death")
-        with self.lock:
-            self.now_running += 1
-            self.max_running = max(self.max_running, self.now_running)
-            self.order.append(req.rid)
-        time.sleep(self.work_s)
-        with self.lock:
-            self.now_running -= 1
-        res.energy = float(req.system.n)
+def header_struct_fields(name):
+    from paper_1906_01211_gb300.amoebapol import HEADER_PATH
+    text = open(HEADER_PATH).read()
+    structs = {nm: body for body, nm in re.findall(r"typedef struct \{([^}]*)\}\s*(\w+);", text)}
+    assert name in structs, name
+    body = re.sub(r"/\*.*?\*/", "", structs[name], flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = re.match(r"((?:const\s+)?(?:long long|unsigned|int|double|char))\s+(.*)", decl).groups()
+        for nm in names.split(","):
+            nm = nm.strip()
+            arr = re.match(r"(\w+)\[(\d+)\]", nm)
+            fields.append((arr.group(1), ctype, int(arr.group(2))) if arr else (nm, ctype, 1))
+    return fields
 
 
-def small(nw=8, seed=0, periodic=True):
-    return make_waters(nw, 10.0 if periodic else 8.0, seed, periodic=periodic)
+CTYPES = {"int": ctypes.c_int, "long long": ctypes.c_longlong, "double": ctypes.c_double, "char": ctypes.c_char}
 
 
-def test_all_requests_complete_and_overlap():
-    srv = FakeServer(n_slots=4, mem_budget_bytes=1 << 40)
-    ids = [srv.submit(small(seed=k)) for k in range(16)]
-    res = [srv.result(i, timeout=10) for i in ids]
-    assert all(r.ok for r in res)
-    assert srv.max_running > 1  # requests ran concurrently
-    assert srv.stats()["done"] == 16
-    srv.close()
+@pytest.mark.parametrize("name", ["amp_server_config", "amp_server_result", "amp_server_counters"])
+def test_binding_structs_match_header(name):
+    from paper_1906_01211_gb300 import amoebapol as ap
+    cls = getattr(ap, name)
+    want = header_struct_fields(name)
+    got = cls._fields_
+    assert [f[0] for f in got] == [w[0] for w in want]
+    for (fname, ftype), (_, ctype, count) in zip(got, want):
+        base = CTYPES[ctype]
+        assert ftype == (base * count if count > 1 else base), fname
 
 
-def test_memory_budget_limits_concurrency():
-    sysm = small()
-    est = estimate_bytes(sysm, "mixed")
-    srv = FakeServer(n_slots=4, mem_budget_bytes=2 * est + est // 2)
-    ids = [srv.submit(small(seed=k)) for k in range(10)]
-    assert all(srv.result(i, timeout=10).ok for i in ids)
-    assert srv.max_running == 2
-    srv.close()
+def test_server_rejects_bad_configuration_before_touching_the_device():
+    from paper_1906_01211_gb300 import amoebapol as ap
+    bad = [dict(n_workers=0), dict(mem_budget_bytes=0), dict(tol_debye=0.0), dict(max_iter=0), dict(precision=7),
+           dict(batch_max_atoms=100, batch_arena_atoms=50), dict(batch_max_atoms=100, batch_max_requests=0),
+           dict(resident_bytes=-1)]
+    base = dict(n_workers=2, mem_budget_bytes=1 << 30, precision=ap.AMP_MIXED, tol_debye=1e-5, max_iter=100,
+                batch_max_atoms=0, batch_arena_atoms=0, batch_max_requests=0, resident_bytes=0)
+    for b in bad:
+        cfg = ap.amp_server_config(**{**base, **b})
+        h = ctypes.c_void_p()
+        assert ap._lib.amp_server_create(ctypes.byref(h), ctypes.byref(cfg), 0) == ap.AMP_ERR_ARG
+        assert not h.value
+    assert ap._lib.amp_server_create(None, None, 0) == ap.AMP_ERR_ARG
 
 
-def test_oversize_request_is_refused_and_others_run():
-    sysm = small()
-    est = estimate_bytes(sysm, "mixed")
-    srv = FakeServer(n_slots=2, mem_budget_bytes=est)
-    big = srv.submit(make_waters(200, 20.0, 1))
-    ok = srv.submit(sysm)
-    r = srv.result(big, timeout=5)
-    assert not r.ok and "memory budget" in r.error
-    assert srv.result(ok, timeout=5).ok
-    srv.close()
-
-
-def test_cancel_queued_request():
-    srv = FakeServer(n_slots=1, mem_budget_bytes=1 << 40, work_s=0.2)
-    first = srv.submit(small(seed=1))
-    time.sleep(0.05)
-    queued = srv.submit(small(seed=2))
-    assert srv.cancel(queued)
-    assert not srv.cancel(first)  # already running
-    assert srv.result(queued, timeout=5).error == "cancelled"
-    assert srv.result(first, timeout=5).ok
-    srv.close()
-
-
-def test_bad_request_fails_alone():
-    bad = small(seed=3)
-    bad.alpha = bad.alpha.copy()
-    bad.alpha[0] = 0.0
-    srv = FakeServer(n_slots=2, mem_budget_bytes=1 << 40)
-    ids = [srv.submit(small(seed=4)), srv.submit(bad), srv.submit(small(seed=5))]
-    res = [srv.result(i, timeout=5) for i in ids]
-    assert res[0].ok and res[2].ok
-    assert not res[1].ok and "alpha" in res[1].error
-    srv.close()
-
-
-def test_dead_worker_is_reported_and_others_continue():
-    srv = FakeServer(n_slots=2, mem_budget_bytes=1 << 40)
-    killer = srv.submit(small(seed=6), key="kill-worker")
-    r = srv.result(killer, timeout=5)
-    assert not r.ok and "worker died" in r.error
-    time.sleep(0.05)
-    assert list(srv.health().values()).count(False) == 1
-    ids = [srv.submit(small(seed=7 + k)) for k in range(4)]
-    assert all(srv.result(i, timeout=10).ok for i in ids)
-    srv.close()
+def test_server_calls_reject_null_arguments():
+    from paper_1906_01211_gb300 import amoebapol as ap
+    t = ctypes.c_longlong(0)
+    z = np.zeros(6)
+    m = np.zeros(2, dtype=np.int32)
+    args = [z.ctypes.data] * 6 + [m.ctypes.data]
+    assert ap._lib.amp_server_submit(None, 2, 0.0, 0.0, 0.0, 0, *args, None, ctypes.byref(t)) == ap.AMP_ERR_ARG
+    assert ap._lib.amp_server_poll(None, 0, None, None) == ap.AMP_ERR_ARG
+    assert ap._lib.amp_server_wait(None, 0, 0.0, None, None) == ap.AMP_ERR_ARG
+    assert ap._lib.amp_server_stats(None, None) == ap.AMP_ERR_ARG
+    ap._lib.amp_server_destroy(None)  # ignored
 
 
 def test_request_stream_is_seeded_and_mixed():
