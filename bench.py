@@ -62,6 +62,8 @@ def parse():
                     help="time only the permanent-multipole energy call on the workload and print it")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement (request stream, rates) as its own JSON line")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batched engine: the stream's small clusters, all submitted at once")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--workers", type=int, default=6, help="serving: context workers beside the batched engine")
     ap.add_argument("--rates", default="1,2", help="serving: arrival rates as multiples of the float64 capacity")
@@ -248,6 +250,34 @@ def run_serving(n_requests: int, workers: int, rates_vs_fp64, rates_vs_capacity,
         out["rates"].append(res)
     srv.close()
     return out
+
+
+def run_batch_only(n_requests: int, max_waters: int = 1024):
+    """The batched engine alone: the stream's clusters of at most max_waters
+    waters, submitted at once (after a warm-up of 32), solved to 1e-5 D in
+    mixed precision. Reports solves/s and the all-pairs interactions per
+    second of the pair phase (n (n - 1) per operator application)."""
+    from paper_1906_01211_gb300.serve import Server, request_stream
+    reqs = [s for s in request_stream(4 * n_requests, seed=4) if s.box is None and s.n <= 3 * max_waters]
+    warm, reqs = reqs[:32], reqs[32:32 + n_requests]
+    with Server(n_workers=1, precision="mixed", tol_debye=1e-5) as srv:
+        for i in [srv.submit(s) for s in warm]:
+            srv.result(i)
+        l0 = srv.stats()["batch_launches"]
+        t0 = time.perf_counter()
+        ids = [srv.submit(s) for s in reqs]
+        res = [srv.result(i) for i in ids]
+        wall = time.perf_counter() - t0
+        launches = srv.stats()["batch_launches"] - l0
+    bad = [r.error for r in res if not r.ok or r.path != "batched"]
+    if bad:
+        raise RuntimeError(bad[0])
+    pair_terms = sum(s.n * (s.n - 1) * (r.iters + 2) for s, r in zip(reqs, res))
+    return {"requests": len(reqs), "waters_max": max_waters, "solves_per_s": len(reqs) / wall, "wall_s": wall,
+            "kernel_launches": launches, "mean_iters": sum(r.iters for r in res) / len(res),
+            "pair_terms_per_s": pair_terms / wall,
+            "note": "pair terms = n (n - 1) per T*v application (iterations + the initial residual + the "
+                    "float64 check), E0 not counted"}
 
 
 def max_over_ranks(t_ms: float, world: int, device) -> float:
@@ -690,6 +720,11 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps({"config": {"workload": "small water clusters of the request stream"},
+                              "batched_engine": run_batch_only(min(args.requests, 2000))}), flush=True)
+        return
     if args.serving:
         if rank == 0:
             sv = run_serving(args.requests, args.workers, [float(x) for x in args.rates.split(",")],

@@ -145,6 +145,26 @@ int amp_predictor_coefficients(int order, double* b);
  * polarization equation (routine efld0_direct2). */
 int amp_permanent_field(amp_ctx* ctx, double* E0);
 
+/* General AMOEBA's second right-hand side (paper Section "Polarizable AMOEBA
+ * force field" names the model; the two exclusion rules are Ren & Ponder's):
+ * the permanent field with scale s_intra (0 <= s <= 1) for two sites of one
+ * molecule instead of 0, E [N][3] (device, caller order):
+ *   E = E0 + sum over intramolecular pairs of s * (Thole-damped bare field),
+ * the "polarization" field E_p beside amp_permanent_field's "direct" E_d.
+ * With mu_d = A^-1 E_d and mu_p = A^-1 E_p (amp_solve_induced on each), the
+ * two-field energy is U = -1/2 C mu_d . E_p (amp_polarization_energy(mu_d,
+ * E_p)). Periodic contexts. */
+int amp_permanent_field_scaled(amp_ctx* ctx, double s_intra, double* E);
+
+/* Gradients of that U at the two solutions (A is symmetric, so no re-solve):
+ *   F = -dU/dr = 1/2 C [ d(mu_p . E_d) + d(mu_d . E_p) + d(mu_p . T mu_d) ],
+ *   dU/dq, dU/dd, dU/dTheta = -1/2 C d(mu_p . E_d + mu_d . E_p)/d(moment)
+ * (moment gradients as in amp_forces, unprojected). mu_d, mu_p [N][3]
+ * (device, caller order); F required, gq, gdip, gquad may be NULL. Periodic
+ * contexts. */
+int amp_two_rhs_forces(amp_ctx* ctx, double s_intra, const double* mu_d, const double* mu_p, double* F, double* gq,
+                       double* gdip, double* gquad);
+
 /* Tmu = T * mu for any mu [N][3] (real + reciprocal + self), the operator
  * applied at each solver iteration (routine tmatxb_pme2). */
 int amp_apply_T(amp_ctx* ctx, const double* mu, double* Tmu);
@@ -176,6 +196,24 @@ int amp_polarization_energy(amp_ctx* ctx, const double* mu, const double* E0, do
  * Multipoles are global-frame, so there are no torque terms. Uses the
  * geometry of the current system; allocates its buffers on the first call. */
 int amp_forces(amp_ctx* ctx, const double* mu, double* F, double* gq, double* gdip, double* gquad);
+
+/* Truncated conjugate gradient of order one (TCG-1), the non-iterative
+ * solver the paper's outlook names (Section "Perspectives on Tinker-HP 1.2
+ * performance"): one diagonal-preconditioned CG step from the direct guess,
+ *   u = alpha E0, r = T u, z = alpha r, gamma = (r.z)/(z.A z), mu_1 = u + gamma z,
+ *   U_1 = -1/2 C mu_1 . E0,
+ * and the exact gradients of U_1 (mu_1 is not the minimiser, so they run
+ * through gamma, r and z: three operator applications, no solve).
+ *   E0    [N][3] the permanent field (device, caller order), required;
+ *   mu    [N][3] mu_1 (may be NULL);  U: kcal/mol into *U (host; may be NULL);
+ *   F     [N][3] -dU_1/dr, gq [N], gdip [N][3], gquad [N][6] the moment
+ *         gradients as in amp_forces (unprojected); F may be NULL (energy
+ *         only; then the moment gradients must be NULL too); periodic
+ *         contexts only for the gradients.
+ * Operator applications in the context's precision; scalars and sums in
+ * float64. AMP_ERR_NOT_CONVERGED if z.A z <= 0. Synchronises the stream. */
+int amp_tcg1(amp_ctx* ctx, const double* E0, double* mu, double* U, double* F, double* gq, double* gdip,
+             double* gquad);
 
 /* Energy of the permanent multipoles with each other and its gradients (paper,
  * Section "Hotspots": routine empole1 computes this energy and its forces).
@@ -231,6 +269,35 @@ int amp_launch_count(const amp_ctx* ctx, long long* n);
 /* Iterations and float64 residual checks of the last solve (host pointers,
  * either may be NULL). */
 int amp_last_solve_stats(const amp_ctx* ctx, int* iters, int* fp64_checks);
+
+/* ---- Local-frame multipoles (AMOEBA, paper Section "Polarizable AMOEBA
+ * force field"; frame conventions of Ren & Ponder). Site i's dipole and
+ * quadrupole are given in a frame fixed by its axis atoms zatom[i],
+ * xatom[i]: v1 = x_z - x_i, v2 = x_x - x_i; kind 0 (Z-then-X): e_z = v1/|v1|;
+ * kind 1 (bisector): e_z = a/|a|, a = v1/|v1| + v2/|v2|; then e_x = the unit
+ * part of v2 normal to e_z, e_y = e_z x e_x, R = [e_x e_y e_z];
+ * d = R d_loc, Theta = R Theta_loc R^T. Any other kind, or axis atoms that are
+ * not two other atoms of the system, leaves the site's moments as given.
+ * Both calls are context-free, enqueue one kernel on cuda_stream
+ * (cudaStream_t as void*; NULL = legacy default stream), take device arrays
+ * in caller order (xyz, dip [N][3], quad [N][6] as in amp_set_system; kind,
+ * zatom, xatom int32 [N]) and allocate nothing. AMP_ERR_ARG for a null
+ * pointer or n_atoms < 1; AMP_ERR_CUDA for a launch error (an error pending
+ * on the thread from an earlier call is left pending). */
+
+/* Global moments dip, quad from the local ones (for amp_set_system). */
+int amp_frames_to_global(int n_atoms, const double* xyz, const double* dip_local, const double* quad_local,
+                         const int* kind, const int* zatom, const int* xatom, double* dip, double* quad,
+                         void* cuda_stream);
+
+/* Frame terms of the forces: F_k -= sum_i dU/dd_i . dd_i/dx_k +
+ * dU/dTheta_i . dTheta_i/dx_k over the sites i whose frames atom k fixes,
+ * from the moment gradients gdip [N][3], gquad [N][6] (unprojected, each
+ * off-diagonal standing for two entries, as amp_forces and amp_tcg1 return
+ * them) of an energy at fixed frames. Adds to F [N][3] (float64 atomics). */
+int amp_frame_forces(int n_atoms, const double* xyz, const double* dip_local, const double* quad_local,
+                     const int* kind, const int* zatom, const int* xatom, const double* gdip, const double* gquad,
+                     double* F, void* cuda_stream);
 
 /* ---- Serving: continuous batching of many independent solves.
  *

@@ -125,6 +125,11 @@ def _load() -> ctypes.CDLL:
         "amp_update_positions": (I, [P, P, ctypes.POINTER(I)]),
         "amp_set_predictor": (I, [P, I]),
         "amp_predictor_coefficients": (I, [I, ctypes.POINTER(D)]),
+        "amp_tcg1": (I, [P, P, P, ctypes.POINTER(D), P, P, P, P]),
+        "amp_permanent_field_scaled": (I, [P, D, P]),
+        "amp_two_rhs_forces": (I, [P, D, P, P, P, P, P, P]),
+        "amp_frames_to_global": (I, [I, P, P, P, P, P, P, P, P, P]),
+        "amp_frame_forces": (I, [I, P, P, P, P, P, P, P, P, P, P]),
         "amp_server_create": (I, [ctypes.POINTER(P), ctypes.POINTER(amp_server_config), I]),
         "amp_server_submit": (I, [P, I, D, D, D, I, P, P, P, P, P, P, P, ctypes.c_char_p,
                                   ctypes.POINTER(ctypes.c_longlong)]),
@@ -235,6 +240,21 @@ def amp_forces(ctx, mu, F, gq=None, gdip=None, gquad=None):
     _check(ctx, _lib.amp_forces(ctx, mu, F, gq, gdip, gquad))
 
 
+def amp_permanent_field_scaled(ctx, s_intra: float, E):
+    _check(ctx, _lib.amp_permanent_field_scaled(ctx, float(s_intra), E))
+
+
+def amp_two_rhs_forces(ctx, s_intra: float, mu_d, mu_p, F, gq=None, gdip=None, gquad=None):
+    _check(ctx, _lib.amp_two_rhs_forces(ctx, float(s_intra), mu_d, mu_p, F, gq, gdip, gquad))
+
+
+def amp_tcg1(ctx, E0, mu=None, F=None, gq=None, gdip=None, gquad=None) -> float:
+    """TCG-1 energy (kcal/mol); mu_1 and the gradients into the non-null device pointers."""
+    u = ctypes.c_double(0.0)
+    _check(ctx, _lib.amp_tcg1(ctx, E0, mu, ctypes.byref(u), F, gq, gdip, gquad))
+    return u.value
+
+
 def amp_multipole_energy(ctx, F=None, gq=None, gdip=None, gquad=None) -> float:
     """Permanent-multipole energy (kcal/mol); gradients into the non-null device pointers."""
     u = ctypes.c_double(0.0)
@@ -262,6 +282,42 @@ def amp_profile_read(ctx) -> dict:
 
 
 AMP_PENDING = 1
+
+
+def amp_frames_to_global(n, xyz, dip_local, quad_local, kind, zatom, xatom, dip, quad, stream=None):
+    code = _lib.amp_frames_to_global(int(n), xyz, dip_local, quad_local, kind, zatom, xatom, dip, quad,
+                                     ctypes.c_void_p(stream or 0))
+    if code != AMP_OK:
+        raise AmpError(code, "amp_frames_to_global")
+
+
+def amp_frame_forces(n, xyz, dip_local, quad_local, kind, zatom, xatom, gdip, gquad, F, stream=None):
+    code = _lib.amp_frame_forces(int(n), xyz, dip_local, quad_local, kind, zatom, xatom, gdip, gquad, F,
+                                 ctypes.c_void_p(stream or 0))
+    if code != AMP_OK:
+        raise AmpError(code, "amp_frame_forces")
+
+
+def frames_to_global(xyz, dip_local, quad_local, kind, zatom, xatom):
+    """Global (dip, quad) torch tensors from local-frame moments (torch CUDA
+    tensors: float64 positions and moments, int32 frame topology)."""
+    import torch
+    n = xyz.shape[0]
+    dip = torch.empty((n, 3), dtype=torch.float64, device=xyz.device)
+    quad = torch.empty((n, 6), dtype=torch.float64, device=xyz.device)
+    amp_frames_to_global(n, xyz.data_ptr(), dip_local.data_ptr(), quad_local.data_ptr(), kind.data_ptr(),
+                         zatom.data_ptr(), xatom.data_ptr(), dip.data_ptr(), quad.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    return dip, quad
+
+
+def add_frame_forces(F, xyz, dip_local, quad_local, kind, zatom, xatom, gdip, gquad):
+    """F += the frame terms of the forces from the moment gradients (in place)."""
+    import torch
+    amp_frame_forces(xyz.shape[0], xyz.data_ptr(), dip_local.data_ptr(), quad_local.data_ptr(), kind.data_ptr(),
+                     zatom.data_ptr(), xatom.data_ptr(), gdip.data_ptr(), gquad.data_ptr(), F.data_ptr(),
+                     torch.cuda.current_stream().cuda_stream)
+    return F
 
 
 def amp_server_create(cfg: amp_server_config, device: int = 0):
@@ -461,6 +517,44 @@ class Polarization:
         gt = torch.empty((n, 6), dtype=torch.float64, device="cuda")
         amp_forces(self.ctx, mu.data_ptr(), F.data_ptr(), gq.data_ptr(), gd.data_ptr(), gt.data_ptr())
         return F, gq, gd, gt
+
+    def permanent_field_scaled(self, s_intra: float, out=None):
+        """The permanent field with scale s_intra for two sites of one molecule (E_p)."""
+        torch = self.torch
+        out = out if out is not None else torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        amp_permanent_field_scaled(self.ctx, s_intra, out.data_ptr())
+        return out
+
+    def two_rhs_forces(self, s_intra: float, mu_d, mu_p):
+        """(F, dU/dq, dU/dd, dU/dTheta6) of U = -1/2 C mu_d . E_p at the two solutions."""
+        torch = self.torch
+        mu_d = self._dev(mu_d, torch.float64)
+        mu_p = self._dev(mu_p, torch.float64)
+        n = mu_d.shape[0]
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gq = torch.empty((n,), dtype=torch.float64, device="cuda")
+        gd = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gt = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        amp_two_rhs_forces(self.ctx, s_intra, mu_d.data_ptr(), mu_p.data_ptr(), F.data_ptr(), gq.data_ptr(),
+                           gd.data_ptr(), gt.data_ptr())
+        return F, gq, gd, gt
+
+    def tcg1(self, E0, gradients: bool = True):
+        """TCG-1: (mu_1, U_1, F, dU_1/dq, dU_1/dd, dU_1/dTheta6); the four
+        gradients are None when gradients is False."""
+        torch = self.torch
+        E0 = self._dev(E0, torch.float64)
+        n = E0.shape[0]
+        mu = torch.empty_like(E0)
+        if not gradients:
+            return (mu, amp_tcg1(self.ctx, E0.data_ptr(), mu.data_ptr()), None, None, None, None)
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gq = torch.empty((n,), dtype=torch.float64, device="cuda")
+        gd = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gt = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        U = amp_tcg1(self.ctx, E0.data_ptr(), mu.data_ptr(), F.data_ptr(), gq.data_ptr(), gd.data_ptr(),
+                     gt.data_ptr())
+        return mu, U, F, gq, gd, gt
 
     def multipole_energy(self, gradients: bool = True):
         """Permanent-multipole energy U (kcal/mol) and, if asked, (F, dU/dq, dU/dd,

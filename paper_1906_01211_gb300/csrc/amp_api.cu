@@ -331,6 +331,46 @@ int amp_permanent_field(amp_ctx* c, double* E0) {
   return cuda_check(c, cudaGetLastError(), "permanent_field launch");
 }
 
+int amp_permanent_field_scaled(amp_ctx* c, double s_intra, double* E) {
+  if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!E) return fail(c, AMP_ERR_ARG, "E is null");
+  if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_permanent_field_scaled: periodic contexts only");
+  if (!(s_intra >= 0.0 && s_intra <= 1.0)) return fail(c, AMP_ERR_ARG, "amp_permanent_field_scaled: 0 <= s <= 1");
+  {
+    PhaseScope ps(c, AMP_PHASE_E0_REAL);
+    launch_e0_real(c, c->E0s);
+    if (s_intra != 0.0) launch_intra_scaled(c, s_intra, c->E0s);
+  }
+  join_geometry(c);
+  launch_add_from_sorted(c, c->E0s, c->e0rec, E);
+  return cuda_check(c, cudaGetLastError(), "permanent_field_scaled launch");
+}
+
+int amp_two_rhs_forces(amp_ctx* c, double s_intra, const double* mu_d, const double* mu_p, double* F, double* gq,
+                       double* gdip, double* gquad) {
+  if (!c) return AMP_ERR_ARG;
+  join_geometry(c);
+  if (!c->have_system) return fail(c, AMP_ERR_STATE, "no system set");
+  if (!mu_d || !mu_p || !F) return fail(c, AMP_ERR_ARG, "mu_d, mu_p and F are required");
+  if (c->cluster) return fail(c, AMP_ERR_ARG, "amp_two_rhs_forces: periodic contexts only");
+  if (!(s_intra >= 0.0 && s_intra <= 1.0)) return fail(c, AMP_ERR_ARG, "amp_two_rhs_forces: 0 <= s <= 1");
+  int r;
+  if (c->tcg_cap < 4LL * c->n) {
+    dev_free(c, c->tcg);
+    c->tcg = nullptr;
+    c->tcg_cap = 0;
+    if ((r = dev_alloc(c, &c->tcg, 10LL * c->n))) return r;
+    c->tcg_cap = 10LL * c->n;
+  }
+  double4_32a *md = c->tcg, *mp = md + c->n;
+  launch_to_sorted(c, mu_d, md);
+  launch_to_sorted(c, mu_p, mp);
+  if ((r = two_rhs_forces(c, s_intra, md, mp, mp + c->n, F, gq, gdip, gquad))) return r;
+  return cuda_check(c, cudaGetLastError(), "two_rhs_forces launch");
+}
+
 int amp_apply_T(amp_ctx* c, const double* mu, double* Tmu) {
   if (!c) return AMP_ERR_ARG;
   join_geometry(c);

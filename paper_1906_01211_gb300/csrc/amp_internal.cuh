@@ -190,6 +190,9 @@ struct amp_ctx {
   double* grid64b = nullptr;
   float* grid32b = nullptr;
   double* mpole_e = nullptr;  // per-atom permanent-multipole energy (sorted order)
+  double4_32a* tcg = nullptr;  // TCG-1 vectors (u, r, z, T z, v, T v, c, P/2, kappa z/2)
+  long long tcg_cap = 0;
+  double* tcg_sc = nullptr;    // TCG-1 scalars (w, s, t, gamma, w/t, kappa, breakdown, U)
   int mpole_e_cap = 0;
 
   // isolated cluster (box == 0): all-pairs kernels, column-slice partial sums
@@ -299,6 +302,17 @@ int force_buffers(amp_ctx* c);
 int pme_potential(amp_ctx* c, bool fp32, bool multipoles, const double4_32a* v, const float4* v32, void* grid_out,
                   cudaStream_t st);
 int multipole_energy(amp_ctx* c, double* U, double* F, double* gq, double* gd, double* gt);
+// gradients of sf c.E + a1.T b1 + a2.T b2 (cell-order vectors), as forces and moment gradients
+int bilinear_forces(amp_ctx* c, const double4_32a* cv, double sf, const double4_32a* a1, const double4_32a* b1,
+                    const double4_32a* a2, const double4_32a* b2, double* F, double* gq, double* gd, double* gt,
+                    const double4_32a* intra_mu, double intra_s);
+// the two-field gradients (work: two vectors)
+int two_rhs_forces(amp_ctx* c, double s, const double4_32a* mu_d, const double4_32a* mu_p, double4_32a* work,
+                   double* F, double* gq, double* gd, double* gt);
+// out += the permanent field with intramolecular scale s minus that with scale 0
+void launch_intra_scaled(amp_ctx* c, double s, double4_32a* out);
+int apply_T_sorted(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* t,
+                   double4_32a* t2);
 void launch_split_multipoles(amp_ctx* c);  // pd and mp_df from the atom records
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
 

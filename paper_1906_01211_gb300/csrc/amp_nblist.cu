@@ -559,10 +559,11 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
         (r = dev_alloc(c, &c->pos_tr, caph)) || (r = dev_alloc(c, &c->Ep64, 6 * caph)))
       return r;
     if (c->cfg.precision == AMP_FP64) {
-      if ((r = dev_alloc(c, &c->T64, 6 * capf)) || (r = dev_alloc(c, &c->intra, caph + 1))) return r;
+      if ((r = dev_alloc(c, &c->T64, 6 * capf))) return r;
     } else {
       if ((r = dev_alloc(c, &c->T32, 6 * capf)) || (r = dev_alloc(c, &c->Ep32, 6 * caph))) return r;
     }
+    if ((r = dev_alloc(c, &c->intra, caph + 1))) return r;
     c->cap_half = caph;
     c->cap_full = capf;
   }

@@ -117,6 +117,21 @@ __device__ __forceinline__ dflt min_image_df(dflt d, const PairGeomDf& g) {
   return sh == 0.f ? d : df_sub(d, df_mul({sh, 0.f}, g.L));
 }
 
+// A pair of two sites of one molecule joins the list intra ([0] count, then
+// pair ids; one atomic per warp): the float64 permanent-field terms
+// (k_intra_fields64) and the scaled fields of the two-field form use it.
+__device__ __forceinline__ void append_intra(bool same, long long pid, int* __restrict__ intra) {
+  const unsigned live = __activemask();
+  const unsigned m = __ballot_sync(live, same);
+  if (m) {
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(intra, __popc(m));
+    base = __shfl_sync(live, base, leader);
+    if (same) intra[1 + base + __popc(m & ((1u << lane) - 1u))] = (int)pid;
+  }
+}
+
 // Mixed path pair build: the displacement from the split positions (minimum
 // image in double-float, then rounded to float), every other quantity in
 // float32 from the float parts of the per-atom records (pd, mp_df), so that
@@ -130,12 +145,14 @@ __global__ void __launch_bounds__(256) k_pair_build32(long long nh, const int* _
                                                       const int* __restrict__ full_start,
                                                       const int* __restrict__ half_start,
                                                       const int* __restrict__ pos_tr, float4* __restrict__ T4,
-                                                      float2* __restrict__ T2, float* __restrict__ Ep) {
+                                                      float2* __restrict__ T2, float* __restrict__ Ep,
+                                                      int* __restrict__ intra) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
   const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
   const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
+  append_intra(__float_as_int(th_i.z) == __float_as_int(th_j.z), pid, intra);
   const dflt dx = min_image_df(df_sub({hi_i.x, lo_i.x}, {hi_j.x, lo_j.x}), gd);
   const dflt dy = min_image_df(df_sub({hi_i.y, lo_i.y}, {hi_j.y, lo_j.y}), gd);
   const dflt dz = min_image_df(df_sub({hi_i.z, lo_i.z}, {hi_j.z, lo_j.z}), gd);
@@ -226,18 +243,7 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
   const int i = half_i[pid], j = half_j[pid];
   const float4 hi_i = pd[3 * (long long)i], lo_i = pd[3 * (long long)i + 1], th_i = pd[3 * (long long)i + 2];
   const float4 hi_j = pd[3 * (long long)j], lo_j = pd[3 * (long long)j + 1], th_j = pd[3 * (long long)j + 2];
-  {  // pairs of two sites of one molecule join the list of k_intra_fields64 (one atomic per warp)
-    const bool same = __float_as_int(th_i.z) == __float_as_int(th_j.z);
-    const unsigned live = __activemask();
-    const unsigned m = __ballot_sync(live, same);
-    if (m) {
-      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(intra, __popc(m));
-      base = __shfl_sync(live, base, leader);
-      if (same) intra[1 + base + __popc(m & ((1u << lane) - 1u))] = (int)pid;
-    }
-  }
+  append_intra(__float_as_int(th_i.z) == __float_as_int(th_j.z), pid, intra);
   const PairTermsDf p = pair_terms_df(hi_i, lo_i, th_i, hi_j, lo_j, th_j, g, tab);
   const dflt(&R)[3] = p.R;
   const dflt NR[3] = {df_neg(R[0]), df_neg(R[1]), df_neg(R[2])};
@@ -400,6 +406,47 @@ __global__ void __launch_bounds__(128) k_intra_fields64(const int* __restrict__ 
     const double bare1 = ir * ir2, bare2 = 3.0 * bare1 * ir2, bare3 = 5.0 * bare2 * ir2;
     const double b1 = B1 - bare1, b2 = B2 - bare2, b3 = B3 - bare3;
     const double4_32a bi = B[i], bj = B[j], ci = C[i], cj = C[j], di = D[i], dj = D[j];
+    double f[6];
+    multipole_field<double>(r3[0], r3[1], r3[2], aj.w, bj.x, bj.y, bj.z, cj.x, cj.y, cj.z, cj.w, dj.x, dj.y, b1,
+                            b2, b3, f[0], f[1], f[2]);
+    multipole_field<double>(-r3[0], -r3[1], -r3[2], ai.w, bi.x, bi.y, bi.z, ci.x, ci.y, ci.z, ci.w, di.x, di.y,
+                            b1, b2, b3, f[3], f[4], f[5]);
+    double* oi = reinterpret_cast<double*>(out + i);
+    double* oj = reinterpret_cast<double*>(out + j);
+    for (int a = 0; a < 3; ++a) {
+      atomicAdd(oi + a, f[a]);
+      atomicAdd(oj + a, f[3 + a]);
+    }
+  }
+}
+
+// The difference between the permanent field with scale s for two sites of
+// one molecule and with scale 0 (the two-field form's E_p - E_d): for each
+// intramolecular pair the Thole-damped bare field times s, kernels
+// s l3 bare1, s l5 bare2, s l7 bare3 (the screened parts cancel), in float64,
+// added to out at both ends (float64 atomics).
+__global__ void __launch_bounds__(128) k_intra_scaled64(const int* __restrict__ intra, const int* __restrict__ half_i,
+                                                        const int* __restrict__ half_j, PairGeom g, double s,
+                                                        const double4_32a* __restrict__ A,
+                                                        const double4_32a* __restrict__ B,
+                                                        const double4_32a* __restrict__ C,
+                                                        const double4_32a* __restrict__ D,
+                                                        double4_32a* __restrict__ out) {
+  const int cnt = intra[0];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    const int pid = intra[1 + k];
+    const int i = half_i[pid], j = half_j[pid];
+    const double4_32a ai = A[i], aj = A[j], bi = B[i], bj = B[j], ci = C[i], cj = C[j], di = D[i], dj = D[j];
+    double r3[3] = {ai.x - aj.x, ai.y - aj.y, ai.z - aj.z};
+    if (g.L > 0.0)
+      for (int a = 0; a < 3; ++a) r3[a] -= g.L * rint(r3[a] * g.invL);
+    const double r2 = r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2];
+    const double r = sqrt(r2), ir = 1.0 / r, ir2 = ir * ir;
+    const double bare1 = ir * ir2, bare2 = 3.0 * bare1 * ir2, bare3 = 5.0 * bare2 * ir2;
+    const double x = fmin(di.z, dj.z) * r2 * r * bi.w * bj.w;
+    const double e = exp(-x);
+    const double l3 = 1.0 - e, l5 = 1.0 - (1.0 + x) * e, l7 = 1.0 - (1.0 + x + 0.6 * x * x) * e;
+    const double b1 = s * l3 * bare1, b2 = s * l5 * bare2, b3 = s * l7 * bare3;
     double f[6];
     multipole_field<double>(r3[0], r3[1], r3[2], aj.w, bj.x, bj.y, bj.z, cj.x, cj.y, cj.z, cj.w, dj.x, dj.y, b1,
                             b2, b3, f[0], f[1], f[2]);
@@ -680,13 +727,24 @@ void launch_pair_build(amp_ctx* c) {
   g32.beta = (float)g.beta;
   g32.twob2 = (float)g.twob2;
   g32.gpre = (float)g.gpre;
+  cudaMemsetAsync(c->intra, 0, sizeof(int), c->stream);
   k_pair_build32<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, geom_df(g), g32,
                                                 c->full_start, c->half_start, c->pos_tr,
                                                 reinterpret_cast<float4*>(c->T32),
-                                                reinterpret_cast<float2*>(c->T32 + 4 * c->cap_full), c->Ep32);
+                                                reinterpret_cast<float2*>(c->T32 + 4 * c->cap_full), c->Ep32,
+                                                c->intra);
 }
 
 // The split positions and moments alone (clusters, which build no pair terms).
+// out += (the permanent field with scale s for two sites of one molecule) -
+// (that with scale 0); periodic contexts (the pair build's intramolecular list).
+void launch_intra_scaled(amp_ctx* c, double s, double4_32a* out) {
+  if (c->n_half == 0) return;
+  c->n_launch += 1;
+  k_intra_scaled64<<<4 * c->n_sm, 128, 0, c->stream>>>(c->intra, c->half_i, c->half_j, geom(c), s, c->atomA,
+                                                       c->atomB, c->atomC, c->atomD, out);
+}
+
 void launch_split_multipoles(amp_ctx* c) {
   c->n_launch += 1;
   k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
