@@ -3,9 +3,10 @@ iterate mu_1, the energy U_1 and its exact gradients (forces and the three
 moment gradients), which run through gamma, r and z.
 
 Tolerances: float64 path 1e-10 relative (2-norm and per atom) on every
-output, as for the polarization forces; mixed path 2e-5 (float32 pair terms
-and reciprocal chain). The oracle's TCG-1 is pinned by finite differences
-in tests/test_oracle_tcg.py.
+output, as for the polarization forces; mixed path 2e-5 on the 2-norm and
+5x that per atom, the factor the mixed dipoles get (TCG-1 has no float64
+refinement: the float32 operator's error reaches the result directly). The
+oracle's TCG-1 is pinned by finite differences in tests/test_oracle_tcg.py.
 """
 import numpy as np
 import pytest
@@ -53,11 +54,12 @@ def test_tcg1_energy_and_gradients_match_oracle(name, precision, tol):
     U_ref, mu_ref, _ = tcg1(op)
     F_ref, gq_ref, gd_ref, gt_ref = tcg1_gradients(op)
     mu, U, F, gq, gd, gt = gpu_tcg(sysm, st, precision)
+    f = 1.0 if precision == "fp64" else 5.0
     assert abs(U / U_ref - 1) < tol
-    assert_fields(mu, mu_ref, tol)
-    assert_fields(F, F_ref, tol)
+    assert_fields(mu, mu_ref, tol, f)
+    assert_fields(F, F_ref, tol, f)
     assert rel(gq, gq_ref) < tol
-    assert_fields(gd, gd_ref, tol)
+    assert_fields(gd, gd_ref, tol, f)
     assert rel(gt, gt_ref) < tol
 
 
