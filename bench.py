@@ -515,7 +515,7 @@ def measured_peaks():
         return {}
 
 
-def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
+def kernel_rooflines(phases, n_pairs, n_atoms, workload=None, K=0):
     """Roofline entries from the live phase timers (one kernel per phase).
 
     real-space T*v (k_t_real_df): bound "hbm". achieved = the algorithmic
@@ -553,6 +553,26 @@ def kernel_rooflines(phases, n_pairs, n_atoms, workload=None):
                     "stored_tensor_bytes": stored, "achieved_stored": ach_stored, "frac_stored": ach_stored / peak,
                     "launch_ms": per, "ms_per_step": ms / steps_seen,
                     "peak_source": "measured" if hbm else "fallback"})
+    # the reciprocal chain of one T*mu and the cell search, from their
+    # sub-phase timers: bytes each must move at least once (grids of K^3
+    # points, per-atom weights), against the HBM copy rate; their working
+    # sets (2 MB grids at K = 64) sit in the 129 MB L2, so these fractions
+    # say how far from a streaming bound the latency-bound steps are
+    if K:
+        nh = K * K * (K // 2 + 1)
+        for key, kern, nbytes in (
+                ("t_spread", "k_spread_dipoles_fx (dipole spreading, fixed point)", 8 * K ** 3 + 288 * n_atoms),
+                ("t_fft", "k_fft_plane_fwd + k_fft_x_conv + k_fft_plane_inv (double-float, 3 passes)",
+                 16 * K ** 3 + 72 * nh),
+                ("t_gather", "k_gather_field_df (field gather, double-float)", 8 * K ** 3 + 288 * n_atoms),
+                ("list_search", "k_neighbours<2> (cell search, owned neighbours into slab rows)", 16 * n_atoms + 4 * n_pairs)):
+            ms, cnt = phases.get(key, (0.0, 0))
+            if cnt:
+                per = ms / cnt
+                ach = nbytes / (per / 1e3) / 1e9
+                out.append({"kernel": kern, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                            "frac": ach / peak, "traffic": None, "algorithmic_bytes": nbytes, "launch_ms": per,
+                            "ms_per_step": ms / steps_seen, "peak_source": "measured" if hbm else "fallback"})
     ms, cnt = phases["pair"]
     if cnt:
         per = ms / cnt
@@ -844,7 +864,7 @@ def main():
     p.profile(False)
 
     # ---- rooflines of our two largest kernels; the dominant one is "roofline"
-    rooflines = kernel_rooflines(phases, n_pairs, n, w.name)
+    rooflines = kernel_rooflines(phases, n_pairs, n, w.name, w.grid)
     roofline = max(rooflines, key=lambda r: r["ms_per_step"])
     phase_ms = {k: round(v[0] / prof_steps, 4) for k, v in phases.items()}
 

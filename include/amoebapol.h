@@ -252,7 +252,11 @@ int amp_pair_count(const amp_ctx* ctx, long long* n_pairs);
 #define AMP_PHASE_FP64_CHECK 7  /* mixed path: float64 residual check */
 #define AMP_PHASE_ENERGY 8      /* energy reduction */
 #define AMP_PHASE_FORCES 9      /* forces and moment gradients (polarization, multipoles) */
-#define AMP_NPHASE 10
+#define AMP_PHASE_T_SPREAD 10   /* within AMP_PHASE_T_RECIP: the dipole spreading */
+#define AMP_PHASE_T_FFT 11      /* within AMP_PHASE_T_RECIP: the 3D FFT convolution */
+#define AMP_PHASE_T_GATHER 12   /* within AMP_PHASE_T_RECIP: the field gather */
+#define AMP_PHASE_LIST_SEARCH 13  /* within AMP_PHASE_LIST: the cell search (k_neighbours) */
+#define AMP_NPHASE 14
 
 /* enable != 0: start recording (clears totals); 0: stop. */
 int amp_profile(amp_ctx* ctx, int enable);

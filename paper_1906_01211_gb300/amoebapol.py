@@ -28,7 +28,8 @@ AMP_ERR_STATE = -6
 AMP_ERR_STALE = -8
 AMP_FP64 = 0
 AMP_MIXED = 1
-PHASES = ("list", "pair", "e0_real", "e0_recip", "t_real", "t_recip", "pcg", "fp64_check", "energy", "forces")
+PHASES = ("list", "pair", "e0_real", "e0_recip", "t_real", "t_recip", "pcg", "fp64_check", "energy", "forces",
+          "t_spread", "t_fft", "t_gather", "list_search")
 
 
 class amp_config(ctypes.Structure):

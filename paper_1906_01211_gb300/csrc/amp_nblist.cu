@@ -649,8 +649,12 @@ int build_cells_and_lists(amp_ctx* c, const double* xyz, const double* q, const 
   ListParams P;
   if ((r = list_params(c, rlist, &P))) return r;
   const int lb = amp_blocks((long long)n * 32, 256);
-  k_neighbours<2><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, c->full_cnt, c->half_cnt,
-                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->slab, c->flags);
+  {
+    PhaseScope ps(c, AMP_PHASE_LIST_SEARCH);
+    k_neighbours<2><<<lb, 256, 0, st>>>(P, c->pos32, c->atomA, c->slot_tmp, c->cell_start, c->full_cnt,
+                                        c->half_cnt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->slab,
+                                        c->flags);
+  }
   c->n_launch += 4;  // scan .. transpose_sort
   if ((r = finish_lists(c, P, false))) return r;
   if (skin <= 0.0) return AMP_OK;

@@ -976,13 +976,21 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
   const int K = c->K, n = c->n;
   c->n_launch += 3;  // spread, convolve, gather (cuFFT kernels not counted)
   if (!v32) return fail(c, AMP_ERR_STATE, "reciprocal field needs the float split of the vector");
-  launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
-             dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
-             (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
+  {
+    PhaseScope ps(c, AMP_PHASE_T_SPREAD, st);
+    launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
+               dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
+               (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
+  }
   if (c->spread_event) cudaEventRecord(c->ev_spread, st);
   bool split = true;
-  const int r = conv_to_phi(c, st, &split);
+  int r;
+  {
+    PhaseScope ps(c, AMP_PHASE_T_FFT, st);
+    r = conv_to_phi(c, st, &split);
+  }
   if (r) return r;
+  PhaseScope ps(c, AMP_PHASE_T_GATHER, st);
   if (set)
     gather_df<true>(c, st, out, split);
   else
@@ -1002,27 +1010,34 @@ int pme_dipole_field32(amp_ctx* c, const float4* v32, double4_32a* out, cudaStre
   int r = AMP_OK;
   if (!own) cudaMemsetAsync(c->spread32, 0, sizeof(float) * ng, st);
   c->n_launch += 2;
-  launch_pdl(k_spread_dipoles32, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
-             dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, K, c->spread32, c->op_stop);
+  {
+    PhaseScope ps(c, AMP_PHASE_T_SPREAD, st);
+    launch_pdl(k_spread_dipoles32, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
+               dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, K, c->spread32, c->op_stop);
+  }
   if (c->spread_event) cudaEventRecord(c->ev_spread, st);
-  if (own) {
-    fft_f32_convolve(c, st);
-  } else {
-    c->n_launch += 1;
-    cufftSetStream(c->plan_r2c, st);
-    cufftSetStream(c->plan_c2r, st);
-    cufftResult fr = cufftExecR2C(c->plan_r2c, c->spread32, reinterpret_cast<cufftComplex*>(c->cgrid32));
-    if (fr == CUFFT_SUCCESS) {
-      k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32, c->op_stop);
-      fr = cufftExecC2R(c->plan_c2r, reinterpret_cast<cufftComplex*>(c->cgrid32), c->phi32);
+  {
+    PhaseScope pf(c, AMP_PHASE_T_FFT, st);
+    if (own) {
+      fft_f32_convolve(c, st);
+    } else {
+      c->n_launch += 1;
+      cufftSetStream(c->plan_r2c, st);
+      cufftSetStream(c->plan_c2r, st);
+      cufftResult fr = cufftExecR2C(c->plan_r2c, c->spread32, reinterpret_cast<cufftComplex*>(c->cgrid32));
+      if (fr == CUFFT_SUCCESS) {
+        k_convolve<<<amp_blocks(nh, 256), 256, 0, st>>>(nh, c->cgrid32, c->G32, c->op_stop);
+        fr = cufftExecC2R(c->plan_c2r, reinterpret_cast<cufftComplex*>(c->cgrid32), c->phi32);
+      }
+      cufftSetStream(c->plan_r2c, c->stream);
+      cufftSetStream(c->plan_c2r, c->stream);
+      if (fr != CUFFT_SUCCESS) r = fail(c, AMP_ERR_CUDA, "cuFFT exec failed (%d)", (int)fr);
     }
-    cufftSetStream(c->plan_r2c, c->stream);
-    cufftSetStream(c->plan_c2r, c->stream);
-    if (fr != CUFFT_SUCCESS) r = fail(c, AMP_ERR_CUDA, "cuFFT exec failed (%d)", (int)fr);
   }
   if (r) return r;
   const long long warps = (n + kGatherAtomsPerWarp - 1) / kGatherAtomsPerWarp;
   const dim3 grid(amp_blocks(warps * 32, kGatherThreads));
+  PhaseScope pg(c, AMP_PHASE_T_GATHER, st);
   if (set)
     launch_pdl(k_gather_field32<true>, grid, dim3(kGatherThreads), 0, st, n, c->theta_df, c->gbase, c->phi32, K, out,
                c->op_stop);
