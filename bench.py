@@ -504,8 +504,8 @@ PAIR_BUILD_FLOPS = 130
 DF_FP32_PER_FP64 = 13
 # DRAM traffic (read + write) per launch of k_t_real_df on water-23556, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# current kernel.
-T_REAL_TRAFFIC = {"water-23556": 182.5e6}
+# current kernel (empty until the current kernel has been captured).
+T_REAL_TRAFFIC = {"water-23556": 68.2e6}
 
 
 def measured_peaks():
@@ -522,9 +522,11 @@ def kernel_rooflines(phases, n_pairs, n_atoms, workload=None, K=0):
     bytes of one T*mu, 80 B per atom (float64 position, dipole, damping
     factor and output field) + 4 B per unique pair (a half-list index),
     divided by the kernel's average launch time; peak = MEASURED_PEAKS.json
-    hbm_gbs. This kernel does not recompute the pair terms: it streams the
-    damped tensor stored per directed entry (48 B) with its neighbour index
-    (4 B) plus 92 B per atom, 21x the algorithmic bytes at water-23556; those
+    hbm_gbs. This kernel does not recompute the damped radial terms: it
+    streams the tensor's two scalars stored per directed entry (16 B) with
+    the neighbour index (4 B), rebuilds r from the positions, and reads
+    132 B per atom (positions and v as hi/lo floats, v and the output in
+    float64, the row start), 8x the algorithmic bytes at water-23556; those
     bytes are reported as stored_tensor_bytes with their own fraction, and
     the DRAM traffic measured by ncu as traffic.
     pair build (k_pair_build_df): bound "alu" on the float32 pipe, which runs
@@ -544,7 +546,7 @@ def kernel_rooflines(phases, n_pairs, n_atoms, workload=None, K=0):
     if cnt:
         per = ms / cnt
         nbytes = 80 * n_atoms + 4 * n_pairs
-        stored = (48 + 4) * 2 * n_pairs + 92 * n_atoms
+        stored = (16 + 4) * 2 * n_pairs + 132 * n_atoms
         ach = nbytes / (per / 1e3) / 1e9
         ach_stored = stored / (per / 1e3) / 1e9
         out.append({"kernel": "k_t_real_df (real-space T*v, double-float)", "bound": "hbm", "achieved": ach,

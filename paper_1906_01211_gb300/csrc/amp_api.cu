@@ -101,7 +101,8 @@ static int alloc_atoms(amp_ctx* c, int n) {
                    (void**)&c->gbase, (void**)&c->E0s, (void**)&c->mu, (void**)&c->res, (void**)&c->zv,
                    (void**)&c->pv, (void**)&c->qv, (void**)&c->tv, (void**)&c->tmp, (void**)&c->p32,
                    (void**)&c->trec, (void**)&c->plo, (void**)&c->vhl, (void**)&c->mp_df, (void**)&c->wv,
-                   (void**)&c->theta_df, (void**)&c->pd, (void**)&c->e0rec, (void**)&c->e0intra};
+                   (void**)&c->theta_df, (void**)&c->pd, (void**)&c->e0rec, (void**)&c->e0intra,
+                   (void**)&c->xhl};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -121,7 +122,8 @@ static int alloc_atoms(amp_ctx* c, int n) {
       (r = dev_alloc(c, &c->p32, cap)) || (r = dev_alloc(c, &c->trec, cap)) || (r = dev_alloc(c, &c->plo, cap)) ||
       (r = dev_alloc(c, &c->wv, cap)) || (r = dev_alloc(c, &c->vhl, 2LL * cap)) ||
       (r = dev_alloc(c, &c->mp_df, 5LL * cap)) || (r = dev_alloc(c, &c->pd, 3LL * cap)) ||
-      (r = dev_alloc(c, &c->e0rec, cap)) || (r = dev_alloc(c, &c->e0intra, cap)))
+      (r = dev_alloc(c, &c->e0rec, cap)) || (r = dev_alloc(c, &c->e0intra, cap)) ||
+      (r = dev_alloc(c, &c->xhl, 2LL * cap)))
     return r;
   c->n_cap = cap;
   return AMP_OK;

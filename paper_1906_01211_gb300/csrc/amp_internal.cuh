@@ -21,9 +21,9 @@
 //   T32: the mixed path's float32 tensor once per full-list entry, in entry
 //     order: (xx, yy, zz, xy) as float4 from the start, (xz, yz) as float2
 //     after cap_full entries
-//   T64: the float64 path's tensor once per full-list entry, in entry order:
-//     32 bytes per entry (hi xx yy zz xy xz yz, lo xx yy) from the start,
-//     then 16 bytes per entry (lo zz xy xz yz) after cap_full entries
+//   C64: the float64 path's pair tensor T = -b1 I + b2 r r^T as its two
+//     scalars, once per full-list entry in entry order: (b1 hi, b1 lo,
+//     b2 hi, b2 lo), 16 bytes; the product kernel rebuilds r from xhl
 //   Ep64/Ep32[pid*6 + side*3 + a]         permanent field at the side's atom
 #pragma once
 
@@ -71,6 +71,7 @@ struct amp_ctx {
   float4* mp_df = nullptr;  // float64 path: q, d, Theta as hi/lo float pairs, 5 float4 per atom
   // float64 path, per atom: (x, y, z, 1/sqrt(alpha)) hi, the same lo, (thole hi, lo, molecule, 0)
   float4* pd = nullptr;
+  float4* xhl = nullptr;    // float64 path, per atom: (x, y, z, 0) hi, the same lo (32 bytes)
   float2* dfm = nullptr;    // float64 path: table of the double-float elementary functions
   float4* pos32 = nullptr;
 
@@ -93,7 +94,7 @@ struct amp_ctx {
   long long slab_cap = 0;
 
   // pair data
-  double* T64 = nullptr;
+  float4* C64 = nullptr;
   double* Ep64 = nullptr;
   float* T32 = nullptr;
   float* Ep32 = nullptr;

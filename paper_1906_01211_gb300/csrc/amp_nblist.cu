@@ -545,7 +545,7 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
   if (speculative && !(c->hibuf[2] & (4 | 8))) return AMP_OK;  // filled in place
   if (c->n_full > c->cap_full || c->n_half > c->cap_half) {
     void** bufs[] = {(void**)&c->full_j, (void**)&c->full_ref, (void**)&c->tr_tmp, (void**)&c->half_i, (void**)&c->half_j,
-                     (void**)&c->T64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32,
+                     (void**)&c->C64, (void**)&c->Ep64, (void**)&c->T32, (void**)&c->Ep32,
                      (void**)&c->pos_tr, (void**)&c->intra};
     for (void** b : bufs) {
       dev_free(c, *b);
@@ -559,7 +559,7 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
         (r = dev_alloc(c, &c->pos_tr, caph)) || (r = dev_alloc(c, &c->Ep64, 6 * caph)))
       return r;
     if (c->cfg.precision == AMP_FP64) {
-      if ((r = dev_alloc(c, &c->T64, 6 * capf))) return r;
+      if ((r = dev_alloc(c, &c->C64, capf))) return r;
     } else {
       if ((r = dev_alloc(c, &c->T32, 6 * capf)) || (r = dev_alloc(c, &c->Ep32, 6 * caph))) return r;
     }

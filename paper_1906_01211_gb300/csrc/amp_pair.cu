@@ -235,9 +235,8 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
                                                        const float2* __restrict__ tab,
                                                        const int* __restrict__ full_start,
                                                        const int* __restrict__ half_start,
-                                                       const int* __restrict__ pos_tr, float4* __restrict__ T8,
-                                                       float4* __restrict__ T4, float* __restrict__ Ep,
-                                                       int* __restrict__ intra) {
+                                                       const int* __restrict__ pos_tr, float4* __restrict__ C64,
+                                                       float* __restrict__ Ep, int* __restrict__ intra) {
   const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pid >= nh) return;
   const int i = half_i[pid], j = half_j[pid];
@@ -266,24 +265,14 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
     b2e = b2u;
     b3e = df_sub(B3, df_mul(d7, bare3));
   }
-  // tensor T = -b1u I + b2u r r^T  (xx, yy, zz, xy, xz, yz)
-  const dflt tv[6] = {df_sub(df_mul(df_mul(b2u, R[0]), R[0]), b1u), df_sub(df_mul(df_mul(b2u, R[1]), R[1]), b1u),
-                      df_sub(df_mul(df_mul(b2u, R[2]), R[2]), b1u), df_mul(df_mul(b2u, R[0]), R[1]),
-                      df_mul(df_mul(b2u, R[0]), R[2]),          df_mul(df_mul(b2u, R[1]), R[2])};
-  // the tensor goes to both full-list entries of the pair (the owner's entry
-  // and the transposed one), so that the product kernel reads every row's
-  // tensors contiguously: 32 bytes (one load there) + 16 bytes in a second array
+  // the tensor T = -b1u I + b2u r r^T as its two scalars, in both full-list
+  // entries of the pair (the owner's and the transposed one), so that the
+  // product kernel reads every row's entries contiguously (16 bytes each)
+  // and rebuilds r from the positions as above
   {
-    const float4 t0 = make_float4(tv[0].hi, tv[1].hi, tv[2].hi, tv[3].hi);
-    const float4 t1 = make_float4(tv[4].hi, tv[5].hi, tv[0].lo, tv[1].lo);
-    const float4 t2 = make_float4(tv[2].lo, tv[3].lo, tv[4].lo, tv[5].lo);
-    const long long k1 = full_start[i] + (pid - half_start[i]), k2 = pos_tr[pid];
-    T8[2 * k1] = t0;
-    T8[2 * k1 + 1] = t1;
-    T4[k1] = t2;
-    T8[2 * k2] = t0;
-    T8[2 * k2 + 1] = t1;
-    T4[k2] = t2;
+    const float4 t = make_float4(b1u.hi, b1u.lo, b2u.hi, b2u.lo);
+    C64[full_start[i] + (pid - half_start[i])] = t;
+    C64[pos_tr[pid]] = t;
   }
   // permanent fields: at i from j (r), at j from i (-r)
   dflt mpi[10], mpj[10];
@@ -310,10 +299,11 @@ __global__ void __launch_bounds__(256) k_pair_build_df(long long nh, const int* 
 }
 
 // Per sorted atom s: mp_df[s] = q, d, Theta as hi/lo float pairs (5 float4);
-// pd[s] = (x, y, z, 1/sqrt(alpha)) hi, the same lo, (Thole a hi, lo, molecule, 0).
+// pd[s] = (x, y, z, 1/sqrt(alpha)) hi, the same lo, (Thole a hi, lo, molecule, 0);
+// xhl[s] (if given) = (x, y, z, 0) hi, the same lo.
 __global__ void k_split_multipoles(int n, const double4_32a* __restrict__ A, const double4_32a* __restrict__ B,
                                    const double4_32a* __restrict__ C, const double4_32a* __restrict__ D,
-                                   float4* __restrict__ mp, float4* __restrict__ pd) {
+                                   float4* __restrict__ mp, float4* __restrict__ pd, float4* __restrict__ xhl) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double4_32a a = A[s], b = B[s], c = C[s], d = D[s];
@@ -327,6 +317,10 @@ __global__ void k_split_multipoles(int n, const double4_32a* __restrict__ A, con
     pd[3 * (long long)s] = make_float4(x.hi, y.hi, z.hi, is.hi);
     pd[3 * (long long)s + 1] = make_float4(x.lo, y.lo, z.lo, is.lo);
     pd[3 * (long long)s + 2] = make_float4(th.hi, th.lo, __int_as_float((int)d.w), 0.f);
+    if (xhl) {
+      xhl[2 * (long long)s] = make_float4(x.hi, y.hi, z.hi, 0.f);
+      xhl[2 * (long long)s + 1] = make_float4(x.lo, y.lo, z.lo, 0.f);
+    }
   }
 }
 
@@ -524,17 +518,19 @@ __global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __res
 
 constexpr int kTRealBlocksPerSm = 4;  // of the 5 (float64) or 6 (mixed) that the registers would allow
 
-// out_i = sum_j T_ij v_j + selfc v_i for the float64 path, in double-float:
-// tensors as hi/lo float pairs, stored by the pair build once per full-list
-// entry in entry order (32 bytes in T8, 16 in T4), v as (hi, lo) records
-// vhl. The lanes of a row read consecutive entries, so the tensor loads are
-// contiguous; only v_j is a gather. Tensors are read once per product:
-// streaming loads keep them from evicting the reciprocal-space grids that run
-// beside this kernel. The next entry's neighbour index is fetched one
-// iteration ahead.
+// Real-space T*v of the float64 path in double-float, one row per group of
+// kRowGroup lanes, rows grid-strided. Each full-list entry holds the pair's
+// two tensor scalars (b1, b2: T = -b1 I + b2 r r^T), 16 bytes read in entry
+// order; r = x_i - x_j (minimum image) is rebuilt from the hi/lo positions
+// with the pair build's own operations, and T v_j = b2 (r . v_j) r - b1 v_j.
+// x_j and v_j (32 bytes each, hi/lo) are gathered per entry; they are shared
+// by the ~70 rows that list atom j and stay in L1/L2, so DRAM streams only
+// the 20 bytes per entry. Lanes 0..2 finish one component each in float64 (a
+// float64 instruction holds the float64 pipe as long for one active lane as
+// for 32), adding the self term selfc v_i.
 __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict__ full_start,
-                                                   const int* __restrict__ full_j, const float4* __restrict__ T8,
-                                                   const float4* __restrict__ T4, double selfc,
+                                                   const int* __restrict__ full_j, const float4* __restrict__ C64,
+                                                   const float4* __restrict__ xhl, PairGeomDf g, double selfc,
                                                    const float4* __restrict__ vhl,
                                                    const double4_32a* __restrict__ v64, double4_32a* __restrict__ out,
                                                    const int* __restrict__ stop) {
@@ -542,32 +538,36 @@ __global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict_
   const int l = threadIdx.x % kRowGroup;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup; i < n; i += gridDim.x * (blockDim.x / kRowGroup)) {
     dflt sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f};
+    float4 xih, xil;
+    ld8_ro(xhl + 2 * (long long)i, xih, xil);
     const int e = full_start[i + 1];
     int k = full_start[i] + l;
     int jn = k < e ? __ldcs(full_j + k) : 0;
     for (; k < e; k += kRowGroup) {
       const int j = jn;
       if (k + kRowGroup < e) jn = __ldcs(full_j + k + kRowGroup);
-      float4 a, b, h, w;
-      ld8_stream(T8 + 2 * (long long)k, a, b);
-      const float4 c = __ldcs(T4 + k);
+      const float4 cb = __ldcs(C64 + k);
+      float4 xh, xl, h, w;
+      ld8_ro(xhl + 2 * (long long)j, xh, xl);
       ld8_ro(vhl + 2 * (long long)j, h, w);
-      // hi: xx=a.x yy=a.y zz=a.z xy=a.w xz=b.x yz=b.y; lo: xx=b.z yy=b.w zz=c.x xy=c.y xz=c.z yz=c.w
-      df_fma(sx, a.x, b.z, h.x, w.x);
-      df_fma(sx, a.w, c.y, h.y, w.y);
-      df_fma(sx, b.x, c.z, h.z, w.z);
-      df_fma(sy, a.w, c.y, h.x, w.x);
-      df_fma(sy, a.y, b.w, h.y, w.y);
-      df_fma(sy, b.y, c.w, h.z, w.z);
-      df_fma(sz, b.x, c.z, h.x, w.x);
-      df_fma(sz, b.y, c.w, h.y, w.y);
-      df_fma(sz, a.z, c.x, h.z, w.z);
+      const dflt r0 = min_image_df(df_sub({xih.x, xil.x}, {xh.x, xl.x}), g);
+      const dflt r1 = min_image_df(df_sub({xih.y, xil.y}, {xh.y, xl.y}), g);
+      const dflt r2 = min_image_df(df_sub({xih.z, xil.z}, {xh.z, xl.z}), g);
+      dflt rv = df_mul(r0, {h.x, w.x});
+      df_fma(rv, r1.hi, r1.lo, h.y, w.y);
+      df_fma(rv, r2.hi, r2.lo, h.z, w.z);
+      const dflt q = df_mul({cb.z, cb.w}, rv);  // b2 (r . v)
+      const float nbh = -cb.x, nbl = -cb.y;     // -b1
+      df_fma(sx, q.hi, q.lo, r0.hi, r0.lo);
+      df_fma(sx, nbh, nbl, h.x, w.x);
+      df_fma(sy, q.hi, q.lo, r1.hi, r1.lo);
+      df_fma(sy, nbh, nbl, h.y, w.y);
+      df_fma(sz, q.hi, q.lo, r2.hi, r2.lo);
+      df_fma(sz, nbh, nbl, h.z, w.z);
     }
     sx = df_group_sum(sx);
     sy = df_group_sum(sy);
     sz = df_group_sum(sz);
-    // lanes 0..2 convert one component each: a float64 instruction holds the
-    // float64 pipe as long for one active lane as for 32
     if (l < 4) {
       double* o = reinterpret_cast<double*>(out + i);
       if (l < 3) {
@@ -703,7 +703,7 @@ void launch_pair_build(amp_ctx* c) {
   // so they are made even when there are no pairs
   c->n_launch += 1;
   k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
-                                                                  c->mp_df, c->pd);
+                                                                  c->mp_df, c->pd, c->xhl);
   if (c->cfg.precision == AMP_FP64) cudaMemsetAsync(c->e0intra, 0, sizeof(double4_32a) * c->n, c->stream);
   if (c->n_half == 0) return;
   const PairGeom g = geom(c);
@@ -713,9 +713,7 @@ void launch_pair_build(amp_ctx* c) {
     const PairGeomDf gd = geom_df(g);
     cudaMemsetAsync(c->intra, 0, sizeof(int), c->stream);
     k_pair_build_df<<<blocks, 256, 0, c->stream>>>(c->n_half, c->half_i, c->half_j, c->pd, c->mp_df, gd, c->dfm,
-                                                   c->full_start, c->half_start, c->pos_tr,
-                                                   reinterpret_cast<float4*>(c->T64),
-                                                   reinterpret_cast<float4*>(c->T64) + 2 * c->cap_full,
+                                                   c->full_start, c->half_start, c->pos_tr, c->C64,
                                                    reinterpret_cast<float*>(c->Ep64), c->intra);
     c->n_launch += 1;
     k_intra_fields64<<<4 * c->n_sm, 128, 0, c->stream>>>(c->intra, c->half_i, c->half_j, g, c->atomA, c->atomB,
@@ -748,7 +746,7 @@ void launch_intra_scaled(amp_ctx* c, double s, double4_32a* out) {
 void launch_split_multipoles(amp_ctx* c) {
   c->n_launch += 1;
   k_split_multipoles<<<amp_blocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->atomA, c->atomB, c->atomC, c->atomD,
-                                                                  c->mp_df, c->pd);
+                                                                  c->mp_df, c->pd, c->xhl);
 }
 
 // Real-space permanent field with the self term +4 beta^3/(3 sqrt(pi)) d_i (d_i from atomB).
@@ -776,9 +774,8 @@ void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out) {
   // otherwise wait for whole blocks of this kernel to finish.
   const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256),
                                           (long long)kTRealBlocksPerSm * c->n_sm);
-  k_t_real_df<<<tb, 256, 0, c->stream>>>(
-      c->n, c->full_start, c->full_j, reinterpret_cast<const float4*>(c->T64),
-      reinterpret_cast<const float4*>(c->T64) + 2 * c->cap_full, g.selfc, c->vhl, v, out, c->op_stop);
+  k_t_real_df<<<tb, 256, 0, c->stream>>>(c->n, c->full_start, c->full_j, c->C64, c->xhl, geom_df(g), g.selfc,
+                                         c->vhl, v, out, c->op_stop);
 }
 
 void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, double4_32a* out) {

@@ -87,7 +87,7 @@ long long estimate_bytes(const Request& r, int precision) {
   if (r.box <= 0.0) return n * 2048 + (16LL << 20);
   const double density = (double)n / (r.box * r.box * r.box);
   const long long half = (long long)(n * 2.0 * M_PI / 3.0 * r.cutoff * r.cutoff * r.cutoff * density) + 1024;
-  const long long per_pair = precision == AMP_MIXED ? 4 * (4 + 4 + 4) + 2 * 24 + 24 + 24 : 4 * (4 + 4 + 4) + 2 * 48 + 48;
+  const long long per_pair = precision == AMP_MIXED ? 4 * (4 + 4 + 4) + 2 * 24 + 24 + 24 : 4 * (4 + 4 + 4) + 2 * 16 + 48;
   const long long K = r.grid, ng = K * K * K, nh = K * K * (K / 2 + 1);
   const long long grids = ng * (8 * 4 + 8 + 4 * 3) + nh * (16 * 3 + 8 * 3);
   return (n * 2048 + half * per_pair) * 5 / 4 + grids + (16LL << 20);
