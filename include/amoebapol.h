@@ -215,6 +215,29 @@ int amp_forces(amp_ctx* ctx, const double* mu, double* F, double* gq, double* gd
 int amp_tcg1(amp_ctx* ctx, const double* E0, double* mu, double* U, double* F, double* gq, double* gdip,
              double* gquad);
 
+/* Divide-and-conquer Jacobi iterations (DC-JI), the polarization solver the
+ * paper's outlook names for the outer level of its multi-timestep integrator
+ * (Section "Perspectives on Tinker-HP 1.2 performance"; Nocito & Beran 2018).
+ * The sites are split into blocks (whole molecules, as the caller chooses);
+ * every iteration solves each block's own equations exactly with the other
+ * blocks' dipoles from the previous iteration:
+ *   mu <- mu + D^-1 (E0 - A mu),  mu^(0) = alpha E0,
+ * D the block diagonal of A = diag(1/alpha) - T (real space, reciprocal space
+ * and self term), until 4.8032047 sqrt(sum |alpha (E0 - A mu)_i|^2 / N) < tol
+ * or max_iter iterations (the solver's criterion).
+ *   E0       [N][3] the permanent field (device, caller order);
+ *   block_of [N] block index of each site in [0, n_blocks) (host, caller
+ *            order); every block must have a site, else AMP_ERR_ARG;
+ *   mu       [N][3] the dipoles on return (device, caller order);
+ *   iters, rms_debye: iterations done and the final RMS (host, may be NULL).
+ * D is assembled from the context's operator one column at a time (3N
+ * operator applications), then each block is symmetrised and factorised by
+ * Cholesky in float64 (AMP_ERR_NOT_CONVERGED if one is not positive
+ * definite); for small systems. Float64 contexts only; allocates and frees
+ * its buffers and synchronises the stream. */
+int amp_dcji(amp_ctx* ctx, const double* E0, const int* block_of, int n_blocks, double tol_debye, int max_iter,
+             double* mu, int* iters, double* rms_debye);
+
 /* Energy of the permanent multipoles with each other and its gradients (paper,
  * Section "Hotspots": routine empole1 computes this energy and its forces).
  * Ewald sum with tin-foil boundary:

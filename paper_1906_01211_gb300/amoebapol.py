@@ -127,6 +127,7 @@ def _load() -> ctypes.CDLL:
         "amp_set_predictor": (I, [P, I]),
         "amp_predictor_coefficients": (I, [I, ctypes.POINTER(D)]),
         "amp_tcg1": (I, [P, P, P, ctypes.POINTER(D), P, P, P, P]),
+        "amp_dcji": (I, [P, P, P, I, D, I, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "amp_permanent_field_scaled": (I, [P, D, P]),
         "amp_two_rhs_forces": (I, [P, D, P, P, P, P, P, P]),
         "amp_frames_to_global": (I, [I, P, P, P, P, P, P, P, P, P]),
@@ -254,6 +255,43 @@ def amp_tcg1(ctx, E0, mu=None, F=None, gq=None, gdip=None, gquad=None) -> float:
     u = ctypes.c_double(0.0)
     _check(ctx, _lib.amp_tcg1(ctx, E0, mu, ctypes.byref(u), F, gq, gdip, gquad))
     return u.value
+
+
+def amp_dcji(ctx, E0, block_of, n_blocks: int, tol_debye: float, max_iter: int, mu) -> tuple[int, float]:
+    """DC-JI into mu (device pointers E0, mu; block_of a host int32 array):
+    (iterations, final RMS in Debye)."""
+    import numpy as np
+    b = np.ascontiguousarray(block_of, dtype=np.int32)
+    it = ctypes.c_int(0)
+    rms = ctypes.c_double(0.0)
+    _check(ctx, _lib.amp_dcji(ctx, E0, b.ctypes.data, int(n_blocks), float(tol_debye), int(max_iter), mu,
+                              ctypes.byref(it), ctypes.byref(rms)))
+    return it.value, rms.value
+
+
+def cell_blocks(xyz, mol, box: float, cells_per_axis: int):
+    """Blocks of whole molecules for DC-JI: (block_of [N], n_blocks). A
+    regular grid of cells_per_axis^3 cells over the box (box > 0) or over the
+    bounding cube of the sites (box = 0); each molecule goes to the cell of
+    its first site; empty cells are dropped and the remaining blocks are
+    numbered in cell order."""
+    import numpy as np
+    xyz = np.asarray(xyz, dtype=np.float64)
+    mol = np.asarray(mol)
+    n = xyz.shape[0]
+    if box > 0.0:
+        L, lo = float(box), np.zeros(3)
+    else:
+        L, lo = float(np.ptp(xyz, axis=0).max()) + 1e-9, xyz.min(axis=0)
+    _, first = np.unique(mol, return_index=True)
+    u = (xyz[first] - lo) / L
+    if box > 0.0:
+        u = u - np.floor(u)
+    c = np.minimum((u * cells_per_axis).astype(np.int64), cells_per_axis - 1)
+    key_of_mol = dict(zip(mol[first].tolist(), ((c[:, 0] * cells_per_axis + c[:, 1]) * cells_per_axis + c[:, 2]).tolist()))
+    keys = np.array([key_of_mol[m] for m in mol.tolist()], dtype=np.int64)
+    used, block_of = np.unique(keys, return_inverse=True)
+    return block_of.astype(np.int32).reshape(n), int(used.size)
 
 
 def amp_multipole_energy(ctx, F=None, gq=None, gdip=None, gquad=None) -> float:
@@ -556,6 +594,15 @@ class Polarization:
         U = amp_tcg1(self.ctx, E0.data_ptr(), mu.data_ptr(), F.data_ptr(), gq.data_ptr(), gd.data_ptr(),
                      gt.data_ptr())
         return mu, U, F, gq, gd, gt
+
+    def dcji(self, E0, block_of, n_blocks: int, tol_debye: float = 1e-8, max_iter: int = 200):
+        """DC-JI (block Jacobi over blocks of whole molecules, block_of from
+        cell_blocks): (mu, iterations, final RMS in Debye)."""
+        torch = self.torch
+        E0 = self._dev(E0, torch.float64)
+        mu = torch.empty_like(E0)
+        it, rms = amp_dcji(self.ctx, E0.data_ptr(), block_of, n_blocks, tol_debye, max_iter, mu.data_ptr())
+        return mu, it, rms
 
     def multipole_energy(self, gradients: bool = True):
         """Permanent-multipole energy U (kcal/mol) and, if asked, (F, dU/dq, dU/dd,

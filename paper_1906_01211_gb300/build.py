@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libamoebapol.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["amp_api.cu", "amp_nblist.cu", "amp_pair.cu", "amp_pme.cu", "amp_pcg.cu", "amp_forces.cu", "amp_mpole.cu", "amp_cluster.cu", "amp_fft.cu", "amp_noalloc.cu", "amp_batch.cu", "amp_server.cu", "amp_tcg.cu", "amp_frames.cu"]
+SOURCES = ["amp_api.cu", "amp_nblist.cu", "amp_pair.cu", "amp_pme.cu", "amp_pcg.cu", "amp_forces.cu", "amp_mpole.cu", "amp_cluster.cu", "amp_fft.cu", "amp_noalloc.cu", "amp_batch.cu", "amp_server.cu", "amp_tcg.cu", "amp_frames.cu", "amp_dcji.cu"]
 
 
 def _nvcc() -> str:
