@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libamoebapol.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["amp_api.cu", "amp_nblist.cu", "amp_pair.cu", "amp_pme.cu", "amp_pcg.cu", "amp_forces.cu", "amp_mpole.cu", "amp_cluster.cu", "amp_fft.cu", "amp_noalloc.cu", "amp_batch.cu", "amp_server.cu", "amp_tcg.cu", "amp_frames.cu", "amp_dcji.cu"]
+SOURCES = ["amp_api.cu", "amp_nblist.cu", "amp_pair.cu", "amp_pme.cu", "amp_pcg.cu", "amp_forces.cu", "amp_mpole.cu", "amp_cluster.cu", "amp_fft.cu", "amp_fft_df.cu", "amp_fft_df_hi.cu", "amp_fft_f32.cu", "amp_fft_f64.cu", "amp_noalloc.cu", "amp_batch.cu", "amp_server.cu", "amp_tcg.cu", "amp_frames.cu", "amp_dcji.cu"]
 
 
 def _nvcc() -> str:
@@ -57,7 +57,7 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     """Compile and link; returns the library path."""
     os.makedirs(OBJ, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + \
-        [os.path.join(CSRC, "amp_internal.cuh"), os.path.join(CSRC, "amp_batch.cuh"),
+        [os.path.join(CSRC, "amp_internal.cuh"), os.path.join(CSRC, "amp_batch.cuh"), os.path.join(CSRC, "amp_fft.cuh"),
          os.path.join(INCLUDE, "amoebapol.h")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(s) for s in srcs)

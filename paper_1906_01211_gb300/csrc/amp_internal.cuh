@@ -115,7 +115,7 @@ struct amp_ctx {
   // max |hi component| of the last split vector: [0, kReduceBlocks) per block,
   // [kReduceBlocks] the whole vector, [kReduceBlocks + 1] arrival counter
   float* vmax_part = nullptr;
-  float4* fft_grid = nullptr;  // double-float complex half spectrum of the own FFT (power-of-two K)
+  float4* fft_grid = nullptr;  // double-float complex half spectrum of the own FFT (its grids)
   float2* fft_G = nullptr;     // influence function on that half spectrum, hi/lo
   float4* fft_tw = nullptr;    // twiddles (cos hi, lo, sin hi, lo)
   // mixed path's float32 reciprocal chain: spreading grid (kept at zero
@@ -267,9 +267,10 @@ int pme_setup(amp_ctx* c);
 int pme_alloc_atoms(amp_ctx* c, int n_cap);
 int pme_influence(amp_ctx* c);
 
-// own 3D FFT convolution (amp_fft.cu), power-of-two grids up to 64
+// own 3D FFT convolution (amp_fft.cuh): even 2,3,5-smooth grids from 16 to 128 (the list in amp_fft.cuh)
 bool fft_own_supported(int K);
 int fft_own_setup(amp_ctx* c);  // buffers and twiddles (K only); G comes from pme_influence
+constexpr int kOwnF32MaxK = 64;  // the mixed operator's own float32 FFT up to this grid, cuFFT above
 void fft_df_convolve(amp_ctx* c, cudaStream_t st);   // gridfx (zeroed on the way) -> phi_df, double-float
 void fft_f32_convolve(amp_ctx* c, cudaStream_t st);  // spread32 (zeroed on the way) -> phi32, float32
 void fft_f64_convolve(amp_ctx* c, cudaStream_t st, double* grid, double* phi);  // grid (zeroed on the way) -> phi

@@ -14,8 +14,8 @@
 // gathered in float64 (float64 atomics, cuFFT float64). The dipoles of every
 // T*mu (the mixed path's are its float32 operator input) are spread in
 // double-float into a 64-bit fixed-point grid, transformed by the
-// double-float FFT of amp_fft.cu on power-of-two grids (else cuFFT float64, a
-// library call, and a split) and gathered in double-float. The force kernels'
+// double-float FFT of amp_fft.cuh on even 2,3,5-smooth grids up to 128 (else
+// cuFFT float64, a library call, and a split) and gathered in double-float. The force kernels'
 // potentials use float64 (float32 in the mixed path) atomics and cuFFT.
 // |b(m)|^2 = 1/|sum_{k=0}^{3} M5(k+1) e^{2 pi i m k/K}|^2; where that sum
 // vanishes (m = K/2, even K) the mean of the neighbours m-1, m+1 is used.
@@ -899,7 +899,7 @@ int pme_geometry(amp_ctx* c) {
     launch_pme_theta(c, c->side);
     pme_theta64(c, c->side);
     const double* phi = c->grid64;
-    if (c->fft_grid64) {  // power-of-two grid: the own float64 FFT, which zeroes spread64 as it reads it
+    if (c->fft_grid64) {  // a grid of the own FFT: its float64 variant, which zeroes spread64 as it reads it
       c->n_launch += 1;
       k_spread_multipoles64<<<amp_blocks((long long)c->n * kOrder * kOrder, 256), 256, 0, c->side>>>(
           c->n, c->theta, c->gbase, c->atomA, c->atomB, c->atomC, c->atomD, c->K, c->spread64);
@@ -1000,7 +1000,7 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
 
 // Reciprocal field of the float32 dipoles v32 in float32 (the mixed path's
 // operator; its float64 residual check takes the double-float chain): float
-// atomics into spread32, the own float32 FFT on power-of-two grids up to 64
+// atomics into spread32, the own float32 FFT on its grids up to kOwnF32MaxK
 // (which zeroes spread32 as it reads it), else cuFFT R2C / C2R float32 with
 // spread32 cleared first, then the float32 gather; out (+)= -grad phi.
 int pme_dipole_field32(amp_ctx* c, const float4* v32, double4_32a* out, cudaStream_t st, bool set) {

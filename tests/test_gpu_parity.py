@@ -139,10 +139,13 @@ def test_small_boxes_ragged_sizes(nw, seed):
     assert abs(U / case.U - 1) < 1e-10
 
 
-@pytest.mark.parametrize("nw,K", [(1000, 32), (300, 16)])
-def test_power_of_two_grids(nw, K):
-    """Grids whose size is a power of two take the float64 path's own
-    double-float FFT; other sizes (24, 15, ...) take cuFFT."""
+@pytest.mark.parametrize("nw,K", [(300, 16), (300, 18), (300, 20), (300, 30), (1000, 32), (300, 36), (300, 40),
+                                  (500, 48), (500, 50), (1000, 60), (300, 72), (300, 80), (300, 96), (300, 100),
+                                  (300, 120), (300, 128)])
+def test_own_fft_grids(nw, K):
+    """Even 2,3,5-smooth grids from 16 to 128 take the own FFT (radix 4, 2,
+    5 and 3 stages; clusters of 2 to 8 CTAs per plane): E0 (float64 variant),
+    T*mu (double-float variant) and the solve against the oracle."""
     L = density_box_edge(nw)
     rc, beta, _ = small_box_settings(L)
     case = Case(make_waters(nw, L, 40 + K), L, rc, beta, K, 1e-10)
@@ -151,6 +154,19 @@ def test_power_of_two_grids(nw, K):
     v = np.random.default_rng(K).normal(size=(case.sys.n, 3)) * 0.1
     assert_fields(s.apply_T(torch.tensor(v)).cpu().numpy(), case.op.apply_T(v), 1e-12)
     assert_dipoles(mu, case.mu, 1e-8)
+
+
+@pytest.mark.parametrize("nw,K", [(300, 48), (300, 72)])
+def test_mixed_own_and_library_fft_grids(nw, K):
+    """The mixed operator's float32 chain takes the own FFT up to K = 64 and
+    cuFFT above; its float64 check takes the own double-float FFT on both."""
+    L = density_box_edge(nw)
+    rc, beta, _ = small_box_settings(L)
+    case = Case(make_waters(nw, L, 60 + K), L, rc, beta, K, 1e-8)
+    s, E0, mu, it, rms, U = run_gpu(case, "mixed")
+    assert rms < case.tol
+    assert_dipoles(mu, case.mu, 1e-5, 5.0)
+    assert abs(U / case.U - 1) < 1e-6
 
 
 def test_isolated_atoms_have_empty_rows():
