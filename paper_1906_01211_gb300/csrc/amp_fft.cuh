@@ -272,20 +272,36 @@ __device__ __forceinline__ void line_fft(typename Tr::S* x, typename Tr::S* w, c
   }
 }
 
-// ---- the plane passes: one cluster of kClus CTAs per x plane (kClus the
-// largest divisor of K/2 up to 8). CTA r owns the packed rows y' in
-// [r R, (r + 1) R) (R = K / (2 kClus)) for the z transforms and the
-// half-spectrum lines mz in [mz_lo(r), mz_lo(r + 1)) for the y transforms;
-// the values that cross over are read from the other CTAs' shared memory
-// (distributed shared memory) between two cluster barriers. Shared memory is
-// dynamic (above 48 KB for the larger grids).
-__host__ __device__ constexpr int clus_of(int half) {
-  return half % 8 == 0 ? 8 : (half % 7 == 0 ? 7 : (half % 6 == 0 ? 6 : (half % 5 == 0 ? 5 : (half % 4 == 0 ? 4 : (half % 3 == 0 ? 3 : (half % 2 == 0 ? 2 : 1))))));
+// ---- the plane passes: one cluster of kClus CTAs per x plane. CTA r owns
+// the packed rows y' in [r R, (r + 1) R) (R = K / (2 kClus)) for the z
+// transforms and the half-spectrum lines mz in [mz_lo(r), mz_lo(r + 1)) for
+// the y transforms; the values that cross over are read from the other CTAs'
+// shared memory (distributed shared memory) between two cluster barriers.
+// kClus divides K/2 and keeps a CTA at six warps or fewer (max(R, M) <= 6):
+// the largest such divisor up to 8, else the smallest one up to 16 (a
+// non-portable cluster size, opted into at launch), else the largest divisor
+// up to 16. Small CTAs matter in the solve, where the plane passes run
+// beside the real-space kernel, which keeps ~49k of an SM's 64k registers:
+// a 352-thread CTA of 56 registers does not fit beside it, a 192-thread one
+// does. Shared memory is dynamic.
+__host__ __device__ constexpr int warps_of(int K, int d) {
+  return (K / 2 / d) > ((K / 2 + 1 + d - 1) / d) ? (K / 2 / d) : ((K / 2 + 1 + d - 1) / d);
+}
+__host__ __device__ constexpr int clus_of(int K) {
+  int best = 1;
+  for (int d = 1; d <= 8; ++d)
+    if ((K / 2) % d == 0 && warps_of(K, d) <= 6) best = d;
+  if (warps_of(K, best) <= 6) return best;
+  for (int d = 9; d <= 16; ++d)
+    if ((K / 2) % d == 0 && warps_of(K, d) <= 6) return d;
+  for (int d = 16; d >= 1; --d)
+    if ((K / 2) % d == 0) return d;
+  return 1;
 }
 
 template <int K>
 struct Plane {
-  static constexpr int kClus = clus_of(K / 2);
+  static constexpr int kClus = clus_of(K);
   static constexpr int kH = K / 2 + 1;               // half-spectrum lines
   static constexpr int R = K / 2 / kClus;            // packed rows per CTA
   static constexpr int M = (kH + kClus - 1) / kClus;  // at most this many mz lines per CTA
@@ -317,7 +333,7 @@ constexpr size_t smem_inv() {
 // 2^fx_info[0] in double-float, float in float32, double in float64),
 // zeroed once read so that the next spreading starts from zero.
 template <int K, typename Tr>
-__global__ void __cluster_dims__(Plane<K>::kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
+__global__ void __launch_bounds__(Plane<K>::NT)
     k_fft_plane_fwd(typename Tr::In* __restrict__ q, const int* __restrict__ fx_info, typename Tr::S* __restrict__ H,
                     const typename Tr::T* __restrict__ tw_g, const int* __restrict__ stop) {
   namespace cg = cooperative_groups;
@@ -423,7 +439,7 @@ __global__ void __launch_bounds__(32 * kLinesB) k_fft_x_conv(typename Tr::S* __r
 // Pass C: inverse y transforms of plane x, the real z lines rebuilt pairwise,
 // inverse z transforms; phi[x][y][z].
 template <int K, typename Tr>
-__global__ void __cluster_dims__(Plane<K>::kClus, 1, 1) __launch_bounds__(Plane<K>::NT)
+__global__ void __launch_bounds__(Plane<K>::NT)
     k_fft_plane_inv(const typename Tr::S* __restrict__ H, typename Tr::P* __restrict__ phi,
                     const typename Tr::T* __restrict__ tw_g, const int* __restrict__ stop) {
   namespace cg = cooperative_groups;
@@ -480,24 +496,50 @@ __global__ void __cluster_dims__(Plane<K>::kClus, 1, 1) __launch_bounds__(Plane<
   }
 }
 
-// The three passes on stream st (the opt-in to more than 48 KB of dynamic
-// shared memory is made once per instantiation).
+// A plane pass: clusters of kClus CTAs along x, programmatic dependent
+// launch as launch_pdl.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plane(void (*kernel)(KArgs...), int clus, dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = (unsigned)clus;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// The three passes on stream st (the opt-ins to more than 48 KB of dynamic
+// shared memory and to clusters above 8 CTAs are made once per
+// instantiation).
 template <int K, typename Tr>
 void run_conv(amp_ctx* c, cudaStream_t st, typename Tr::In* grid, const int* fx_info, typename Tr::S* H,
               const typename Tr::T* tw, const typename Tr::G* G, typename Tr::P* phi, const int* stop) {
   static_assert(K % 2 == 0 && smooth(K), "even 2^a 3^b 5^c grids only");
-  constexpr int kGroups = K / kLinesB;
+  constexpr int kGroups = K / kLinesB, kC = Plane<K>::kClus;
   constexpr size_t sa = smem_fwd<K, Tr>(), sc = smem_inv<K, Tr>();
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_fft_plane_fwd<K, Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(k_fft_plane_inv<K, Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    if (kC > 8) {
+      cudaFuncSetAttribute(k_fft_plane_fwd<K, Tr>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      cudaFuncSetAttribute(k_fft_plane_inv<K, Tr>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
   });
   c->n_launch += 3;
-  launch_pdl(k_fft_plane_fwd<K, Tr>, dim3(K * Plane<K>::kClus), dim3(Plane<K>::NT), sa, st, grid, fx_info, H, tw,
-             stop);
+  launch_plane(k_fft_plane_fwd<K, Tr>, kC, dim3(K * kC), dim3(Plane<K>::NT), sa, st, grid, fx_info, H, tw, stop);
   launch_pdl(k_fft_x_conv<K, Tr>, dim3((K / 2 + 1) * kGroups), dim3(32 * kLinesB), 0, st, H, tw, G, stop);
-  launch_pdl(k_fft_plane_inv<K, Tr>, dim3(K * Plane<K>::kClus), dim3(Plane<K>::NT), sc, st, H, phi, tw, stop);
+  launch_plane(k_fft_plane_inv<K, Tr>, kC, dim3(K * kC), dim3(Plane<K>::NT), sc, st, H, phi, tw, stop);
 }
 
 // The supported grid sizes (even, 2^a 3^b 5^c, 16 .. 128; the others use

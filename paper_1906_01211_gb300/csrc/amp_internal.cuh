@@ -43,6 +43,7 @@ constexpr double kDebye = 4.8032047;
 constexpr double kCoulomb = 332.0637133;
 constexpr double kSqrtPi = 1.7724538509055160273;
 constexpr int kRowGroup = 16;       // lanes that share one neighbour row
+constexpr int kTRealForkAtoms = 48000;  // float64 path: the real-space kernel starts at the fork from here on
 constexpr int kForcePairStride = 24;  // backward per-pair record (doubles)
 constexpr int kForceAtomStride = 16;  // backward per-atom reciprocal record (doubles)
 constexpr int kReduceBlocks = 296;  // 2 x 152 SMs: blocks of the PCG kernels

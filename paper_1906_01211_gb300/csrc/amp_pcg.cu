@@ -471,6 +471,24 @@ enum RealMode { kRealDf, kRealF32, kRealDirectDf };
 // reciprocal part is the double-float chain for the float64 path and the
 // mixed path's float64 check (kRealDirectDf, which first splits v into
 // (p32, plo) for both parts), the float32 chain for the mixed operator.
+// Whether the real-space kernel waits for the reciprocal chain's spreading
+// (it then shares the GPU with the latency-bound FFT passes rather than with
+// the spreading, which fills every SM) or starts at the fork. The chain's
+// kernels are launched early (programmatic dependent launch) and hold their
+// SM resources while they wait for the kernel before them; on large grids
+// these are many cluster CTAs, and a real-space kernel that starts after the
+// spreading finds the SMs taken. Measured (float64 path): water-23556
+// (K = 64) solve 0.92 ms after the spreading, 1.03 ms from the fork;
+// water-96000 (K = 100) 4.22 ms after the spreading, 2.95 ms from the fork.
+// The mixed operator's chain on large grids is cuFFT's, launched the
+// ordinary way: after the spreading at both sizes (1.94 vs 2.17 ms at
+// water-96000). The float64 residual check starts it at the fork.
+static bool real_after_spread(const amp_ctx* c, RealMode mode) {
+  if (mode == kRealDirectDf) return false;
+  if (mode == kRealDf) return c->n < kTRealForkAtoms;
+  return true;
+}
+
 static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, const float4* vlo, double4_32a* t,
                        double4_32a* t2, RealMode mode) {
   int r;
@@ -484,7 +502,7 @@ static int fork_join_T(amp_ctx* c, const double4_32a* v, const float4* v32, cons
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     {
       PhaseScope ps(c, AMP_PHASE_T_RECIP, c->side);
-      c->spread_event = mode != kRealDirectDf;
+      c->spread_event = real_after_spread(c, mode);
       r = mode == kRealF32 ? pme_dipole_field32(c, v32, t2, c->side, true)
                            : pme_dipole_field(c, v, v32, vlo, t2, c->side, true);
       if (c->spread_event) cudaStreamWaitEvent(c->stream, c->ev_spread, 0);
