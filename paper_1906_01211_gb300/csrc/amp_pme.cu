@@ -331,19 +331,12 @@ __device__ __forceinline__ int fixed_scale(float m, float sc, int cmax) {
   return fixed_scale_bound(3.f * sc * m * (float)cmax);
 }
 
-// round(f * 2^s) (ties toward +infinity) as a 64-bit integer, by integer
-// operations on the bits of f: the signed significand m (24 bits) times 2^sh,
-// shifted left when sh >= 0 and otherwise rounded off in 32-bit arithmetic.
-// Finite f only; zero and subnormals (below the grid's resolution) give 0.
+// round(f * 2^s) to the nearest 64-bit integer (ties to even), by the
+// conversion instruction: -60 <= s <= 120 makes 2^s an exact float, the
+// product is exact while it is a normal float, and fixed_scale keeps it
+// below 2^61 in magnitude; products below 2^-126 round to 0 either way.
 __device__ __forceinline__ long long to_fixed(float f, int s) {
-  const unsigned u = __float_as_uint(f);
-  const int e = (int)((u >> 23) & 0xffu);
-  const int m0 = e ? (int)((u & 0x7fffffu) | 0x800000u) : 0;
-  const int m = (u >> 31) ? -m0 : m0;
-  const int sh = e - 150 + s;
-  if (sh >= 0) return (long long)m << min(sh, 39);
-  const int k = min(-sh, 30);  // |m| < 2^24: from 2^-30 on the value rounds to 0
-  return (long long)((m + (1 << (k - 1))) >> k);
+  return __float2ll_rn(f * __int_as_float((127 + s) << 23));
 }
 
 // Q(g) = sum_i mu_i . grad W_i(g) with mu = v32 + vlo. One thread per
