@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(Plane<K>::NT)
   using S = typename Tr::S;
   using T = typename Tr::T;
   constexpr int kH = PL::kH, R = PL::R, NT = PL::NT, kC = PL::kClus;
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;  // the same for every CTA of the cluster
-  pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tw = reinterpret_cast<T*>(smem_raw);
@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(32 * kLinesB) k_fft_x_conv(typename Tr::S* __r
                                                             const typename Tr::G* __restrict__ Gh,
                                                             const int* __restrict__ stop) {
   using Rl = typename Tr::R;
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;
-  pdl_wait();
   pdl_trigger();
   constexpr int kH = K / 2 + 1, kGroups = K / kLinesB;
   __shared__ typename Tr::T tw[K];
@@ -458,8 +458,8 @@ __global__ void __launch_bounds__(Plane<K>::NT)
   using S = typename Tr::S;
   using T = typename Tr::T;
   constexpr int kH = PL::kH, R = PL::R, NT = PL::NT, kC = PL::kClus;
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;
-  pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tw = reinterpret_cast<T*>(smem_raw);

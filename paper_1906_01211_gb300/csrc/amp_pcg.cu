@@ -286,8 +286,8 @@ __global__ void __launch_bounds__(NT) k_cg_dots(int n, const double4_32a* __rest
                                                 const double4_32a* __restrict__ t2, const double2* __restrict__ al,
                                                 double4_32a* __restrict__ w, double* __restrict__ part,
                                                 const int* __restrict__ fl) {
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (fl[F_STOP]) return;
-  pdl_wait();
   pdl_trigger();
   double rz = 0.0, zw = 0.0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -311,8 +311,8 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
                                                 double* __restrict__ part,
                                                 float* __restrict__ vmax, double* __restrict__ scal,
                                                 int* __restrict__ fl, double tol, int max_iter) {
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (fl[F_STOP]) return;
-  pdl_wait();
   pdl_trigger();
   double rho, m;
   reduce_partials(part, vec_blocks(n), rho, m);

@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles_fx(int n, con
                                                                       int* __restrict__ fx_info, float sc, int K,
                                                                       unsigned long long* __restrict__ grid,
                                                                       const int* __restrict__ stop) {
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;
-  pdl_wait();
   pdl_trigger();
   const int sfx = fixed_scale(vmax[kReduceBlocks], sc, kOrder * kOrder * kOrder * fx_info[1]);
   if (blockIdx.x == 0 && threadIdx.x == 0) fx_info[0] = sfx;
@@ -439,8 +439,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_field_df(int n, const
                                                                      const float2* __restrict__ phi, int K,
                                                                      double4_32a* __restrict__ out,
                                                                      const int* __restrict__ stop) {
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;
-  pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31, seg = lane / kOrder, tz = lane - seg * kOrder;
   const int warp = (blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
@@ -565,8 +565,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread_dipoles32(int n, cons
                                                                      const float4* __restrict__ v32, int K,
                                                                      float* __restrict__ grid,
                                                                      const int* __restrict__ stop) {
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;
-  pdl_wait();
   pdl_trigger();
   const long long item = (long long)blockIdx.x * kSpreadThreads + threadIdx.x;
   if (item >= (long long)n * (kOrder * kOrder)) return;
@@ -605,8 +605,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_field32(int n, const 
                                                                     const float* __restrict__ phi, int K,
                                                                     double4_32a* __restrict__ out,
                                                                     const int* __restrict__ stop) {
+  pdl_wait();  // first: a kernel never completes before the one it depends on
   if (stop && *stop) return;
-  pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31, seg = lane / kOrder, tz = lane - seg * kOrder;
   const int warp = (blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
@@ -971,9 +971,11 @@ int pme_dipole_field(amp_ctx* c, const double4_32a* v, const float4* v32, const 
   if (!v32) return fail(c, AMP_ERR_STATE, "reciprocal field needs the float split of the vector");
   {
     PhaseScope ps(c, AMP_PHASE_T_SPREAD, st);
-    launch_pdl(k_spread_dipoles_fx, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
-               dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info,
-               (float)((double)K / c->cfg.box), K, c->gridfx, c->op_stop);
+    // an ordinary launch: the chain starts behind an event wait (the fork),
+    // and nothing should depend on how a dependent launch treats one
+    k_spread_dipoles_fx<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
+        n, c->theta_df, c->gbase, v32, vlo, c->vmax_part, c->fx_info, (float)((double)K / c->cfg.box), K,
+        c->gridfx, c->op_stop);
   }
   if (c->spread_event) cudaEventRecord(c->ev_spread, st);
   bool split = true;
@@ -1005,8 +1007,8 @@ int pme_dipole_field32(amp_ctx* c, const float4* v32, double4_32a* out, cudaStre
   c->n_launch += 2;
   {
     PhaseScope ps(c, AMP_PHASE_T_SPREAD, st);
-    launch_pdl(k_spread_dipoles32, dim3(amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads)),
-               dim3(kSpreadThreads), 0, st, n, c->theta_df, c->gbase, v32, K, c->spread32, c->op_stop);
+    k_spread_dipoles32<<<amp_blocks((long long)n * kOrder * kOrder, kSpreadThreads), kSpreadThreads, 0, st>>>(
+        n, c->theta_df, c->gbase, v32, K, c->spread32, c->op_stop);
   }
   if (c->spread_event) cudaEventRecord(c->ev_spread, st);
   {
