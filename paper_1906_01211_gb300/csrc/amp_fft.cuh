@@ -185,7 +185,7 @@ __device__ __forceinline__ dflt grid_in(const unsigned long long* q, long long g
 __device__ __forceinline__ float grid_in(const float* q, long long g, int) { return q[g]; }
 
 // ---- the line transform
-// Radix of the stage with m points left to factor on a line of K: 4, then
+// Radix of the stage with m points of the line left to factor: 4, then
 // 2, 5, 3. At K = 64 radix-4 stages have 16 butterflies for a warp's 32
 // lanes; serialised under ncu the three double-float passes then take 39 us
 // against 34.7 us with six radix-2 stages, but inside the solve, beside the
@@ -193,10 +193,10 @@ __device__ __forceinline__ float grid_in(const float* q, long long g, int) { ret
 // water-23556: float64 solve 0.90 against 0.94 ms, the FFT phase 0.47
 // against 0.54 ms per step): fewer stages, fewer shared-memory round trips
 // and warp barriers to share the SMs with.
-__host__ __device__ constexpr int pick_radix(int K, int m) {
+__host__ __device__ constexpr int pick_radix(int m) {
   return m % 4 == 0 ? 4 : (m % 2 == 0 ? 2 : (m % 5 == 0 ? 5 : 3));
 }
-__host__ __device__ constexpr int n_stages(int K, int m) { return m <= 1 ? 0 : 1 + n_stages(K, m / pick_radix(K, m)); }
+__host__ __device__ constexpr int n_stages(int m) { return m <= 1 ? 0 : 1 + n_stages(m / pick_radix(m)); }
 __host__ __device__ constexpr bool smooth(int m) {
   return m <= 1 ? m == 1 : (m % 2 == 0 ? smooth(m / 2) : (m % 3 == 0 ? smooth(m / 3) : (m % 5 == 0 ? smooth(m / 5) : false)));
 }
@@ -239,12 +239,12 @@ __device__ __forceinline__ void dft_small(Cx<typename Tr::R>* v, const typename 
   }
 }
 
-// one Stockham stage of radix pick_radix(K, K / Ns), src -> dst, by one warp
+// one Stockham stage of radix pick_radix(K / Ns), src -> dst, by one warp
 template <int K, int Ns, bool kFwd, typename Tr>
 __device__ __forceinline__ void stockham_stage(const typename Tr::S* src, typename Tr::S* dst,
                                                const typename Tr::T* tw) {
   using Rl = typename Tr::R;
-  constexpr int R = pick_radix(K, K / Ns), Q = K / R, step = K / (Ns * R);
+  constexpr int R = pick_radix(K / Ns), Q = K / R, step = K / (Ns * R);
   for (int j = threadIdx.x & 31; j < Q; j += 32) {
     const int jm = j % Ns;
     Cx<Rl> v[R];
@@ -267,7 +267,7 @@ __device__ __forceinline__ void stockham(typename Tr::S* a, typename Tr::S* b, c
   if constexpr (Ns < K) {
     stockham_stage<K, Ns, kFwd, Tr>(a, b, tw);
     __syncwarp();
-    stockham<K, Ns * pick_radix(K, K / Ns), kFwd, Tr>(b, a, tw);
+    stockham<K, Ns * pick_radix(K / Ns), kFwd, Tr>(b, a, tw);
   }
 }
 
@@ -276,7 +276,7 @@ __device__ __forceinline__ void stockham(typename Tr::S* a, typename Tr::S* b, c
 template <int K, bool kFwd, typename Tr>
 __device__ __forceinline__ void line_fft(typename Tr::S* x, typename Tr::S* w, const typename Tr::T* tw) {
   stockham<K, 1, kFwd, Tr>(x, w, tw);
-  if constexpr (n_stages(K, K) % 2 == 1) {
+  if constexpr (n_stages(K) % 2 == 1) {
     for (int k = threadIdx.x & 31; k < K; k += 32) x[k] = w[k];
     __syncwarp();
   }
