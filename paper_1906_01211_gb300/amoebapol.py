@@ -545,6 +545,21 @@ class Polarization:
         E0 = self._dev(E0, torch.float64)
         return amp_polarization_energy(self.ctx, mu.data_ptr(), E0.data_ptr())
 
+    def energy_on_device(self, mu, E0, out):
+        """U into out (a one-element float64 CUDA tensor) on the context's
+        stream, without waiting for it (amp_polarization_energy_noalloc): a
+        loop of steps reads it back when it needs it, not every step."""
+        torch = self.torch
+        mu = self._dev(mu, torch.float64)
+        E0 = self._dev(E0, torch.float64)
+        if out.device.type != "cuda" or out.dtype != torch.float64 or out.numel() < 1:
+            raise ValueError("out must be a float64 CUDA tensor with at least one element")
+        code = amp_polarization_energy_noalloc(int(mu.shape[0]), mu.data_ptr(), E0.data_ptr(), out.data_ptr(),
+                                               self.stream.cuda_stream)
+        if code != AMP_OK:
+            raise AmpError(code, "amp_polarization_energy_noalloc failed")
+        return out
+
     def forces(self, mu):
         """(F, dU/dq, dU/dd, dU/dTheta6) at the converged dipoles mu."""
         torch = self.torch

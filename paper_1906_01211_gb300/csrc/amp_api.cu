@@ -169,10 +169,15 @@ int amp_create(amp_ctx** out, const amp_config* cfg, void* cuda_stream) {
     amp_destroy(c);
     return AMP_ERR_CUDA;
   }
-  if (cudaMallocHost((void**)&c->hbuf, 8 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->hibuf, 8 * sizeof(int)) != cudaSuccess) {
+  if (cudaHostAlloc((void**)&c->hbuf, 8 * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&c->hibuf, 8 * sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
     amp_destroy(c);
     return AMP_ERR_OOM;
+  }
+  if (cudaHostGetDevicePointer((void**)&c->hbuf_d, c->hbuf, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&c->hibuf_d, c->hibuf, 0) != cudaSuccess) {
+    amp_destroy(c);
+    return AMP_ERR_CUDA;
   }
   // The reciprocal-space chain runs on the side stream beside the real-space
   // kernel and is the longer of the two: give its blocks priority.

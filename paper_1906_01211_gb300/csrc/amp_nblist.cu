@@ -474,6 +474,17 @@ __global__ void __launch_bounds__(256) k_transpose_sort(int n, const int* __rest
   }
 }
 
+// The list totals and the build flags into the mapped host readback
+// (hibuf[0], hibuf[1], hibuf[2, 6)), after every kernel that sets a flag.
+__global__ void k_list_readback(const int* __restrict__ full_total, const int* __restrict__ half_total,
+                                const int* __restrict__ flags, int* __restrict__ h) {
+  if (threadIdx.x == 0) {
+    h[0] = *full_total;
+    h[1] = *half_total;
+    for (int k = 0; k < 4; ++k) h[2 + k] = flags[k];
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -533,9 +544,8 @@ int finish_lists(amp_ctx* c, const ListParams& P, bool from_candidates) {
     k_transpose_sort<<<lb, 256, 0, st>>>(n, c->full_start, c->half_cnt, c->tr_tmp, c->half_i, c->full_j, c->full_ref,
                                         c->pos_tr, g, c->half_start, c->flags);
   }
-  cudaMemcpyAsync(&c->hibuf[0], c->full_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&c->hibuf[1], c->half_start + n, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&c->hibuf[2], c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, st);  // flags[0..3] -> hibuf[2..5]
+  c->n_launch += 1;
+  k_list_readback<<<1, 32, 0, st>>>(c->full_start + n, c->half_start + n, c->flags, c->hibuf_d);
   if ((r = cuda_check(c, cudaStreamSynchronize(st), "list count"))) return r;
   if (c->hibuf[2] & 2) return fail(c, AMP_ERR_ARG, "alpha must be > 0 for every site");
   c->n_full = c->hibuf[0];

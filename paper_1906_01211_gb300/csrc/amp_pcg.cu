@@ -247,6 +247,18 @@ __device__ __forceinline__ bool finish_z(int n, double zz, float vm, double* __r
   return true;
 }
 
+// The solver state for the host: flags [0, 4) and scalars [0, 4) into the
+// mapped host readback, by the thread that wrote them last (the host reads
+// them after synchronising the stream).
+__device__ __forceinline__ void publish(const int* fl, const double* scal, int* __restrict__ hfl,
+                                        double* __restrict__ hsc) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hfl[k] = fl[k];
+    hsc[k] = scal[k];
+  }
+}
+
 // r = E0 - mu/alpha + t (t (+ t2) = T mu); z = alpha r and its float split
 // (z32, zlo: the operator's input); convergence test on z. Starts (or
 // restarts) the recurrence: the next step has beta = 0.
@@ -257,7 +269,8 @@ __global__ void __launch_bounds__(NT) k_cg_init(int n, const double4_32a* __rest
                                                 float4* __restrict__ z32, float4* __restrict__ zlo,
                                                 float4* __restrict__ zhl, double* __restrict__ part,
                                                 float* __restrict__ vmax, double* __restrict__ scal,
-                                                int* __restrict__ fl, double tol) {
+                                                int* __restrict__ fl, int* __restrict__ hfl,
+                                                double* __restrict__ hsc, double tol) {
   double zz = 0.0;
   float vm = 0.f;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -277,6 +290,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(int n, const double4_32a* __rest
     const bool conv = rms < tol;
     fl[F_STOP] = conv ? 1 : 0;
     fl[F_STATUS] = conv ? 1 : 0;
+    publish(fl, scal, hfl, hsc);
   }
 }
 
@@ -310,7 +324,9 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
                                                 float4* __restrict__ zlo, float4* __restrict__ zhl,
                                                 double* __restrict__ part,
                                                 float* __restrict__ vmax, double* __restrict__ scal,
-                                                int* __restrict__ fl, double tol, int max_iter) {
+                                                int* __restrict__ fl, int* __restrict__ hfl,
+                                                double* __restrict__ hsc, double tol, int max_iter,
+                                                bool last_of_chunk) {
   pdl_wait();  // first: a kernel never completes before the one it depends on
   if (fl[F_STOP]) return;
   pdl_trigger();
@@ -359,6 +375,7 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
     if (bad) {
       fl[F_STOP] = 1;
       fl[F_STATUS] = 3;
+      publish(fl, scal, hfl, hsc);
       return;
     }
     scal[0] = rho;
@@ -371,6 +388,7 @@ __global__ void __launch_bounds__(NT) k_cg_step(int n, double4_32a* __restrict__
       fl[F_STOP] = 1;
       fl[F_STATUS] = 2;
     }
+    if (last_of_chunk || fl[F_STOP]) publish(fl, scal, hfl, hsc);
   }
 }
 
@@ -425,10 +443,14 @@ __global__ void __launch_bounds__(NT) k_energy_partial(long long m, const double
   write_partials(part, s, 0.0);
 }
 
-__global__ void __launch_bounds__(NT) k_energy_finish(const double* __restrict__ part, double* __restrict__ out) {
+__global__ void __launch_bounds__(NT) k_energy_finish(const double* __restrict__ part, double* __restrict__ out,
+                                                      double* __restrict__ hout) {
   double s, unused;
   reduce_partials(part, NB, s, unused);
-  if (threadIdx.x == 0) *out = -0.5 * kCoulomb * s;
+  if (threadIdx.x == 0) {
+    *out = -0.5 * kCoulomb * s;
+    *hout = *out;
+  }
 }
 
 }  // namespace
@@ -557,15 +579,16 @@ static int apply_T_sorted_fp64_check(amp_ctx* c, const double4_32a* v, double4_3
   return fork_join_T(c, v, nullptr, nullptr, t, t2, kRealDirectDf);
 }
 
-static int read_flags(amp_ctx* c) {
-  cudaMemcpyAsync(c->hibuf, c->iflags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream);
-  cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
-  return cuda_check(c, cudaStreamSynchronize(c->stream), "solver flag read");
-}
+// The last k_cg_init / k_cg_step that ran wrote the flags and scalars into
+// the mapped host readback (hibuf[0, 4), hbuf[0, 4)): synchronise and read.
+static int read_flags(amp_ctx* c) { return cuda_check(c, cudaStreamSynchronize(c->stream), "solver flag read"); }
 
 // One iteration: w's operator part T z (skipped on the device once the solve
-// has stopped), then k_cg_dots and k_cg_step.
-static int enqueue_iteration(amp_ctx* c) {
+// has stopped), then k_cg_dots and k_cg_step. The host reads the flags after
+// the last iteration of a chunk: that step, or the one that stops the solve,
+// publishes them (a write to host memory at the end of every step would
+// lengthen each step's completion).
+static int enqueue_iteration(amp_ctx* c, bool last_of_chunk) {
   const int n = c->n;
   cudaStream_t st = c->stream;
   float4* lo = c->cfg.precision == AMP_MIXED ? nullptr : c->plo;
@@ -579,7 +602,8 @@ static int enqueue_iteration(amp_ctx* c) {
   launch_pdl(k_cg_dots, dim3(nb), dim3(NT), 0, st, n, c->res, c->zv, c->tv, c->trec, c->alph, c->wv, c->partials,
              c->iflags);
   launch_pdl(k_cg_step, dim3(nb), dim3(NT), 0, st, n, c->mu, c->res, c->zv, c->pv, c->qv, c->wv, c->alph, c->p32,
-             lo, lo ? c->vhl : nullptr, c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye, c->cfg.max_iter);
+             lo, lo ? c->vhl : nullptr, c->partials, c->vmax_part, c->scal, c->iflags, c->hibuf_d, c->hbuf_d,
+             c->cfg.tol_debye, c->cfg.max_iter, last_of_chunk);
   return AMP_OK;
 }
 
@@ -600,7 +624,8 @@ static int restart(amp_ctx* c, bool fp64_operator) {
   PhaseScope ps(c, AMP_PHASE_PCG);
   c->n_launch += 1;
   k_cg_init<<<vec_blocks(c->n), NT, 0, c->stream>>>(c->n, c->E0s, c->mu, c->tv, c->trec, c->alph, c->res, c->zv, c->p32, lo,
-                                      lo ? c->vhl : nullptr, c->partials, c->vmax_part, c->scal, c->iflags, c->cfg.tol_debye);
+                                      lo ? c->vhl : nullptr, c->partials, c->vmax_part, c->scal, c->iflags,
+                                      c->hibuf_d, c->hbuf_d, c->cfg.tol_debye);
   return AMP_OK;
 }
 
@@ -693,7 +718,7 @@ int solve(amp_ctx* c, bool use_guess) {
   for (int round = 0; round < 8; ++round) {
     while (true) {
       for (int k = 0; k < chunk; ++k)
-        if ((r = enqueue_iteration(c))) return r;
+        if ((r = enqueue_iteration(c, k == chunk - 1))) return r;
       if ((r = read_flags(c))) return r;
       chunk = kPcgChunk;
       if (c->hibuf[F_STOP]) break;
@@ -722,9 +747,8 @@ int energy(amp_ctx* c, const double* mu, const double* E0, double* U) {
     PhaseScope ps(c, AMP_PHASE_ENERGY);
     c->n_launch += 2;
     k_energy_partial<<<NB, NT, 0, c->stream>>>(3LL * c->n, mu, E0, c->partials);
-    k_energy_finish<<<1, NT, 0, c->stream>>>(c->partials, c->scal + 3);
+    k_energy_finish<<<1, NT, 0, c->stream>>>(c->partials, c->scal + 3, c->hbuf_d + 3);
   }
-  cudaMemcpyAsync(c->hbuf + 3, c->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   int r = cuda_check(c, cudaStreamSynchronize(c->stream), "energy");
   if (r) return r;
   *U = c->hbuf[3];
