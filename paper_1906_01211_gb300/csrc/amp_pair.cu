@@ -516,7 +516,15 @@ __global__ void __launch_bounds__(256) k_row_sum_pairvec(int n, const int* __res
   }
 }
 
-constexpr int kTRealBlocksPerSm = 4;  // of the 5 (float64) or 6 (mixed) that the registers would allow
+// Resident blocks per SM of the real-space products (rows grid-strided, so
+// one wave). Float64 path: every block its registers allow (5 at 48
+// registers; against 4: water-23556 solve 0.869 vs 0.891 ms, water-96000
+// unchanged; a cap above the residency leaves a second, partial wave: 6 gave
+// 3.32 vs 2.87 ms there). Mixed: 4 of the 8 the registers allow, which keeps
+// room for the reciprocal chain's blocks beside it (5 and 6 measured within
+// the noise).
+constexpr int kTRealBlocksPerSmDf = 5;
+constexpr int kTRealBlocksPerSm32 = 4;
 
 // Real-space T*v of the float64 path in double-float, one row per group of
 // kRowGroup lanes, rows grid-strided. Each full-list entry holds the pair's
@@ -528,7 +536,7 @@ constexpr int kTRealBlocksPerSm = 4;  // of the 5 (float64) or 6 (mixed) that th
 // the 20 bytes per entry. Lanes 0..2 finish one component each in float64 (a
 // float64 instruction holds the float64 pipe as long for one active lane as
 // for 32), adding the self term selfc v_i.
-__global__ void __launch_bounds__(256) k_t_real_df(int n, const int* __restrict__ full_start,
+__global__ void __launch_bounds__(256, kTRealBlocksPerSmDf) k_t_real_df(int n, const int* __restrict__ full_start,
                                                    const int* __restrict__ full_j, const float4* __restrict__ C64,
                                                    const float4* __restrict__ xhl, PairGeomDf g, double selfc,
                                                    const float4* __restrict__ vhl,
@@ -768,12 +776,8 @@ void launch_e0_real(amp_ctx* c, double4_32a* out) {
 void launch_t_real(amp_ctx* c, const double4_32a* v, double4_32a* out) {
   const PairGeom g = geom(c);
   c->n_launch += 1;
-  // At most kTRealBlocksPerSm blocks per SM (the rows are grid-strided): the
-  // register file then keeps room for the reciprocal-space chain's blocks,
-  // which run beside this kernel on the higher-priority stream and would
-  // otherwise wait for whole blocks of this kernel to finish.
   const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256),
-                                          (long long)kTRealBlocksPerSm * c->n_sm);
+                                          (long long)kTRealBlocksPerSmDf * c->n_sm);
   k_t_real_df<<<tb, 256, 0, c->stream>>>(c->n, c->full_start, c->full_j, c->C64, c->xhl, geom_df(g), g.selfc,
                                          c->vhl, v, out, c->op_stop);
 }
@@ -782,7 +786,7 @@ void launch_t_real32(amp_ctx* c, const float4* v32, const double4_32a* v64, doub
   const PairGeom g = geom(c);
   c->n_launch += 1;
   const int tb = (int)std::min<long long>(amp_blocks((long long)c->n * kRowGroup, 256),
-                                          (long long)kTRealBlocksPerSm * c->n_sm);
+                                          (long long)kTRealBlocksPerSm32 * c->n_sm);
   k_t_real32<<<tb, 256, 0, c->stream>>>(c->n, c->full_start, c->full_j, reinterpret_cast<const float4*>(c->T32),
                                         reinterpret_cast<const float2*>(c->T32 + 4 * c->cap_full), g.selfc, v32, v64,
                                         out, c->op_stop);
