@@ -166,6 +166,8 @@ struct ListParams {
   int slab;   // slab row capacity (kMode 2)
   double L, rc2;
   float Lf, invLf, lo2, hi2;
+  float hcell;   // cell edge L / nc
+  float reach2;  // (rc + 0.05)^2: a cell farther than this from the atom holds no candidate
 };
 
 // Exact float64 decision, operation by operation as the plain definition
@@ -210,7 +212,9 @@ __device__ __forceinline__ void emit_round(bool in, int i, int k, unsigned lt, i
 // Candidates of atom i: cells within two cells per axis (cell edge >= rc/2;
 // every cell when there are fewer than five per axis). For each (x, y) cell
 // column the z cells form one or two runs of consecutive cells, hence of
-// consecutive atoms, scanned 32 at a time. kMode 0 counts the full and owned
+// consecutive atoms; the runs of all columns are scanned 32 candidates at a
+// time, in a fixed order (so the rows come out in the same order whatever
+// the trimming of the runs). kMode 0 counts the full and owned
 // neighbours; 1 writes them at the row offsets; 2 counts and writes the owned
 // neighbours into a slab row of P.slab entries (flag bit 4 if one overflows),
 // so that a single scan of the candidates suffices.
@@ -232,69 +236,113 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
   const int ci[3] = {cself / (nc * nc), (cself / nc) % nc, cself % nc};
   const bool all = nc < 5;
   const int span = all ? nc : 5;
-  int zr[2][2], nr;  // z runs [zr[r][0], zr[r][1]]
-  if (all) {
-    zr[0][0] = 0, zr[0][1] = nc - 1, nr = 1;
-  } else if (ci[2] - 2 < 0) {
-    zr[0][0] = 0, zr[0][1] = ci[2] + 2, zr[1][0] = ci[2] - 2 + nc, zr[1][1] = nc - 1, nr = 2;
-  } else if (ci[2] + 2 >= nc) {
-    zr[0][0] = ci[2] - 2, zr[0][1] = nc - 1, zr[1][0] = 0, zr[1][1] = ci[2] + 2 - nc, nr = 2;
-  } else {
-    zr[0][0] = ci[2] - 2, zr[0][1] = ci[2] + 2, nr = 1;
-  }
   int nfull = 0, nhalf = 0;
   const int fbase = kMode == 1 ? full_start[i] : 0;
   const int hbase = kMode == 1 ? half_start[i] : 0;
   int* srow = kMode == 2 ? slab + (long long)i * P.slab : nullptr;
-  // lane c < span^2 fetches the atom ranges of (x, y) column c up front, so
-  // the scan below waits on no cell_start load
-  // With five or more cells per axis the periodic image of a candidate follows
-  // from its cell offset: the run's atoms are compared with atom i moved by
-  // minus that image shift (sx, sy per column, sz per z run), which is the
-  // minimum image of every candidate within the cutoff. With fewer cells the
-  // float minimum image is taken per candidate.
+  // Lane c < span^2 holds column c's z runs up front: run 0 the cells
+  // without a periodic shift, run 1 the wrapped ones. With five or more cells
+  // per axis the image of a candidate follows from its cell offset: the run's
+  // atoms are compared with atom i moved by minus that image shift (sx, sy per
+  // column, sz for run 1), which is the minimum image of every candidate
+  // within the cutoff; the runs are trimmed to the cells whose nearest point
+  // lies within the list radius (plus a margin far above the rounding of the
+  // float positions), so a trimmed cell holds no candidate that could be
+  // emitted. With fewer cells the float minimum image is taken per candidate
+  // and nothing is trimmed.
   const int ncol = span * span;
-  int rs[2] = {0, 0}, re[2] = {0, 0};
-  float sxl = 0.f, syl = 0.f;
+  int st0 = 0, len0 = 0, st1 = 0, len1 = 0, code = 0;  // code: x and y shift + 1, two bits each
   if (lane < ncol) {
     const int ox = lane / span, oy = lane % span;
-    const int cxr = ci[0] + ox - 2, cyr = ci[1] + oy - 2;  // unwrapped (when !all)
-    const int cx = all ? ox : (cxr + nc) % nc;
-    const int cy = all ? oy : (cyr + nc) % nc;
-    if (!all) {
-      sxl = cxr < 0 ? -P.Lf : (cxr >= nc ? P.Lf : 0.f);
-      syl = cyr < 0 ? -P.Lf : (cyr >= nc ? P.Lf : 0.f);
-    }
-    const int base = (cx * nc + cy) * nc;
-    for (int r = 0; r < nr; ++r) {
-      rs[r] = cell_start[base + zr[r][0]];
-      re[r] = cell_start[base + zr[r][1] + 1];
-    }
-  }
-  // z shift of run r: the second run is the wrapped one
-  const float szr[2] = {0.f, all ? 0.f : (ci[2] - 2 < 0 ? -P.Lf : P.Lf)};
-  for (int col = 0; col < ncol; ++col) {
-    const float sx = __shfl_sync(0xffffffffu, sxl, col), sy = __shfl_sync(0xffffffffu, syl, col);
-    for (int r = 0; r < nr; ++r) {
-      const int s = __shfl_sync(0xffffffffu, rs[r], col), e = __shfl_sync(0xffffffffu, re[r], col);
-      const float px = pi.x - sx, py = pi.y - sy, pz = pi.z - szr[r];
-      for (int k0 = s; k0 < e; k0 += 32) {
-        const int k = k0 + lane;
-        bool in = false;
-        if (k < e && k != i) {
-          const float4 pj = pos32[k];
-          float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
-          if (all) {
-            dx -= P.Lf * rintf(dx * P.invLf);
-            dy -= P.Lf * rintf(dy * P.invLf);
-            dz -= P.Lf * rintf(dz * P.invLf);
-          }
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
+    if (all) {
+      const int base = (ox * nc + oy) * nc;
+      st0 = cell_start[base];
+      len0 = cell_start[base + nc] - st0;
+      code = 1 | (1 << 2);
+    } else {
+      const int cxr = ci[0] + ox - 2, cyr = ci[1] + oy - 2;  // unwrapped
+      const int cx = (cxr + nc) % nc, cy = (cyr + nc) % nc;
+      code = (cxr < 0 ? 0 : (cxr >= nc ? 2 : 1)) | ((cyr < 0 ? 0 : (cyr >= nc ? 2 : 1)) << 2);
+      const float h = P.hcell;
+      const float dxm = fmaxf(0.f, fmaxf((float)cxr * h - pi.x, pi.x - (float)(cxr + 1) * h));
+      const float dym = fmaxf(0.f, fmaxf((float)cyr * h - pi.y, pi.y - (float)(cyr + 1) * h));
+      const float rem = P.reach2 - (dxm * dxm + dym * dym);
+      if (rem >= 0.f) {
+        int zlo = ci[2] - 2, zhi = ci[2] + 2;  // unwrapped z cells kept: [zlo, zhi]
+        for (; zlo < ci[2]; ++zlo) {
+          const float d = pi.z - (float)(zlo + 1) * h;
+          if (d * d <= rem) break;
         }
-        emit_round<kMode>(in, i, k, lt, nfull, nhalf, fbase, hbase, srow, P.slab, full_j, full_ref, half_i, half_j);
+        for (; zhi > ci[2]; --zhi) {
+          const float d = (float)zhi * h - pi.z;
+          if (d * d <= rem) break;
+        }
+        const int base = (cx * nc + cy) * nc;
+        const int a = max(zlo, 0), b = min(zhi, nc - 1);
+        if (a <= b) {
+          st0 = cell_start[base + a];
+          len0 = cell_start[base + b + 1] - st0;
+        }
+        if (zlo < 0) {
+          st1 = cell_start[base + zlo + nc];
+          len1 = cell_start[base + nc] - st1;
+        } else if (zhi >= nc) {
+          st1 = cell_start[base];
+          len1 = cell_start[base + zhi - nc + 1] - st1;
+        }
       }
     }
+  }
+  // The candidates of all runs, in column order and run 0 before run 1,
+  // packed 32 to a round: lane t of a round finds its column by a binary
+  // search over the inclusive prefix sums of the column lengths.
+  const int tot = len0 + len1;
+  int inc = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  const int total = __shfl_sync(0xffffffffu, inc, 31);
+  const int exc = inc - tot;
+  const int meta = len0 | (code << 26);
+  const float sz1 = all ? 0.f : (ci[2] - 2 < 0 ? -P.Lf : P.Lf);  // shift of every run 1
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int t = t0 + lane;
+    int col = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, inc, col + step - 1);
+      if (v <= t) col += step;
+    }
+    const int ex = __shfl_sync(0xffffffffu, exc, col), m = __shfl_sync(0xffffffffu, meta, col);
+    const int s0 = __shfl_sync(0xffffffffu, st0, col), s1 = __shfl_sync(0xffffffffu, st1, col);
+    bool in = false;
+    int k = -1;
+    if (t < total) {
+      const int o = t - ex, l0 = m & ((1 << 26) - 1), cd = m >> 26;
+      const float sx = (float)((cd & 3) - 1) * P.Lf, sy = (float)((cd >> 2) - 1) * P.Lf;
+      float sz = 0.f;
+      if (o < l0) {
+        k = s0 + o;
+      } else {
+        k = s1 + (o - l0);
+        sz = sz1;
+      }
+      if (k != i) {
+        const float4 pj = pos32[k];
+        const float px = pi.x - sx, py = pi.y - sy, pz = pi.z - sz;
+        float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+        if (all) {
+          dx -= P.Lf * rintf(dx * P.invLf);
+          dy -= P.Lf * rintf(dy * P.invLf);
+          dz -= P.Lf * rintf(dz * P.invLf);
+        }
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < P.hi2) in = (r2 <= P.lo2) ? true : exact_in_range(ai, A[k], P.L, P.rc2);
+      }
+    }
+    emit_round<kMode>(in, i, k, lt, nfull, nhalf, fbase, hbase, srow, P.slab, full_j, full_ref, half_i, half_j);
   }
   if (kMode != 1 && lane == 0) {
     full_cnt[i] = nfull;
@@ -516,6 +564,8 @@ int list_params(amp_ctx* c, double rc, ListParams* P) {
   P->invLf = (float)(1.0 / L);
   P->lo2 = (float)(rc * rc - 0.01);
   P->hi2 = (float)(rc * rc + 0.01);
+  P->hcell = (float)(L / (double)(c->nc > 0 ? c->nc : 1));
+  P->reach2 = (float)((rc + 0.05) * (rc + 0.05));
   return AMP_OK;
 }
 

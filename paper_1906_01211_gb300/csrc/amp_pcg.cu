@@ -500,8 +500,8 @@ enum RealMode { kRealDf, kRealF32, kRealDirectDf };
 // SM resources while they wait for the kernel before them; on large grids
 // these are many cluster CTAs, and a real-space kernel that starts after the
 // spreading finds the SMs taken. Measured (float64 path): water-23556
-// (K = 64) solve 0.92 ms after the spreading, 1.03 ms from the fork;
-// water-96000 (K = 100) 4.22 ms after the spreading, 2.95 ms from the fork.
+// (K = 64) solve 0.873 ms after the spreading, 1.011 ms from the fork;
+// water-96000 (K = 100) 4.01 ms after the spreading, 2.87 ms from the fork.
 // The mixed operator's chain on large grids is cuFFT's, launched the
 // ordinary way: after the spreading at both sizes (1.94 vs 2.17 ms at
 // water-96000). The float64 residual check starts it at the fork.
