@@ -137,3 +137,44 @@ def test_list_refill_paths_on_one_context():
         ref = op.apply_T(v)
         assert np.linalg.norm(t - ref) < 1e-12 * np.linalg.norm(ref)
     s.close()
+
+
+def test_atoms_on_cell_faces_and_box_edges():
+    """Oxygens exactly on the cell lattice of the neighbour search (seven
+    cells per axis, so each atom's candidate runs are trimmed to the cells
+    within reach of it), on the box's faces at 0 and some moved by one box
+    edge (-L or +L) out of the box: every pair within the cutoff must still be
+    found, with the oracle's pair count, field, T*v and dipoles."""
+    from oracle.solver import solve
+    from paper_1906_01211_gb300.synth import small_box_settings
+    nc = 7
+    L = 26.2345
+    h = L / nc
+    rc, beta, K = small_box_settings(L)
+    assert int(np.floor(2.0 * L / rc)) == nc
+    base = make_waters(nc ** 3, L, 17)
+    rng = np.random.default_rng(17)
+    ijk = np.stack(np.meshgrid(np.arange(nc), np.arange(nc), np.arange(nc), indexing="ij"), -1).reshape(-1, 3)
+    target = ijk * h
+    image = np.zeros_like(target)
+    pick = rng.random(len(target)) < 0.3
+    axis = rng.integers(0, 3, len(target))
+    image[pick, axis[pick]] = rng.choice([-L, L], pick.sum())
+    shift = np.repeat(target + image - base.xyz[0::3], 3, axis=0)
+    sysm = System(xyz=base.xyz + shift, q=base.q, dip=base.dip, quad=base.quad, alpha=base.alpha,
+                  thole=base.thole, mol=base.mol, box=L)
+    setup = Setup(box=L, cutoff=rc, beta=beta, grid=K, order=5)
+    op = Operator(sysm, setup)
+    from paper_1906_01211_gb300 import amoebapol as ap
+    s = ap.Polarization(ap.Config(box=L, cutoff=rc, ewald_beta=beta, pme_grid=K, tol_debye=1e-10))
+    s.set_synthetic(sysm)
+    assert s.pair_count() == op.n_pairs
+    E0 = s.permanent_field()
+    assert_fields(E0.cpu().numpy(), op.permanent_field(), 1e-12)
+    v = np.random.default_rng(3).normal(size=(sysm.n, 3)) * 0.1
+    assert_fields(s.apply_T(torch.tensor(v)).cpu().numpy(), op.apply_T(v), 1e-12)
+    mu, it, rms = s.solve(E0)
+    mu_ref, it_ref, _ = solve(op, op.permanent_field(), 1e-10)
+    assert it == it_ref
+    d = mu.cpu().numpy() - mu_ref
+    assert DEBYE * np.sqrt((d * d).sum() / sysm.n) < 1e-8
