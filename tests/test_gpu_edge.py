@@ -1,8 +1,9 @@
 """Edge cases of the float64 path through the C ABI: the smallest inputs, an
 iteration cap that stops the solve early (the partial iterate must equal the
 oracle's PCG iterate after the same number of steps), a zero right-hand side,
-and bitwise reproducibility of T*v (integer accumulation of the reciprocal
-grid, fixed-order sums elsewhere)."""
+bitwise reproducibility of T*v (integer accumulation of the reciprocal
+grid, fixed-order sums elsewhere), and atoms on the cell faces of the
+neighbour search and on the box faces."""
 import numpy as np
 import pytest
 
