@@ -537,6 +537,8 @@ DF_FP32_PER_FP64 = 13
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernel (empty until the current kernel has been captured).
 T_REAL_TRAFFIC = {"water-23556": 68.4e6}
+# kernels launched by one amp_polarization_energy_noalloc call (block partials, final sum)
+NOALLOC_ENERGY_LAUNCHES = 2
 
 
 def measured_peaks():
@@ -864,7 +866,9 @@ def main():
         applications.append(1 + it)
     torch.cuda.synchronize()
     U = float(U_dev.item())
-    launches = p.launch_count() - launches0
+    # the context counts its own launches; the energy's two kernels per step
+    # (amp_polarization_energy_noalloc, no context) are added here
+    launches = p.launch_count() - launches0 + NOALLOC_ENERGY_LAUNCHES * args.steps
     clk = clocks.stop() if clocks else None
     t_total = max_over_ranks(sum(step_ms), world, dev)
     apps = sum(applications)
