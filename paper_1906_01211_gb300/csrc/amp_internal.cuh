@@ -326,7 +326,7 @@ void launch_split_multipoles(amp_ctx* c);  // pd and mp_df from the atom records
 int energy(amp_ctx* c, const double* mu, const double* E0, double* U);
 
 // isolated clusters (amp_cluster.cu)
-constexpr int kClusterMaxSlices = 16;
+constexpr int kClusterMaxSlices = 32;
 int cluster_setup(amp_ctx* c, const double* xyz, const double* q, const double* dip, const double* quad,
                   const double* alpha, const double* thole, const int* mol);
 void cluster_permanent_field(amp_ctx* c, double4_32a* out);
