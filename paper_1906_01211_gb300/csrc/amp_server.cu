@@ -81,7 +81,9 @@ void box_settings(Request& r) {
 
 // Upper estimate of the device bytes of a context solving r (buffers per
 // atom, per pair of the lists with their float64/mixed tensors, PME grids),
-// used to admit a request that needs a new context.
+// used to admit a request that needs a new context. An isolated cluster
+// holds about 1.7 KB per atom: the all-pairs kernels' column-slice partial
+// sums (kClusterMaxSlices x 32 B) and the atom records and solver vectors.
 long long estimate_bytes(const Request& r, int precision) {
   const long long n = r.n;
   if (r.box <= 0.0) return n * 2048 + (16LL << 20);
