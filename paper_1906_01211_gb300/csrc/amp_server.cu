@@ -82,11 +82,12 @@ void box_settings(Request& r) {
 // Upper estimate of the device bytes of a context solving r (buffers per
 // atom, per pair of the lists with their float64/mixed tensors, PME grids),
 // used to admit a request that needs a new context. An isolated cluster
-// holds about 1.7 KB per atom: the all-pairs kernels' column-slice partial
-// sums (kClusterMaxSlices x 32 B) and the atom records and solver vectors.
+// holds up to ~2.8 KB per atom: the all-pairs kernels' column-slice partial
+// sums (kClusterMaxSlices x 32 B), the B-spline buffers every context
+// allocates (~1 KB), the atom records and the solver vectors.
 long long estimate_bytes(const Request& r, int precision) {
   const long long n = r.n;
-  if (r.box <= 0.0) return n * 2048 + (16LL << 20);
+  if (r.box <= 0.0) return n * 3072 + (16LL << 20);
   const double density = (double)n / (r.box * r.box * r.box);
   const long long half = (long long)(n * 2.0 * M_PI / 3.0 * r.cutoff * r.cutoff * r.cutoff * density) + 1024;
   const long long per_pair = precision == AMP_MIXED ? 4 * (4 + 4 + 4) + 2 * 24 + 24 + 24 : 4 * (4 + 4 + 4) + 2 * 16 + 48;
