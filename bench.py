@@ -66,6 +66,9 @@ def parse():
                     help="only the serving measurement (request stream, rates) as its own JSON line")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batched engine: the stream's small clusters, all submitted at once")
+    ap.add_argument("--cluster-only", type=int, default=0, metavar="WATERS",
+                    help="only single-system solves of one isolated water cluster of this many waters "
+                         "(the workers' largest requests), mixed and float64")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--workers", type=int, default=6, help="serving: context workers beside the batched engine")
     ap.add_argument("--rates", default="1,2", help="serving: arrival rates as multiples of the float64 capacity")
@@ -252,6 +255,50 @@ def run_serving(n_requests: int, workers: int, rates_vs_fp64, rates_vs_capacity,
         res.update({"arrival_per_s": lam, "rate_vs": label, "factor": f})
         out["rates"].append(res)
     srv.close()
+    return out
+
+
+def run_cluster_only(n_waters: int, steps: int, warmup: int, seed: int = 5):
+    """One isolated water cluster (all pairs, no Ewald) solved through the
+    single-system calls, as the server's workers solve clusters too large for
+    the batched engine: per precision the whole solve (set_system, permanent
+    field, PCG to 1e-5 D with the mixed path's float64 check) with a host
+    clock around it, and T*v alone with CUDA events (all-pairs interactions
+    per second, n (n - 1) per application)."""
+    import numpy as np
+    import torch
+    from paper_1906_01211_gb300 import amoebapol as ap
+    from paper_1906_01211_gb300.synth import density_box_edge, make_waters
+    s = make_waters(n_waters, density_box_edge(n_waters), seed, periodic=False)
+    stream = torch.cuda.current_stream()
+    out = {"n_atoms": s.n}
+    for prec in ("mixed", "fp64"):
+        p = ap.Polarization(ap.Config(box=0.0, tol_debye=1e-5, precision=prec), stream)
+        ms, its = [], []
+        for k in range(warmup + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.set_synthetic(s)
+            E0 = p.permanent_field()
+            mu, it, rms = p.solve(E0)
+            torch.cuda.synchronize()
+            if k >= warmup:
+                ms.append((time.perf_counter() - t0) * 1e3)
+                its.append(it)
+        v = torch.randn(s.n, 3, dtype=torch.float64, device="cuda", generator=torch.Generator(
+            device="cuda").manual_seed(seed)) * 0.1
+        p.apply_T(v)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            p.apply_T(v)
+        e1.record(stream)
+        e1.synchronize()
+        t_ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"solve_ms_median": float(np.median(ms)), "iters": its[-1], "apply_T_ms": t_ms,
+                     "pair_terms_per_s": s.n * (s.n - 1) / (t_ms / 1e3)}
+        p.close()
     return out
 
 
@@ -777,6 +824,12 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
+    if args.cluster_only:
+        if rank == 0:
+            print(json.dumps({"config": {"workload": f"isolated water cluster, {args.cluster_only} waters"},
+                              "cluster_solve": run_cluster_only(args.cluster_only, args.steps, args.warmup)}),
+                  flush=True)
+        return
     if args.batch_only:
         if rank == 0:
             print(json.dumps({"config": {"workload": "small water clusters of the request stream"},
