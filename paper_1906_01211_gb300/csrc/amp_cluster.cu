@@ -247,12 +247,32 @@ __global__ void __launch_bounds__(kTileI) k_cluster_field_df(int n, int cols_per
 
 // The mixed path's T*v over all pairs in float32: positions, 1/sqrt(alpha),
 // Thole a and molecule as float records (clu32, made once per geometry), v
-// as floats, so the tiles are staged without float64 conversions.
+// as floats, so the tiles are staged without float64 conversions. A full
+// tile without the row's own atom runs an unrolled loop with no self test
+// (the kernel is bound by instruction issue: T*v of a 12,288-atom cluster
+// 0.272 against 0.319 ms with the tested loop everywhere).
 struct JTile32 {
   float4 p[kTileJ];  // x, y, z, 1/sqrt(alpha)
   float th[kTileJ];
   float4 v[kTileJ];
 };
+
+// One pair's term T_ij v_j of the float32 all-pairs product, added to (sx, sy, sz).
+__device__ __forceinline__ void tv32_pair(const float4& pi, float thi, const float4& pj, float thj, const float4& vj,
+                                          float& sx, float& sy, float& sz) {
+  const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+  const float r2 = rx * rx + ry * ry + rz * rz;
+  const float ir = rsqrtf(r2);
+  const float ir2 = ir * ir;
+  const float x = fminf(thi, thj) * r2 * r2 * ir * pi.w * pj.w;
+  const float e = expf(-x);
+  const float b1 = (1.f - e) * ir * ir2;
+  const float b2 = 3.f * (1.f - (1.f + x) * e) * ir2 * ir2 * ir;
+  const float sv = b2 * (vj.x * rx + vj.y * ry + vj.z * rz);
+  sx += sv * rx - b1 * vj.x;
+  sy += sv * ry - b1 * vj.y;
+  sz += sv * rz - b1 * vj.z;
+}
 
 __global__ void __launch_bounds__(kTileI) k_cluster_tv32(int n, int cols_per_slice, const float4* __restrict__ clu32,
                                                          const float4* __restrict__ v32,
@@ -281,21 +301,12 @@ __global__ void __launch_bounds__(kTileI) k_cluster_tv32(int n, int cols_per_sli
     const int cnt = min(kTileJ, j1 - jt);
     float sx = 0.f, sy = 0.f, sz = 0.f;
     if (i < n) {
-      for (int k = 0; k < cnt; ++k) {
-        if (jt + k == i) continue;
-        const float4 pj = t.p[k], vj = t.v[k];
-        const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        const float ir = rsqrtf(r2);
-        const float ir2 = ir * ir;
-        const float x = fminf(thi, t.th[k]) * r2 * r2 * ir * pi.w * pj.w;
-        const float e = expf(-x);
-        const float b1 = (1.f - e) * ir * ir2;
-        const float b2 = 3.f * (1.f - (1.f + x) * e) * ir2 * ir2 * ir;
-        const float sv = b2 * (vj.x * rx + vj.y * ry + vj.z * rz);
-        sx += sv * rx - b1 * vj.x;
-        sy += sv * ry - b1 * vj.y;
-        sz += sv * rz - b1 * vj.z;
+      if (cnt == kTileJ && (i < jt || i >= jt + kTileJ)) {  // a full tile without the row's own atom
+#pragma unroll 8
+        for (int k = 0; k < kTileJ; ++k) tv32_pair(pi, thi, t.p[k], t.th[k], t.v[k], sx, sy, sz);
+      } else {
+        for (int k = 0; k < cnt; ++k)
+          if (jt + k != i) tv32_pair(pi, thi, t.p[k], t.th[k], t.v[k], sx, sy, sz);
       }
     }
     ax += (double)sx;
