@@ -305,7 +305,6 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
   }
   const int total = __shfl_sync(0xffffffffu, inc, 31);
   const int exc = inc - tot;
-  const int meta = len0 | (code << 26);
   const float sz1 = all ? 0.f : (ci[2] - 2 < 0 ? -P.Lf : P.Lf);  // shift of every run 1
   for (int t0 = 0; t0 < total; t0 += 32) {
     const int t = t0 + lane;
@@ -315,12 +314,13 @@ __global__ void k_neighbours(ListParams P, const float4* __restrict__ pos32, con
       const int v = __shfl_sync(0xffffffffu, inc, col + step - 1);
       if (v <= t) col += step;
     }
-    const int ex = __shfl_sync(0xffffffffu, exc, col), m = __shfl_sync(0xffffffffu, meta, col);
+    const int ex = __shfl_sync(0xffffffffu, exc, col), l0 = __shfl_sync(0xffffffffu, len0, col);
     const int s0 = __shfl_sync(0xffffffffu, st0, col), s1 = __shfl_sync(0xffffffffu, st1, col);
+    const int cd = __shfl_sync(0xffffffffu, code, col);
     bool in = false;
     int k = -1;
     if (t < total) {
-      const int o = t - ex, l0 = m & ((1 << 26) - 1), cd = m >> 26;
+      const int o = t - ex;
       const float sx = (float)((cd & 3) - 1) * P.Lf, sy = (float)((cd >> 2) - 1) * P.Lf;
       float sz = 0.f;
       if (o < l0) {
