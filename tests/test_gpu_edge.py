@@ -179,3 +179,19 @@ def test_atoms_on_cell_faces_and_box_edges():
     assert it == it_ref
     d = mu.cpu().numpy() - mu_ref
     assert DEBYE * np.sqrt((d * d).sum() / sysm.n) < 1e-8
+
+
+def test_energy_on_device_matches_host_energy():
+    """The binding's energy_on_device (the allocation-free energy call, on the
+    context's stream, result left on the device) gives the context's energy,
+    up to the order of the two reductions."""
+    w = WATER_648
+    s = solver(w)
+    s.set_synthetic(w.system())
+    E0 = s.permanent_field()
+    mu, _, _ = s.solve(E0)
+    U = s.energy(mu, E0)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    s.energy_on_device(mu, E0, out)
+    torch.cuda.synchronize()
+    assert abs(out.item() / U - 1.0) < 1e-12
