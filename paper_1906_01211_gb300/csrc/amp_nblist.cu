@@ -14,10 +14,11 @@
 //      the caller's index, so the cell order does not depend on atomics;
 //   3. gather the atom records into cell order (float64 + wrapped float32);
 //   4. one warp per atom scans the candidates in the cells within two cells
-//      per axis (cell edge >= rc/2), as runs of consecutive atoms along z:
-//      float32 distance pre-filter with a margin, exact float64 decision
-//      d.d < rc^2 for candidates near the cutoff; counts, and the owned
-//      neighbours into a slab row;
+//      per axis (cell edge >= rc/2), as runs of consecutive atoms along z,
+//      each run trimmed to the cells within reach of the atom and all runs
+//      packed 32 candidates to a round: float32 distance pre-filter with a
+//      margin, exact float64 decision d.d < rc^2 for candidates near the
+//      cutoff; counts, and the owned neighbours into a slab row;
 //   5. scan the row counts; copy the slab rows into the full rows and the half
 //      list (or, if a slab row overflowed, scan the candidates again and write
 //      them at the row offsets);
