@@ -548,7 +548,10 @@ class Polarization:
     def energy_on_device(self, mu, E0, out):
         """U into out (a one-element float64 CUDA tensor) on the context's
         stream, without waiting for it (amp_polarization_energy_noalloc): a
-        loop of steps reads it back when it needs it, not every step."""
+        loop of steps reads it back when it needs it, not every step. At most
+        AMP_NOALLOC_MAX_ATOMS atoms; its scratch is shared by every call of
+        the process, so calls whose kernels could overlap (other streams)
+        must not be issued concurrently."""
         torch = self.torch
         mu = self._dev(mu, torch.float64)
         E0 = self._dev(E0, torch.float64)
